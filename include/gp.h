@@ -1,0 +1,166 @@
+/*
+ * gp.h -- C-ABI of libgp.so, the GB300 (sm_103a) exact Gaussian-process engine for the compactly supported
+ * nonstationary kernel of arXiv 2411.05869 ("Compactly-supported nonstationary kernels for computing exact
+ * Gaussian processes on big data").
+ *
+ * The library evaluates, for one or many hyperparameter settings theta on a fixed point set X,
+ *   log p(z | beta, theta) = -1/2 log det C_z - 1/2 r^T C_z^{-1} r - n/2 log(2 pi),   r = z - W beta
+ * (Sec. 3.3, first display; C_z from Eq. Zcov) and the predictive mean
+ *   m* = mu* + C_{y,z} C_z^{-1} r   (Sec. 3.2, first display of m_{y|z}),
+ * exactly, through a sparse supernodal Cholesky factorization of C_z. C_z = C_core * C_sparse + tau^2 I:
+ *   C_sparse(x, x') = s0 f0(x, x'; r0) + sum_{i=1..n1} f_i(x) f_i(x')          (Sec. 2.1, Eq. C_sparse)
+ *   f_i(x) = sum_{j=1..n2} g_ij(x),  g(x) = a exp{b [1 - (1 - |x-h|^2/r^2)^{-1}]} for |x-h| < r  (Eq. bumpFcn)
+ *   f0(x, x'; r0) = (1-q)^8 (35 q^3 + 25 q^2 + 8 q + 1), q = |x-x'|/r0 < 1                     (Eq. compSupp)
+ *   C_core(x, x') = core_var * f0(x, x'; core_radius): a compactly supported Wendland-type core, so the
+ *   support of C_core bounds the sparsity pattern of C_z (Sec. 2, product kernel C_y = C_core x C_sparse).
+ * Distances are anisotropic: q^2 = sum_k ((x_k - x'_k)/rad_k)^2 with one radius per coordinate (Sec. 5.1, 5.2).
+ *
+ * Conventions (all entry points):
+ *   - "d_" pointers are DEVICE memory on the context's device; every other pointer is host memory.
+ *   - The caller owns every buffer it passes; the library owns the opaque handles and frees them only in
+ *     the matching *_free / gp_destroy. Handles are not thread-safe; use one context per host thread.
+ *   - Every call is ordered on the context's CUDA stream. gp_assemble and gp_create synchronise that stream
+ *     (they build host-side plans); gp_factor, gp_factor_update, gp_loglik and gp_predict are asynchronous
+ *     unless documented otherwise, and their device outputs are valid once the stream reaches them.
+ *   - A status is returned and never aborts; gp_last_error gives the message of the last failure.
+ *   - Row-major layouts: X is n x d (point k at X[k*d .. k*d+d-1]); batched vectors are B x n.
+ */
+#ifndef GP_H_
+#define GP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GP_API __attribute__((visibility("default")))
+#else
+#define GP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GP_OK = 0,
+  GP_ERR_ARG = 1,      /* bad argument (null, size, dimension, mismatched handles) */
+  GP_ERR_NOMEM = 2,    /* device memory allocation failed or would exceed the context budget */
+  GP_ERR_NOT_PD = 3,   /* a pivot was not positive (reported per proposal by gp_factor_info) */
+  GP_ERR_CUDA = 4,     /* a CUDA runtime error */
+  GP_ERR_TIMEOUT = 5,  /* a bounded device wait ran out (no kernel here spins on another) */
+  GP_ERR_STATE = 6     /* call out of order (e.g. predict before loglik) */
+} gp_status;
+
+typedef enum {
+  GP_FP64 = 0,         /* every step in FP64 */
+  GP_MIXED = 1         /* off-diagonal supernode updates on TF32 tensor cores with FP32 accumulation and FP32
+                          off-diagonal storage; diagonal blocks, log-det and refinement residuals in FP64 */
+} gp_precision;
+
+typedef struct gp_ctx gp_ctx;
+typedef struct gp_pointset gp_pointset;
+typedef struct gp_factor_s gp_factor_t;   /* a numeric factorization (B proposals) */
+
+/* One hyperparameter setting (host memory, FP64). Sec. 2.1 lists theta_sparse = (s0, r0, {h, a, b, r});
+ * core_var / core_radius parameterise the compact core, noise_var is tau^2 of Eq. Zcov (constant).
+ * h is n1*n2*bump_dims (bump (i,j) at h[(i*n2+j)*bump_dims ...]); a, b, r are n1*n2, row-major over (i,j).
+ * Bumps act on the leading bump_dims coordinates (space-time: the spatial ones, Sec. 5.2). */
+typedef struct {
+  int d, n1, n2, bump_dims;
+  double core_var;
+  const double* core_radius;  /* [d] must equal the radii the point set was assembled with */
+  double s0;
+  const double* r0;           /* [d] Wendland radii of C_sparse; entries of C_z outside the core support are 0 */
+  const double* h;
+  const double* a;
+  const double* b;
+  const double* r;
+  double noise_var;
+} gp_hyper;
+
+typedef struct {
+  int64_t n;            /* points */
+  int d;
+  int64_t nnz;          /* nonzeros of the full symmetric pattern of C_z */
+  int64_t ncells;       /* cells of the unit grid in u = x / core_radius */
+  int64_t nnzL;         /* exact nonzeros of the Cholesky factor (sum of column counts) */
+  int64_t nsuper;       /* relaxed supernodes */
+  int64_t panel_entries;/* stored panel entries (supernodal storage incl. explicit zeros) */
+  int64_t update_entries;/* peak update-matrix workspace entries (per proposal) */
+  int32_t nlevels;      /* levels of the supernodal elimination tree */
+  int32_t max_front;    /* largest frontal matrix order */
+  double flops;         /* algorithmic factorization flops: sum over columns of eta_j^2 */
+} gp_pointset_info_t;
+
+typedef struct {
+  int B;
+  int precision;              /* gp_precision */
+  int64_t bytes;              /* device bytes held by the factor */
+  int32_t not_pd_count;       /* proposals whose factorization met a non-positive pivot */
+} gp_factor_info_t;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream). mem_budget_bytes caps the device memory the context's handles may hold (0 = no cap).
+ * Errors: GP_ERR_ARG (bad device), GP_ERR_CUDA. */
+GP_API gp_status gp_create(gp_ctx** ctx, int device, void* cuda_stream, size_t mem_budget_bytes);
+GP_API void gp_destroy(gp_ctx* ctx);
+/* Message of the last failure on this context (static storage owned by the context; "" if none). */
+GP_API const char* gp_last_error(const gp_ctx* ctx);
+
+/* Steps A1, A2, A5, A6: cell list of the unit grid in u = x / core_radius, exact support pattern of C_z
+ * (all pairs with q^2 = sum_k (u_ik - u_jk)^2 < 1, FP64 without contraction), nested-dissection ordering and
+ * symbolic analysis (etree, column counts, relaxed supernodes, frontal plan). Depends only on X and the core
+ * radii, so one point set serves every theta with the same core radii (Sec. 3.3 notes the pattern of C_z
+ * is otherwise theta dependent; a compact core fixes it).
+ *   d_X: n x d FP64 (device), d in {1,2,3}; core_radius: host [d] > 0.
+ * Synchronous. Errors: GP_ERR_ARG (n < 1, d outside 1..3, radius <= 0, grid of more than max(2^24, 8n) cells),
+ * GP_ERR_NOMEM, GP_ERR_CUDA. */
+GP_API gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
+                      gp_pointset** ps);
+GP_API void gp_pointset_free(gp_pointset* ps);
+GP_API gp_status gp_pointset_info(const gp_pointset* ps, gp_pointset_info_t* info);
+
+/* Export a structural array of the point set to host memory (for bit-exact checks):
+ *   what = 0 perm[n] int32 (new -> old), 1 parent[n] int32 (etree, -1 root), 2 eta[n] int32 (column counts),
+ *   3 rowptr[n+1] int64, 4 col[nnz] int32 (pattern, columns ascending), 5 sn_first[nsuper+1] int32,
+ *   6 sn_rowptr[nsuper+1] int64, 7 sn_rows int32 (rows below each supernode, ascending),
+ *   8 sn_parent[nsuper] int32, 9 sn_level[nsuper] int32, 10 cell_perm[n] int32 (points by (cell, index)).
+ * `bytes` must equal the array size. Synchronous. Errors: GP_ERR_ARG. */
+GP_API gp_status gp_pointset_export(const gp_pointset* ps, int what, void* host_dst, size_t bytes);
+
+/* Steps A3, A4, A7 for B proposals sharing the point set: bump features, kernel values of the pattern
+ * (fused with the scatter into supernodal panels) and the supernodal numeric Cholesky of P C_z P^T.
+ * thetas: host array of B settings. Allocates the factor (B copies of the panels plus workspace).
+ * A non-positive pivot does not fail the call: it marks that proposal (gp_factor_info, and gp_loglik then
+ * returns -inf for it). Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA. Asynchronous after allocation. */
+GP_API gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, gp_precision precision,
+                    gp_factor_t** f);
+/* Re-run A3, A4, A7 on an existing factor with B new settings (same B, precision and point set): the
+ * allocation-free inner call of an MCMC loop. Asynchronous. Errors: GP_ERR_ARG, GP_ERR_CUDA. */
+GP_API gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas);
+GP_API void gp_factor_free(gp_factor_t* f);
+/* Synchronous (reads the per-proposal pivot flags). */
+GP_API gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, int32_t* not_pd_column /* [B] or NULL */);
+
+/* Steps A8-A11: forward/backward supernodal solves, quadratic form r^T C_z^{-1} r, log-determinant
+ * 2 sum_j log L_jj in a fixed-order tree, and (GP_MIXED) FP64 iterative refinement of alpha = C_z^{-1} r with
+ * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-12 or 10 sweeps.
+ *   d_resid: B x n FP64 (r = z - mu per proposal, original point order); d_out: B FP64 log-likelihoods
+ *   (-inf for proposals with a non-positive pivot); d_err_est: B FP64 final relative residual (nullable).
+ * Keeps alpha for gp_predict. Asynchronous. Errors: GP_ERR_ARG, GP_ERR_CUDA. */
+GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err_est);
+
+/* Step A12: m*_k = mu*_k + sum_j C_y(x*_k, x_j) alpha_j over the training neighbours of x*_k found in the
+ * cell list (no noise term; Sec. 3.2), for proposal b of the factor, after gp_loglik.
+ *   d_Xtest: m x d FP64; d_mu_test: m FP64 or NULL (zero mean); d_mean: m FP64 output.
+ * Asynchronous. Errors: GP_ERR_ARG, GP_ERR_STATE (no alpha yet), GP_ERR_CUDA. */
+GP_API gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
+                     const double* d_mu_test, double* d_mean);
+
+/* Number of kernel launches this context has issued (a counter for launch accounting). */
+GP_API int64_t gp_launch_count(const gp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H_ */

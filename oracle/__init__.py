@@ -60,6 +60,7 @@ def lib():
         L.or_cell_keys.argtypes = [c_i64, ctypes.c_int, P, P, P]
         L.or_nd_order.restype = c_i64
         L.or_nd_order.argtypes = [c_i64, ctypes.c_int, P, P, P, P, P, P, P, P]
+        L.or_etree_postorder.argtypes = [c_i64, P, P, P, P]
         L.or_supernodes.restype = c_i64
         L.or_supernodes.argtypes = [c_i64, P, P, P]
         L.or_symbolic.restype = c_i64
@@ -181,6 +182,20 @@ def nd_order(X, rho, rowptr, col, with_tree: bool = False):
     if with_tree:
         return perm, lo[:nn].copy(), hi[:nn].copy(), kind[:nn].copy()
     return perm
+
+
+def etree_postorder(rowptr, col, perm) -> np.ndarray:
+    """Relabel an ordering by a postorder of its elimination tree (same fill, subtrees contiguous)."""
+    n = perm.shape[0]
+    out = np.empty(n, dtype=np.int32)
+    lib().or_etree_postorder(n, _p(np.ascontiguousarray(rowptr, np.int64)), _p(np.ascontiguousarray(col, np.int32)),
+                             _p(np.ascontiguousarray(perm, np.int32)), _p(out))
+    return out
+
+
+def fill_order(X, rho, rowptr, col) -> np.ndarray:
+    """The factorization order: nested dissection, then the etree postorder relabelling."""
+    return etree_postorder(rowptr, col, nd_order(X, rho, rowptr, col))
 
 
 def symbolic(rowptr, col, perm, want_rows: bool = True):

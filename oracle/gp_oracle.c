@@ -14,6 +14,7 @@
  *   or_dense_cov         C_z = C_y + tau^2 I{x = x'} (Sec. 3.1, Eq. Zcov), all pairs
  *   or_pattern_*         brute-force O(n^2) support pattern (pairs with q^2 < 1 of the compact core)
  *   or_nd_order          geometric nested-dissection ordering (the paper is silent; the build's rule)
+ *   or_etree_postorder   fill-preserving relabelling of an order by a postorder of its elimination tree
  *   or_symbolic          etree, column counts, supernodes from explicit column structures
  *   or_dense_chol, or_dense_loglik, or_sample_dense   dense Cholesky, log-likelihood of Sec. 3.3
  *   or_sparse_chol, or_sparse_loglik                  left-looking sparse Cholesky, same log-likelihood
@@ -525,6 +526,44 @@ int64_t or_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   free(snof);
   colstruct_free(&cs);
   return ns;
+}
+
+/*
+ * Fill-preserving relabelling of an ordering by a postorder of its elimination tree (children visited in
+ * increasing index order, roots in increasing order). The factor of the relabelled matrix has the same
+ * column counts (permuted) and the same fill; each subtree becomes a contiguous range of columns, so chains
+ * of the tree become runs j, j+1, ... . out_perm[new] = perm[post[new]].
+ */
+void or_etree_postorder(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, int32_t* out_perm) {
+  colstruct_t cs;
+  colstruct_build(&cs, n, rowptr, col, perm);
+  int32_t* head = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* next = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t j = 0; j < n; j++) head[j] = -1;
+  for (int64_t j = n - 1; j >= 0; j--) {            /* prepend in decreasing order: lists ascend */
+    int32_t p = cs.parent[j];
+    if (p >= 0) { next[j] = head[p]; head[p] = (int32_t)j; }
+  }
+  int64_t k = 0;
+  for (int64_t root = 0; root < n; root++) {
+    if (cs.parent[root] != -1) continue;
+    int64_t top = 0;
+    stack[top++] = (int32_t)root;
+    while (top > 0) {
+      int32_t v = stack[top - 1];
+      int32_t c = head[v];
+      if (c != -1) {                                 /* descend into the next unvisited child */
+        head[v] = next[c];
+        stack[top++] = c;
+      } else {
+        top--;
+        out_perm[k++] = perm[v];
+      }
+    }
+  }
+  free(head); free(next); free(stack);
+  colstruct_free(&cs);
 }
 
 /* ---------------------------------------------------------------- dense path (n up to a few thousand) */

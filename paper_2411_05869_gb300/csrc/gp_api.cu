@@ -1,0 +1,367 @@
+// gp_api.cu -- the C-ABI of libgp.so (declared in include/gp.h): handle management, argument checks,
+// device memory accounting and the calls into the step implementations.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gp_internal.cuh"
+
+// ------------------------------------------------------------------------------------------ memory
+void* dev_alloc(gp_ctx* ctx, std::vector<DevBuf>& owner, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->budget && ctx->held + bytes > ctx->budget)
+    throw GpError{GP_ERR_NOMEM, "device memory budget exceeded (" + std::to_string(ctx->held + bytes) + " > " +
+                                    std::to_string(ctx->budget) + " bytes)"};
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw GpError{GP_ERR_NOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e)};
+  }
+  owner.push_back(DevBuf{p, bytes});
+  ctx->held += bytes;
+  return p;
+}
+
+void dev_free_all(gp_ctx* ctx, std::vector<DevBuf>& owner) {
+  if (!owner.empty()) cudaStreamSynchronize(ctx->stream);
+  for (auto& b : owner) {
+    cudaFree(b.p);
+    ctx->held -= std::min(ctx->held, b.bytes);
+  }
+  owner.clear();
+}
+
+namespace {
+
+gp_status fail(gp_ctx* ctx, const GpError& e) {
+  if (ctx) ctx->err = e.msg;
+  return e.st;
+}
+
+template <class F>
+gp_status guarded(gp_ctx* ctx, F&& body) {
+  try {
+    if (ctx) GP_CUDA(cudaSetDevice(ctx->device));
+    body();
+    if (ctx) ctx->err.clear();
+    return GP_OK;
+  } catch (const GpError& e) {
+    return fail(ctx, e);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, GpError{GP_ERR_NOMEM, "host allocation failed"});
+  } catch (const std::exception& e) {
+    return fail(ctx, GpError{GP_ERR_STATE, e.what()});
+  }
+}
+
+template <class T>
+T* upload(gp_ctx* ctx, std::vector<DevBuf>& owner, const std::vector<T>& v) {
+  T* p = dalloc<T>(ctx, owner, std::max<size_t>(v.size(), 1));
+  if (!v.empty()) h2d(ctx, p, v.data(), v.size());
+  return p;
+}
+
+void check_hyper(const gp_pointset* ps, const gp_hyper& h, const gp_hyper& h0) {
+  GP_REQUIRE(h.d == ps->d, "theta.d differs from the point set dimension");
+  GP_REQUIRE(h.n1 >= 0 && h.n1 <= GP_MAX_N1 && h.n2 >= 0, "theta.n1 must be in 0..32 and n2 >= 0");
+  GP_REQUIRE(h.bump_dims >= 0 && h.bump_dims <= h.d, "theta.bump_dims must be in 0..d");
+  GP_REQUIRE(h.n1 == h0.n1 && h.n2 == h0.n2 && h.bump_dims == h0.bump_dims, "all proposals must share n1, n2, bump_dims");
+  GP_REQUIRE(h.core_radius && h.r0, "theta.core_radius and theta.r0 are required");
+  for (int k = 0; k < h.d; k++) {
+    GP_REQUIRE(h.core_radius[k] == ps->rho[k], "theta.core_radius must equal the radii of gp_assemble");
+    GP_REQUIRE(h.r0[k] > 0.0, "theta.r0 must be positive");
+  }
+  int64_t nb = (int64_t)h.n1 * h.n2;
+  GP_REQUIRE(nb == 0 || (h.h && h.a && h.b && h.r), "bump arrays are required when n1*n2 > 0");
+  GP_REQUIRE(std::isfinite(h.core_var) && std::isfinite(h.s0) && std::isfinite(h.noise_var), "non-finite theta");
+}
+
+void pack_thetas(gp_factor_t* f, const gp_hyper* th) {
+  const gp_hyper& h0 = th[0];
+  ThetaDims td{h0.d, h0.n1, h0.n2, h0.bump_dims};
+  int64_t st = theta_stride_of(td);
+  std::vector<double> buf((size_t)st * f->B, 0.0);
+  for (int b = 0; b < f->B; b++) {
+    const gp_hyper& h = th[b];
+    check_hyper(f->ps, h, h0);
+    double* p = buf.data() + (size_t)st * b;
+    p[TH_CORE_VAR] = h.core_var;
+    p[TH_S0] = h.s0;
+    p[TH_NOISE] = h.noise_var;
+    for (int k = 0; k < 3; k++) {
+      p[TH_CRAD + k] = k < h.d ? h.core_radius[k] : 1.0;
+      p[TH_R0 + k] = k < h.d ? h.r0[k] : 1.0;
+    }
+    int64_t nb = (int64_t)h.n1 * h.n2;
+    double* q = p + TH_BUMPS;
+    for (int64_t ij = 0; ij < nb; ij++) {
+      for (int k = 0; k < h.bump_dims; k++) *q++ = h.h[ij * h.bump_dims + k];
+      *q++ = h.a[ij];
+      *q++ = h.b[ij];
+      *q++ = h.r[ij];
+    }
+  }
+  f->theta_stride = st;
+  f->n1max = h0.n1;
+  h2d(f->ctx, f->theta_dev, buf.data(), buf.size());
+  GP_CUDA(cudaStreamSynchronize(f->ctx->stream));   // buf leaves scope
+  f->thetas_host.assign(th, th + f->B);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------ context
+extern "C" gp_status gp_create(gp_ctx** out, int device, void* cuda_stream, size_t mem_budget_bytes) {
+  if (!out) return GP_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GP_ERR_ARG;
+  }
+  gp_ctx* ctx = new gp_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->budget = mem_budget_bytes;
+  gp_status st = guarded(ctx, [&] { GP_CUDA(cudaFree(nullptr)); });
+  if (st != GP_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return GP_OK;
+}
+
+extern "C" void gp_destroy(gp_ctx* ctx) { delete ctx; }
+
+extern "C" const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int64_t gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ------------------------------------------------------------------------------------------ point sets
+extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
+                                 gp_pointset** out) {
+  if (!ctx) return GP_ERR_ARG;
+  if (!out) return fail(ctx, GpError{GP_ERR_ARG, "ps is null"});
+  *out = nullptr;
+  gp_pointset* ps = new gp_pointset();
+  gp_status st = guarded(ctx, [&] {
+    GP_REQUIRE(d_X && core_radius, "d_X and core_radius are required");
+    GP_REQUIRE(n >= 1 && n < ((int64_t)1 << 31) - 1, "n must be in 1..2^31-2");
+    GP_REQUIRE(d >= 1 && d <= GP_MAX_D, "d must be 1, 2 or 3");
+    for (int k = 0; k < d; k++) GP_REQUIRE(core_radius[k] > 0.0 && std::isfinite(core_radius[k]), "core_radius must be positive");
+    ps->ctx = ctx;
+    ps->n = n;
+    ps->d = d;
+    for (int k = 0; k < d; k++) ps->rho[k] = core_radius[k];
+    assemble_pointset(ctx, ps, d_X);       // A1, A2, A5 on the device
+    // A6 on the host from the device pattern and order
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col(ps->nnz), perm(n);
+    d2h(ctx, rp.data(), ps->rowptr, n + 1);
+    d2h(ctx, col.data(), ps->col, ps->nnz);
+    d2h(ctx, perm.data(), ps->perm, n);
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+    build_symbolic(n, rp.data(), col.data(), perm.data(), ps->sp);
+    SymPlan& sp = ps->sp;
+    h2d(ctx, ps->perm, sp.perm.data(), n);
+    DevPlan& dp = ps->dp;
+    dp.w = upload(ctx, ps->bufs, sp.sn_w);
+    dp.r = upload(ctx, ps->bufs, sp.sn_r);
+    dp.loff = upload(ctx, ps->bufs, sp.sn_loff);
+    dp.uoff = upload(ctx, ps->bufs, sp.sn_uoff);
+    dp.frow_off = upload(ctx, ps->bufs, sp.sn_frow);
+    dp.frows = upload(ctx, ps->bufs, sp.frows);
+    dp.ch_ptr = upload(ctx, ps->bufs, sp.ch_ptr);
+    dp.ch_idx = upload(ctx, ps->bufs, sp.ch_idx);
+    dp.relidx_off = upload(ctx, ps->bufs, sp.relidx_off);
+    dp.relidx = upload(ctx, ps->bufs, sp.relidx);
+    dp.sn_first = upload(ctx, ps->bufs, sp.sn_first);
+    dp.sn_of_col = upload(ctx, ps->bufs, sp.sn_of_col);
+    dp.ea_tab = upload(ctx, ps->bufs, sp.ea_tab);
+    dp.small_list = upload(ctx, ps->bufs, sp.small_list);
+    dp.large_fronts = upload(ctx, ps->bufs, sp.large_fronts);
+    dp.step_pre = upload(ctx, ps->bufs, sp.step_pre);
+    dp.lev_sn = upload(ctx, ps->bufs, sp.lev_sn);
+    dp.sn_parent = upload(ctx, ps->bufs, sp.sn_parent);
+    compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+  if (st != GP_OK) {
+    dev_free_all(ctx, ps->bufs);
+    delete ps;
+    return st;
+  }
+  *out = ps;
+  return GP_OK;
+}
+
+extern "C" void gp_pointset_free(gp_pointset* ps) {
+  if (!ps) return;
+  if (ps->ctx) {
+    cudaSetDevice(ps->ctx->device);
+    dev_free_all(ps->ctx, ps->bufs);
+  }
+  delete ps;
+}
+
+extern "C" gp_status gp_pointset_info(const gp_pointset* ps, gp_pointset_info_t* info) {
+  if (!ps || !info) return GP_ERR_ARG;
+  const SymPlan& sp = ps->sp;
+  info->n = ps->n;
+  info->d = ps->d;
+  info->nnz = ps->nnz;
+  info->ncells = ps->ncells;
+  info->nnzL = sp.nnzL;
+  info->nsuper = sp.ns;
+  info->panel_entries = sp.panel_entries;
+  info->update_entries = sp.update_entries;
+  info->nlevels = sp.nlevels;
+  info->max_front = sp.max_front;
+  info->flops = sp.flops;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_pointset_export(const gp_pointset* ps, int what, void* dst, size_t bytes) {
+  if (!ps || !dst) return GP_ERR_ARG;
+  gp_ctx* ctx = ps->ctx;
+  const SymPlan& sp = ps->sp;
+  auto host = [&](const void* src, size_t b) -> gp_status {
+    if (b != bytes) return fail(ctx, GpError{GP_ERR_ARG, "export size mismatch: expected " + std::to_string(b)});
+    if (b) memcpy(dst, src, b);
+    return GP_OK;
+  };
+  auto dev = [&](const void* src, size_t b) -> gp_status {
+    if (b != bytes) return fail(ctx, GpError{GP_ERR_ARG, "export size mismatch: expected " + std::to_string(b)});
+    return guarded(ctx, [&] {
+      GP_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, ctx->stream));
+      GP_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+  };
+  const size_t n = (size_t)ps->n;
+  switch (what) {
+    case 0: return host(sp.perm.data(), n * 4);
+    case 1: return host(sp.parent.data(), n * 4);
+    case 2: return host(sp.eta.data(), n * 4);
+    case 3: return dev(ps->rowptr, (n + 1) * 8);
+    case 4: return dev(ps->col, (size_t)ps->nnz * 4);
+    case 5: return host(sp.sn_first.data(), sp.sn_first.size() * 4);
+    case 6: return host(sp.sn_rowptr.data(), sp.sn_rowptr.size() * 8);
+    case 7: return host(sp.sn_rows.data(), sp.sn_rows.size() * 4);
+    case 8: return host(sp.sn_parent.data(), sp.sn_parent.size() * 4);
+    case 9: return host(sp.sn_level.data(), sp.sn_level.size() * 4);
+    case 10: return dev(ps->cell_perm, n * 4);
+    default: return fail(ctx, GpError{GP_ERR_ARG, "unknown export"});
+  }
+}
+
+// ------------------------------------------------------------------------------------------ factors
+extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, gp_precision prec,
+                               gp_factor_t** out) {
+  if (!ctx) return GP_ERR_ARG;
+  if (!out) return fail(ctx, GpError{GP_ERR_ARG, "f is null"});
+  *out = nullptr;
+  gp_factor_t* f = new gp_factor_t();
+  gp_status st = guarded(ctx, [&] {
+    GP_REQUIRE(ps && ps->ctx == ctx, "point set missing or from another context");
+    GP_REQUIRE(thetas && B >= 1, "B >= 1 settings are required");
+    GP_REQUIRE(prec == GP_FP64 || prec == GP_MIXED, "unknown precision");
+    const SymPlan& sp = ps->sp;
+    f->ctx = ctx;
+    f->ps = ps;
+    f->B = B;
+    f->prec = prec;
+    ThetaDims td{thetas[0].d, thetas[0].n1, thetas[0].n2, thetas[0].bump_dims};
+    GP_REQUIRE(td.d == ps->d, "theta.d differs from the point set dimension");
+    GP_REQUIRE(td.n1 >= 0 && td.n1 <= GP_MAX_N1, "n1 must be in 0..32");
+    f->theta_dev = dalloc<double>(ctx, f->bufs, (size_t)theta_stride_of(td) * B);
+    f->F = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * td.n1 + 1);
+    f->panels = dalloc<double>(ctx, f->bufs, (size_t)B * sp.panel_entries);
+    f->upd = dalloc<double>(ctx, f->bufs, (size_t)B * sp.update_entries);
+    f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
+    f->notpd = dalloc<int32_t>(ctx, f->bufs, B);
+    f->alpha = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
+    f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
+    f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);
+    f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
+    f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride);
+    pack_thetas(f, thetas);
+    factor_run(ctx, f);
+  });
+  if (st != GP_OK) {
+    dev_free_all(ctx, f->bufs);
+    delete f;
+    return st;
+  }
+  *out = f;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
+    GP_REQUIRE(thetas, "thetas required");
+    GP_REQUIRE(thetas[0].n1 == f->n1max, "n1 must match the factor");
+    pack_thetas(f, thetas);
+    f->have_alpha = false;
+    factor_run(ctx, f);
+  });
+}
+
+extern "C" void gp_factor_free(gp_factor_t* f) {
+  if (!f) return;
+  if (f->ctx) {
+    cudaSetDevice(f->ctx->device);
+    dev_free_all(f->ctx, f->bufs);
+  }
+  delete f;
+}
+
+extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, int32_t* not_pd_column) {
+  if (!f || !info) return GP_ERR_ARG;
+  gp_ctx* ctx = f->ctx;
+  std::vector<int32_t> flags(f->B);
+  gp_status st = guarded(ctx, [&] {
+    d2h(ctx, flags.data(), f->notpd, f->B);
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+  if (st != GP_OK) return st;
+  info->B = f->B;
+  info->precision = f->prec;
+  int64_t bytes = 0;
+  for (auto& b : f->bufs) bytes += (int64_t)b.bytes;
+  info->bytes = bytes;
+  info->not_pd_count = 0;
+  for (int b = 0; b < f->B; b++) {   // flags hold the smallest failing permuted column, INT_MAX if none
+    bool bad = flags[b] != 0x7fffffff;
+    if (bad) info->not_pd_count++;
+    if (not_pd_column) not_pd_column[b] = bad ? flags[b] : -1;
+  }
+  return GP_OK;
+}
+
+// ------------------------------------------------------------------------------------------ solves
+extern "C" gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err_est) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
+    GP_REQUIRE(d_resid && d_out, "d_resid and d_out are required");
+    loglik_run(ctx, f, d_resid, d_out, d_err_est);
+    f->have_alpha = true;
+  });
+}
+
+extern "C" gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
+                                const double* d_mu_test, double* d_mean) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
+    GP_REQUIRE(b >= 0 && b < f->B, "proposal index out of range");
+    GP_REQUIRE(m >= 0 && (m == 0 || (d_Xtest && d_mean)), "d_Xtest and d_mean are required");
+    if (!f->have_alpha) throw GpError{GP_ERR_STATE, "gp_predict needs gp_loglik first (alpha = C_z^-1 r)"};
+    if (m > 0) predict_run(ctx, f, b, d_Xtest, m, d_mu_test, d_mean);
+  });
+}

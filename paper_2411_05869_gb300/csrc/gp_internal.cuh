@@ -1,0 +1,237 @@
+// gp_internal.cuh -- shared declarations of the GB300 exact sparse-GP library (libgp.so).
+//
+// Step map (the hot path, in order):
+//   A1 cell list            assemble.cu  (u = x / core_radius, cell keys, radix sort, cell ranges)
+//   A2 support pattern      assemble.cu  (neighbour cells, q^2 < 1 without contraction, CSR rows ascending)
+//   A5 nested dissection    assemble.cu  (level-synchronous geometric bisection with one-sided separators)
+//   A6 symbolic analysis    symbolic.cpp (etree, column counts, relaxed supernodes, frontal plan)
+//   A3/A4 kernel values     values.cu    (bump features, C_z entries fused with the scatter into panels)
+//   A7 numeric factor       factor.cu    (level-by-level multifrontal supernodal Cholesky)
+//   A8-A11 solves           solve.cu     (forward/backward supernodal solves, log-det, refinement)
+//   A12 predictive mean     predict.cu
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gp.h"
+
+#define GP_MAX_D 3
+#define GP_MAX_N1 32
+#define GP_ND_LEAF 64          // nested-dissection leaves hold at most this many points
+#define GP_RELAX_WIDTH 16      // relaxed amalgamation: merge when the merged supernode is this narrow
+#define GP_TILE 64             // dense tile edge of the large-front kernels
+#define GP_SMALL_M 96          // fronts up to this order are factored by one CTA in shared memory
+
+// ------------------------------------------------------------------------------------------ errors
+struct GpError {
+  gp_status st;
+  std::string msg;
+};
+
+#define GP_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      throw GpError{GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};            \
+  } while (0)
+
+#define GP_CHECK_LAUNCH(ctx)                                                                     \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess)                                                                       \
+      throw GpError{GP_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)};      \
+    (ctx)->launches++;                                                                           \
+  } while (0)
+
+#define GP_REQUIRE(cond, what)                                                                   \
+  do {                                                                                           \
+    if (!(cond)) throw GpError{GP_ERR_ARG, what};                                                \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------ context
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;     // 0 = unlimited
+  size_t held = 0;       // bytes currently held by this context's handles
+  int64_t launches = 0;
+  std::string err;
+};
+
+// Device buffer owned by a handle; charged against the context budget.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+void* dev_alloc(gp_ctx* ctx, std::vector<DevBuf>& owner, size_t bytes);
+void dev_free_all(gp_ctx* ctx, std::vector<DevBuf>& owner);
+template <class T>
+T* dalloc(gp_ctx* ctx, std::vector<DevBuf>& owner, size_t count) {
+  return static_cast<T*>(dev_alloc(ctx, owner, count * sizeof(T)));
+}
+template <class T>
+void h2d(gp_ctx* ctx, T* dst, const T* src, size_t count) {
+  GP_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+}
+template <class T>
+void d2h(gp_ctx* ctx, T* dst, const T* src, size_t count) {
+  GP_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+// ------------------------------------------------------------------------------------------ symbolic plan
+// Host-side result of A6, plus the device copies the numeric kernels read.
+struct SymPlan {
+  int64_t n = 0;
+  int64_t ns = 0;                    // supernodes
+  int32_t nlevels = 0;
+  std::vector<int32_t> perm;         // final order: nested dissection relabelled by its etree postorder
+  std::vector<int32_t> parent, eta;  // etree and exact column counts (permuted columns)
+  std::vector<int32_t> sn_first;     // ns+1
+  std::vector<int64_t> sn_rowptr;    // ns+1 into sn_rows
+  std::vector<int32_t> sn_rows;      // rows strictly below each supernode (ascending)
+  std::vector<int32_t> sn_parent, sn_level;
+  std::vector<int32_t> sn_w, sn_r;   // width, rows below
+  std::vector<int64_t> sn_loff;      // panel offset (column-major m x w, ld m)
+  std::vector<int64_t> sn_uoff;      // update-matrix offset (r x r column-major)
+  std::vector<int64_t> sn_frow;      // offset of the front row list (m entries: own columns then sn_rows)
+  std::vector<int32_t> frows;        // concatenated front rows
+  std::vector<int32_t> ch_ptr, ch_idx;        // children (ascending) of each supernode
+  std::vector<int64_t> relidx_off;   // per supernode: offset of its r relative indices into the parent front
+  std::vector<int32_t> relidx;
+  std::vector<int32_t> lev_ptr, lev_sn;       // supernodes grouped by level (ascending index within)
+  std::vector<int32_t> sn_of_col;    // supernode of each permuted column
+  int64_t nnzL = 0;
+  int64_t panel_entries = 0;
+  int64_t update_entries = 0;        // peak of the update-matrix memory plan
+  int64_t vec_update_entries = 0;    // sum of r over supernodes (solve update vectors)
+  double flops = 0.0;
+  int32_t max_front = 0;
+
+  // schedule for the numeric factorization, per level
+  struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
+  struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off; };
+  struct Level {
+    std::vector<EaLaunch> ea;        // one per child slot
+    int64_t small_off = 0; int32_t nsmall = 0;   // into small_list
+    std::vector<StepLaunch> steps;   // large fronts, one per block column
+  };
+  std::vector<Level> levels;
+  std::vector<int2> ea_tab;          // (child supernode, first column) per extend-add CTA (8 columns each)
+  std::vector<int32_t> small_list;   // supernodes factored in shared memory
+  std::vector<int32_t> large_fronts; // per step: fronts (sorted by width descending within a level)
+  std::vector<int64_t> step_pre;     // per step: prefix of TRSM tasks then of UPDATE tasks (2*(nfront+1))
+};
+
+// Device mirror of the plan (pointers into one allocation set owned by the point set).
+struct DevPlan {
+  int32_t *w, *r;
+  int64_t *loff, *uoff, *frow_off;
+  int32_t* frows;
+  int32_t *ch_ptr, *ch_idx;
+  int64_t* relidx_off;
+  int32_t* relidx;
+  int32_t* sn_first;
+  int32_t* sn_of_col;
+  int2* ea_tab;
+  int32_t* small_list;
+  int32_t* large_fronts;
+  int64_t* step_pre;
+  int32_t* lev_sn;
+  int32_t* sn_parent;
+};
+
+void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
+
+// ------------------------------------------------------------------------------------------ handles
+struct gp_pointset {
+  gp_ctx* ctx = nullptr;
+  std::vector<DevBuf> bufs;
+  int64_t n = 0;
+  int d = 0;
+  double rho[GP_MAX_D] = {1, 1, 1};
+  double* X = nullptr;          // n x d copy of the points
+  double* U = nullptr;          // n x d scaled coordinates, index order
+  double* Us = nullptr;         // n x d scaled coordinates, cell order
+  int32_t* cell_perm = nullptr; // cell order -> point
+  int64_t* cell_start = nullptr;// ncells + 1
+  int64_t ncells = 0;
+  int64_t c0[GP_MAX_D] = {0, 0, 0};
+  int64_t nc[GP_MAX_D] = {1, 1, 1};
+  int64_t* rowptr = nullptr;    // n+1
+  int32_t* col = nullptr;       // nnz
+  int64_t nnz = 0;
+  int32_t* perm = nullptr;      // new -> old
+  int32_t* pinv = nullptr;      // old -> new
+  int64_t* dest = nullptr;      // per CSR entry: panel offset of its lower-triangle copy, or -1
+  SymPlan sp;
+  DevPlan dp{};
+};
+
+struct gp_factor_s {
+  gp_ctx* ctx = nullptr;
+  gp_pointset* ps = nullptr;
+  std::vector<DevBuf> bufs;
+  int B = 0;
+  gp_precision prec = GP_FP64;
+  double* theta_dev = nullptr;  // B packed settings
+  int64_t theta_stride = 0;
+  double* F = nullptr;          // B x n x n1 bump features
+  int n1max = 0;
+  double* panels = nullptr;     // FP64 panels, B x panel_entries
+  float* panels32 = nullptr;    // GP_MIXED: FP32 panels (off-diagonal rows), B x panel_entries
+  double* upd = nullptr;        // B x update_entries
+  float* upd32 = nullptr;
+  double* val = nullptr;        // B x nnz CSR values of C_z (refinement SpMV)
+  int32_t* notpd = nullptr;     // B: smallest failing permuted column (INT_MAX = none)
+  double* alpha = nullptr;      // B x n
+  double* work = nullptr;       // solve workspace
+  double* red = nullptr;        // reduction partials, B x red_stride
+  int64_t red_stride = 0;
+  int64_t work_stride = 0;
+  bool have_alpha = false;
+  std::vector<gp_hyper> thetas_host;
+};
+
+// ------------------------------------------------------------------------------------------ packed theta
+// Layout on the device per proposal: [core_var, s0, noise_var, core_radius[3], r0[3], then per bump
+// (h[bump_dims], a, b, r)]. n1/n2/bump_dims are shared by the batch.
+struct ThetaDims {
+  int d, n1, n2, bd;
+};
+#define TH_CORE_VAR 0
+#define TH_S0 1
+#define TH_NOISE 2
+#define TH_CRAD 3
+#define TH_R0 6
+#define TH_BUMPS 9
+inline int64_t theta_stride_of(const ThetaDims& t) { return TH_BUMPS + (int64_t)t.n1 * t.n2 * (t.bd + 3); }
+
+// ------------------------------------------------------------------------------------------ launchers
+// sort.cu
+size_t radix_sort_temp_bytes(int64_t n);
+void radix_sort_pairs(gp_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t n, int begin_bit, int end_bit,
+                      void* temp);
+void exclusive_scan_i64(gp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, void* temp);
+size_t scan_temp_bytes(int64_t n);
+
+// assemble.cu
+void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X);
+
+// values.cu / factor.cu / solve.cu / predict.cu
+void factor_run(gp_ctx* ctx, gp_factor_t* f);
+void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err);
+void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, const double* d_mu, double* d_mean);
+void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+inline unsigned grid_for(int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return (unsigned)g;
+}

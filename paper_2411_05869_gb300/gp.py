@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libgp.so (include/gp.h). Argument marshalling only: every step runs in the library.
+
+PyTorch supplies device memory (CUDA tensors) and streams. The library is the only compute path; when it is
+missing or cannot load, these calls raise, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+c_i64 = ctypes.c_int64
+c_int = ctypes.c_int
+c_dbl = ctypes.c_double
+P = ctypes.c_void_p
+DP = ctypes.POINTER(ctypes.c_double)
+
+GP_FP64, GP_MIXED = 0, 1
+STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_NOMEM", 3: "GP_ERR_NOT_PD", 4: "GP_ERR_CUDA",
+          5: "GP_ERR_TIMEOUT", 6: "GP_ERR_STATE"}
+EXPORTS = {"perm": (0, np.int32), "parent": (1, np.int32), "eta": (2, np.int32), "rowptr": (3, np.int64),
+           "col": (4, np.int32), "sn_first": (5, np.int32), "sn_rowptr": (6, np.int64), "sn_rows": (7, np.int32),
+           "sn_parent": (8, np.int32), "sn_level": (9, np.int32), "cell_perm": (10, np.int32)}
+
+
+class GpHyper(ctypes.Structure):
+    _fields_ = [("d", c_int), ("n1", c_int), ("n2", c_int), ("bump_dims", c_int), ("core_var", c_dbl),
+                ("core_radius", DP), ("s0", c_dbl), ("r0", DP), ("h", DP), ("a", DP), ("b", DP), ("r", DP),
+                ("noise_var", c_dbl)]
+
+
+class PointsetInfo(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("d", c_int), ("nnz", c_i64), ("ncells", c_i64), ("nnzL", c_i64),
+                ("nsuper", c_i64), ("panel_entries", c_i64), ("update_entries", c_i64), ("nlevels", ctypes.c_int32),
+                ("max_front", ctypes.c_int32), ("flops", c_dbl)]
+
+
+class FactorInfo(ctypes.Structure):
+    _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32)]
+
+
+SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_pointset_free", "gp_pointset_info",
+           "gp_pointset_export", "gp_factor", "gp_factor_update", "gp_factor_free", "gp_factor_info", "gp_loglik",
+           "gp_predict", "gp_launch_count"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Open libgp.so (building it with nvcc when absent or stale) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libgp.so not found at {_build.LIB}; run paper_2411_05869_gb300.build")
+    L = ctypes.CDLL(_build.LIB)
+    L.gp_create.restype = c_int
+    L.gp_create.argtypes = [ctypes.POINTER(P), c_int, P, ctypes.c_size_t]
+    L.gp_destroy.argtypes = [P]
+    L.gp_destroy.restype = None
+    L.gp_last_error.restype = ctypes.c_char_p
+    L.gp_last_error.argtypes = [P]
+    L.gp_assemble.restype = c_int
+    L.gp_assemble.argtypes = [P, P, c_i64, c_int, DP, ctypes.POINTER(P)]
+    L.gp_pointset_free.argtypes = [P]
+    L.gp_pointset_free.restype = None
+    L.gp_pointset_info.restype = c_int
+    L.gp_pointset_info.argtypes = [P, ctypes.POINTER(PointsetInfo)]
+    L.gp_pointset_export.restype = c_int
+    L.gp_pointset_export.argtypes = [P, c_int, P, ctypes.c_size_t]
+    L.gp_factor.restype = c_int
+    L.gp_factor.argtypes = [P, P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(P)]
+    L.gp_factor_update.restype = c_int
+    L.gp_factor_update.argtypes = [P, P, ctypes.POINTER(GpHyper)]
+    L.gp_factor_free.argtypes = [P]
+    L.gp_factor_free.restype = None
+    L.gp_factor_info.restype = c_int
+    L.gp_factor_info.argtypes = [P, ctypes.POINTER(FactorInfo), P]
+    L.gp_loglik.restype = c_int
+    L.gp_loglik.argtypes = [P, P, P, P, P]
+    L.gp_predict.restype = c_int
+    L.gp_predict.argtypes = [P, P, c_int, P, c_i64, P, P]
+    L.gp_launch_count.restype = c_i64
+    L.gp_launch_count.argtypes = [P]
+    _lib = L
+    return L
+
+
+class GpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(DP)
+
+
+class _HyperPack:
+    """Keeps the numpy arrays behind a ctypes gp_hyper array alive for the duration of a call."""
+
+    def __init__(self, thetas: Sequence):
+        self.keep: List[np.ndarray] = []
+        self.arr = (GpHyper * len(thetas))()
+        for k, hp in enumerate(thetas):
+            def arr(x):
+                a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+                if a.size == 0:
+                    a = np.zeros(1)
+                self.keep.append(a)
+                return _dp(a)
+            self.arr[k] = GpHyper(hp.d, hp.n1, hp.n2, hp.bump_dims, float(hp.core_var), arr(hp.core_radius),
+                                  float(hp.s0), arr(hp.r0), arr(hp.h), arr(hp.a), arr(hp.b), arr(hp.r),
+                                  float(hp.noise_var))
+
+
+class Context:
+    """A library context on one CUDA device and stream (gp_create)."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget_bytes: int = 0):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = P()
+        st = self.lib.gp_create(ctypes.byref(h), device, P(stream.cuda_stream), mem_budget_bytes)
+        if st != 0:
+            raise GpError(st, "gp_create failed")
+        self.h = h
+
+    def check(self, st: int):
+        if st != 0:
+            raise GpError(st, self.lib.gp_last_error(self.h).decode())
+
+    def launches(self) -> int:
+        return int(self.lib.gp_launch_count(self.h))
+
+    def assemble(self, X, core_radius) -> "PointSet":
+        """Steps A1, A2, A5, A6 for a CUDA float64 tensor X (n x d)."""
+        import torch
+        assert X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+        X = X.contiguous()
+        rad = np.ascontiguousarray(np.asarray(core_radius, dtype=np.float64))
+        h = P()
+        self.check(self.lib.gp_assemble(self.h, P(X.data_ptr()), X.shape[0], X.shape[1], _dp(rad), ctypes.byref(h)))
+        return PointSet(self, h)
+
+    def factor(self, ps: "PointSet", thetas: Sequence, precision: int = GP_FP64) -> "Factor":
+        """Steps A3, A4, A7 for B = len(thetas) settings."""
+        pack = _HyperPack(thetas)
+        h = P()
+        self.check(self.lib.gp_factor(self.h, ps.h, pack.arr, len(thetas), precision, ctypes.byref(h)))
+        return Factor(self, ps, h, len(thetas))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PointSet:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def info(self) -> dict:
+        inf = PointsetInfo()
+        self.ctx.check(self.ctx.lib.gp_pointset_info(self.h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in PointsetInfo._fields_}
+
+    def export(self, name: str) -> np.ndarray:
+        what, dt = EXPORTS[name]
+        inf = self.info()
+        n, nnz, ns = inf["n"], inf["nnz"], inf["nsuper"]
+        if name == "sn_rows":
+            size = int(self.export("sn_rowptr")[-1])
+        else:
+            size = {"perm": n, "parent": n, "eta": n, "rowptr": n + 1, "col": nnz, "sn_first": ns + 1,
+                    "sn_rowptr": ns + 1, "sn_parent": ns, "sn_level": ns, "cell_perm": n}[name]
+        out = np.empty(size, dtype=dt)
+        self.ctx.check(self.ctx.lib.gp_pointset_export(self.h, what, out.ctypes.data_as(P), out.nbytes))
+        return out
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.gp_pointset_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Factor:
+    def __init__(self, ctx: Context, ps: PointSet, h, B: int):
+        self.ctx, self.ps, self.h, self.B = ctx, ps, h, B
+
+    def update(self, thetas: Sequence):
+        """Re-run A3, A4, A7 in place with new settings (same B)."""
+        assert len(thetas) == self.B
+        pack = _HyperPack(thetas)
+        self.ctx.check(self.ctx.lib.gp_factor_update(self.ctx.h, self.h, pack.arr))
+
+    def info(self):
+        inf = FactorInfo()
+        cols = np.empty(self.B, dtype=np.int32)
+        self.ctx.check(self.ctx.lib.gp_factor_info(self.h, ctypes.byref(inf), cols.ctypes.data_as(P)))
+        d = {k: getattr(inf, k) for k, _ in FactorInfo._fields_}
+        d["not_pd_column"] = cols
+        return d
+
+    def loglik(self, resid, out=None, err=None):
+        """Steps A8-A11: resid is a CUDA float64 tensor (n,) or (B, n); returns the B log-likelihoods."""
+        import torch
+        r = resid.contiguous()
+        assert r.is_cuda and r.dtype == torch.float64
+        if out is None:
+            out = torch.empty(self.B, dtype=torch.float64, device=r.device)
+        self.ctx.check(self.ctx.lib.gp_loglik(self.ctx.h, self.h, P(r.data_ptr()), P(out.data_ptr()),
+                                              P(_ptr(err)) if err is not None else None))
+        return out
+
+    def predict(self, Xtest, mu_test=None, b: int = 0, out=None):
+        """Step A12 for proposal b at CUDA float64 test points (m x d)."""
+        import torch
+        Xt = Xtest.contiguous()
+        m = Xt.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=Xt.device)
+        mu = None if mu_test is None else mu_test.contiguous()
+        self.ctx.check(self.ctx.lib.gp_predict(self.ctx.h, self.h, b, P(Xt.data_ptr()), m,
+                                               P(mu.data_ptr()) if mu is not None else None, P(out.data_ptr())))
+        return out
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.gp_factor_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path through the C-ABI against the oracle, element by element.
+
+Structure (pattern, order, etree, column counts, supernodes, row structures) must match bit for bit;
+FP64 log-likelihoods to 1e-10 relative; alpha and predictive means to 1e-9 of their scale (the same
+factorization carried through two triangular solves and one more product).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_05869_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LOGLIK_RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2411_05869_gb300 import gp
+    return gp.Context(0)
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _cases():
+    return {
+        "spatial_2d_n2000": lambda: synth.spatial_2d(n=2000, m=300, seed=synth.SEED_BASE + 1),
+        "spacetime_n6000": lambda: synth.uniform_spacetime(6000, 400, 40.0, 8, seed=77, ndays=60),
+        "station_600x20": lambda: synth.station_spacetime(nsites=600, ndays=20, ncomp=10, nnz_row=60.0, grid=12,
+                                                          grid_days=3, seed=78, nbumps=16),
+    }
+
+
+@pytest.fixture(scope="module", params=list(_cases().keys()))
+def case(request, ctx):
+    w = _cases()[request.param]()
+    hp = w.hyper
+    if w.resid is None:
+        y = oracle.sample_dense(hp, w.X, w.normals)
+        w.resid = y + math.sqrt(hp.noise_var) * w.noise
+    rp, col = oracle.pattern(w.X, hp.core_radius)
+    perm = oracle.fill_order(w.X, hp.core_radius, rp, col)
+    sym = oracle.symbolic(rp, col, perm)
+    ps = ctx.assemble(_dev(w.X), hp.core_radius)
+    return dict(name=request.param, w=w, rp=rp, col=col, perm=perm, sym=sym, ps=ps)
+
+
+def test_pattern_bit_exact(case):
+    ps = case["ps"]
+    assert np.array_equal(ps.export("rowptr"), case["rp"])
+    assert np.array_equal(ps.export("col"), case["col"])
+
+
+def test_cell_list_sorted_by_cell_then_index(case):
+    w = case["w"]
+    key = oracle.cell_keys(w.X, w.hyper.core_radius)
+    cp = case["ps"].export("cell_perm")
+    ref = np.lexsort((np.arange(len(key)), key))
+    assert np.array_equal(cp, ref)
+
+
+def test_order_and_symbolic_bit_exact(case):
+    ps, sym = case["ps"], case["sym"]
+    assert np.array_equal(ps.export("perm"), case["perm"])
+    assert np.array_equal(ps.export("parent"), sym["parent"])
+    assert np.array_equal(ps.export("eta"), sym["eta"])
+    assert np.array_equal(ps.export("sn_first"), sym["sn_first"])
+    assert np.array_equal(ps.export("sn_rowptr"), sym["sn_rowptr"])
+    assert np.array_equal(ps.export("sn_rows"), sym["sn_rows"])
+    assert np.array_equal(ps.export("sn_parent"), sym["sn_parent"])
+    assert np.array_equal(ps.export("sn_level"), sym["sn_level"])
+    inf = ps.info()
+    assert inf["nnzL"] == sym["nnzL"]
+
+
+def test_loglik_fp64_matches_oracle(case, ctx):
+    w, ps = case["w"], case["ps"]
+    ref = oracle.sparse_loglik(w.hyper, w.X, case["rp"], case["col"], case["perm"], w.resid, want_alpha=True)
+    f = ctx.factor(ps, [w.hyper])
+    err = torch.empty(1, dtype=torch.float64, device="cuda")
+    ll = f.loglik(_dev(w.resid), err=err)
+    got = float(ll.cpu()[0])
+    assert abs(got - ref["loglik"]) <= LOGLIK_RTOL * abs(ref["loglik"]), (got, ref["loglik"])
+    assert float(err.cpu()[0]) < 1e-12
+    # predictive mean at test points (and alpha through it)
+    mu = np.linspace(-0.5, 0.5, w.Xtest.shape[0])
+    m_ref = oracle.predict(w.hyper, w.X, ref["alpha"], w.Xtest, mu)
+    m_gpu = f.predict(_dev(w.Xtest), _dev(mu)).cpu().numpy()
+    scale = max(1.0, np.abs(m_ref).max())
+    assert np.abs(m_gpu - m_ref).max() <= 1e-9 * scale
+    f.free()
+
+
+def test_batched_proposals_each_match_oracle(case, ctx):
+    w, ps = case["w"], case["ps"]
+    rng = np.random.default_rng(5)
+    thetas = [w.hyper] + [synth.perturb(rng, w.hyper) for _ in range(2)]
+    f = ctx.factor(ps, thetas)
+    R = np.stack([w.resid, w.resid * 0.5 + 0.1, np.roll(w.resid, 7)])
+    ll = f.loglik(_dev(R)).cpu().numpy()
+    for b, hp in enumerate(thetas):
+        ref = oracle.sparse_loglik(hp, w.X, case["rp"], case["col"], case["perm"], R[b])
+        assert abs(ll[b] - ref["loglik"]) <= LOGLIK_RTOL * abs(ref["loglik"]), (b, ll[b], ref["loglik"])
+    f.free()
+
+
+def test_repeatable_bitwise(case, ctx):
+    w, ps = case["w"], case["ps"]
+    f = ctx.factor(ps, [w.hyper])
+    r = _dev(w.resid)
+    a = f.loglik(r).cpu().numpy().copy()
+    f.update([w.hyper])
+    b = f.loglik(r).cpu().numpy().copy()
+    assert a.tobytes() == b.tobytes()
+    f.free()
+
+
+def test_not_positive_definite_is_flagged(ctx):
+    w = synth.spatial_2d(n=500, m=1, seed=31)
+    hp = w.hyper.copy()
+    hp.noise_var = -50.0
+    ps = ctx.assemble(_dev(w.X), hp.core_radius)
+    f = ctx.factor(ps, [w.hyper, hp])
+    ll = f.loglik(_dev(np.ones((2, 500)))).cpu().numpy()
+    assert np.isfinite(ll[0]) and ll[1] == -np.inf
+    inf = f.info()
+    assert inf["not_pd_count"] == 1 and inf["not_pd_column"][0] == -1 and inf["not_pd_column"][1] >= 0
+
+
+@pytest.mark.parametrize("n,d", [(1, 2), (7, 1), (64, 3), (65, 2), (300, 1)])
+def test_edge_sizes(ctx, n, d):
+    rng = np.random.default_rng(n + d)
+    X = rng.uniform(0, 1, (n, d))
+    rho = np.full(d, 0.3)
+    nb = 2
+    hp = synth.Hyper(d=d, n1=1, n2=nb, bump_dims=d, core_var=1.2, core_radius=rho, s0=0.9, r0=rho.copy(),
+                     h=rng.uniform(0, 1, nb * d), a=np.array([1.0, 0.7]), b=np.ones(nb), r=np.array([0.4, 0.3]),
+                     noise_var=0.05)
+    r = rng.standard_normal(n)
+    rp, col = oracle.pattern(X, rho)
+    perm = oracle.fill_order(X, rho, rp, col)
+    ref = oracle.sparse_loglik(hp, X, rp, col, perm, r, want_alpha=True)
+    ps = ctx.assemble(_dev(X), rho)
+    assert np.array_equal(ps.export("col"), col)
+    assert np.array_equal(ps.export("perm"), perm)
+    f = ctx.factor(ps, [hp])
+    ll = float(f.loglik(_dev(r)).cpu()[0])
+    assert abs(ll - ref["loglik"]) <= LOGLIK_RTOL * abs(ref["loglik"])
