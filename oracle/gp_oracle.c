@@ -401,7 +401,9 @@ static void colstruct_free(colstruct_t* cs) {
  * child of j+1.
  * Relaxed amalgamation, supernodes taken in increasing column order: while the supernode c that ends at
  * first(p)-1 has its supernodal parent equal to p, merge c into p if the merged width is <= 16 or if the
- * explicit zeros added by the merge are at most 10 % of the merged panel entries (10 * added <= entries).
+ * explicit zeros of the merged panel are at most 10 % of its entries (10 * zeros <= entries). Bounding the
+ * total, not only the zeros one merge adds, keeps chains of separators from compounding into wide, mostly
+ * empty supernodes.
  * A panel of columns [f, l] with r rows below l holds sum_{j=f..l} (l - j + 1 + r) entries; r = eta_l - 1.
  * Returns the supernode count; sn_first[ns+1] are the first columns (sn_first[ns] = n).
  */
@@ -454,9 +456,8 @@ int64_t or_supernodes(int64_t n, const int32_t* parent, const int32_t* eta, int3
       int64_t ent = panel_entries(cf, pl, r);
       int64_t ex = st_exact[top - 1] + pex;
       int64_t mz = ent - ex;
-      int64_t added = mz - st_zeros[top - 1] - pz;
       int64_t width = pl - cf + 1;
-      if (width <= SN_RELAX_WIDTH || 10 * added <= ent) {
+      if (width <= SN_RELAX_WIDTH || 10 * mz <= ent) {
         pf = cf; pex = ex; pz = mz;
         top--;
       } else {

@@ -12,8 +12,8 @@
 //     leaves in postorder; eta_j is the subtree sum of these weights (minus one per child, plus one per leaf);
 //   * fundamental supernodes (parent(j) = j+1, eta_j = eta_{j+1} + 1, j the only child of j+1), then relaxed
 //     amalgamation in increasing column order: the supernode ending right before p merges into p when p is its
-//     supernodal parent and either the merged width is <= 16 or the explicit zeros the merge adds are at most
-//     10 % of the merged panel;
+//     supernodal parent and either the merged width is <= 16 or the merged panel holds at most 10 % explicit
+//     zeros (a bound on the total, so merges along a chain of separators cannot compound);
 //   * row structure of every supernode, frontal row lists, extend-add relative indices, supernode levels,
 //     an update-matrix memory plan (first fit, freed once the parent level has assembled), and the per-level
 //     launch schedule of the numeric kernels.
@@ -226,8 +226,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       int64_t ent = panel(c.f, p.l, eta[p.l] - 1);
       int64_t ex = c.exact + p.exact;
       int64_t mz = ent - ex;
-      int64_t added = mz - c.zeros - p.zeros;
-      if (p.l - c.f + 1 <= GP_RELAX_WIDTH || 10 * added <= ent) {
+      if (p.l - c.f + 1 <= GP_RELAX_WIDTH || 10 * mz <= ent) {
         p = SN{c.f, p.l, ex, mz};
         stk.pop_back();
       } else {
