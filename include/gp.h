@@ -157,6 +157,16 @@ GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, d
 GP_API gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
                      const double* d_mu_test, double* d_mean);
 
+/* Launch profiler. gp_profile(ctx, 1) clears the counters and brackets every later launch of the listed
+ * kernel classes with CUDA events on the context stream; gp_profile(ctx, 0) stops. gp_profile_read
+ * synchronises the stream and returns, for one class, the summed device time (ms), the launch count and the
+ * useful flops those launches performed (0 where no flop count applies). Classes:
+ *   0 A4 kernel values, 1 A7 extend-add, 2 A7 small fronts, 3 A7 diagonal-block POTRF, 4 A7 TRSM,
+ *   5 A7 trailing update (SYRK/GEMM), 6 A8-A10 solve sweep (one span per gp_loglik), 7 A12 prediction.
+ * Errors: GP_ERR_ARG (class out of range), GP_ERR_CUDA. */
+GP_API gp_status gp_profile(gp_ctx* ctx, int enable);
+GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops);
+
 /* Number of kernel launches this context has issued (a counter for launch accounting). */
 GP_API int64_t gp_launch_count(const gp_ctx* ctx);
 

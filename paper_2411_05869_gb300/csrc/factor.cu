@@ -303,6 +303,7 @@ void factor_run(gp_ctx* ctx, gp_factor_t* f) {
     k_zero_updates<<<dim3(nl, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd, UE);
     GP_CHECK_LAUNCH(ctx);
     for (const auto& ea : lv.ea) {
+      ProfScope ps_(ctx, KC_EXTEND_ADD);
       k_extend_add<<<dim3((unsigned)ea.ncta, B), 128, 0, st>>>(dp.ea_tab + ea.tab_off, dp, d_sn_parent, f->panels,
                                                                f->upd, PE, UE);
       GP_CHECK_LAUNCH(ctx);
@@ -314,6 +315,7 @@ void factor_run(gp_ctx* ctx, gp_factor_t* f) {
         int32_t s = sp.small_list[lv.small_off + q];
         mmax = std::max(mmax, sp.sn_w[s] + sp.sn_r[s]);
       }
+      ProfScope ps_(ctx, KC_FRONT_SMALL);
       k_small_front<<<dim3(lv.nsmall, B), 256, (size_t)mmax * mmax * sizeof(double), st>>>(
           dp.small_list + lv.small_off, dp, f->panels, f->upd, PE, UE, f->notpd);
       GP_CHECK_LAUNCH(ctx);
@@ -322,14 +324,19 @@ void factor_run(gp_ctx* ctx, gp_factor_t* f) {
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
       const int64_t* pre_up = pre_tr + stp.nfront + 1;
-      k_potrf<<<dim3(stp.nfront, B), 128, 0, st>>>(fronts, stp.kb, dp, f->panels, f->upd, PE, UE, f->notpd);
-      GP_CHECK_LAUNCH(ctx);
+      {
+        ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
+        k_potrf<<<dim3(stp.nfront, B), 128, 0, st>>>(fronts, stp.kb, dp, f->panels, f->upd, PE, UE, f->notpd);
+        GP_CHECK_LAUNCH(ctx);
+      }
       if (stp.trsm_total > 0) {
+        ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
         k_trsm<<<dim3((unsigned)stp.trsm_total, B), 256, 2 * T * T * sizeof(double), st>>>(
             fronts, pre_tr, stp.nfront, stp.kb, dp, f->panels, PE);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.upd_total > 0) {
+        ProfScope ps_(ctx, KC_UPDATE, B * stp.upd_flops);
         k_update<<<dim3((unsigned)stp.upd_total, B), 256, 2 * T * T * sizeof(double), st>>>(
             fronts, pre_up, stp.nfront, stp.kb, dp, f->panels, f->upd, PE, UE);
         GP_CHECK_LAUNCH(ctx);

@@ -140,6 +140,44 @@ extern "C" const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.
 
 extern "C" int64_t gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+namespace {
+void prof_collect(gp_ctx* ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  for (int k = 0; k < KC_COUNT; k++) {
+    for (auto& ev : ctx->prof_ev[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) ctx->prof_ms[k] += ms;
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+    ctx->prof_ev[k].clear();
+  }
+}
+}  // namespace
+
+extern "C" gp_status gp_profile(gp_ctx* ctx, int enable) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    prof_collect(ctx);
+    for (int k = 0; k < KC_COUNT; k++) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_n[k] = 0;
+      ctx->prof_flops[k] = 0.0;
+    }
+    ctx->prof = enable != 0;
+  });
+}
+
+extern "C" gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops) {
+  if (!ctx || kclass < 0 || kclass >= KC_COUNT) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    prof_collect(ctx);
+    if (total_ms) *total_ms = ctx->prof_ms[kclass];
+    if (launches) *launches = ctx->prof_n[kclass];
+    if (flops) *flops = ctx->prof_flops[kclass];
+  });
+}
+
 // ------------------------------------------------------------------------------------------ point sets
 extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
                                  gp_pointset** out) {

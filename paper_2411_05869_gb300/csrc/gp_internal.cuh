@@ -53,6 +53,10 @@ struct GpError {
   } while (0)
 
 // ------------------------------------------------------------------------------------------ context
+// Kernel classes timed by the optional launch profiler (gp_profile / gp_profile_read).
+enum KClass { KC_VALUES = 0, KC_EXTEND_ADD, KC_FRONT_SMALL, KC_POTRF, KC_TRSM, KC_UPDATE, KC_SOLVE, KC_PREDICT,
+              KC_ASSEMBLE, KC_COUNT };
+
 struct gp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -60,6 +64,35 @@ struct gp_ctx {
   size_t held = 0;       // bytes currently held by this context's handles
   int64_t launches = 0;
   std::string err;
+  // launch profiler: CUDA events around every launch of a class, on the context stream
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_COUNT];
+  double prof_ms[KC_COUNT] = {};
+  int64_t prof_n[KC_COUNT] = {};
+  double prof_flops[KC_COUNT] = {};
+  cudaEvent_t prof_open = nullptr;
+};
+
+// RAII timer of one launch (no-op unless profiling); `flops` is the useful work the launch performs.
+struct ProfScope {
+  gp_ctx* c;
+  int cls;
+  ProfScope(gp_ctx* ctx, int k, double flops = 0.0) : c(ctx), cls(k) {
+    if (!c->prof) return;
+    cudaEvent_t a;
+    cudaEventCreate(&a);
+    cudaEventRecord(a, c->stream);
+    c->prof_open = a;
+    c->prof_flops[k] += flops;
+  }
+  ~ProfScope() {
+    if (!c->prof) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, c->stream);
+    c->prof_ev[cls].push_back({c->prof_open, b});
+    c->prof_n[cls]++;
+  }
 };
 
 // Device buffer owned by a handle; charged against the context budget.
@@ -113,7 +146,8 @@ struct SymPlan {
 
   // schedule for the numeric factorization, per level
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
-  struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off; };
+  struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
+                      double potrf_flops, trsm_flops, upd_flops; };   // useful flops of the step's launches
   struct Level {
     std::vector<EaLaunch> ea;        // one per child slot
     int64_t small_off = 0; int32_t nsmall = 0;   // into small_list

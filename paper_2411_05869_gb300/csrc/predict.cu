@@ -138,6 +138,7 @@ void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t
   }
   const double* theta = f->theta_dev + (int64_t)b * f->theta_stride;
   const double* F = f->F + (int64_t)b * ps->n * h0.n1;
+  ProfScope ps_(ctx, KC_PREDICT);
   k_predict<<<grid_for(m, 8), 256, 0, ctx->stream>>>(d_Xt, m, d_mu, g, ps->X, ps->Us, ps->cell_perm, ps->cell_start,
                                                      theta, h0.n1, h0.n2, h0.bump_dims, F,
                                                      f->alpha + (int64_t)b * ps->n, d_mean);

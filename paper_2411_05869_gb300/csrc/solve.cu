@@ -442,7 +442,10 @@ void residual_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_
 }
 
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err) {
-  solve_run(ctx, f, d_resid, true);
+  {
+    ProfScope ps_(ctx, KC_SOLVE);   // the whole forward/backward sweep as one timed span
+    solve_run(ctx, f, d_resid, true);
+  }
   int nblk = (int)((f->ps->n + 1023) / 1024);
   k_loglik<<<f->B, 256, 0, ctx->stream>>>(f->ps->n, f->red, f->red_stride, nblk, f->notpd, d_out, nullptr);
   GP_CHECK_LAUNCH(ctx);

@@ -446,6 +446,17 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           sp.step_pre.push_back(acc);
         }
         stp.upd_total = acc;
+        stp.potrf_flops = stp.trsm_flops = stp.upd_flops = 0.0;
+        for (int32_t t = 0; t < cnt; t++) {
+          int32_t s = sp.large_fronts[stp.fr_off + t];
+          double m = (double)sp.sn_w[s] + sp.sn_r[s];
+          double c0 = (double)kb * GP_TILE;
+          double bw = std::min<double>(GP_TILE, sp.sn_w[s] - c0);
+          double M = m - c0 - bw;
+          stp.potrf_flops += bw * bw * bw / 3.0;
+          stp.trsm_flops += M * bw * bw;
+          stp.upd_flops += 2.0 * bw * M * (M + 1.0) / 2.0;
+        }
         lv.steps.push_back(stp);
       }
     }

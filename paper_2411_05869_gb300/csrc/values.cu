@@ -167,6 +167,7 @@ void values_run(gp_ctx* ctx, gp_factor_t* f) {
     GP_CHECK_LAUNCH(ctx);
   }
   GP_CUDA(cudaMemsetAsync(f->panels, 0, sizeof(double) * (size_t)f->B * ps->sp.panel_entries, ctx->stream));
+  ProfScope ps_(ctx, KC_VALUES);
   k_values<<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, n, ps->d, ps->U, ps->X,
                                                           f->theta_dev, f->theta_stride, f->B, h0.n1, f->F,
                                                           ps->dest, ps->nnz, ps->sp.panel_entries, f->val,

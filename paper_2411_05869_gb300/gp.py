@@ -45,7 +45,9 @@ class FactorInfo(ctypes.Structure):
 
 SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_pointset_free", "gp_pointset_info",
            "gp_pointset_export", "gp_factor", "gp_factor_update", "gp_factor_free", "gp_factor_info", "gp_loglik",
-           "gp_predict", "gp_launch_count"]
+           "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read"]
+KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
+          "predict": 7}
 
 _lib = None
 
@@ -92,6 +94,10 @@ def load(build_if_missing: bool = True):
     L.gp_predict.argtypes = [P, P, c_int, P, c_i64, P, P]
     L.gp_launch_count.restype = c_i64
     L.gp_launch_count.argtypes = [P]
+    L.gp_profile.restype = c_int
+    L.gp_profile.argtypes = [P, c_int]
+    L.gp_profile_read.restype = c_int
+    L.gp_profile_read.argtypes = [P, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]
     _lib = L
     return L
 
@@ -150,6 +156,19 @@ class Context:
 
     def launches(self) -> int:
         return int(self.lib.gp_launch_count(self.h))
+
+    def profile(self, enable: bool):
+        """Start (clearing counters) or stop the per-kernel-class launch profiler."""
+        self.check(self.lib.gp_profile(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        """{class: (total ms, launches, useful flops)} accumulated since profile(True)."""
+        out = {}
+        for name, k in KCLASS.items():
+            ms, n, fl = c_dbl(), c_i64(), c_dbl()
+            self.check(self.lib.gp_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+            out[name] = (ms.value, n.value, fl.value)
+        return out
 
     def assemble(self, X, core_radius) -> "PointSet":
         """Steps A1, A2, A5, A6 for a CUDA float64 tensor X (n x d)."""
