@@ -285,7 +285,13 @@ __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
 
 }  // namespace
 
+void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f);
+
 void factor_run(gp_ctx* ctx, gp_factor_t* f) {
+  if (f->prec == GP_MIXED) {
+    factor_run_mixed(ctx, f);
+    return;
+  }
   gp_pointset* ps = f->ps;
   const SymPlan& sp = ps->sp;
   const DevPlan& dp = ps->dp;

@@ -1,0 +1,417 @@
+// factor_mixed.cu -- step A7 in mixed precision (GP_MIXED): the multifrontal supernodal Cholesky of
+// P C_z P^T with the off-diagonal supernode updates on TF32 tensor cores (tcgen05, FP32 accumulation in
+// tensor memory) and every diagonal 64 x 64 block kept, updated and factored in FP64.
+//
+// Storage per proposal: FP32 panels row-major (row i of supernode s at loff32 + i * ldw, K = column index
+// contiguous, as the tensor-core operands want), FP64 diagonal tiles (tile t of s at doff + t * 4096, row-major
+// 64 x 64), FP32 update matrices (row-major r x r). Entries (i, j) of a front with i, j < w in the same 64-block
+// live in the FP64 tile, every other panel entry in FP32.
+// Per level: zero the update matrices, extend-add the children (FP32 sums into the parent's FP32 entries and
+// FP64 tiles), factor fronts of order <= 96 wholly in FP64 shared memory, and step the large fronts 64 columns
+// at a time: POTRF of the FP64 diagonal tile, TRSM of the rows below in FP32 (result rounded to nearest TF32,
+// so the tensor cores, which read the top 19 bits, see unbiased operands), then the trailing update
+// F[i, j] -= sum_l L[i, l] L[j, l] over 128 x 128 tiles on the tensor cores with FP64 accumulation into the
+// diagonal tiles.
+#include <climits>
+
+#include "gp_internal.cuh"
+#include "tc_gemm.cuh"
+
+void values_run_mixed(gp_ctx* ctx, gp_factor_t* f);
+
+namespace {
+
+constexpr int T = GP_TILE;
+
+struct MixFront {
+  int32_t w, r, ldw;
+  int64_t m;
+  float* P;     // FP32 panel (m x ldw)
+  double* D;    // FP64 diagonal tiles
+  float* Uu;    // FP32 update matrix (r x r)
+};
+
+__device__ __forceinline__ MixFront mix_front(const DevPlan& dp, int32_t s, float* p32, double* dg, float* u32) {
+  MixFront fr;
+  fr.w = dp.w[s];
+  fr.r = dp.r[s];
+  fr.ldw = dp.ldw[s];
+  fr.m = (int64_t)fr.w + fr.r;
+  fr.P = p32 + dp.loff32[s];
+  fr.D = dg + dp.doff[s];
+  fr.Uu = u32 + dp.uoff[s];
+  return fr;
+}
+
+__device__ __forceinline__ bool in_diag(const MixFront& fr, int64_t i, int64_t j) {
+  return i < fr.w && (i >> 6) == (j >> 6);
+}
+__device__ __forceinline__ double* diag_at(const MixFront& fr, int64_t i, int64_t j) {
+  return fr.D + (i >> 6) * (T * T) + (i & 63) * T + (j & 63);
+}
+__device__ __forceinline__ double mix_get(const MixFront& fr, int64_t i, int64_t j) {
+  if (j < fr.w) return in_diag(fr, i, j) ? *diag_at(fr, i, j) : (double)fr.P[i * fr.ldw + j];
+  return (double)fr.Uu[(i - fr.w) * fr.r + (j - fr.w)];
+}
+__device__ __forceinline__ void mix_set(const MixFront& fr, int64_t i, int64_t j, double v) {
+  if (j < fr.w) {
+    if (in_diag(fr, i, j)) *diag_at(fr, i, j) = v;
+    else fr.P[i * fr.ldw + j] = (float)v;
+  } else {
+    fr.Uu[(i - fr.w) * fr.r + (j - fr.w)] = (float)v;
+  }
+}
+__device__ __forceinline__ void mix_add(const MixFront& fr, int64_t i, int64_t j, float v) {
+  if (j < fr.w) {
+    if (in_diag(fr, i, j)) *diag_at(fr, i, j) += (double)v;
+    else fr.P[i * fr.ldw + j] += v;
+  } else {
+    fr.Uu[(i - fr.w) * fr.r + (j - fr.w)] += v;
+  }
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ double checked_sqrt(double d, int32_t* notpd, int32_t col) {
+  if (!(d > 0.0)) {
+    atomicMin(notpd, col);
+    return 1.0;
+  }
+  return sqrt(d);
+}
+
+__global__ void k_zero_updates32(const int32_t* __restrict__ list, DevPlan dp, float* __restrict__ upd, int64_t UE) {
+  int32_t s = list[blockIdx.x];
+  float* U = upd + (int64_t)blockIdx.z * UE + dp.uoff[s];
+  int64_t cnt = (int64_t)dp.r[s] * dp.r[s];
+  for (int64_t t = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.y * blockDim.x)
+    U[t] = 0.f;
+}
+
+// One CTA per (child, 8 rows of its update matrix): row a of U_child, columns b <= a, into the parent front.
+__global__ void k_extend_add32(const int2* __restrict__ tab, DevPlan dp, float* __restrict__ p32,
+                               double* __restrict__ dg, float* __restrict__ u32, int64_t P32E, int64_t DE,
+                               int64_t UE) {
+  int2 task = tab[blockIdx.x];
+  int32_t c = task.x, a0 = task.y;
+  int b = blockIdx.y;
+  float* pp = p32 + (int64_t)b * P32E;
+  double* pd = dg + (int64_t)b * DE;
+  float* pu = u32 + (int64_t)b * UE;
+  int32_t p = dp.sn_parent[c];
+  int32_t rc = dp.r[c];
+  const float* Uc = pu + dp.uoff[c];
+  const int32_t* rel = dp.relidx + dp.relidx_off[c];
+  MixFront fp = mix_front(dp, p, pp, pd, pu);
+  int32_t a1 = min(a0 + 8, rc);
+  for (int32_t a = a0; a < a1; a++) {
+    int32_t tr = rel[a];
+    for (int32_t bc = threadIdx.x; bc <= a; bc += blockDim.x) mix_add(fp, tr, rel[bc], Uc[(int64_t)a * rc + bc]);
+  }
+}
+
+// Fronts of order <= GP_SMALL_M: the whole partial factorization in FP64 shared memory.
+__global__ void k_small_front32(const int32_t* __restrict__ list, DevPlan dp, float* __restrict__ p32,
+                                double* __restrict__ dg, float* __restrict__ u32, int64_t P32E, int64_t DE,
+                                int64_t UE, int32_t* __restrict__ notpd) {
+  extern __shared__ double A[];
+  int32_t s = list[blockIdx.x];
+  int b = blockIdx.y;
+  MixFront fr = mix_front(dp, s, p32 + (int64_t)b * P32E, dg + (int64_t)b * DE, u32 + (int64_t)b * UE);
+  const int m = (int)fr.m, w = fr.w;
+  const int32_t first = dp.sn_first[s];
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t % m, j = t / m;
+    if (i >= j) A[t] = mix_get(fr, i, j);
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int k = 0; k < w; k++) {
+    if (threadIdx.x == 0) {
+      piv = checked_sqrt(A[k * m + k], notpd + b, first + k);
+      A[k * m + k] = piv;
+    }
+    __syncthreads();
+    double inv = 1.0 / piv;
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * m + i] *= inv;
+    __syncthreads();
+    int S = m - k - 1;
+    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
+      int i = k + 1 + t % S, j = k + 1 + t / S;
+      if (i >= j) A[j * m + i] -= A[k * m + i] * A[k * m + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t % m, j = t / m;
+    if (i >= j) mix_set(fr, i, j, A[t]);
+  }
+}
+
+__device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_t t) {
+  int lo = 0, hi = nfront - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP64 POTRF of diagonal tile kb.
+__global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp, double* __restrict__ dg, int64_t DE,
+                          int32_t* __restrict__ notpd) {
+  __shared__ double A[T * T];
+  __shared__ double piv;
+  int32_t s = fronts[blockIdx.x];
+  int b = blockIdx.y;
+  double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const int w = dp.w[s], bw = min(T, w - kb * T);
+  const int32_t first = dp.sn_first[s] + kb * T;
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) A[t] = D[t];   // [i][j] row-major
+  __syncthreads();
+  for (int k = 0; k < bw; k++) {
+    if (threadIdx.x == 0) {
+      piv = checked_sqrt(A[k * T + k], notpd + b, first + k);
+      A[k * T + k] = piv;
+    }
+    __syncthreads();
+    double inv = 1.0 / piv;
+    for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[i * T + k] *= inv;
+    __syncthreads();
+    int S = bw - k - 1;
+    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
+      int i = k + 1 + t / S, j = k + 1 + t % S;
+      if (i >= j) A[i * T + j] -= A[i * T + k] * A[j * T + k];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) D[t] = A[t];
+}
+
+// FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile); outputs rounded to TF32.
+__global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
+                         DevPlan dp, float* __restrict__ p32, const double* __restrict__ dg, int64_t P32E,
+                         int64_t DE) {
+  __shared__ float L[T * (T + 1)];
+  __shared__ float X[T * (T + 1)];   // X[row][col]
+  int64_t t = blockIdx.x;
+  int fi = find_front(pre, nfront, t);
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  float* P = p32 + (int64_t)b * P32E + dp.loff32[s];
+  const double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const int w = dp.w[s], ldw = dp.ldw[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
+  const int64_t r0 = c1 + (t - pre[fi]) * T;
+  const int nr = (int)imin64(T, m - r0);
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+    int i = q / T, j = q % T;
+    L[i * (T + 1) + j] = (i < bw && j <= i) ? (float)D[i * T + j] : 0.f;
+    X[i * (T + 1) + j] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
+  }
+  __syncthreads();
+  // X <- X L^{-T}: column j of X = (X[:, j] - sum_{l<j} X[:, l] L[j, l]) / L[j, j], row-parallel
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    if (i >= nr) continue;
+    for (int j = 0; j < bw; j++) {
+      float acc = X[i * (T + 1) + j];
+      for (int l = 0; l < j; l++) acc -= X[i * (T + 1) + l] * L[j * (T + 1) + l];
+      X[i * (T + 1) + j] = acc / L[j * (T + 1) + j];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+    int i = q / T, j = q % T;
+    if (i < nr && j < bw) P[(r0 + i) * ldw + c0 + j] = tf32_rn(X[i * (T + 1) + j]);
+  }
+}
+
+// Trailing update of block column kb on the tensor cores: one CTA per 128 x 128 lower-triangular tile
+// (I >= J) of the rows/columns after the block column; K = the block column's width.
+__global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                   int nfront, int kb, DevPlan dp, float* __restrict__ p32,
+                                                   double* __restrict__ dg, float* __restrict__ u32, int64_t P32E,
+                                                   int64_t DE, int64_t UE, int32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * tcg::STAGE_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * tcg::STAGE_BYTES + 64);
+  __shared__ const float* arows[128];
+  __shared__ const float* brows[128];
+  int64_t t = blockIdx.x;
+  int fi = find_front(pre, nfront, t);
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  MixFront fr = mix_front(dp, s, p32 + (int64_t)b * P32E, dg + (int64_t)b * DE, u32 + (int64_t)b * UE);
+  const int c0 = kb * T, bw = min(T, fr.w - c0), c1 = c0 + bw;
+  int64_t loc = t - pre[fi];
+  int64_t I = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
+  while ((I + 1) * (I + 2) / 2 <= loc) I++;
+  while (I * (I + 1) / 2 > loc) I--;
+  int64_t J = loc - I * (I + 1) / 2;
+  const int64_t i0 = c1 + I * 128, j0 = c1 + J * 128;
+  {
+    int q = threadIdx.x;
+    int64_t ia = i0 + q, jb = j0 + q;
+    arows[q] = ia < fr.m ? fr.P + ia * fr.ldw + c0 : nullptr;
+    brows[q] = jb < fr.m ? fr.P + jb * fr.ldw + c0 : nullptr;
+  }
+  if (threadIdx.x == 0) {
+    tcg::mbar_init(&bars[0], 1);
+    tcg::mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (threadIdx.x < 32) tcg::tmem_alloc(tslot, 128);
+  tcg::tc_fence_before();
+  __syncthreads();
+  tcg::tc_fence_after();
+  const uint32_t tmem = *tslot;
+  bool ok = tcg::tile_mma(smem, arows, brows, bw, fr.P, tmem);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = i0 + warp * 32 + lane;
+  if (ok) {
+    for (int cc = 0; cc < 128; cc += 32) {
+      float v[32];
+      tcg::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+      if (i < fr.m) {
+#pragma unroll 4
+        for (int q = 0; q < 32; q++) {
+          int64_t j = j0 + cc + q;
+          if (j <= i && j < fr.m) mix_add(fr, i, j, -v[q]);
+        }
+      }
+    }
+  }
+  tcg::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tcg::tmem_dealloc(tmem, 128);
+}
+
+bool g_attrs = false;
+void set_attrs() {
+  if (g_attrs) return;
+  GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
+  GP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES + 1024));
+  g_attrs = true;
+}
+
+__global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// dest32[e]: FP32 panel offset (row-major) or DIAG_FLAG | diagonal-tile offset for lower entries, else -1.
+__global__ void k_dest32(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
+                         const int32_t* __restrict__ pinv, DevPlan dp, int64_t* __restrict__ dest) {
+  int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int32_t pi = pinv[i];
+  for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+    int32_t pj = pinv[col[e]];
+    if (pi < pj) {
+      dest[e] = -1;
+      continue;
+    }
+    int32_t s = dp.sn_of_col[pj];
+    int32_t f = dp.sn_first[s], w = dp.w[s], r = dp.r[s];
+    int64_t lr;
+    if (pi < f + w) {
+      lr = pi - f;
+    } else {
+      const int32_t* R = dp.frows + dp.frow_off[s] + w;
+      int lo = 0, hi = r;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (R[mid] < pi) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo == r || R[lo] != pi) {
+        dest[e] = -1;
+        continue;
+      }
+      lr = w + lo;
+    }
+    int64_t lc = pj - f;
+    if (lr < w && (lr >> 6) == (lc >> 6))
+      dest[e] = DIAG_FLAG | (dp.doff[s] + (lr >> 6) * (T * T) + (lr & 63) * T + (lc & 63));
+    else
+      dest[e] = dp.loff32[s] + lr * dp.ldw[s] + lc;
+  }
+}
+
+}  // namespace
+
+void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps) {
+  ps->dest32 = dalloc<int64_t>(ctx, ps->bufs, ps->nnz);
+  k_dest32<<<grid_for(ps->n * 32, 256), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, ps->n, ps->pinv, ps->dp,
+                                                               ps->dest32);
+  GP_CHECK_LAUNCH(ctx);
+}
+
+void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
+  gp_pointset* ps = f->ps;
+  const SymPlan& sp = ps->sp;
+  const DevPlan& dp = ps->dp;
+  cudaStream_t st = ctx->stream;
+  set_attrs();
+  const int B = f->B;
+  const int64_t P32E = sp.panel32_entries, DE = sp.diag_entries, UE = sp.update_entries;
+  values_run_mixed(ctx, f);   // A3, A4 into the FP32 panels and FP64 tiles (zeroed first)
+  k_fill_i32<<<grid_for(B, 128), 128, 0, st>>>(f->notpd, B, INT_MAX);
+  GP_CHECK_LAUNCH(ctx);
+  GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), st));
+  for (int32_t L = 0; L < sp.nlevels; L++) {
+    const SymPlan::Level& lv = sp.levels[L];
+    int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
+    k_zero_updates32<<<dim3(nl, 8, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd32, UE);
+    GP_CHECK_LAUNCH(ctx);
+    for (const auto& ea : lv.ea) {
+      ProfScope ps_(ctx, KC_EXTEND_ADD);
+      k_extend_add32<<<dim3((unsigned)ea.ncta, B), 128, 0, st>>>(dp.ea_tab + ea.tab_off, dp, f->panels32, f->diag,
+                                                                 f->upd32, P32E, DE, UE);
+      GP_CHECK_LAUNCH(ctx);
+    }
+    if (lv.nsmall > 0) {
+      int32_t mmax = 1;
+      for (int32_t q = 0; q < lv.nsmall; q++) {
+        int32_t s = sp.small_list[lv.small_off + q];
+        mmax = std::max(mmax, sp.sn_w[s] + sp.sn_r[s]);
+      }
+      ProfScope ps_(ctx, KC_FRONT_SMALL);
+      k_small_front32<<<dim3(lv.nsmall, B), 256, (size_t)mmax * mmax * sizeof(double), st>>>(
+          dp.small_list + lv.small_off, dp, f->panels32, f->diag, f->upd32, P32E, DE, UE, f->notpd);
+      GP_CHECK_LAUNCH(ctx);
+    }
+    for (const auto& stp : lv.steps) {
+      const int32_t* fronts = dp.large_fronts + stp.fr_off;
+      const int64_t* pre_tr = dp.step_pre + stp.pre_off;
+      const int64_t* pre128 = dp.step_pre128 + stp.pre128_off;
+      {
+        ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
+        k_potrf64<<<dim3(stp.nfront, B), 128, 0, st>>>(fronts, stp.kb, dp, f->diag, DE, f->notpd);
+        GP_CHECK_LAUNCH(ctx);
+      }
+      if (stp.trsm_total > 0) {
+        ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
+        k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 64, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
+                                                                   f->panels32, f->diag, P32E, DE);
+        GP_CHECK_LAUNCH(ctx);
+      }
+      if (stp.upd128_total > 0) {
+        ProfScope ps_(ctx, KC_UPDATE, B * stp.upd_flops);
+        k_update_tc<<<dim3((unsigned)stp.upd128_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
+            fronts, pre128, stp.nfront, stp.kb, dp, f->panels32, f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
+        GP_CHECK_LAUNCH(ctx);
+      }
+    }
+  }
+}

@@ -224,6 +224,10 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     dp.step_pre = upload(ctx, ps->bufs, sp.step_pre);
     dp.lev_sn = upload(ctx, ps->bufs, sp.lev_sn);
     dp.sn_parent = upload(ctx, ps->bufs, sp.sn_parent);
+    dp.ldw = upload(ctx, ps->bufs, sp.sn_ldw);
+    dp.loff32 = upload(ctx, ps->bufs, sp.sn_loff32);
+    dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
+    dp.step_pre128 = upload(ctx, ps->bufs, sp.step_pre128);
     compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });
@@ -316,15 +320,24 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     GP_REQUIRE(td.n1 >= 0 && td.n1 <= GP_MAX_N1, "n1 must be in 0..32");
     f->theta_dev = dalloc<double>(ctx, f->bufs, (size_t)theta_stride_of(td) * B);
     f->F = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * td.n1 + 1);
-    f->panels = dalloc<double>(ctx, f->bufs, (size_t)B * sp.panel_entries);
-    f->upd = dalloc<double>(ctx, f->bufs, (size_t)B * sp.update_entries);
+    if (prec == GP_FP64) {
+      f->panels = dalloc<double>(ctx, f->bufs, (size_t)B * sp.panel_entries);
+      f->upd = dalloc<double>(ctx, f->bufs, (size_t)B * sp.update_entries);
+    } else {
+      if (!ps->dest32) compute_dest_map_mixed(ctx, ps);
+      f->panels32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
+      f->diag = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
+      f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
+      f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
+      f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
+    }
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
     f->notpd = dalloc<int32_t>(ctx, f->bufs, B);
     f->alpha = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
     f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
     f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);
     f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
-    f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride);
+    f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride + 4 * (size_t)B + 8);
     pack_thetas(f, thetas);
     factor_run(ctx, f);
   });

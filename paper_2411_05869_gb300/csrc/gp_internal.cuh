@@ -143,10 +143,17 @@ struct SymPlan {
   int64_t vec_update_entries = 0;    // sum of r over supernodes (solve update vectors)
   double flops = 0.0;
   int32_t max_front = 0;
+  // mixed-precision layout: FP32 panels row-major (m x ldw, ldw = w rounded up to 4, 16-byte aligned rows),
+  // FP64 64 x 64 diagonal tiles (row-major), FP32 update matrices (row-major r x r)
+  std::vector<int32_t> sn_ldw;
+  std::vector<int64_t> sn_loff32, sn_doff;
+  int64_t panel32_entries = 0, diag_entries = 0;
+  std::vector<int64_t> step_pre128;  // per step: prefix of 128 x 128 update tiles (nfront + 1 entries)
 
   // schedule for the numeric factorization, per level
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
   struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
+                      int64_t pre128_off; int64_t upd128_total;
                       double potrf_flops, trsm_flops, upd_flops; };   // useful flops of the step's launches
   struct Level {
     std::vector<EaLaunch> ea;        // one per child slot
@@ -176,6 +183,9 @@ struct DevPlan {
   int64_t* step_pre;
   int32_t* lev_sn;
   int32_t* sn_parent;
+  int32_t* ldw;
+  int64_t *loff32, *doff;
+  int64_t* step_pre128;
 };
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
@@ -201,6 +211,7 @@ struct gp_pointset {
   int32_t* perm = nullptr;      // new -> old
   int32_t* pinv = nullptr;      // old -> new
   int64_t* dest = nullptr;      // per CSR entry: panel offset of its lower-triangle copy, or -1
+  int64_t* dest32 = nullptr;    // mixed layout: FP32 panel offset, or DIAG_FLAG | diagonal-tile offset, or -1
   SymPlan sp;
   DevPlan dp{};
 };
@@ -216,7 +227,10 @@ struct gp_factor_s {
   double* F = nullptr;          // B x n x n1 bump features
   int n1max = 0;
   double* panels = nullptr;     // FP64 panels, B x panel_entries
-  float* panels32 = nullptr;    // GP_MIXED: FP32 panels (off-diagonal rows), B x panel_entries
+  float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
+  double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
+  double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n
+  int32_t* tiles_err = nullptr; // GP_MIXED: set when a bounded tensor-core wait ran out
   double* upd = nullptr;        // B x update_entries
   float* upd32 = nullptr;
   double* val = nullptr;        // B x nnz CSR values of C_z (refinement SpMV)
@@ -260,6 +274,8 @@ void factor_run(gp_ctx* ctx, gp_factor_t* f);
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err);
 void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, const double* d_mu, double* d_mean);
 void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
+void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
+#define DIAG_FLAG ((int64_t)1 << 62)
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 

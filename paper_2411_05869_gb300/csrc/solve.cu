@@ -1,15 +1,20 @@
-// solve.cu -- steps A8-A10 (and the FP64 residual of A11): supernodal forward and backward solves with the
-// multifrontal factor, the quadratic form, the log-determinant and the log-likelihood
+// solve.cu -- steps A8-A11: supernodal forward and backward solves with the multifrontal factor, the
+// quadratic form, the log-determinant, FP64 iterative refinement (mixed precision) and the log-likelihood
 //   log p(z | beta, theta) = -1/2 log det C_z - 1/2 r^T C_z^{-1} r - n/2 log(2 pi)      (Sec. 3.3)
-// with log det C_z = 2 sum_j log L_jj and r^T C_z^{-1} r = |L^{-1} P r|^2.
+// with log det C_z = 2 sum_j log L_jj.
 //
 // Forward (levels ascending): the front vector of supernode s (m entries, own columns then the rows below)
 // starts as the permuted right-hand side on its columns, receives every child's update vector through the
 // child's relative indices (children in order), then x = L11^{-1} f_1 and f_2 -= L21 x; f_2 is the update
 // vector handed to the parent. Backward (levels descending): t = x - L21^T alpha'(rows below), then
 // L11^T z = t. Fronts of order <= 96 use one CTA; larger ones advance 64 columns per launch, every CTA
-// re-solving the 64 x 64 diagonal block from L2 and applying it to its own 64-row (or 64-column) tile.
-// Sums (log-det, quadratic form, residual norms) use fixed-shape trees, so results are bitwise reproducible.
+// re-solving the 64 x 64 diagonal block and applying it to its own 64-row (or 64-column) tile.
+// The kernels read the factor through an accessor: FP64 column-major panels (GP_FP64) or FP32 row-major
+// panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the quadratic form is |L^{-1} P r|^2; in GP_MIXED
+// alpha is refined in FP64 (residual r - C alpha from the FP64 CSR values, correction through the same
+// factor) until |r - C alpha| / |r| <= 1e-12 or 10 sweeps, and the quadratic form is r^T alpha.
+// Sums use fixed-shape trees, so results are bitwise reproducible.
+#include <algorithm>
 #include <cmath>
 
 #include "gp_internal.cuh"
@@ -18,13 +23,46 @@ namespace {
 
 constexpr int T = GP_TILE;
 
-__global__ void k_rhs(const double* __restrict__ resid, const int32_t* __restrict__ perm, int64_t n,
-                      DevPlan dp, double* __restrict__ work, int64_t ws) {
+// ---------------------------------------------------------------------------------------- factor access
+struct AccF64 {
+  const double* P;
+  int64_t m;
+  __device__ __forceinline__ double L(int64_t i, int64_t j) const { return P[j * m + i]; }
+};
+struct AccMix {
+  const float* P;
+  const double* D;
+  int w, ldw;
+  __device__ __forceinline__ double L(int64_t i, int64_t j) const {
+    if (i < w && (i >> 6) == (j >> 6)) return D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)];
+    return (double)P[i * ldw + j];
+  }
+};
+struct StoreF64 {
+  const double* P;
+  int64_t PE;
+  using Acc = AccF64;
+  __device__ __forceinline__ AccF64 acc(const DevPlan& dp, int32_t s, int b) const {
+    return AccF64{P + (int64_t)b * PE + dp.loff[s], (int64_t)dp.w[s] + dp.r[s]};
+  }
+};
+struct StoreMix {
+  const float* P;
+  const double* D;
+  int64_t P32E, DE;
+  using Acc = AccMix;
+  __device__ __forceinline__ AccMix acc(const DevPlan& dp, int32_t s, int b) const {
+    return AccMix{P + (int64_t)b * P32E + dp.loff32[s], D + (int64_t)b * DE + dp.doff[s], dp.w[s], dp.ldw[s]};
+  }
+};
+
+__global__ void k_rhs(const double* __restrict__ rhs, const int32_t* __restrict__ perm, int64_t n, DevPlan dp,
+                      double* __restrict__ work, int64_t ws) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (j >= n) return;
   int32_t s = dp.sn_of_col[j];
-  work[(int64_t)b * ws + dp.frow_off[s] + (j - dp.sn_first[s])] = resid[(int64_t)b * n + perm[j]];
+  work[(int64_t)b * ws + dp.frow_off[s] + (j - dp.sn_first[s])] = rhs[(int64_t)b * n + perm[j]];
 }
 
 // Children's update vectors into the front vector of each supernode of the list.
@@ -42,25 +80,26 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ list, DevPlan dp, doubl
 }
 
 // Forward elimination of a whole (small) front by one CTA.
-__global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, const double* __restrict__ panels,
-                            int64_t PE, double* __restrict__ work, int64_t ws, int64_t xv_off) {
+template <class St>
+__global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, St store, double* __restrict__ work,
+                            int64_t ws, int64_t xv_off) {
   __shared__ double xs;
   int32_t s = list[blockIdx.x];
   int b = blockIdx.y;
-  const double* P = panels + (int64_t)b * PE + dp.loff[s];
+  auto A = store.acc(dp, s, b);
   double* fv = work + (int64_t)b * ws + dp.frow_off[s];
   double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   for (int j = 0; j < w; j++) {
     if (threadIdx.x == 0) {
-      xs = fv[j] / P[(int64_t)j * m + j];
+      xs = fv[j] / A.L(j, j);
       fv[j] = xs;
       xv[j] = xs;
     }
     __syncthreads();
     double x = xs;
-    for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) fv[i] -= P[(int64_t)j * m + i] * x;
+    for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) fv[i] -= A.L(i, j) * x;
     __syncthreads();
   }
 }
@@ -102,12 +141,12 @@ __device__ __forceinline__ void block_upper_solve(const double* L, double* t, in
   __syncthreads();
 }
 
-// One block column kb of the forward solve for every large front of a step. Tasks: [0, nfront) write the
-// block's solution to x (a separate vector, since the other tasks still read the block's right-hand side);
-// the rest (from the tile prefix) update one 64-row tile below the block.
+// One block column kb of the forward solve for every large front of a step. Tasks [0, nfront) write the
+// block's solution to x (a separate vector: the other tasks still read the block's right-hand side); the
+// rest (from the 64-row tile prefix) update one 64-row tile below the block.
+template <class St>
 __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                           DevPlan dp, const double* __restrict__ panels, int64_t PE, double* __restrict__ work,
-                           int64_t ws, int64_t xv_off) {
+                           DevPlan dp, St store, double* __restrict__ work, int64_t ws, int64_t xv_off) {
   __shared__ double L[T * T];
   __shared__ double x[T];
   int64_t t = blockIdx.x;
@@ -115,14 +154,14 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
   int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
   int32_t s = fronts[fi];
   int b = blockIdx.y;
-  const double* P = panels + (int64_t)b * PE + dp.loff[s];
+  auto A = store.acc(dp, s, b);
   double* fv = work + (int64_t)b * ws + dp.frow_off[s];
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
   for (int q = threadIdx.x; q < bw * bw; q += blockDim.x) {
     int i = q % bw, j = q / bw;
-    L[j * T + i] = i >= j ? P[(int64_t)(c0 + j) * m + c0 + i] : 0.0;
+    L[j * T + i] = i >= j ? A.L(c0 + i, c0 + j) : 0.0;
   }
   for (int q = threadIdx.x; q < bw; q += blockDim.x) x[q] = fv[c0 + q];
   __syncthreads();
@@ -135,30 +174,29 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
   int64_t r0 = c1 + (t - nfront - pre[fi]) * T;
   for (int64_t i = r0 + threadIdx.x; i < imin64(r0 + T, m); i += blockDim.x) {
     double acc = 0.0;
-    for (int l = 0; l < bw; l++) acc += P[(int64_t)(c0 + l) * m + i] * x[l];
+    for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
     fv[i] -= acc;
   }
 }
 
 // t_j = x_j - sum_{a < r} L[w + a, j] alpha'(R_s[a]) for every column j of the front (warp per column);
 // small fronts then finish L11^T z = t in the same CTA and write alpha'.
-__global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, DevPlan dp,
-                           const double* __restrict__ panels, int64_t PE, double* __restrict__ work, int64_t ws,
-                           int64_t apv_off, int64_t xv_off) {
+template <class St>
+__global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, DevPlan dp, St store,
+                           double* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
   __shared__ double zs;
   int32_t s = list[blockIdx.x];
   int b = blockIdx.y;
-  const double* P = panels + (int64_t)b * PE + dp.loff[s];
+  auto A = store.acc(dp, s, b);
   double* W = work + (int64_t)b * ws;
   double* fv = W + dp.frow_off[s];
   double* apv = W + apv_off;
   const int w = dp.w[s], r = dp.r[s];
-  const int64_t m = (int64_t)w + r;
   const int32_t* R = dp.frows + dp.frow_off[s] + w;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = warp; j < w; j += nw) {
     double acc = 0.0;
-    for (int a = lane; a < r; a += 32) acc += P[(int64_t)j * m + w + a] * apv[R[a]];
+    for (int a = lane; a < r; a += 32) acc += A.L(w + a, j) * apv[R[a]];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) fv[j] = W[xv_off + dp.sn_first[s] + j] - acc;
   }
@@ -167,23 +205,23 @@ __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, De
   const int32_t first = dp.sn_first[s];
   for (int j = w - 1; j >= 0; j--) {
     if (threadIdx.x == 0) {
-      zs = fv[j] / P[(int64_t)j * m + j];
+      zs = fv[j] / A.L(j, j);
       fv[j] = zs;
       apv[first + j] = zs;
     }
     __syncthreads();
     double z = zs;
-    for (int k = threadIdx.x; k < j; k += blockDim.x) fv[k] -= P[(int64_t)k * m + j] * z;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) fv[k] -= A.L(j, k) * z;
     __syncthreads();
   }
 }
 
 // One block column kb of the backward solve for every large front of a step. Tasks per front: one writer
 // (z of the block into alpha') and kb column tiles of the earlier columns (t_k -= L[J, k]^T z_J).
-__global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp,
-                           const double* __restrict__ panels, int64_t PE, double* __restrict__ work, int64_t ws,
-                           int64_t apv_off) {
-  __shared__ double L[T * (T + 1)];   // the diagonal block, then (reused) the tile's rows of the block
+template <class St>
+__global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
+                           double* __restrict__ work, int64_t ws, int64_t apv_off) {
+  __shared__ double L[T * (T + 1)];   // the diagonal block, then (reused) the block's rows for the tile
   __shared__ double z[T];
   double* Lt = L;
   int64_t t = blockIdx.x;
@@ -191,15 +229,14 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
   int task = (int)(t % (kb + 1));   // 0 = writer, 1..kb = column tile task-1
   int32_t s = fronts[fi];
   int b = blockIdx.y;
-  const double* P = panels + (int64_t)b * PE + dp.loff[s];
+  auto A = store.acc(dp, s, b);
   double* W = work + (int64_t)b * ws;
   double* fv = W + dp.frow_off[s];
   const int w = dp.w[s];
-  const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0);
   for (int q = threadIdx.x; q < bw * bw; q += blockDim.x) {
     int i = q % bw, j = q / bw;
-    L[j * T + i] = i >= j ? P[(int64_t)(c0 + j) * m + c0 + i] : 0.0;
+    L[j * T + i] = i >= j ? A.L(c0 + i, c0 + j) : 0.0;
   }
   for (int q = threadIdx.x; q < bw; q += blockDim.x) z[q] = fv[c0 + q];
   __syncthreads();
@@ -211,10 +248,9 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
     return;
   }
   const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
-  // Lt[l][k] = L[c0 + l, k0 + k]: the block's rows for the tile's columns (global reads coalesced by rows)
   for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {
     int l = q % bw, k = q / bw;
-    Lt[l * (T + 1) + k] = P[(int64_t)(k0 + k) * m + c0 + l];
+    Lt[l * (T + 1) + k] = A.L(c0 + l, k0 + k);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < T; k += blockDim.x) {
@@ -225,9 +261,9 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
 }
 
 // Per-block partial sums: log L_jj and x_j^2 (x = forward solution on own columns).
-__global__ void k_partials(int64_t n, DevPlan dp, const double* __restrict__ panels, int64_t PE,
-                           const double* __restrict__ work, int64_t ws, int64_t xv_off, double* __restrict__ red,
-                           int64_t rs, int nblk) {
+template <class St>
+__global__ void k_partials(int64_t n, DevPlan dp, St store, const double* __restrict__ work, int64_t ws,
+                           int64_t xv_off, double* __restrict__ red, int64_t rs, int nblk) {
   __shared__ double sa[1024], sb[1024];
   int b = blockIdx.y;
   int64_t j = (int64_t)blockIdx.x * 1024 + threadIdx.x;
@@ -235,8 +271,8 @@ __global__ void k_partials(int64_t n, DevPlan dp, const double* __restrict__ pan
   if (j < n) {
     int32_t s = dp.sn_of_col[j];
     int64_t jl = j - dp.sn_first[s];
-    int64_t m = (int64_t)dp.w[s] + dp.r[s];
-    la = log(panels[(int64_t)b * PE + dp.loff[s] + jl * m + jl]);
+    auto A = store.acc(dp, s, b);
+    la = log(A.L(jl, jl));
     double x = work[(int64_t)b * ws + xv_off + j];
     lb = x * x;
   }
@@ -256,9 +292,8 @@ __global__ void k_partials(int64_t n, DevPlan dp, const double* __restrict__ pan
   }
 }
 
-// Fixed-order reduction of the partials and the log-likelihood of each proposal.
-__global__ void k_loglik(int64_t n, const double* __restrict__ red, int64_t rs, int nblk,
-                         const int32_t* __restrict__ notpd, double* __restrict__ out, double* __restrict__ stats) {
+// Fixed-order sum of nblk partials (two series a, b) per proposal.
+__global__ void k_sum2(const double* __restrict__ red, int64_t rs, int nblk, double* __restrict__ out) {
   __shared__ double sa[256], sb[256];
   int b = blockIdx.x;
   double ta = 0.0, tb = 0.0;
@@ -279,15 +314,22 @@ __global__ void k_loglik(int64_t n, const double* __restrict__ red, int64_t rs, 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double logdet = 2.0 * ta;
-    double ll = -0.5 * logdet - 0.5 * tb - 0.5 * (double)n * log(2.0 * 3.14159265358979323846);
-    if (notpd[b] != 0x7fffffff) ll = -INFINITY;
-    out[b] = ll;
-    if (stats) {
-      stats[2 * b] = logdet;
-      stats[2 * b + 1] = tb;
-    }
+    out[2 * b] = ta;
+    out[2 * b + 1] = tb;
   }
+}
+
+__global__ void k_finish(int B, int64_t n, const double* __restrict__ s_logdet, const double* __restrict__ s_quad,
+                         const int32_t* __restrict__ notpd, const int32_t* __restrict__ tc_err,
+                         double* __restrict__ out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double logdet = 2.0 * s_logdet[2 * b];
+  double quad = s_quad[2 * b + 1];
+  double ll = -0.5 * logdet - 0.5 * quad - 0.5 * (double)n * log(2.0 * 3.14159265358979323846);
+  if (notpd[b] != 0x7fffffff) ll = -INFINITY;
+  if (tc_err && *tc_err) ll = NAN;
+  out[b] = ll;
 }
 
 __global__ void k_alpha(const double* __restrict__ work, int64_t ws, int64_t apv_off, const int32_t* __restrict__ perm,
@@ -297,83 +339,96 @@ __global__ void k_alpha(const double* __restrict__ work, int64_t ws, int64_t apv
   if (j < n) alpha[(int64_t)b * n + perm[j]] = work[(int64_t)b * ws + apv_off + j];
 }
 
-// res = r - C alpha (warp per CSR row, fixed lane order) and per-block sums of res^2 and r^2.
+// res = r - C alpha (warp per CSR row, fixed lane order) and per-block sums of res^2, r^2 and r . alpha.
 __global__ void k_residual(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
                            int64_t nnz, const double* __restrict__ val, const double* __restrict__ alpha,
                            const double* __restrict__ resid, double* __restrict__ res, double* __restrict__ red,
                            int64_t rs, int nblk) {
-  __shared__ double s1[8], s2[8];
+  __shared__ double s1[8], s2[8], s3[8];
   int b = blockIdx.y;
   int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
+  const double* a = alpha + (int64_t)b * n;
   if (i < n) {
     const double* v = val + (int64_t)b * nnz;
-    const double* a = alpha + (int64_t)b * n;
     for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) acc += v[e] * a[col[e]];
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  double rr = 0.0, ri = 0.0;
+  double rr = 0.0, ri = 0.0, ra = 0.0;
   if (i < n && lane == 0) {
     ri = resid[(int64_t)b * n + i];
     rr = ri - acc;
+    ra = ri * a[i];
     if (res) res[(int64_t)b * n + i] = rr;
   }
   if (lane == 0) {
     s1[warp] = rr * rr;
     s2[warp] = ri * ri;
+    s3[warp] = ra;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a1 = 0.0, a2 = 0.0;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int q = 0; q < 8; q++) {
       a1 += s1[q];
       a2 += s2[q];
+      a3 += s3[q];
     }
     red[(int64_t)b * rs + blockIdx.x] = a1;
     red[(int64_t)b * rs + nblk + blockIdx.x] = a2;
+    red[(int64_t)b * rs + 2 * nblk + blockIdx.x] = a3;
   }
 }
 
-__global__ void k_relres(const double* __restrict__ red, int64_t rs, int nblk, double* __restrict__ err) {
-  __shared__ double sa[256], sb[256];
+// Fixed-order reduction of the residual partials: err[b] = |res| / |r|, rdot[b] = r . alpha.
+__global__ void k_relres(const double* __restrict__ red, int64_t rs, int nblk, double* __restrict__ err,
+                         double* __restrict__ rdot) {
+  __shared__ double sa[256], sb[256], sc[256];
   int b = blockIdx.x;
-  double ta = 0.0, tb = 0.0;
+  double ta = 0.0, tb = 0.0, tc = 0.0;
   for (int base = 0; base < nblk; base += 256) {
     int i = base + threadIdx.x;
     sa[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + i] : 0.0;
     sb[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + nblk + i] : 0.0;
+    sc[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + 2 * nblk + i] : 0.0;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
       if (threadIdx.x < o) {
         sa[threadIdx.x] += sa[threadIdx.x + o];
         sb[threadIdx.x] += sb[threadIdx.x + o];
+        sc[threadIdx.x] += sc[threadIdx.x + o];
       }
       __syncthreads();
     }
     ta += sa[0];
     tb += sb[0];
+    tc += sc[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) err[b] = tb > 0.0 ? sqrt(ta / tb) : sqrt(ta);
+  if (threadIdx.x == 0) {
+    if (err) err[b] = tb > 0.0 ? sqrt(ta / tb) : sqrt(ta);
+    if (rdot) rdot[2 * b + 1] = tc;
+  }
 }
 
-}  // namespace
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) y[i] += x[i];
+}
 
-// Forward and backward solves for all B right-hand sides; alpha (original order) into f->alpha.
-// Returns nothing; the front vectors keep x for the quadratic form until the backward pass overwrites them,
-// so the partial sums are taken in between.
-void solve_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, bool partials) {
+template <class St>
+void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs, double* alpha_out, bool partials) {
   gp_pointset* ps = f->ps;
   const SymPlan& sp = ps->sp;
   const DevPlan& dp = ps->dp;
   cudaStream_t st = ctx->stream;
   const int B = f->B;
-  const int64_t n = ps->n, PE = sp.panel_entries, ws = f->work_stride;
+  const int64_t n = ps->n, ws = f->work_stride;
   const int64_t apv_off = sp.sn_frow[sp.ns];   // work layout: front vectors, alpha' (n), x (n)
   const int64_t xv_off = apv_off + n;
   GP_CUDA(cudaMemsetAsync(f->work, 0, sizeof(double) * (size_t)B * ws, st));
-  k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(d_resid, ps->perm, n, dp, f->work, ws);
+  k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(rhs, ps->perm, n, dp, f->work, ws);
   GP_CHECK_LAUNCH(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
@@ -383,71 +438,106 @@ void solve_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, bool partials
       GP_CHECK_LAUNCH(ctx);
     }
     if (lv.nsmall > 0) {
-      k_fwd_small<<<dim3(lv.nsmall, B), 128, 0, st>>>(dp.small_list + lv.small_off, dp, f->panels, PE, f->work, ws,
-                                                       xv_off);
+      k_fwd_small<St><<<dim3(lv.nsmall, B), 128, 0, st>>>(dp.small_list + lv.small_off, dp, store, f->work, ws,
+                                                          xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
     for (const auto& stp : lv.steps) {
       int64_t tasks = stp.nfront + stp.trsm_total;
-      k_fwd_step<<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off,
-                                                          stp.nfront, stp.kb, dp, f->panels, PE, f->work, ws, xv_off);
+      k_fwd_step<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off,
+                                                              dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp,
+                                                              store, f->work, ws, xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
   }
   if (partials) {
     int nblk = (int)((n + 1023) / 1024);
-    k_partials<<<dim3(nblk, B), 1024, 0, st>>>(n, dp, f->panels, PE, f->work, ws, xv_off, f->red, f->red_stride,
-                                                nblk);
+    k_partials<St><<<dim3(nblk, B), 1024, 0, st>>>(n, dp, store, f->work, ws, xv_off, f->red, f->red_stride, nblk);
     GP_CHECK_LAUNCH(ctx);
   }
   for (int32_t L = sp.nlevels - 1; L >= 0; L--) {
     const SymPlan::Level& lv = sp.levels[L];
     if (lv.nsmall > 0) {
-      k_bwd_prep<<<dim3(lv.nsmall, B), 256, 0, st>>>(dp.small_list + lv.small_off, 1, dp, f->panels, PE, f->work, ws,
-                                                      apv_off, xv_off);
+      k_bwd_prep<St><<<dim3(lv.nsmall, B), 256, 0, st>>>(dp.small_list + lv.small_off, 1, dp, store, f->work, ws,
+                                                         apv_off, xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
     if (!lv.steps.empty()) {
       const auto& s0 = lv.steps[0];
-      k_bwd_prep<<<dim3(s0.nfront, B), 256, 0, st>>>(dp.large_fronts + s0.fr_off, 0, dp, f->panels, PE, f->work, ws,
-                                                      apv_off, xv_off);
+      k_bwd_prep<St><<<dim3(s0.nfront, B), 256, 0, st>>>(dp.large_fronts + s0.fr_off, 0, dp, store, f->work, ws,
+                                                         apv_off, xv_off);
       GP_CHECK_LAUNCH(ctx);
       for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
         const auto& stp = lv.steps[q];
         int64_t tasks = (int64_t)stp.nfront * (stp.kb + 1);
-        k_bwd_step<<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp,
-                                                            f->panels, PE, f->work, ws, apv_off);
+        k_bwd_step<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp,
+                                                                store, f->work, ws, apv_off);
         GP_CHECK_LAUNCH(ctx);
       }
     }
   }
-  k_alpha<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(f->work, ws, apv_off, ps->perm, n, f->alpha);
+  k_alpha<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(f->work, ws, apv_off, ps->perm, n, alpha_out);
   GP_CHECK_LAUNCH(ctx);
 }
 
-void residual_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_res, double* d_err) {
+// Residual of alpha for right-hand sides rhs: res (nullable) = rhs - C alpha; err[b] = |res|/|rhs|;
+// rdot[2b+1] = rhs . alpha. Partials go to the workspace (free once alpha has been extracted).
+void residual_impl(gp_ctx* ctx, gp_factor_t* f, const double* rhs, const double* alpha, double* res, double* err,
+                   double* rdot) {
   gp_pointset* ps = f->ps;
   const int64_t n = ps->n;
   int nblk = (int)((n + 7) / 8);
-  // the partial buffer of the log-likelihood is sized for n/1024 blocks; residual partials use work space
-  double* red = f->work;   // work is free after alpha has been extracted
-  int64_t rs = 2 * (int64_t)nblk + 2;
-  GP_REQUIRE(rs <= f->work_stride, "residual partials exceed the workspace");
-  k_residual<<<dim3(nblk, f->B), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, n, ps->nnz, f->val, f->alpha, d_resid,
-                                                        d_res, red, f->work_stride, nblk);
+  GP_REQUIRE(3 * (int64_t)nblk + 2 <= f->work_stride, "residual partials exceed the workspace");
+  k_residual<<<dim3(nblk, f->B), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, n, ps->nnz, f->val, alpha, rhs, res,
+                                                        f->work, f->work_stride, nblk);
   GP_CHECK_LAUNCH(ctx);
-  k_relres<<<f->B, 256, 0, ctx->stream>>>(red, f->work_stride, nblk, d_err);
+  k_relres<<<f->B, 256, 0, ctx->stream>>>(f->work, f->work_stride, nblk, err, rdot);
   GP_CHECK_LAUNCH(ctx);
-  (void)rs;
 }
 
+}  // namespace
+
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err) {
-  {
-    ProfScope ps_(ctx, KC_SOLVE);   // the whole forward/backward sweep as one timed span
-    solve_run(ctx, f, d_resid, true);
+  ProfScope ps_(ctx, KC_SOLVE);   // the whole solve (with refinement) as one timed span
+  gp_pointset* ps = f->ps;
+  const int B = f->B;
+  const int64_t n = ps->n;
+  const int nblk = (int)((n + 1023) / 1024);
+  // f->red: B x red_stride partials, then 4B sums
+  double* sums = f->red + (size_t)B * f->red_stride;
+  double* s_log = sums;            // [2b] = sum log L_jj, [2b+1] = sum x^2
+  double* s_quad = sums + 2 * B;   // [2b+1] = r . alpha (mixed)
+  if (f->prec == GP_FP64) {
+    StoreF64 store{f->panels, ps->sp.panel_entries};
+    solve_impl(ctx, f, store, d_resid, f->alpha, true);
+    k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
+    GP_CHECK_LAUNCH(ctx);
+    k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_log, f->notpd, nullptr, d_out);
+    GP_CHECK_LAUNCH(ctx);
+    if (d_err) residual_impl(ctx, f, d_resid, f->alpha, nullptr, d_err, nullptr);
+    return;
   }
-  int nblk = (int)((f->ps->n + 1023) / 1024);
-  k_loglik<<<f->B, 256, 0, ctx->stream>>>(f->ps->n, f->red, f->red_stride, nblk, f->notpd, d_out, nullptr);
+  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries};
+  solve_impl(ctx, f, store, d_resid, f->alpha, true);
+  k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
   GP_CHECK_LAUNCH(ctx);
-  if (d_err) residual_run(ctx, f, d_resid, nullptr, d_err);
+  // A11: FP64 iterative refinement of alpha
+  double* res = f->delta;                       // B x n residual
+  double* cor = f->delta + (size_t)B * n;       // B x n correction
+  double* errv = f->red;                        // B relative residuals (partials are consumed already)
+  std::vector<double> herr(B);
+  for (int it = 0; it < 10; it++) {
+    residual_impl(ctx, f, d_resid, f->alpha, res, errv, nullptr);
+    d2h(ctx, herr.data(), errv, B);
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+    double worst = 0.0;
+    for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
+    if (worst <= 1e-12) break;
+    solve_impl(ctx, f, store, res, cor, false);
+    k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);
+    GP_CHECK_LAUNCH(ctx);
+  }
+  residual_impl(ctx, f, d_resid, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
+  k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
+  GP_CHECK_LAUNCH(ctx);
 }

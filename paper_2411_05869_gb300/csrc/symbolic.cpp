@@ -315,6 +315,23 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   }
   sp.sn_frow[ns] = froff;
   sp.panel_entries = loff;
+  sp.sn_ldw.resize(ns);
+  sp.sn_loff32.resize(ns);
+  sp.sn_doff.resize(ns);
+  {
+    int64_t o32 = 0, od = 0;
+    for (int64_t s = 0; s < ns; s++) {
+      int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
+      int64_t ldw = (w + 3) / 4 * 4;
+      sp.sn_ldw[s] = (int32_t)ldw;
+      sp.sn_loff32[s] = o32;
+      o32 += (m * ldw + 3) / 4 * 4;
+      sp.sn_doff[s] = od;
+      od += (w + GP_TILE - 1) / GP_TILE * GP_TILE * GP_TILE;
+    }
+    sp.panel32_entries = o32;
+    sp.diag_entries = std::max<int64_t>(od, 1);
+  }
   sp.frows.resize(froff);
   for (int64_t s = 0; s < ns; s++) {
     int64_t f = sp.sn_first[s], w = sp.sn_w[s];
@@ -457,6 +474,19 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           stp.trsm_flops += M * bw * bw;
           stp.upd_flops += 2.0 * bw * M * (M + 1.0) / 2.0;
         }
+        // 128 x 128 tiles of the trailing lower triangle (tensor-core update of the mixed path)
+        stp.pre128_off = (int64_t)sp.step_pre128.size();
+        acc = 0;
+        sp.step_pre128.push_back(0);
+        for (int32_t t = 0; t < cnt; t++) {
+          int32_t s = sp.large_fronts[stp.fr_off + t];
+          int64_t m = sp.sn_w[s] + sp.sn_r[s];
+          int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, sp.sn_w[s]);
+          int64_t nt = (m - c1 + 127) / 128;
+          acc += tri(nt);
+          sp.step_pre128.push_back(acc);
+        }
+        stp.upd128_total = acc;
         lv.steps.push_back(stp);
       }
     }

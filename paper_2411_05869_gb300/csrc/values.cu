@@ -52,12 +52,15 @@ __global__ void k_features(const double* __restrict__ X, int64_t n, int d, const
   }
 }
 
-// Warp per row of the pattern; B proposals per entry (geometry shared).
+// Warp per row of the pattern; B proposals per entry (geometry shared). MIXED: lower entries go to the
+// FP32 row-major panels or, inside a 64 x 64 diagonal block, to the FP64 diagonal tiles (dest flag bit).
+template <bool MIXED>
 __global__ void k_values(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n, int d,
                          const double* __restrict__ U, const double* __restrict__ X,
                          const double* __restrict__ theta, int64_t tstride, int B, int n1,
                          const double* __restrict__ F, const int64_t* __restrict__ dest, int64_t nnz,
-                         int64_t panel_entries, double* __restrict__ val, double* __restrict__ panels) {
+                         int64_t panel_entries, double* __restrict__ val, double* __restrict__ panels,
+                         float* __restrict__ p32, double* __restrict__ diag, int64_t diag_entries) {
   int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -98,7 +101,14 @@ __global__ void k_values(const int64_t* __restrict__ rowptr, const int32_t* __re
       }
       if (j == i) v += th[TH_NOISE];
       val[(int64_t)b * nnz + e] = v;
-      if (de >= 0) panels[(int64_t)b * panel_entries + de] = v;
+      if (MIXED) {
+        if (de >= 0) {
+          if (de & DIAG_FLAG) diag[(int64_t)b * diag_entries + (de & ~DIAG_FLAG)] = v;
+          else p32[(int64_t)b * panel_entries + de] = (float)v;
+        }
+      } else if (de >= 0) {
+        panels[(int64_t)b * panel_entries + de] = v;
+      }
     }
   }
 }
@@ -168,9 +178,28 @@ void values_run(gp_ctx* ctx, gp_factor_t* f) {
   }
   GP_CUDA(cudaMemsetAsync(f->panels, 0, sizeof(double) * (size_t)f->B * ps->sp.panel_entries, ctx->stream));
   ProfScope ps_(ctx, KC_VALUES);
-  k_values<<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, n, ps->d, ps->U, ps->X,
-                                                          f->theta_dev, f->theta_stride, f->B, h0.n1, f->F,
-                                                          ps->dest, ps->nnz, ps->sp.panel_entries, f->val,
-                                                          f->panels);
+  k_values<false><<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(
+      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, ps->dest,
+      ps->nnz, ps->sp.panel_entries, f->val, f->panels, nullptr, nullptr, 0);
+  GP_CHECK_LAUNCH(ctx);
+}
+
+void values_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
+  gp_pointset* ps = f->ps;
+  const SymPlan& sp = ps->sp;
+  const int64_t n = ps->n;
+  const gp_hyper& h0 = f->thetas_host[0];
+  dim3 gf(grid_for(n, 128), f->B);
+  if (h0.n1 > 0) {
+    k_features<<<gf, 128, 0, ctx->stream>>>(ps->X, n, ps->d, f->theta_dev, f->theta_stride, h0.n1, h0.n2,
+                                            h0.bump_dims, f->F);
+    GP_CHECK_LAUNCH(ctx);
+  }
+  GP_CUDA(cudaMemsetAsync(f->panels32, 0, sizeof(float) * (size_t)f->B * sp.panel32_entries, ctx->stream));
+  GP_CUDA(cudaMemsetAsync(f->diag, 0, sizeof(double) * (size_t)f->B * sp.diag_entries, ctx->stream));
+  ProfScope ps_(ctx, KC_VALUES);
+  k_values<true><<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(
+      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, ps->dest32,
+      ps->nnz, sp.panel32_entries, f->val, nullptr, f->panels32, f->diag, sp.diag_entries);
   GP_CHECK_LAUNCH(ctx);
 }

@@ -152,3 +152,36 @@ def test_edge_sizes(ctx, n, d):
     f = ctx.factor(ps, [hp])
     ll = float(f.loglik(_dev(r)).cpu()[0])
     assert abs(ll - ref["loglik"]) <= LOGLIK_RTOL * abs(ref["loglik"])
+
+
+MIXED_RTOL = 1e-6
+
+
+def test_loglik_mixed_matches_oracle(case, ctx):
+    """GP_MIXED: TF32 tensor-core updates, FP64 diagonal tiles, FP64 refinement; loglik within 1e-6."""
+    from paper_2411_05869_gb300 import gp
+    w, ps = case["w"], case["ps"]
+    ref = oracle.sparse_loglik(w.hyper, w.X, case["rp"], case["col"], case["perm"], w.resid, want_alpha=True)
+    f = ctx.factor(ps, [w.hyper], gp.GP_MIXED)
+    err = torch.empty(1, dtype=torch.float64, device="cuda")
+    ll = float(f.loglik(_dev(w.resid), err=err).cpu()[0])
+    assert abs(ll - ref["loglik"]) <= MIXED_RTOL * abs(ref["loglik"]), (ll, ref["loglik"])
+    assert float(err.cpu()[0]) <= 1e-12
+    mu = np.zeros(w.Xtest.shape[0])
+    m_ref = oracle.predict(w.hyper, w.X, ref["alpha"], w.Xtest, mu)
+    m_gpu = f.predict(_dev(w.Xtest), _dev(mu)).cpu().numpy()
+    assert np.abs(m_gpu - m_ref).max() <= 1e-9 * max(1.0, np.abs(m_ref).max())
+    f.free()
+
+
+def test_mixed_batched_each_proposal(case, ctx):
+    from paper_2411_05869_gb300 import gp
+    w, ps = case["w"], case["ps"]
+    rng = np.random.default_rng(9)
+    thetas = [synth.perturb(rng, w.hyper) for _ in range(3)]
+    f = ctx.factor(ps, thetas, gp.GP_MIXED)
+    ll = f.loglik(_dev(np.stack([w.resid] * 3))).cpu().numpy()
+    for b, hp in enumerate(thetas):
+        ref = oracle.sparse_loglik(hp, w.X, case["rp"], case["col"], case["perm"], w.resid)
+        assert abs(ll[b] - ref["loglik"]) <= MIXED_RTOL * abs(ref["loglik"]), (b, ll[b], ref["loglik"])
+    f.free()
