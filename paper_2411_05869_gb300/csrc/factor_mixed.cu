@@ -8,10 +8,10 @@
 // live in the FP64 tile, every other panel entry in FP32.
 // Per level: zero the update matrices, extend-add the children (FP32 sums into the parent's FP32 entries and
 // FP64 tiles), factor fronts of order <= 96 wholly in FP64 shared memory, and step the large fronts 64 columns
-// at a time: POTRF of the FP64 diagonal tile, TRSM of the rows below in FP32 (result rounded to nearest TF32,
-// so the tensor cores, which read the top 19 bits, see unbiased operands), then the trailing update
-// F[i, j] -= sum_l L[i, l] L[j, l] over 128 x 128 tiles on the tensor cores with FP64 accumulation into the
-// diagonal tiles.
+// at a time: POTRF of the FP64 diagonal tile, TRSM of the rows below in FP32, then the trailing update
+// F[i, j] -= sum_l L[i, l] L[j, l] over 128 x 128 tiles on the tensor cores, each FP32 operand split into two
+// round-to-nearest TF32 parts (three products per step, about 21 bits kept), with the tile results added in
+// FP64 to the diagonal tiles and in FP32 elsewhere.
 #include <climits>
 
 #include "gp_internal.cuh"
@@ -68,12 +68,6 @@ __device__ __forceinline__ void mix_add(const MixFront& fr, int64_t i, int64_t j
   } else {
     fr.Uu[(i - fr.w) * fr.r + (j - fr.w)] += v;
   }
-}
-
-__device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
 }
 
 __device__ __forceinline__ double checked_sqrt(double d, int32_t* notpd, int32_t col) {
@@ -193,7 +187,7 @@ __global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp
   for (int t = threadIdx.x; t < T * T; t += blockDim.x) D[t] = A[t];
 }
 
-// FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile); outputs rounded to TF32.
+// FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile, one thread per row).
 __global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
                          DevPlan dp, float* __restrict__ p32, const double* __restrict__ dg, int64_t P32E,
                          int64_t DE) {
@@ -228,7 +222,7 @@ __global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __re
   __syncthreads();
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
     int i = q / T, j = q % T;
-    if (i < nr && j < bw) P[(r0 + i) * ldw + c0 + j] = tf32_rn(X[i * (T + 1) + j]);
+    if (i < nr && j < bw) P[(r0 + i) * ldw + c0 + j] = X[i * (T + 1) + j];
   }
 }
 
@@ -272,7 +266,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
   __syncthreads();
   tcg::tc_fence_after();
   const uint32_t tmem = *tslot;
-  bool ok = tcg::tile_mma(smem, arows, brows, bw, fr.P, tmem);
+  bool ok = tcg::tile_mma_split3(smem, arows, brows, bw, tmem);
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = i0 + warp * 32 + lane;

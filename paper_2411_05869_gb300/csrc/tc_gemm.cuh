@@ -187,4 +187,83 @@ __device__ __forceinline__ bool tile_mma(uint8_t* smem, const float* const* a_ro
   return ok;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Split-TF32 variant: each FP32 operand x is split into hi = rn_tf32(x) and lo = rn_tf32(x - hi) while it is
+// staged (global -> registers -> shared), and the tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T
+// (three K=8 instructions per step), which carries about 21 significant bits through the products instead of
+// the 11 of one TF32 pass (the split of Ootomo and Yokota, 2022). One stage of four 16 KB buffers per chunk;
+// several CTAs per SM overlap one another's loads and instructions.
+constexpr int SPLIT_SMEM_BYTES = 4 * STAGE_BYTES + 1024;
+
+__device__ __forceinline__ uint32_t to_tf32_bits(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return u;
+}
+
+__device__ __forceinline__ void split_store(uint8_t* hi, uint8_t* lo, uint32_t off, float4 v) {
+  uint32_t h0 = to_tf32_bits(v.x), h1 = to_tf32_bits(v.y), h2 = to_tf32_bits(v.z), h3 = to_tf32_bits(v.w);
+  uint32_t l0 = to_tf32_bits(v.x - __uint_as_float(h0)), l1 = to_tf32_bits(v.y - __uint_as_float(h1));
+  uint32_t l2 = to_tf32_bits(v.z - __uint_as_float(h2)), l3 = to_tf32_bits(v.w - __uint_as_float(h3));
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h0, h1, h2, h3);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l0, l1, l2, l3);
+}
+
+__device__ __forceinline__ float4 load4(const float* row, int k, int K) {
+  if (!row || k >= K) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if (k + 4 <= K) return *reinterpret_cast<const float4*>(row + k);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  v.x = row[k];
+  if (k + 1 < K) v.y = row[k + 1];
+  if (k + 2 < K) v.z = row[k + 2];
+  return v;
+}
+
+// smem: A_hi, A_lo, B_hi, B_lo (STAGE_BYTES each, 1024-aligned base), then one mbarrier at +4*STAGE_BYTES.
+__device__ __forceinline__ bool tile_mma_split3(uint8_t* smem, const float* const* a_rows, const float* const* b_rows,
+                                                int K, uint32_t tmem_d) {
+  uint8_t* aH = smem;
+  uint8_t* aL = smem + STAGE_BYTES;
+  uint8_t* bH = smem + 2 * STAGE_BYTES;
+  uint8_t* bL = smem + 3 * STAGE_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * STAGE_BYTES);
+  const uint32_t sAH = smem_u32(aH), sAL = smem_u32(aL), sBH = smem_u32(bH), sBL = smem_u32(bL);
+  const int nchunk = (K + KC - 1) / KC;
+  const uint32_t idesc = idesc_tf32(TM, TN);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int c = 0; c < nchunk; c++) {
+    if (c > 0) {   // the previous chunk's instructions must be done with the buffers
+      if (!mbar_wait(bar, phase)) ok = false;
+      phase ^= 1;
+    }
+    for (int p = threadIdx.x; p < TM * (KC / 4); p += 128) {
+      int row = p >> 3, piece = p & 7;
+      int k = c * KC + piece * 4;
+      uint32_t off = chunk_offset(row, piece * 4);
+      split_store(aH, aL, off, load4(a_rows[row], k, K));
+      split_store(bH, bL, off, load4(b_rows[row], k, K));
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < KC / 8; kk++) {
+        const uint32_t o = kk * 256;
+        uint64_t ah = smem_desc(sAH + o, 128, 1024), al = smem_desc(sAL + o, 128, 1024);
+        uint64_t bh = smem_desc(sBH + o, 128, 1024), bl = smem_desc(sBL + o, 128, 1024);
+        mma_tf32(tmem_d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem_d, ah, bl, idesc, 1u);
+        mma_tf32(tmem_d, ah, bh, idesc, 1u);
+      }
+      mma_commit(bar);
+    }
+    __syncthreads();
+  }
+  if (!mbar_wait(bar, phase)) ok = false;
+  tc_fence_after();
+  return ok;
+}
+
 }  // namespace tcg
