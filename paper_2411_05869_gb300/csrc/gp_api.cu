@@ -134,7 +134,18 @@ extern "C" gp_status gp_create(gp_ctx** out, int device, void* cuda_stream, size
   return GP_OK;
 }
 
-extern "C" void gp_destroy(gp_ctx* ctx) { delete ctx; }
+namespace {
+// A handle keeps its context alive: gp_destroy before the last *_free only marks the context.
+void ctx_release(gp_ctx* ctx) {
+  if (--ctx->live == 0 && ctx->destroyed) delete ctx;
+}
+}  // namespace
+
+extern "C" void gp_destroy(gp_ctx* ctx) {
+  if (!ctx) return;
+  ctx->destroyed = true;
+  if (ctx->live == 0) delete ctx;
+}
 
 extern "C" const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -236,17 +247,20 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     delete ps;
     return st;
   }
+  ctx->live++;
   *out = ps;
   return GP_OK;
 }
 
 extern "C" void gp_pointset_free(gp_pointset* ps) {
   if (!ps) return;
-  if (ps->ctx) {
-    cudaSetDevice(ps->ctx->device);
-    dev_free_all(ps->ctx, ps->bufs);
+  gp_ctx* ctx = ps->ctx;
+  if (ctx) {
+    cudaSetDevice(ctx->device);
+    dev_free_all(ctx, ps->bufs);
   }
   delete ps;
+  if (ctx) ctx_release(ctx);
 }
 
 extern "C" gp_status gp_pointset_info(const gp_pointset* ps, gp_pointset_info_t* info) {
@@ -346,6 +360,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     delete f;
     return st;
   }
+  ctx->live++;
   *out = f;
   return GP_OK;
 }
@@ -364,11 +379,13 @@ extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hype
 
 extern "C" void gp_factor_free(gp_factor_t* f) {
   if (!f) return;
-  if (f->ctx) {
-    cudaSetDevice(f->ctx->device);
-    dev_free_all(f->ctx, f->bufs);
+  gp_ctx* ctx = f->ctx;
+  if (ctx) {
+    cudaSetDevice(ctx->device);
+    dev_free_all(ctx, f->bufs);
   }
   delete f;
+  if (ctx) ctx_release(ctx);
 }
 
 extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, int32_t* not_pd_column) {

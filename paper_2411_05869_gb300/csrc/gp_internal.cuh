@@ -64,6 +64,8 @@ struct gp_ctx {
   size_t held = 0;       // bytes currently held by this context's handles
   int64_t launches = 0;
   std::string err;
+  int64_t live = 0;          // point sets and factors still holding this context
+  bool destroyed = false;    // gp_destroy was called; the context goes with its last handle
   // launch profiler: CUDA events around every launch of a class, on the context stream
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_COUNT];

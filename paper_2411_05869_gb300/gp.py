@@ -5,8 +5,10 @@ missing or cannot load, these calls raise, there is no fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -50,6 +52,25 @@ KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4,
           "predict": 7}
 
 _lib = None
+_LIVE = {"factor": weakref.WeakSet(), "pointset": weakref.WeakSet(), "context": weakref.WeakSet()}
+_EXIT_HOOKED = False
+
+
+def _free_all():
+    """Free the library handles still alive at interpreter exit, factors first, while CUDA is still up."""
+    for kind in ("factor", "pointset", "context"):
+        for obj in list(_LIVE[kind]):
+            try:
+                obj.close() if kind == "context" else obj.free()
+            except Exception:
+                pass
+
+
+def _hook_exit():
+    global _EXIT_HOOKED
+    if not _EXIT_HOOKED:
+        atexit.register(_free_all)   # registered after torch initialised CUDA, so it runs before its teardown
+        _EXIT_HOOKED = True
 
 
 def library_path() -> str:
@@ -149,6 +170,8 @@ class Context:
         if st != 0:
             raise GpError(st, "gp_create failed")
         self.h = h
+        _hook_exit()
+        _LIVE["context"].add(self)
 
     def check(self, st: int):
         if st != 0:
@@ -202,6 +225,7 @@ class Context:
 class PointSet:
     def __init__(self, ctx: Context, h):
         self.ctx, self.h = ctx, h
+        _LIVE["pointset"].add(self)
 
     def info(self) -> dict:
         inf = PointsetInfo()
@@ -236,6 +260,7 @@ class PointSet:
 class Factor:
     def __init__(self, ctx: Context, ps: PointSet, h, B: int):
         self.ctx, self.ps, self.h, self.B = ctx, ps, h, B
+        _LIVE["factor"].add(self)
 
     def update(self, thetas: Sequence):
         """Re-run A3, A4, A7 in place with new settings (same B)."""
