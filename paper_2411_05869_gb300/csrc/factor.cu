@@ -107,10 +107,10 @@ __global__ void k_small_front(const int32_t* __restrict__ list, DevPlan dp, doub
     double inv = 1.0 / piv;
     for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * m + i] *= inv;
     __syncthreads();
-    int S = m - k - 1;
-    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
-      int i = k + 1 + t % S, j = k + 1 + t / S;
-      if (i >= j) A[j * m + i] -= A[k * m + i] * A[k * m + j];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 columns x 32 rows (blockDim = 256)
+    for (int j = k + 1 + ty; j < m; j += 8) {
+      const double ajk = A[k * m + j];
+      for (int i = j + tx; i < m; i += 32) A[j * m + i] -= A[k * m + i] * ajk;
     }
     __syncthreads();
   }
@@ -154,10 +154,10 @@ __global__ void k_potrf(const int32_t* __restrict__ fronts, int kb, DevPlan dp, 
     double inv = 1.0 / piv;
     for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[k * T + i] *= inv;
     __syncthreads();
-    int S = bw - k - 1;
-    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
-      int i = k + 1 + t % S, j = k + 1 + t / S;
-      if (i >= j) A[j * T + i] -= A[k * T + i] * A[k * T + j];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 4 columns x 32 rows (blockDim = 128)
+    for (int j = k + 1 + ty; j < bw; j += 4) {
+      const double ajk = A[k * T + j];
+      for (int i = j + tx; i < bw; i += 32) A[j * T + i] -= A[k * T + i] * ajk;
     }
     __syncthreads();
   }

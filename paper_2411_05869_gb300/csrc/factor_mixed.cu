@@ -133,10 +133,11 @@ __global__ void k_small_front32(const int32_t* __restrict__ list, DevPlan dp, fl
     double inv = 1.0 / piv;
     for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[k * m + i] *= inv;
     __syncthreads();
-    int S = m - k - 1;
-    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
-      int i = k + 1 + t % S, j = k + 1 + t / S;
-      if (i >= j) A[j * m + i] -= A[k * m + i] * A[k * m + j];
+    // trailing lower triangle: 8 columns x 32 rows of threads (blockDim = 256)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = k + 1 + ty; j < m; j += 8) {
+      const double ajk = A[k * m + j];
+      for (int i = j + tx; i < m; i += 32) A[j * m + i] -= A[k * m + i] * ajk;
     }
     __syncthreads();
   }
@@ -177,10 +178,11 @@ __global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp
     double inv = 1.0 / piv;
     for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[i * T + k] *= inv;
     __syncthreads();
-    int S = bw - k - 1;
-    for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
-      int i = k + 1 + t / S, j = k + 1 + t % S;
-      if (i >= j) A[i * T + j] -= A[i * T + k] * A[j * T + k];
+    // trailing lower triangle: 8 rows x 16 columns of threads (blockDim = 128)
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int i = k + 1 + ty; i < bw; i += 8) {
+      const double aik = A[i * T + k];
+      for (int j = k + 1 + tx; j <= i; j += 16) A[i * T + j] -= aik * A[j * T + k];
     }
     __syncthreads();
   }
@@ -269,23 +271,32 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
   bool ok = tcg::tile_mma_split3(smem, arows, brows, bw, tmem);
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = i0 + warp * 32 + lane;
+  // Epilogue: TMEM (thread = row) -> shared tile (XOR-swizzled by row so neither side has bank conflicts)
+  // -> global read-modify-write with a warp per row, 32 consecutive columns per access.
+  float* S = reinterpret_cast<float*>(smem);   // 128 x 128 FP32, reuses the operand buffers
   if (ok) {
+    const int r = warp * 32 + lane;
     for (int cc = 0; cc < 128; cc += 32) {
       float v[32];
       tcg::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
-      if (i < fr.m) {
-#pragma unroll 4
-        for (int q = 0; q < 32; q++) {
-          int64_t j = j0 + cc + q;
-          if (j <= i && j < fr.m) mix_add(fr, i, j, -v[q]);
-        }
-      }
+#pragma unroll
+      for (int q = 0; q < 32; q++) S[r * 128 + ((cc + q) ^ (r & 31))] = v[q];
     }
   }
   tcg::tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) tcg::tmem_dealloc(tmem, 128);
+  if (!ok) return;
+  for (int r = warp; r < 128; r += 4) {
+    const int64_t i = i0 + r;
+    if (i >= fr.m) break;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int c = q * 32 + lane;
+      const int64_t j = j0 + c;
+      if (j <= i && j < fr.m) mix_add(fr, i, j, -S[r * 128 + (c ^ (r & 31))]);
+    }
+  }
 }
 
 bool g_attrs = false;

@@ -239,6 +239,7 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     dp.loff32 = upload(ctx, ps->bufs, sp.sn_loff32);
     dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
     dp.step_pre128 = upload(ctx, ps->bufs, sp.step_pre128);
+    dp.large_kb = upload(ctx, ps->bufs, sp.large_kb);
     compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });

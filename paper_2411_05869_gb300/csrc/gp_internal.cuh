@@ -166,6 +166,9 @@ struct SymPlan {
   std::vector<int2> ea_tab;          // (child supernode, first column) per extend-add CTA (8 columns each)
   std::vector<int32_t> small_list;   // supernodes factored in shared memory
   std::vector<int32_t> large_fronts; // per step: fronts (sorted by width descending within a level)
+  std::vector<int32_t> large_kb;     // block-column index of each large_fronts entry (its step)
+  struct LevelLarge { int64_t off = 0; int64_t count = 0; };    // all steps' entries of a level, contiguous
+  std::vector<LevelLarge> level_large;
   std::vector<int64_t> step_pre;     // per step: prefix of TRSM tasks then of UPDATE tasks (2*(nfront+1))
 };
 
@@ -188,6 +191,7 @@ struct DevPlan {
   int32_t* ldw;
   int64_t *loff32, *doff;
   int64_t* step_pre128;
+  int32_t* large_kb;
 };
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);

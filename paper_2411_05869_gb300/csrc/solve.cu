@@ -39,6 +39,7 @@ struct AccMix {
   }
 };
 struct StoreF64 {
+  static constexpr bool kRowMajor = false;
   const double* P;
   int64_t PE;
   using Acc = AccF64;
@@ -47,6 +48,7 @@ struct StoreF64 {
   }
 };
 struct StoreMix {
+  static constexpr bool kRowMajor = true;
   const float* P;
   const double* D;
   int64_t P32E, DE;
@@ -141,24 +143,19 @@ __device__ __forceinline__ void block_upper_solve(const double* L, double* t, in
   __syncthreads();
 }
 
-// One block column kb of the forward solve for every large front of a step. Tasks [0, nfront) write the
-// block's solution to x (a separate vector: the other tasks still read the block's right-hand side); the
-// rest (from the 64-row tile prefix) update one 64-row tile below the block.
+// Forward, block column kb of every large front of a step: x_J = L_JJ^{-1} f_J (one CTA per front, written
+// to the front vector and to x) ...
 template <class St>
-__global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                           DevPlan dp, St store, double* __restrict__ work, int64_t ws, int64_t xv_off) {
+__global__ void k_fwd_tri(const int32_t* __restrict__ fronts, int kb, DevPlan dp, St store, double* __restrict__ work,
+                          int64_t ws, int64_t xv_off) {
   __shared__ double L[T * T];
   __shared__ double x[T];
-  int64_t t = blockIdx.x;
-  bool writer = t < nfront;
-  int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
-  int32_t s = fronts[fi];
+  int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
   double* fv = work + (int64_t)b * ws + dp.frow_off[s];
   const int w = dp.w[s];
-  const int64_t m = (int64_t)w + dp.r[s];
-  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
+  const int c0 = kb * T, bw = min(T, w - c0);
   for (int q = threadIdx.x; q < bw * bw; q += blockDim.x) {
     int i = q % bw, j = q / bw;
     L[j * T + i] = i >= j ? A.L(c0 + i, c0 + j) : 0.0;
@@ -166,16 +163,55 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
   for (int q = threadIdx.x; q < bw; q += blockDim.x) x[q] = fv[c0 + q];
   __syncthreads();
   block_lower_solve(L, x, bw);
-  if (writer) {
-    double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
-    for (int q = threadIdx.x; q < bw; q += blockDim.x) xv[c0 + q] = x[q];
-    return;
+  double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
+  for (int q = threadIdx.x; q < bw; q += blockDim.x) {
+    fv[c0 + q] = x[q];
+    xv[c0 + q] = x[q];
   }
-  int64_t r0 = c1 + (t - nfront - pre[fi]) * T;
-  for (int64_t i = r0 + threadIdx.x; i < imin64(r0 + T, m); i += blockDim.x) {
-    double acc = 0.0;
-    for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
-    fv[i] -= acc;
+}
+
+// ... then f_i -= L[i, J] x_J for the rows below the block, one CTA per 64-row tile (tile prefix of the
+// step). Row-major panels: a half-warp reads one row's 64 entries as 16 float4; column-major: thread per row.
+template <class St>
+__global__ void k_fwd_gemv(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
+                           DevPlan dp, St store, double* __restrict__ work, int64_t ws) {
+  __shared__ double x[T];
+  int64_t t = blockIdx.x;
+  int fi = find_front(pre, nfront, t);
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
+  const int w = dp.w[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
+  const int64_t r0 = c1 + (t - pre[fi]) * T, rend = imin64(r0 + T, m);
+  for (int q = threadIdx.x; q < T; q += blockDim.x) x[q] = q < bw ? fv[c0 + q] : 0.0;
+  __syncthreads();
+  if constexpr (St::kRowMajor) {
+    const int lane = threadIdx.x & 31, l16 = lane & 15, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int l = l16 * 4;
+    for (int64_t base = r0 + 2 * warp; base < rend; base += 2 * nw) {
+      const int64_t i = base + (lane >> 4);
+      double acc = 0.0;
+      if (i < rend && l < bw) {
+        const float* row = A.P + i * A.ldw + c0;
+        if (l + 4 <= bw) {
+          float4 v = *reinterpret_cast<const float4*>(row + l);
+          acc = (double)v.x * x[l] + (double)v.y * x[l + 1] + (double)v.z * x[l + 2] + (double)v.w * x[l + 3];
+        } else {
+          for (int q = l; q < bw; q++) acc += (double)row[q] * x[q];
+        }
+      }
+      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (i < rend && l16 == 0) fv[i] -= acc;
+    }
+  } else {
+    for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
+      fv[i] -= acc;
+    }
   }
 }
 
@@ -216,18 +252,51 @@ __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, De
   }
 }
 
-// One block column kb of the backward solve for every large front of a step. Tasks per front: one writer
-// (z of the block into alpha') and kb column tiles of the earlier columns (t_k -= L[J, k]^T z_J).
+// Backward, large fronts: t_j = x_j - sum_a L[w + a, j] alpha'(R_s[a]) for the 64-column stripe of one
+// task (a task per (front, stripe) over all of a level's large fronts). Row-major: 64 threads across the
+// stripe's columns x 4 row groups, fixed-order combination; column-major: a warp per column.
 template <class St>
-__global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
-                           double* __restrict__ work, int64_t ws, int64_t apv_off) {
-  __shared__ double L[T * (T + 1)];   // the diagonal block, then (reused) the block's rows for the tile
+__global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32_t* __restrict__ kbs, DevPlan dp,
+                                 St store, double* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
+  __shared__ double part[4][T];
+  int32_t s = fronts[blockIdx.x];
+  const int j0 = kbs[blockIdx.x] * T;
+  int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  double* W = work + (int64_t)b * ws;
+  double* fv = W + dp.frow_off[s];
+  const double* apv = W + apv_off;
+  const double* xv = W + xv_off + dp.sn_first[s];
+  const int w = dp.w[s], r = dp.r[s];
+  const int nj = min(T, w - j0);
+  const int32_t* R = dp.frows + dp.frow_off[s] + w;
+  if constexpr (St::kRowMajor) {
+    const int c = threadIdx.x & 63, g = threadIdx.x >> 6;   // blockDim = 256
+    double acc = 0.0;
+    if (c < nj)
+      for (int a = g; a < r; a += 4) acc += (double)A.P[(int64_t)(w + a) * A.ldw + j0 + c] * apv[R[a]];
+    part[g][c] = acc;
+    __syncthreads();
+    if (g == 0 && c < nj) fv[j0 + c] = xv[j0 + c] - (((part[0][c] + part[1][c]) + part[2][c]) + part[3][c]);
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int jj = warp; jj < nj; jj += nw) {
+      const int j = j0 + jj;
+      double acc = 0.0;
+      for (int a = lane; a < r; a += 32) acc += A.L(w + a, j) * apv[R[a]];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) fv[j] = xv[j] - acc;
+    }
+  }
+}
+
+// Backward, block column kb of every large front of a step: z_J = L_JJ^{-T} t_J, one CTA per front ...
+template <class St>
+__global__ void k_bwd_tri(const int32_t* __restrict__ fronts, int kb, DevPlan dp, St store, double* __restrict__ work,
+                          int64_t ws, int64_t apv_off) {
+  __shared__ double L[T * T];
   __shared__ double z[T];
-  double* Lt = L;
-  int64_t t = blockIdx.x;
-  int fi = (int)(t / (kb + 1));
-  int task = (int)(t % (kb + 1));   // 0 = writer, 1..kb = column tile task-1
-  int32_t s = fronts[fi];
+  int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
   double* W = work + (int64_t)b * ws;
@@ -241,22 +310,48 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
   for (int q = threadIdx.x; q < bw; q += blockDim.x) z[q] = fv[c0 + q];
   __syncthreads();
   block_upper_solve(L, z, bw);
-  if (task == 0) {   // the block's right-hand side stays in place: the other tasks are still reading it
-    double* apv = W + apv_off;
-    const int32_t first = dp.sn_first[s];
-    for (int q = threadIdx.x; q < bw; q += blockDim.x) apv[first + c0 + q] = z[q];
-    return;
+  double* apv = W + apv_off;
+  const int32_t first = dp.sn_first[s];
+  for (int q = threadIdx.x; q < bw; q += blockDim.x) {
+    fv[c0 + q] = z[q];
+    apv[first + c0 + q] = z[q];
   }
-  const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
-  for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {
-    int l = q % bw, k = q / bw;
-    Lt[l * (T + 1) + k] = A.L(c0 + l, k0 + k);
-  }
+}
+
+// ... then t_k -= L[J, k]^T z_J for the earlier columns k < c0, one CTA per 64-column tile (kb per front).
+template <class St>
+__global__ void k_bwd_gemvt(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
+                            double* __restrict__ work, int64_t ws) {
+  __shared__ double z[T];
+  __shared__ double Lt[St::kRowMajor ? 1 : T * (T + 1)];
+  int64_t t = blockIdx.x;
+  int fi = (int)(t / kb);
+  const int k0 = (int)(t % kb) * T;   // columns [k0, k0 + 64) < c0
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
+  const int w = dp.w[s];
+  const int c0 = kb * T, bw = min(T, w - c0);
+  for (int q = threadIdx.x; q < T; q += blockDim.x) z[q] = q < bw ? fv[c0 + q] : 0.0;
   __syncthreads();
-  for (int k = threadIdx.x; k < T; k += blockDim.x) {
-    double acc = 0.0;
-    for (int l = 0; l < bw; l++) acc += Lt[l * (T + 1) + k] * z[l];
-    fv[k0 + k] -= acc;
+  if constexpr (St::kRowMajor) {
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {   // row c0 + l is contiguous over k
+      double acc = 0.0;
+      for (int l = 0; l < bw; l++) acc += (double)A.P[(int64_t)(c0 + l) * A.ldw + k0 + k] * z[l];
+      fv[k0 + k] -= acc;
+    }
+  } else {
+    for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {   // column k0 + k is contiguous over l
+      int l = q % bw, k = q / bw;
+      Lt[l * (T + 1) + k] = A.L(c0 + l, k0 + k);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l < bw; l++) acc += Lt[l * (T + 1) + k] * z[l];
+      fv[k0 + k] -= acc;
+    }
   }
 }
 
@@ -443,11 +538,14 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       GP_CHECK_LAUNCH(ctx);
     }
     for (const auto& stp : lv.steps) {
-      int64_t tasks = stp.nfront + stp.trsm_total;
-      k_fwd_step<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off,
-                                                              dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp,
-                                                              store, f->work, ws, xv_off);
+      k_fwd_tri<St><<<dim3(stp.nfront, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.kb, dp, store, f->work,
+                                                        ws, xv_off);
       GP_CHECK_LAUNCH(ctx);
+      if (stp.trsm_total > 0) {
+        k_fwd_gemv<St><<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(
+            dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, f->work, ws);
+        GP_CHECK_LAUNCH(ctx);
+      }
     }
   }
   if (partials) {
@@ -463,16 +561,21 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       GP_CHECK_LAUNCH(ctx);
     }
     if (!lv.steps.empty()) {
-      const auto& s0 = lv.steps[0];
-      k_bwd_prep<St><<<dim3(s0.nfront, B), 256, 0, st>>>(dp.large_fronts + s0.fr_off, 0, dp, store, f->work, ws,
-                                                         apv_off, xv_off);
+      const auto& ll = sp.level_large[L];   // one task per (large front, 64-column stripe)
+      k_bwd_prep_large<St><<<dim3((unsigned)ll.count, B), 256, 0, st>>>(
+          dp.large_fronts + ll.off, dp.large_kb + ll.off, dp, store, f->work, ws, apv_off, xv_off);
       GP_CHECK_LAUNCH(ctx);
       for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
         const auto& stp = lv.steps[q];
-        int64_t tasks = (int64_t)stp.nfront * (stp.kb + 1);
-        k_bwd_step<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp,
-                                                                store, f->work, ws, apv_off);
+        k_bwd_tri<St><<<dim3(stp.nfront, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.kb, dp, store, f->work,
+                                                          ws, apv_off);
         GP_CHECK_LAUNCH(ctx);
+        if (stp.kb > 0) {
+          int64_t tasks = (int64_t)stp.nfront * stp.kb;
+          k_bwd_gemvt<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.nfront, stp.kb,
+                                                                   dp, store, f->work, ws);
+          GP_CHECK_LAUNCH(ctx);
+        }
       }
     }
   }

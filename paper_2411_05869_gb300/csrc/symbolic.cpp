@@ -398,6 +398,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
 
   // ---- launch schedule
   sp.levels.assign(sp.nlevels, SymPlan::Level());
+  sp.level_large.assign(sp.nlevels, SymPlan::LevelLarge());
   for (int32_t L = 0; L < sp.nlevels; L++) {
     SymPlan::Level& lv = sp.levels[L];
     // extend-add: k-th child of every supernode of this level, 8 update columns per CTA
@@ -427,6 +428,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
     }
     lv.nsmall = (int32_t)((int64_t)sp.small_list.size() - lv.small_off);
     std::stable_sort(large.begin(), large.end(), [&](int32_t a, int32_t b) { return sp.sn_w[a] > sp.sn_w[b]; });
+    sp.level_large[L].off = (int64_t)sp.large_fronts.size();
     if (!large.empty()) {
       int64_t maxw = sp.sn_w[large[0]];
       for (int32_t kb = 0; (int64_t)kb * GP_TILE < maxw; kb++) {
@@ -438,6 +440,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
         for (int32_t s : large)
           if ((int64_t)sp.sn_w[s] > (int64_t)kb * GP_TILE) {
             sp.large_fronts.push_back(s);
+            sp.large_kb.push_back(kb);
             cnt++;
           }
         stp.nfront = cnt;
@@ -490,5 +493,6 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
         lv.steps.push_back(stp);
       }
     }
+    sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
   }
 }
