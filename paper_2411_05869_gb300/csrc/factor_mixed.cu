@@ -287,14 +287,31 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
   __syncthreads();
   if (threadIdx.x < 32) tcg::tmem_dealloc(tmem, 128);
   if (!ok) return;
-  for (int r = warp; r < 128; r += 4) {
-    const int64_t i = i0 + r;
-    if (i >= fr.m) break;
+  // two rows (r, r + 4) x 4 column groups per step: all 8 loads issued before any store
+  for (int r = warp; r < 128; r += 8) {
+    float* pf[8];
+    double* pd[8];
+    float of[8], av[8];
+    double od[8];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int c = q * 32 + lane;
-      const int64_t j = j0 + c;
-      if (j <= i && j < fr.m) mix_add(fr, i, j, -S[r * 128 + (c ^ (r & 31))]);
+    for (int e = 0; e < 8; e++) {
+      const int rr = r + (e >> 2) * 4, c = (e & 3) * 32 + lane;
+      const int64_t i = i0 + rr, j = j0 + c;
+      pf[e] = nullptr;
+      pd[e] = nullptr;
+      if (i < fr.m && j <= i) {
+        av[e] = S[rr * 128 + (c ^ (rr & 31))];
+        if (j >= fr.w) pf[e] = fr.Uu + (i - fr.w) * fr.r + (j - fr.w);
+        else if (in_diag(fr, i, j)) pd[e] = diag_at(fr, i, j);
+        else pf[e] = fr.P + i * fr.ldw + j;
+        if (pf[e]) of[e] = *pf[e];
+        if (pd[e]) od[e] = *pd[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      if (pf[e]) *pf[e] = of[e] - av[e];
+      if (pd[e]) *pd[e] = od[e] - (double)av[e];
     }
   }
 }

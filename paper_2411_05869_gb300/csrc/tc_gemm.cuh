@@ -232,17 +232,31 @@ __device__ __forceinline__ bool tile_mma_split3(uint8_t* smem, const float* cons
   const uint32_t idesc = idesc_tf32(TM, TN);
   uint32_t phase = 0;
   bool ok = true;
+  // registers of the chunk being staged: 8 16-byte pieces of A and of B per thread, all loads in flight
+  // together; chunk c+1 is fetched while chunk c's instructions run
+  constexpr int PER = TM * (KC / 4) / 128;
+  float4 va[PER], vb[PER];
+  auto fetch = [&](int c) {
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+      int p = threadIdx.x + it * 128;
+      int row = p >> 3, k = c * KC + (p & 7) * 4;
+      va[it] = load4(a_rows[row], k, K);
+      vb[it] = load4(b_rows[row], k, K);
+    }
+  };
+  fetch(0);
   for (int c = 0; c < nchunk; c++) {
     if (c > 0) {   // the previous chunk's instructions must be done with the buffers
       if (!mbar_wait(bar, phase)) ok = false;
       phase ^= 1;
     }
-    for (int p = threadIdx.x; p < TM * (KC / 4); p += 128) {
-      int row = p >> 3, piece = p & 7;
-      int k = c * KC + piece * 4;
-      uint32_t off = chunk_offset(row, piece * 4);
-      split_store(aH, aL, off, load4(a_rows[row], k, K));
-      split_store(bH, bL, off, load4(b_rows[row], k, K));
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+      int p = threadIdx.x + it * 128;
+      uint32_t off = chunk_offset(p >> 3, (p & 7) * 4);
+      split_store(aH, aL, off, va[it]);
+      split_store(bH, bL, off, vb[it]);
     }
     fence_proxy_async();
     __syncthreads();
@@ -259,6 +273,7 @@ __device__ __forceinline__ bool tile_mma_split3(uint8_t* smem, const float* cons
       }
       mma_commit(bar);
     }
+    if (c + 1 < nchunk) fetch(c + 1);   // global loads overlap the tensor-core work of chunk c
     __syncthreads();
   }
   if (!mbar_wait(bar, phase)) ok = false;
