@@ -167,6 +167,22 @@ GP_API gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_
 GP_API gp_status gp_profile(gp_ctx* ctx, int enable);
 GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops);
 
+/* Support-pattern row counts without any device allocation (the paper has no counterpart: this serves
+ * callers that must not allocate device memory, such as code running under another framework's memory
+ * allocator or a memory budget it does not own, that want each point's neighbour count, e.g. to size their
+ * own buffers or to pick core radii for a target row count before calling gp_assemble).
+ *   d_X: n x d FP64 (device); core_radius: host [d]; d_counts: n int64 (device output), d_counts[i] = number
+ *   of points j (i included) with sum_k ((x_ik - x_jk) / core_radius_k)^2 < 1, the row lengths of the pattern
+ *   gp_assemble builds for the same input.
+ * It runs the cell list and count pass of gp_assemble with all scratch in one static device array of 16 MiB
+ * that every GPU loading the library keeps until exit: n <= 65536 and at most 2^20 cells of the unit grid in
+ * x / core_radius (GP_ERR_ARG beyond). It calls no cudaMalloc/cudaFree. The first call on a device looks up
+ * the array's device address; make that first call before any stream capture. Calls share the array, so
+ * calls that overlap on the GPU race. Synchronises the context stream once (for the grid extent).
+ * Errors: GP_ERR_ARG, GP_ERR_CUDA. */
+GP_API gp_status gp_pattern_counts_noalloc(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
+                                           int64_t* d_counts);
+
 /* Number of kernel launches this context has issued (a counter for launch accounting). */
 GP_API int64_t gp_launch_count(const gp_ctx* ctx);
 

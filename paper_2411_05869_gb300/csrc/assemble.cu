@@ -609,3 +609,105 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X) {
   GP_CUDA(cudaStreamSynchronize(st));
   dev_free_all(ctx, tmp);
 }
+
+// ------------------------------------------------------------------------------------------ no-allocation counts
+// gp_pattern_counts_noalloc: the count pass of the support pattern (cell list plus per-point neighbour count)
+// for callers that cannot allocate device memory. All of its scratch lives in this one file-scope device array,
+// which every GPU that loads the library holds until the process exits. Every call shares it and it keeps the
+// last call's contents; the call writes every scratch entry it later reads (the min/max words are reset from
+// the host), so no state leaks from one call to the next, but two calls that overlap on the GPU (different
+// streams or contexts on one device) race on it.
+#define GP_NOALLOC_MAX_N 65536
+#define GP_NOALLOC_MAX_CELLS (1 << 20)
+#define GP_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+void* g_noalloc_base[64] = {};   // device address of g_noalloc_scratch, looked up once per device
+
+struct Carver {
+  char* base;
+  size_t used, cap;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (used + bytes > cap) throw GpError{GP_ERR_ARG, "gp_pattern_counts_noalloc: scratch array too small"};
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+}  // namespace
+
+extern "C" gp_status gp_pattern_counts_noalloc(gp_ctx* ctx, const double* d_X, int64_t n, int d,
+                                               const double* core_radius, int64_t* d_counts) {
+  if (!ctx) return GP_ERR_ARG;
+  try {
+    GP_CUDA(cudaSetDevice(ctx->device));
+    GP_REQUIRE(d_X && core_radius && d_counts, "d_X, core_radius and d_counts are required");
+    GP_REQUIRE(n >= 1 && n <= GP_NOALLOC_MAX_N, "gp_pattern_counts_noalloc: n must be in 1..65536");
+    GP_REQUIRE(d >= 1 && d <= GP_MAX_D, "d must be 1, 2 or 3");
+    for (int k = 0; k < d; k++)
+      GP_REQUIRE(core_radius[k] > 0.0 && std::isfinite(core_radius[k]), "core_radius must be positive");
+    GP_REQUIRE(ctx->device >= 0 && ctx->device < 64, "device index out of range");
+    // host code sees only a stand-in for the array: fetch its device address with the device current
+    if (!g_noalloc_base[ctx->device]) {
+      void* p = nullptr;
+      GP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_base[ctx->device] = p;
+    }
+    cudaStream_t st = ctx->stream;
+    Carver cv{static_cast<char*>(g_noalloc_base[ctx->device]), 0, GP_NOALLOC_SCRATCH_BYTES};
+    double* U = cv.take<double>((size_t)n * d);
+    double* Us = cv.take<double>((size_t)n * d);
+    uint64_t* keys = cv.take<uint64_t>(n + 1);
+    uint32_t* vals = cv.take<uint32_t>(n + 1);
+    int32_t* cell_perm = cv.take<int32_t>(n);
+    int64_t* key_of = cv.take<int64_t>(n);
+    unsigned long long* mnmx = cv.take<unsigned long long>(6);
+    double* mm_dev = cv.take<double>(6);
+    void* sort_tmp = cv.take<char>(radix_sort_temp_bytes(n));
+    const unsigned long long init[6] = {~0ull, 0ull, ~0ull, 0ull, ~0ull, 0ull};
+    GP_CUDA(cudaMemcpyAsync(mnmx, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    double rho[3] = {1.0, 1.0, 1.0};
+    for (int k = 0; k < d; k++) rho[k] = core_radius[k];
+    k_scale<<<grid_for(n, 256), 256, 0, st>>>(d_X, n, d, rho[0], rho[1], rho[2], U, mnmx);
+    GP_CHECK_LAUNCH(ctx);
+    k_decode_minmax<<<1, 32, 0, st>>>(mnmx, d, mm_dev);
+    GP_CHECK_LAUNCH(ctx);
+    double mm[6];
+    GP_CUDA(cudaMemcpyAsync(mm, mm_dev, sizeof(double) * 2 * d, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(cudaStreamSynchronize(st));
+    Grid g{};
+    g.d = d;
+    double cells = 1.0;
+    for (int k = 0; k < d; k++) {
+      GP_REQUIRE(std::isfinite(mm[2 * k]) && std::isfinite(mm[2 * k + 1]), "non-finite coordinate in X");
+      g.c0[k] = (long long)std::floor(mm[2 * k]);
+      g.nc[k] = (long long)std::floor(mm[2 * k + 1]) - g.c0[k] + 1;
+      cells *= (double)g.nc[k];
+    }
+    for (int k = d; k < 3; k++) {
+      g.c0[k] = 0;
+      g.nc[k] = 1;
+    }
+    GP_REQUIRE(cells <= (double)GP_NOALLOC_MAX_CELLS,
+               "gp_pattern_counts_noalloc: more than 2^20 cells (point extent over core radius too large)");
+    const int64_t ncells = (int64_t)cells;
+    int64_t* cell_start = cv.take<int64_t>(ncells + 1);
+    k_cell_keys<<<grid_for(n, 256), 256, 0, st>>>(U, n, g, keys, vals);
+    GP_CHECK_LAUNCH(ctx);
+    radix_sort_pairs(ctx, keys, vals, n, 0, bits_for((uint64_t)ncells), sort_tmp);
+    k_cell_start<<<grid_for(n + 1, 256), 256, 0, st>>>(keys, n, ncells, cell_start);
+    GP_CHECK_LAUNCH(ctx);
+    k_gather_sorted<<<grid_for(n, 256), 256, 0, st>>>(U, vals, n, d, Us, cell_perm, keys, key_of);
+    GP_CHECK_LAUNCH(ctx);
+    k_pattern<false><<<grid_for(n, 128), 128, 0, st>>>(Us, cell_perm, cell_start, n, g, d_counts, nullptr, nullptr);
+    GP_CHECK_LAUNCH(ctx);
+    ctx->err.clear();
+    return GP_OK;
+  } catch (const GpError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
