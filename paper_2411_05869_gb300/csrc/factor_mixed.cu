@@ -228,10 +228,13 @@ __global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __re
   }
 }
 
-// Trailing update of block column kb on the tensor cores: one CTA per 128 x 128 lower-triangular tile
-// (I >= J) of the rows/columns after the block column; K = the block column's width.
+// Trailing updates on the tensor cores, one CTA per 128 x 128 tile, F[i, j] -= sum_{l in K} L[i, l] L[j, l]
+// for j <= i. Modes (block column kb, 256-column group [g0, gend) containing it):
+//   0: rows/columns after the block column, lower-triangular tiles, K = the block column;
+//   1: intra-group: rows >= c1 x columns [c1, gend), rectangular tiles, K = the block column;
+//   2: group end: rows/columns >= gend, lower-triangular tiles, K = the whole group [g0, gend).
 __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                                   int nfront, int kb, DevPlan dp, float* __restrict__ p32,
+                                                   int nfront, int kb, int mode, DevPlan dp, float* __restrict__ p32,
                                                    double* __restrict__ dg, float* __restrict__ u32, int64_t P32E,
                                                    int64_t DE, int64_t UE, int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -246,17 +249,34 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
   int b = blockIdx.y;
   MixFront fr = mix_front(dp, s, p32 + (int64_t)b * P32E, dg + (int64_t)b * DE, u32 + (int64_t)b * UE);
   const int c0 = kb * T, bw = min(T, fr.w - c0), c1 = c0 + bw;
+  const int g0 = (kb / GP_GROUP) * GP_GROUP * T, gend = min(g0 + GP_GROUP * T, fr.w);
   int64_t loc = t - pre[fi];
-  int64_t I = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
-  while ((I + 1) * (I + 2) / 2 <= loc) I++;
-  while (I * (I + 1) / 2 > loc) I--;
-  int64_t J = loc - I * (I + 1) / 2;
-  const int64_t i0 = c1 + I * 128, j0 = c1 + J * 128;
+  int64_t I, J, base, jlim;
+  int K, kc;
+  if (mode == 1) {
+    const int64_t ntc = (gend - c1 + 127) / 128;
+    I = loc / ntc;
+    J = loc % ntc;
+    base = c1;
+    jlim = gend;
+    K = bw;
+    kc = c0;
+  } else {
+    I = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= loc) I++;
+    while (I * (I + 1) / 2 > loc) I--;
+    J = loc - I * (I + 1) / 2;
+    base = mode == 2 ? gend : c1;
+    jlim = fr.m;
+    K = mode == 2 ? gend - g0 : bw;
+    kc = mode == 2 ? g0 : c0;
+  }
+  const int64_t i0 = base + I * 128, j0 = base + J * 128;
   {
     int q = threadIdx.x;
     int64_t ia = i0 + q, jb = j0 + q;
-    arows[q] = ia < fr.m ? fr.P + ia * fr.ldw + c0 : nullptr;
-    brows[q] = jb < fr.m ? fr.P + jb * fr.ldw + c0 : nullptr;
+    arows[q] = ia < fr.m ? fr.P + ia * fr.ldw + kc : nullptr;
+    brows[q] = jb < jlim ? fr.P + jb * fr.ldw + kc : nullptr;
   }
   if (threadIdx.x == 0) {
     tcg::mbar_init(&bars[0], 1);
@@ -268,7 +288,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
   __syncthreads();
   tcg::tc_fence_after();
   const uint32_t tmem = *tslot;
-  bool ok = tcg::tile_mma_split3(smem, arows, brows, bw, tmem);
+  bool ok = tcg::tile_mma_split3(smem, arows, brows, K, tmem);
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Epilogue: TMEM (thread = row) -> shared tile (XOR-swizzled by row so neither side has bank conflicts)
@@ -299,7 +319,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ f
       const int64_t i = i0 + rr, j = j0 + c;
       pf[e] = nullptr;
       pd[e] = nullptr;
-      if (i < fr.m && j <= i) {
+      if (i < fr.m && j <= i && j < jlim) {
         av[e] = S[rr * 128 + (c ^ (rr & 31))];
         if (j >= fr.w) pf[e] = fr.Uu + (i - fr.w) * fr.r + (j - fr.w);
         else if (in_diag(fr, i, j)) pd[e] = diag_at(fr, i, j);
@@ -428,10 +448,19 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                                                                    f->panels32, f->diag, P32E, DE);
         GP_CHECK_LAUNCH(ctx);
       }
-      if (stp.upd128_total > 0) {
-        ProfScope ps_(ctx, KC_UPDATE, B * stp.upd_flops);
-        k_update_tc<<<dim3((unsigned)stp.upd128_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
-            fronts, pre128, stp.nfront, stp.kb, dp, f->panels32, f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
+      (void)pre128;
+      if (stp.intra_total > 0) {   // this block's update of the rest of its 256-column group
+        ProfScope ps_(ctx, KC_UPDATE, B * stp.intra_flops);
+        k_update_tc<<<dim3((unsigned)stp.intra_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
+            dp.upd_fronts + stp.intra_off, dp.upd_pre + stp.intra_pre_off, stp.n_intra, stp.kb, 1, dp, f->panels32,
+            f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
+        GP_CHECK_LAUNCH(ctx);
+      }
+      if (stp.group_total > 0) {   // fronts whose group ends here: the deferred update with K = group width
+        ProfScope ps_(ctx, KC_UPDATE, B * stp.group_flops);
+        k_update_tc<<<dim3((unsigned)stp.group_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
+            dp.upd_fronts + stp.group_off, dp.upd_pre + stp.group_pre_off, stp.n_group, stp.kb, 2, dp, f->panels32,
+            f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
         GP_CHECK_LAUNCH(ctx);
       }
     }

@@ -240,6 +240,8 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
     dp.step_pre128 = upload(ctx, ps->bufs, sp.step_pre128);
     dp.large_kb = upload(ctx, ps->bufs, sp.large_kb);
+    dp.upd_fronts = upload(ctx, ps->bufs, sp.upd_fronts);
+    dp.upd_pre = upload(ctx, ps->bufs, sp.upd_pre);
     compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });
