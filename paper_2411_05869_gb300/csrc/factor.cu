@@ -132,8 +132,11 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
 
 // POTRF of the diagonal block of block column kb, one CTA per large front.
 __global__ void k_potrf(const int32_t* __restrict__ fronts, int kb, DevPlan dp, double* __restrict__ panels,
-                        double* __restrict__ upd, int64_t PE, int64_t UE, int32_t* __restrict__ notpd) {
-  __shared__ double A[T * T];
+                        double* __restrict__ upd, int64_t PE, int64_t UE, int32_t* __restrict__ notpd,
+                        double* __restrict__ dinv, int64_t DE) {
+  extern __shared__ double sm64[];
+  double* A = sm64;           // factor, column-major
+  double* R = sm64 + T * T;   // factor, row-major (input of the inverse)
   __shared__ double piv;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
@@ -161,10 +164,16 @@ __global__ void k_potrf(const int32_t* __restrict__ fronts, int kb, DevPlan dp, 
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < bw * bw; t += blockDim.x) {
-    int i = t % bw, j = t / bw;
-    if (i >= j) fr.P[(int64_t)(c0 + j) * fr.m + c0 + i] = A[j * T + i];
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+    int i = t % T, j = t / T;
+    bool lower = i >= j && i < bw;
+    if (lower) fr.P[(int64_t)(c0 + j) * fr.m + c0 + i] = A[j * T + i];
+    R[i * T + j] = lower ? A[j * T + i] : 0.0;
   }
+  __syncthreads();
+  tri_inverse_lower(R, A, bw);   // inverse of the diagonal block (row-major) for the solves
+  double* DI = dinv + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) DI[t] = A[t];
 }
 
 // TRSM: rows below the diagonal block (within the panel) times L11^{-T}; one CTA per 64-row tile.
@@ -275,6 +284,7 @@ void set_attrs() {
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
   GP_CUDA(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
   GP_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
+  GP_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
   g_attrs_set = true;
 }
 
@@ -286,8 +296,23 @@ __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
 }  // namespace
 
 void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f);
+void set_attrs_mixed();
+static void factor_body(gp_ctx* ctx, gp_factor_t* f);
 
+// A3, A4, A7: the launch sequence is fixed by the plan, so it is captured once per factor as a CUDA graph
+// and replayed (theta only changes the device-side parameter block).
 void factor_run(gp_ctx* ctx, gp_factor_t* f) {
+  set_attrs();
+  set_attrs_mixed();
+  if (!use_graphs(ctx)) {
+    factor_body(ctx, f);
+    return;
+  }
+  if (!f->gx_factor) f->gx_factor = capture_graph(ctx, [&] { factor_body(ctx, f); }, &f->n_factor);
+  replay_graph(ctx, f->gx_factor, f->n_factor);
+}
+
+static void factor_body(gp_ctx* ctx, gp_factor_t* f) {
   if (f->prec == GP_MIXED) {
     factor_run_mixed(ctx, f);
     return;
@@ -332,7 +357,8 @@ void factor_run(gp_ctx* ctx, gp_factor_t* f) {
       const int64_t* pre_up = pre_tr + stp.nfront + 1;
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf<<<dim3(stp.nfront, B), 128, 0, st>>>(fronts, stp.kb, dp, f->panels, f->upd, PE, UE, f->notpd);
+        k_potrf<<<dim3(stp.nfront, B), 128, 2 * T * T * sizeof(double), st>>>(
+            fronts, stp.kb, dp, f->panels, f->upd, PE, UE, f->notpd, f->dinv, sp.diag_entries);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.trsm_total > 0) {

@@ -159,12 +159,15 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
 
 // FP64 POTRF of diagonal tile kb.
 __global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp, double* __restrict__ dg, int64_t DE,
-                          int32_t* __restrict__ notpd) {
-  __shared__ double A[T * T];
+                          int32_t* __restrict__ notpd, double* __restrict__ dinv) {
+  extern __shared__ double sm64[];
+  double* A = sm64;
+  double* Inv = sm64 + T * T;
   __shared__ double piv;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  double* DI = dinv + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], bw = min(T, w - kb * T);
   const int32_t first = dp.sn_first[s] + kb * T;
   for (int t = threadIdx.x; t < T * T; t += blockDim.x) A[t] = D[t];   // [i][j] row-major
@@ -186,7 +189,11 @@ __global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < T * T; t += blockDim.x) D[t] = A[t];
+  tri_inverse_lower(A, Inv, bw);   // for the solves: a matrix-vector product per block instead of a substitution
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+    D[t] = A[t];
+    DI[t] = Inv[t];
+  }
 }
 
 // FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile, one thread per row).
@@ -342,6 +349,7 @@ void set_attrs() {
   GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
   GP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES + 1024));
+  GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
   g_attrs = true;
 }
 
@@ -392,6 +400,8 @@ __global__ void k_dest32(const int64_t* __restrict__ rowptr, const int32_t* __re
 
 }  // namespace
 
+void set_attrs_mixed() { set_attrs(); }
+
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps) {
   ps->dest32 = dalloc<int64_t>(ctx, ps->bufs, ps->nnz);
   k_dest32<<<grid_for(ps->n * 32, 256), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, ps->n, ps->pinv, ps->dp,
@@ -439,7 +449,8 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       const int64_t* pre128 = dp.step_pre128 + stp.pre128_off;
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf64<<<dim3(stp.nfront, B), 128, 0, st>>>(fronts, stp.kb, dp, f->diag, DE, f->notpd);
+        k_potrf64<<<dim3(stp.nfront, B), 128, 2 * T * T * sizeof(double), st>>>(fronts, stp.kb, dp, f->diag, DE,
+                                                                               f->notpd, f->dinv);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.trsm_total > 0) {

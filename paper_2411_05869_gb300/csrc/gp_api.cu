@@ -351,6 +351,8 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
     f->notpd = dalloc<int32_t>(ctx, f->bufs, B);
     f->alpha = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
+    f->dinv = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
+    f->rhs = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
     f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
     f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);
     f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
@@ -360,6 +362,8 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
   });
   if (st != GP_OK) {
     dev_free_all(ctx, f->bufs);
+    for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor})
+      if (g) cudaGraphExecDestroy(g);
     delete f;
     return st;
   }
@@ -387,6 +391,8 @@ extern "C" void gp_factor_free(gp_factor_t* f) {
     cudaSetDevice(ctx->device);
     dev_free_all(ctx, f->bufs);
   }
+  for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor})
+    if (g) cudaGraphExecDestroy(g);
   delete f;
   if (ctx) ctx_release(ctx);
 }

@@ -247,6 +247,11 @@ struct gp_factor_s {
   float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
   double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
   double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n
+  double* dinv = nullptr;       // FP64 inverses of the 64 x 64 diagonal blocks (row-major), B x diag_entries
+  double* rhs = nullptr;        // B x n copy of the caller's residual (the solve graph reads it from here)
+  // CUDA graphs of the fixed launch sequences, captured on first use and replayed (launch counts per replay)
+  cudaGraphExec_t gx_factor = nullptr, gx_solve = nullptr, gx_cor = nullptr;
+  int64_t n_factor = 0, n_solve = 0, n_cor = 0;
   int32_t* tiles_err = nullptr; // GP_MIXED: set when a bounded tensor-core wait ran out
   double* upd = nullptr;        // B x update_entries
   float* upd32 = nullptr;
@@ -295,6 +300,64 @@ void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 #define DIAG_FLAG ((int64_t)1 << 62)
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Graph replay is used on an explicit (non-legacy) stream when the launch profiler is off.
+inline bool use_graphs(const gp_ctx* ctx) { return ctx->stream != nullptr && !ctx->prof; }
+
+// Capture the launches `body` issues on the context stream into an executable graph; *nlaunch receives the
+// number of kernels captured (the context's counter is restored: replays add it per launch).
+template <class F>
+cudaGraphExec_t capture_graph(gp_ctx* ctx, F&& body, int64_t* nlaunch) {
+  const int64_t l0 = ctx->launches;
+  GP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    body();
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(ctx->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ctx->launches = l0;
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  GP_CUDA(cudaStreamEndCapture(ctx->stream, &g));
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) throw GpError{GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+  *nlaunch = ctx->launches - l0;
+  ctx->launches = l0;
+  return ex;
+}
+
+inline void replay_graph(gp_ctx* ctx, cudaGraphExec_t ex, int64_t nlaunch) {
+  GP_CUDA(cudaGraphLaunch(ex, ctx->stream));
+  ctx->launches += nlaunch;
+}
+
+// Inverse of a bw x bw lower-triangular block (row-major, leading dimension GP_TILE, shared memory) into Inv
+// (same layout), one column per thread: Inv[j][j] = 1/A[j][j], Inv[i][j] = -(sum_{j<=k<i} A[i][k] Inv[k][j]) / A[i][i].
+// Entries outside the lower bw x bw triangle are set to zero. Ends with a barrier.
+__device__ __forceinline__ void tri_inverse_lower(const double* A, double* Inv, int bw) {
+  constexpr int T = GP_TILE;
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) Inv[q] = 0.0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < bw; j += blockDim.x) {
+    Inv[j * T + j] = 1.0 / A[j * T + j];
+    for (int i = j + 1; i < bw; i++) {
+      double s0 = 0.0, s1 = 0.0;
+      int k = j;
+      for (; k + 1 < i; k += 2) {
+        s0 += A[i * T + k] * Inv[k * T + j];
+        s1 += A[i * T + k + 1] * Inv[(k + 1) * T + j];
+      }
+      if (k < i) s0 += A[i * T + k] * Inv[k * T + j];
+      Inv[i * T + j] = -(s0 + s1) / A[i * T + i];
+    }
+  }
+  __syncthreads();
+}
 
 inline unsigned grid_for(int64_t work, int per_block) {
   int64_t g = (work + per_block - 1) / per_block;

@@ -8,7 +8,8 @@
 // child's relative indices (children in order), then x = L11^{-1} f_1 and f_2 -= L21 x; f_2 is the update
 // vector handed to the parent. Backward (levels descending): t = x - L21^T alpha'(rows below), then
 // L11^T z = t. Fronts of order <= 96 use one CTA; larger ones advance 64 columns per launch, every CTA
-// re-solving the 64 x 64 diagonal block and applying it to its own 64-row (or 64-column) tile.
+// multiplying by the inverted 64 x 64 diagonal block (formed in FP64 by the factorization) and applying the
+// result to its own 64-row (or 64-column) tile.
 // The kernels read the factor through an accessor: FP64 column-major panels (GP_FP64) or FP32 row-major
 // panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the quadratic form is |L^{-1} P r|^2; in GP_MIXED
 // alpha is refined in FP64 (residual r - C alpha from the FP64 CSR values, correction through the same
@@ -42,6 +43,11 @@ struct StoreF64 {
   static constexpr bool kRowMajor = false;
   const double* P;
   int64_t PE;
+  const double* DI;   // inverses of the 64 x 64 diagonal blocks
+  int64_t DE;
+  __device__ __forceinline__ const double* inv(const DevPlan& dp, int32_t s, int b) const {
+    return DI + (int64_t)b * DE + dp.doff[s];
+  }
   using Acc = AccF64;
   __device__ __forceinline__ AccF64 acc(const DevPlan& dp, int32_t s, int b) const {
     return AccF64{P + (int64_t)b * PE + dp.loff[s], (int64_t)dp.w[s] + dp.r[s]};
@@ -52,6 +58,10 @@ struct StoreMix {
   const float* P;
   const double* D;
   int64_t P32E, DE;
+  const double* DI;
+  __device__ __forceinline__ const double* inv(const DevPlan& dp, int32_t s, int b) const {
+    return DI + (int64_t)b * DE + dp.doff[s];
+  }
   using Acc = AccMix;
   __device__ __forceinline__ AccMix acc(const DevPlan& dp, int32_t s, int b) const {
     return AccMix{P + (int64_t)b * P32E + dp.loff32[s], D + (int64_t)b * DE + dp.doff[s], dp.w[s], dp.ldw[s]};
@@ -116,78 +126,45 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// Solve the bw x bw lower block L_JJ x = t in shared memory (warp 0); x overwrites t.
-__device__ __forceinline__ void block_lower_solve(const double* L, double* t, int bw) {
-  if (threadIdx.x < 32) {
-    for (int j = 0; j < bw; j++) {
-      double x = t[j] / L[j * T + j];
-      __syncwarp();
-      for (int i = j + 1 + threadIdx.x; i < bw; i += 32) t[i] -= L[j * T + i] * x;
-      if (threadIdx.x == 0) t[j] = x;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-// Solve L_JJ^T z = t (upper triangular) in shared memory (warp 0); z overwrites t.
-__device__ __forceinline__ void block_upper_solve(const double* L, double* t, int bw) {
-  if (threadIdx.x < 32) {
-    for (int j = bw - 1; j >= 0; j--) {
-      double z = t[j] / L[j * T + j];
-      __syncwarp();
-      for (int k = threadIdx.x; k < j; k += 32) t[k] -= L[k * T + j] * z;
-      if (threadIdx.x == 0) t[j] = z;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
+// Load the inverse of diagonal block kb (row-major 64 x 64, FP64) into shared memory with a padded stride.
+__device__ __forceinline__ void load_inverse(const double* Inv, double* Li) {
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) Li[(q / T) * (T + 1) + (q % T)] = Inv[q];
 }
 
-// Forward, block column kb of every large front of a step: x_J = L_JJ^{-1} f_J (one CTA per front, written
-// to the front vector and to x) ...
+// Forward, block column kb of every large front of a step, one launch: every CTA forms x_J = inv(L_JJ) f_J
+// (a 64 x 64 product with the inverted diagonal block); tasks [0, nfront) write x_J to x (the front vector's
+// block stays untouched, others read it), the rest (64-row tile prefix) apply f_i -= L[i, J] x_J to one tile.
+// Row-major panels: a half-warp reads one row's 64 entries as 16 float4; column-major: thread per row.
 template <class St>
-__global__ void k_fwd_tri(const int32_t* __restrict__ fronts, int kb, DevPlan dp, St store, double* __restrict__ work,
-                          int64_t ws, int64_t xv_off) {
-  __shared__ double L[T * T];
-  __shared__ double x[T];
-  int32_t s = fronts[blockIdx.x];
-  int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
-  const int w = dp.w[s];
-  const int c0 = kb * T, bw = min(T, w - c0);
-  for (int q = threadIdx.x; q < bw * bw; q += blockDim.x) {
-    int i = q % bw, j = q / bw;
-    L[j * T + i] = i >= j ? A.L(c0 + i, c0 + j) : 0.0;
-  }
-  for (int q = threadIdx.x; q < bw; q += blockDim.x) x[q] = fv[c0 + q];
-  __syncthreads();
-  block_lower_solve(L, x, bw);
-  double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
-  for (int q = threadIdx.x; q < bw; q += blockDim.x) {
-    fv[c0 + q] = x[q];
-    xv[c0 + q] = x[q];
-  }
-}
-
-// ... then f_i -= L[i, J] x_J for the rows below the block, one CTA per 64-row tile (tile prefix of the
-// step). Row-major panels: a half-warp reads one row's 64 entries as 16 float4; column-major: thread per row.
-template <class St>
-__global__ void k_fwd_gemv(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                           DevPlan dp, St store, double* __restrict__ work, int64_t ws) {
-  __shared__ double x[T];
-  int64_t t = blockIdx.x;
-  int fi = find_front(pre, nfront, t);
-  int32_t s = fronts[fi];
-  int b = blockIdx.y;
+__global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
+                           DevPlan dp, St store, double* __restrict__ work, int64_t ws, int64_t xv_off) {
+  __shared__ double Li[T * (T + 1)];
+  __shared__ double fb[T], x[T];
+  const int64_t t = blockIdx.x;
+  const bool writer = t < nfront;
+  const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
   double* fv = work + (int64_t)b * ws + dp.frow_off[s];
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
-  const int64_t r0 = c1 + (t - pre[fi]) * T, rend = imin64(r0 + T, m);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) x[q] = q < bw ? fv[c0 + q] : 0.0;
+  load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
+  for (int q = threadIdx.x; q < T; q += blockDim.x) fb[q] = q < bw ? fv[c0 + q] : 0.0;
   __syncthreads();
+  for (int q = threadIdx.x; q < T; q += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l <= q; l++) acc += Li[q * (T + 1) + l] * fb[l];
+    x[q] = q < bw ? acc : 0.0;
+  }
+  __syncthreads();
+  if (writer) {
+    double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
+    for (int q = threadIdx.x; q < bw; q += blockDim.x) xv[c0 + q] = x[q];
+    return;
+  }
+  const int64_t r0 = c1 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
   if constexpr (St::kRowMajor) {
     const int lane = threadIdx.x & 31, l16 = lane & 15, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int l = l16 * 4;
@@ -215,8 +192,8 @@ __global__ void k_fwd_gemv(const int32_t* __restrict__ fronts, const int64_t* __
   }
 }
 
-// t_j = x_j - sum_{a < r} L[w + a, j] alpha'(R_s[a]) for every column j of the front (warp per column);
-// small fronts then finish L11^T z = t in the same CTA and write alpha'.
+// Backward, small fronts (one CTA each): t_j = x_j - sum_{a < r} L[w + a, j] alpha'(R_s[a]) (warp per
+// column), then L11^T z = t by substitution; z is written to alpha'.
 template <class St>
 __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, DevPlan dp, St store,
                            double* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
@@ -290,51 +267,40 @@ __global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32
   }
 }
 
-// Backward, block column kb of every large front of a step: z_J = L_JJ^{-T} t_J, one CTA per front ...
+// Backward, block column kb of every large front of a step, one launch: every CTA forms
+// z_J = inv(L_JJ)^T t_J; task 0 of a front writes z_J to alpha', tasks 1..kb apply t_k -= L[J, k]^T z_J to
+// one 64-column tile of the earlier columns k < c0.
 template <class St>
-__global__ void k_bwd_tri(const int32_t* __restrict__ fronts, int kb, DevPlan dp, St store, double* __restrict__ work,
-                          int64_t ws, int64_t apv_off) {
-  __shared__ double L[T * T];
-  __shared__ double z[T];
-  int32_t s = fronts[blockIdx.x];
-  int b = blockIdx.y;
+__global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
+                           double* __restrict__ work, int64_t ws, int64_t apv_off) {
+  __shared__ double Li[T * (T + 1)];   // the inverse block, then (column-major path) the block's rows
+  __shared__ double tb[T], z[T];
+  const int64_t t = blockIdx.x;
+  const int fi = (int)(t / (kb + 1));
+  const int task = (int)(t % (kb + 1));
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
   double* W = work + (int64_t)b * ws;
   double* fv = W + dp.frow_off[s];
   const int w = dp.w[s];
   const int c0 = kb * T, bw = min(T, w - c0);
-  for (int q = threadIdx.x; q < bw * bw; q += blockDim.x) {
-    int i = q % bw, j = q / bw;
-    L[j * T + i] = i >= j ? A.L(c0 + i, c0 + j) : 0.0;
-  }
-  for (int q = threadIdx.x; q < bw; q += blockDim.x) z[q] = fv[c0 + q];
+  load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
+  for (int q = threadIdx.x; q < T; q += blockDim.x) tb[q] = q < bw ? fv[c0 + q] : 0.0;
   __syncthreads();
-  block_upper_solve(L, z, bw);
-  double* apv = W + apv_off;
-  const int32_t first = dp.sn_first[s];
-  for (int q = threadIdx.x; q < bw; q += blockDim.x) {
-    fv[c0 + q] = z[q];
-    apv[first + c0 + q] = z[q];
+  for (int q = threadIdx.x; q < T; q += blockDim.x) {   // z_q = sum_{l >= q} inv[l][q] t_l
+    double acc = 0.0;
+    for (int l = q; l < bw; l++) acc += Li[l * (T + 1) + q] * tb[l];
+    z[q] = q < bw ? acc : 0.0;
   }
-}
-
-// ... then t_k -= L[J, k]^T z_J for the earlier columns k < c0, one CTA per 64-column tile (kb per front).
-template <class St>
-__global__ void k_bwd_gemvt(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
-                            double* __restrict__ work, int64_t ws) {
-  __shared__ double z[T];
-  __shared__ double Lt[St::kRowMajor ? 1 : T * (T + 1)];
-  int64_t t = blockIdx.x;
-  int fi = (int)(t / kb);
-  const int k0 = (int)(t % kb) * T;   // columns [k0, k0 + 64) < c0
-  int32_t s = fronts[fi];
-  int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
-  const int w = dp.w[s];
-  const int c0 = kb * T, bw = min(T, w - c0);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) z[q] = q < bw ? fv[c0 + q] : 0.0;
   __syncthreads();
+  if (task == 0) {
+    double* apv = W + apv_off;
+    const int32_t first = dp.sn_first[s];
+    for (int q = threadIdx.x; q < bw; q += blockDim.x) apv[first + c0 + q] = z[q];
+    return;
+  }
+  const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
   if constexpr (St::kRowMajor) {
     for (int k = threadIdx.x; k < T; k += blockDim.x) {   // row c0 + l is contiguous over k
       double acc = 0.0;
@@ -342,7 +308,9 @@ __global__ void k_bwd_gemvt(const int32_t* __restrict__ fronts, int nfront, int 
       fv[k0 + k] -= acc;
     }
   } else {
-    for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {   // column k0 + k is contiguous over l
+    double* Lt = Li;   // reuse: the block's rows for the tile's columns, staged by columns (contiguous)
+    __syncthreads();
+    for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {
       int l = q % bw, k = q / bw;
       Lt[l * (T + 1) + k] = A.L(c0 + l, k0 + k);
     }
@@ -538,14 +506,10 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       GP_CHECK_LAUNCH(ctx);
     }
     for (const auto& stp : lv.steps) {
-      k_fwd_tri<St><<<dim3(stp.nfront, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.kb, dp, store, f->work,
-                                                        ws, xv_off);
+      k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 128, 0, st>>>(
+          dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, f->work, ws,
+          xv_off);
       GP_CHECK_LAUNCH(ctx);
-      if (stp.trsm_total > 0) {
-        k_fwd_gemv<St><<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(
-            dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, f->work, ws);
-        GP_CHECK_LAUNCH(ctx);
-      }
     }
   }
   if (partials) {
@@ -567,15 +531,9 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       GP_CHECK_LAUNCH(ctx);
       for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
         const auto& stp = lv.steps[q];
-        k_bwd_tri<St><<<dim3(stp.nfront, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.kb, dp, store, f->work,
-                                                          ws, apv_off);
+        k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 64, 0, st>>>(
+            dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, f->work, ws, apv_off);
         GP_CHECK_LAUNCH(ctx);
-        if (stp.kb > 0) {
-          int64_t tasks = (int64_t)stp.nfront * stp.kb;
-          k_bwd_gemvt<St><<<dim3((unsigned)tasks, B), 64, 0, st>>>(dp.large_fronts + stp.fr_off, stp.nfront, stp.kb,
-                                                                   dp, store, f->work, ws);
-          GP_CHECK_LAUNCH(ctx);
-        }
       }
     }
   }
@@ -600,6 +558,18 @@ void residual_impl(gp_ctx* ctx, gp_factor_t* f, const double* rhs, const double*
 
 }  // namespace
 
+// Run `body` directly, or through a CUDA graph captured on first use (the launch sequence depends only on
+// the plan; every pointer it uses belongs to the factor).
+template <class F>
+static void run_maybe_graph(gp_ctx* ctx, cudaGraphExec_t* gx, int64_t* nl, F&& body) {
+  if (!use_graphs(ctx)) {
+    body();
+    return;
+  }
+  if (!*gx) *gx = capture_graph(ctx, body, nl);
+  replay_graph(ctx, *gx, *nl);
+}
+
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err) {
   ProfScope ps_(ctx, KC_SOLVE);   // the whole solve (with refinement) as one timed span
   gp_pointset* ps = f->ps;
@@ -610,37 +580,45 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   double* sums = f->red + (size_t)B * f->red_stride;
   double* s_log = sums;            // [2b] = sum log L_jj, [2b+1] = sum x^2
   double* s_quad = sums + 2 * B;   // [2b+1] = r . alpha (mixed)
+  // the solve graph reads the right-hand side from the factor's own buffer
+  GP_CUDA(cudaMemcpyAsync(f->rhs, d_resid, sizeof(double) * (size_t)B * n, cudaMemcpyDeviceToDevice, ctx->stream));
   if (f->prec == GP_FP64) {
-    StoreF64 store{f->panels, ps->sp.panel_entries};
-    solve_impl(ctx, f, store, d_resid, f->alpha, true);
-    k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
-    GP_CHECK_LAUNCH(ctx);
+    StoreF64 store{f->panels, ps->sp.panel_entries, f->dinv, ps->sp.diag_entries};
+    run_maybe_graph(ctx, &f->gx_solve, &f->n_solve, [&] {
+      solve_impl(ctx, f, store, f->rhs, f->alpha, true);
+      k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
+      GP_CHECK_LAUNCH(ctx);
+    });
     k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_log, f->notpd, nullptr, d_out);
     GP_CHECK_LAUNCH(ctx);
-    if (d_err) residual_impl(ctx, f, d_resid, f->alpha, nullptr, d_err, nullptr);
+    if (d_err) residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err, nullptr);
     return;
   }
-  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries};
-  solve_impl(ctx, f, store, d_resid, f->alpha, true);
-  k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
-  GP_CHECK_LAUNCH(ctx);
+  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries, f->dinv};
+  run_maybe_graph(ctx, &f->gx_solve, &f->n_solve, [&] {
+    solve_impl(ctx, f, store, f->rhs, f->alpha, true);
+    k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
+    GP_CHECK_LAUNCH(ctx);
+  });
   // A11: FP64 iterative refinement of alpha
   double* res = f->delta;                       // B x n residual
   double* cor = f->delta + (size_t)B * n;       // B x n correction
   double* errv = f->red;                        // B relative residuals (partials are consumed already)
   std::vector<double> herr(B);
   for (int it = 0; it < 10; it++) {
-    residual_impl(ctx, f, d_resid, f->alpha, res, errv, nullptr);
+    residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
     d2h(ctx, herr.data(), errv, B);
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
     double worst = 0.0;
     for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
     if (worst <= 1e-12) break;
-    solve_impl(ctx, f, store, res, cor, false);
-    k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);
-    GP_CHECK_LAUNCH(ctx);
+    run_maybe_graph(ctx, &f->gx_cor, &f->n_cor, [&] {
+      solve_impl(ctx, f, store, res, cor, false);
+      k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);
+      GP_CHECK_LAUNCH(ctx);
+    });
   }
-  residual_impl(ctx, f, d_resid, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
+  residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
   k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
   GP_CHECK_LAUNCH(ctx);
 }

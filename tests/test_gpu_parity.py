@@ -185,3 +185,29 @@ def test_mixed_batched_each_proposal(case, ctx):
         ref = oracle.sparse_loglik(hp, w.X, case["rp"], case["col"], case["perm"], w.resid)
         assert abs(ll[b] - ref["loglik"]) <= MIXED_RTOL * abs(ref["loglik"]), (b, ll[b], ref["loglik"])
     f.free()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_launches(case, ctx, precision):
+    """On an explicit stream the factor and solve launch sequences are captured once as CUDA graphs and
+    replayed; results must equal the directly launched ones (default stream) bit for bit."""
+    from paper_2411_05869_gb300 import gp
+    w, ps = case["w"], case["ps"]
+    rng = np.random.default_rng(11)
+    th = [synth.perturb(rng, w.hyper) for _ in range(2)]
+    r = _dev(np.stack([w.resid, 0.5 * w.resid]))
+    f0 = ctx.factor(ps, th, precision)
+    direct = f0.loglik(r).cpu().numpy().copy()
+    s = torch.cuda.Stream()
+    ctx2 = gp.Context(0, stream=s)
+    with torch.cuda.stream(s):
+        X2 = _dev(w.X)
+        ps2 = ctx2.assemble(X2, w.hyper.core_radius)
+        f2 = ctx2.factor(ps2, th, precision)      # captures and replays the factor graph
+        a = f2.loglik(r).cpu().numpy().copy()     # captures and replays the solve graph(s)
+        f2.update(th)                             # replays
+        b = f2.loglik(r).cpu().numpy().copy()
+    s.synchronize()
+    assert a.tobytes() == direct.tobytes() and b.tobytes() == direct.tobytes()
+    f2.free()
+    f0.free()
