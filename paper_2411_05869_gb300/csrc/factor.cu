@@ -171,7 +171,7 @@ __global__ void k_potrf(const int32_t* __restrict__ fronts, int kb, DevPlan dp, 
     R[i * T + j] = lower ? A[j * T + i] : 0.0;
   }
   __syncthreads();
-  tri_inverse_lower(R, A, bw);   // inverse of the diagonal block (row-major) for the solves
+  tri_inverse_lower<double>(R, A, bw);   // inverse of the diagonal block (row-major) for the solves
   double* DI = dinv + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   for (int t = threadIdx.x; t < T * T; t += blockDim.x) DI[t] = A[t];
 }

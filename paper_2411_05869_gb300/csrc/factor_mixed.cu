@@ -189,10 +189,13 @@ __global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp
     }
     __syncthreads();
   }
-  tri_inverse_lower(A, Inv, bw);   // for the solves: a matrix-vector product per block instead of a substitution
+  // inverse for the solves (a matrix-vector product per block instead of a substitution); FP32 suffices here
+  // because the mixed solve only preconditions the FP64 refinement
+  float* Invf = reinterpret_cast<float*>(Inv);
+  tri_inverse_lower<float>(A, Invf, bw);
   for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
     D[t] = A[t];
-    DI[t] = Inv[t];
+    DI[t] = (double)Invf[t];
   }
 }
 

@@ -339,21 +339,24 @@ inline void replay_graph(gp_ctx* ctx, cudaGraphExec_t ex, int64_t nlaunch) {
 // Inverse of a bw x bw lower-triangular block (row-major, leading dimension GP_TILE, shared memory) into Inv
 // (same layout), one column per thread: Inv[j][j] = 1/A[j][j], Inv[i][j] = -(sum_{j<=k<i} A[i][k] Inv[k][j]) / A[i][i].
 // Entries outside the lower bw x bw triangle are set to zero. Ends with a barrier.
-__device__ __forceinline__ void tri_inverse_lower(const double* A, double* Inv, int bw) {
+// R is the arithmetic type: double for the FP64 path; float where the result only preconditions an FP64
+// refinement (the mixed path), since FP64 instructions issue at a small fraction of the FP32 rate on GB300.
+template <class R>
+__device__ __forceinline__ void tri_inverse_lower(const double* A, R* Inv, int bw) {
   constexpr int T = GP_TILE;
-  for (int q = threadIdx.x; q < T * T; q += blockDim.x) Inv[q] = 0.0;
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) Inv[q] = R(0);
   __syncthreads();
   for (int j = threadIdx.x; j < bw; j += blockDim.x) {
-    Inv[j * T + j] = 1.0 / A[j * T + j];
+    Inv[j * T + j] = R(1) / R(A[j * T + j]);
     for (int i = j + 1; i < bw; i++) {
-      double s0 = 0.0, s1 = 0.0;
+      R s0 = R(0), s1 = R(0);
       int k = j;
       for (; k + 1 < i; k += 2) {
-        s0 += A[i * T + k] * Inv[k * T + j];
-        s1 += A[i * T + k + 1] * Inv[(k + 1) * T + j];
+        s0 += R(A[i * T + k]) * Inv[k * T + j];
+        s1 += R(A[i * T + k + 1]) * Inv[(k + 1) * T + j];
       }
-      if (k < i) s0 += A[i * T + k] * Inv[k * T + j];
-      Inv[i * T + j] = -(s0 + s1) / A[i * T + i];
+      if (k < i) s0 += R(A[i * T + k]) * Inv[k * T + j];
+      Inv[i * T + j] = -(s0 + s1) / R(A[i * T + i]);
     }
   }
   __syncthreads();
