@@ -157,45 +157,116 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// FP64 POTRF of diagonal tile kb.
-__global__ void k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp, double* __restrict__ dg, int64_t DE,
-                          int32_t* __restrict__ notpd, double* __restrict__ dinv) {
+// FP64 POTRF of diagonal tile kb, right-looking in shared memory (row stride T + 1, so walks down a column are
+// free of bank conflicts). The pivots d_k = L_kk^2 stay unscaled during the elimination: step k forms the scaled
+// column s_j = a_jk / d_k once, then a_ij -= a_ik s_j over the trailing triangle k < j <= i. That triangle is
+// numbered column by column from the last column, so step k's work is a prefix of one fixed list, spread evenly
+// over all threads, and the entry (k + 1, k + 1) closes the prefix; its thread forms the next reciprocal 1 / d_{k+1}.
+// Square roots and the column scaling L_ik = a_ik / sqrt(d_k) follow in one parallel pass, then the FP32 inverse
+// of L for the solves. GB300 issues FP64 at a small fraction of its FP32 rate, so the kernel keeps FP64 to the
+// elimination itself.
+constexpr int PT = T + 1;
+constexpr int POTRF_THREADS = 256;
+constexpr size_t POTRF_SMEM = (size_t)T * PT * sizeof(double) + (size_t)T * PT * sizeof(float) +
+                              (size_t)T * T * sizeof(float) + (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
+
+__device__ __forceinline__ double pivot_recip(double* a, int32_t* notpd, int32_t col) {
+  double d = *a;
+  if (!(d > 0.0)) {
+    atomicMin(notpd, col);
+    d = 1.0;
+    *a = d;
+  }
+  return 1.0 / d;
+}
+
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
+                                                           double* __restrict__ dg, int64_t DE,
+                                                           int32_t* __restrict__ notpd, double* __restrict__ dinv) {
   extern __shared__ double sm64[];
-  double* A = sm64;
-  double* Inv = sm64 + T * T;
-  __shared__ double piv;
+  double* A = sm64;                                      // T x PT
+  float* Lf = reinterpret_cast<float*>(A + T * PT);     // T x PT, FP32 copy of L
+  float* Inv = Lf + T * PT;                              // T x T, row-major
+  uint16_t* tab = reinterpret_cast<uint16_t*>(Inv + T * T);
+  __shared__ double rd[T];   // 1 / d_k
+  __shared__ double sc[T];   // scaled column of the current step; later 1 / L_kk
+  __shared__ float rf[T];    // 1 / L_kk in FP32
+  const int tid = threadIdx.x;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   double* DI = dinv + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], bw = min(T, w - kb * T);
   const int32_t first = dp.sn_first[s] + kb * T;
-  for (int t = threadIdx.x; t < T * T; t += blockDim.x) A[t] = D[t];   // [i][j] row-major
+  int32_t* flag = notpd + b;
+  for (int t = tid; t < T * T; t += POTRF_THREADS) A[(t >> 6) * PT + (t & 63)] = D[t];
+  // trailing-entry list for this bw: column j = bw - 1 - c holds rows j .. bw - 1 at offsets c (c + 1) / 2 ..
+  const int ne = bw * (bw - 1) / 2;
+  for (int e = tid; e < ne; e += POTRF_THREADS) {
+    int c = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((c + 1) * (c + 2) / 2 <= e) c++;
+    while (c * (c + 1) / 2 > e) c--;
+    const int j = bw - 1 - c, i = j + (e - c * (c + 1) / 2);
+    tab[e] = (uint16_t)((i << 8) | j);
+  }
   __syncthreads();
-  for (int k = 0; k < bw; k++) {
-    if (threadIdx.x == 0) {
-      piv = checked_sqrt(A[k * T + k], notpd + b, first + k);
-      A[k * T + k] = piv;
-    }
+  if (tid == 0) rd[0] = pivot_recip(A, flag, first);
+  __syncthreads();
+  for (int k = 0; k + 1 < bw; k++) {
+    if (tid < bw - 1 - k) sc[k + 1 + tid] = A[(k + 1 + tid) * PT + k] * rd[k];
     __syncthreads();
-    double inv = 1.0 / piv;
-    for (int i = k + 1 + threadIdx.x; i < bw; i += blockDim.x) A[i * T + k] *= inv;
-    __syncthreads();
-    // trailing lower triangle: 8 rows x 16 columns of threads (blockDim = 128)
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int i = k + 1 + ty; i < bw; i += 8) {
-      const double aik = A[i * T + k];
-      for (int j = k + 1 + tx; j <= i; j += 16) A[i * T + j] -= aik * A[j * T + k];
+    const int cnt = (bw - 1 - k) * (bw - k) / 2;
+    for (int e = tid; e < cnt; e += POTRF_THREADS) {
+      const int ij = tab[e], i = ij >> 8, j = ij & 255;
+      const double v = A[i * PT + j] - A[i * PT + k] * sc[j];
+      A[i * PT + j] = v;
+      if (j == k + 1 && i == j) rd[k + 1] = pivot_recip(A + i * PT + j, flag, first + k + 1);
     }
     __syncthreads();
   }
-  // inverse for the solves (a matrix-vector product per block instead of a substitution); FP32 suffices here
-  // because the mixed solve only preconditions the FP64 refinement
-  float* Invf = reinterpret_cast<float*>(Inv);
-  tri_inverse_lower<float>(A, Invf, bw);
-  for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
-    D[t] = A[t];
-    DI[t] = (double)Invf[t];
+  if (tid < bw) {
+    const double l = sqrt(A[tid * PT + tid]);
+    A[tid * PT + tid] = l;
+    sc[tid] = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
+    rf[tid] = (float)(1.0 / l);
+  }
+  __syncthreads();
+  for (int t = tid; t < T * T; t += POTRF_THREADS) {
+    const int i = t >> 6, j = t & 63;
+    float lf = 0.f;
+    if (i < bw && j <= i) {
+      double v = A[i * PT + j];
+      if (j < i) {
+        v *= sc[j];
+        A[i * PT + j] = v;
+      }
+      lf = (float)v;
+    }
+    Lf[i * PT + j] = lf;
+    Inv[t] = 0.f;
+  }
+  __syncthreads();
+  // FP32 inverse of L, one thread per column: Inv[i][j] = -(sum_{j <= l < i} L[i][l] Inv[l][j]) / L[i][i]
+  if (tid < bw) {
+    const int j = tid;
+    Inv[j * T + j] = rf[j];
+    for (int i = j + 1; i < bw; i++) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int l = j;
+      for (; l + 3 < i; l += 4) {
+        s0 = fmaf(Lf[i * PT + l], Inv[l * T + j], s0);
+        s1 = fmaf(Lf[i * PT + l + 1], Inv[(l + 1) * T + j], s1);
+        s2 = fmaf(Lf[i * PT + l + 2], Inv[(l + 2) * T + j], s2);
+        s3 = fmaf(Lf[i * PT + l + 3], Inv[(l + 3) * T + j], s3);
+      }
+      for (; l < i; l++) s0 = fmaf(Lf[i * PT + l], Inv[l * T + j], s0);
+      Inv[i * T + j] = -((s0 + s1) + (s2 + s3)) * rf[i];
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < T * T; t += POTRF_THREADS) {
+    D[t] = A[(t >> 6) * PT + (t & 63)];
+    DI[t] = (double)Inv[t];
   }
 }
 
@@ -352,7 +423,7 @@ void set_attrs() {
   GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
   GP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES + 1024));
-  GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
+  GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   g_attrs = true;
 }
 
@@ -452,7 +523,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       const int64_t* pre128 = dp.step_pre128 + stp.pre128_off;
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf64<<<dim3(stp.nfront, B), 128, 2 * T * T * sizeof(double), st>>>(fronts, stp.kb, dp, f->diag, DE,
+        k_potrf64<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
                                                                                f->notpd, f->dinv);
         GP_CHECK_LAUNCH(ctx);
       }
