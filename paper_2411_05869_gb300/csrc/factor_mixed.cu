@@ -12,7 +12,12 @@
 // F[i, j] -= sum_l L[i, l] L[j, l] over 128 x 128 tiles on the tensor cores, each FP32 operand split into two
 // round-to-nearest TF32 parts (three products per step, about 21 bits kept), with the tile results added in
 // FP64 to the diagonal tiles and in FP32 elsewhere.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "gp_internal.cuh"
 #include "tc_gemm.cuh"
@@ -270,10 +275,16 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   }
 }
 
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
 // FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile, one thread per row).
 __global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                         DevPlan dp, float* __restrict__ p32, const double* __restrict__ dg, int64_t P32E,
-                         int64_t DE) {
+                         DevPlan dp, float* __restrict__ p32, float* __restrict__ oph, float* __restrict__ opl,
+                         const double* __restrict__ dg, int64_t P32E, int64_t DE) {
   __shared__ float L[T * (T + 1)];
   __shared__ float X[T * (T + 1)];   // X[row][col]
   int64_t t = blockIdx.x;
@@ -303,117 +314,295 @@ __global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __re
     }
   }
   __syncthreads();
+  // the L entries and their TF32 pair (hi = rn(x), lo = rn(x - hi)), the tensor-core operands of the updates
+  const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
     int i = q / T, j = q % T;
-    if (i < nr && j < bw) P[(r0 + i) * ldw + c0 + j] = X[i * (T + 1) + j];
+    if (i < nr && j < bw) {
+      const float x = X[i * (T + 1) + j];
+      const int64_t o = (r0 + i) * ldw + c0 + j;
+      P[o] = x;
+      const float hi = tf32_rn(x);
+      oph[ob + o] = hi;
+      opl[ob + o] = tf32_rn(x - hi);
+    }
   }
 }
 
-// Trailing updates on the tensor cores, one CTA per 128 x 128 tile, F[i, j] -= sum_{l in K} L[i, l] L[j, l]
-// for j <= i. Modes (block column kb, 256-column group [g0, gend) containing it):
-//   0: rows/columns after the block column, lower-triangular tiles, K = the block column;
+// ---------------------------------------------------------------------------------------------------------
+// Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x 128 tiles, j <= i.
+// Modes (block column kb, 256-column group [g0, gend) containing it):
 //   1: intra-group: rows >= c1 x columns [c1, gend), rectangular tiles, K = the block column;
 //   2: group end: rows/columns >= gend, lower-triangular tiles, K = the whole group [g0, gend).
-__global__ void __launch_bounds__(128) k_update_tc(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                                   int nfront, int kb, int mode, DevPlan dp, float* __restrict__ p32,
-                                                   double* __restrict__ dg, float* __restrict__ u32, int64_t P32E,
-                                                   int64_t DE, int64_t UE, int32_t* __restrict__ err) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * tcg::STAGE_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * tcg::STAGE_BYTES + 64);
-  __shared__ const float* arows[128];
-  __shared__ const float* brows[128];
-  int64_t t = blockIdx.x;
-  int fi = find_front(pre, nfront, t);
-  int32_t s = fronts[fi];
-  int b = blockIdx.y;
-  MixFront fr = mix_front(dp, s, p32 + (int64_t)b * P32E, dg + (int64_t)b * DE, u32 + (int64_t)b * UE);
-  const int c0 = kb * T, bw = min(T, fr.w - c0), c1 = c0 + bw;
-  const int g0 = (kb / GP_GROUP) * GP_GROUP * T, gend = min(g0 + GP_GROUP * T, fr.w);
-  int64_t loc = t - pre[fi];
-  int64_t I, J, base, jlim;
-  int K, kc;
+// The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
+// tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
+// significant bits survive the products instead of the 11 of one TF32 pass).
+//
+// One persistent CTA per SM walks the launch's tiles (all fronts, all proposals) with three roles:
+//   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a 3-stage ring of 128-byte-swizzled tiles;
+//   warp 1 (one lane): tcgen05.mma, 12 instructions per chunk, into one of two TMEM accumulators;
+//   warps 2-9: the epilogue, which drains the other accumulator (tcgen05.ld -> swizzled 32 x 32 shared slab ->
+//              coalesced read-modify-write of the front, 16 loads in flight per lane) while the next tile's
+//              MMAs run.
+// Diagonal tiles (same rows for A and B) load one operand pair. Waits are bounded; a wait that runs out sets
+// *err and the CTA winds down.
+constexpr int UW_THREADS = 320;
+constexpr int UW_STAGES = 3;
+constexpr int UW_OP = 128 * 32 * 4;      // one operand chunk: 128 rows x 32 FP32 (128-byte rows)
+constexpr int UW_STAGE = 4 * UW_OP;      // A_hi, A_lo, B_hi, B_lo
+constexpr int UW_EPI = 8 * 32 * 32 * 4;  // a 32 x 32 FP32 slab per epilogue warp
+constexpr int UW_BAR = 256;
+constexpr int UW_SMEM = UW_STAGES * UW_STAGE + UW_EPI + UW_BAR + 1024;
+constexpr uint32_t UW_TMEM_COLS = 256;   // two 128-column FP32 accumulators
+
+struct UTile {
+  int32_t s, slot;
+  int b, w, r, ldw, K, kc;
+  int64_t m, i0, j0, jlim;
+};
+
+__device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                             int nfront, int64_t total, int kb, int mode, const DevPlan& dp,
+                                             const int32_t* __restrict__ slot_of, int64_t tt) {
+  UTile u;
+  u.b = (int)(tt / total);
+  const int64_t t = tt - (int64_t)u.b * total;
+  const int fi = find_front(pre, nfront, t);
+  u.s = fronts[fi];
+  u.slot = slot_of[u.s];
+  u.w = dp.w[u.s];
+  u.r = dp.r[u.s];
+  u.ldw = dp.ldw[u.s];
+  u.m = (int64_t)u.w + u.r;
+  const int c0 = kb * T, bw = min(T, u.w - c0), c1 = c0 + bw;
+  const int g0 = (kb / GP_GROUP) * GP_GROUP * T, gend = min(g0 + GP_GROUP * T, u.w);
+  const int64_t loc = t - pre[fi];
+  int64_t I, J, base;
   if (mode == 1) {
     const int64_t ntc = (gend - c1 + 127) / 128;
     I = loc / ntc;
-    J = loc % ntc;
+    J = loc - I * ntc;
     base = c1;
-    jlim = gend;
-    K = bw;
-    kc = c0;
+    u.jlim = gend;
+    u.K = bw;
+    u.kc = c0;
   } else {
-    I = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
+    I = (int64_t)((sqrtf(8.f * (float)loc + 1.f) - 1.f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= loc) I++;
     while (I * (I + 1) / 2 > loc) I--;
     J = loc - I * (I + 1) / 2;
-    base = mode == 2 ? gend : c1;
-    jlim = fr.m;
-    K = mode == 2 ? gend - g0 : bw;
-    kc = mode == 2 ? g0 : c0;
+    base = gend;
+    u.jlim = u.m;
+    u.K = gend - g0;
+    u.kc = g0;
   }
-  const int64_t i0 = base + I * 128, j0 = base + J * 128;
-  {
-    int q = threadIdx.x;
-    int64_t ia = i0 + q, jb = j0 + q;
-    arows[q] = ia < fr.m ? fr.P + ia * fr.ldw + kc : nullptr;
-    brows[q] = jb < jlim ? fr.P + jb * fr.ldw + kc : nullptr;
-  }
+  u.i0 = base + I * 128;
+  u.j0 = base + J * 128;
+  return u;
+}
+
+__global__ void __launch_bounds__(UW_THREADS, 1)
+    k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
+                int64_t ntiles, int kb, int mode, DevPlan dp, const uint8_t* __restrict__ tmaps,
+                const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
+                float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* epi = reinterpret_cast<float*>(smem + UW_STAGES * UW_STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + UW_STAGES * UW_STAGE + UW_EPI);
+  uint64_t* full = bars;                       // [UW_STAGES] operands landed
+  uint64_t* empty = bars + UW_STAGES;          // [UW_STAGES] MMAs done reading
+  uint64_t* tfull = bars + 2 * UW_STAGES;      // [2] accumulator complete
+  uint64_t* tempty = bars + 2 * UW_STAGES + 2; // [2] accumulator drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * UW_STAGES + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = tcg::smem_u32(smem);
   if (threadIdx.x == 0) {
-    tcg::mbar_init(&bars[0], 1);
-    tcg::mbar_init(&bars[1], 1);
+    for (int q = 0; q < UW_STAGES; q++) {
+      tcg::mbar_init(&full[q], 1);
+      tcg::mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; q++) {
+      tcg::mbar_init(&tfull[q], 1);
+      tcg::mbar_init(&tempty[q], 8);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (threadIdx.x < 32) tcg::tmem_alloc(tslot, 128);
+  if (warp == 1) tcg::tmem_alloc(tslot, UW_TMEM_COLS);
   tcg::tc_fence_before();
   __syncthreads();
   tcg::tc_fence_after();
   const uint32_t tmem = *tslot;
-  bool ok = tcg::tile_mma_split3(smem, arows, brows, K, tmem);
-  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Epilogue: TMEM (thread = row) -> shared tile (XOR-swizzled by row so neither side has bank conflicts)
-  // -> global read-modify-write with a warp per row, 32 consecutive columns per access.
-  float* S = reinterpret_cast<float*>(smem);   // 128 x 128 FP32, reuses the operand buffers
-  if (ok) {
-    const int r = warp * 32 + lane;
-    for (int cc = 0; cc < 128; cc += 32) {
-      float v[32];
-      tcg::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(err, 1);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {   // TMA producer
+      uint32_t st = 0, ph = 0;
+      for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
+        const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const uint8_t* mh = tmaps + (int64_t)u.slot * 256;
+        const uint8_t* ml = mh + 128;
+        tcg::tmap_acquire(mh);
+        tcg::tmap_acquire(ml);
+        const bool same = u.i0 == u.j0;
+        const int nch = (u.K + 31) / 32;
+        for (int c = 0; c < nch; c++) {
+          if (!tcg::mbar_wait(&empty[st], ph ^ 1)) {
+            fail();
+            break;
+          }
+          const uint32_t sa = sbase + st * UW_STAGE;
+          tcg::mbar_arrive_expect_tx(&full[st], same ? 2 * UW_OP : 4 * UW_OP);
+          const int x = u.kc + c * 32;
+          tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
+          tcg::tma_load_3d(sa + UW_OP, ml, x, (int)u.i0, u.b, &full[st]);
+          if (!same) {
+            tcg::tma_load_3d(sa + 2 * UW_OP, mh, x, (int)u.j0, u.b, &full[st]);
+            tcg::tma_load_3d(sa + 3 * UW_OP, ml, x, (int)u.j0, u.b, &full[st]);
+          }
+          if (++st == UW_STAGES) {
+            st = 0;
+            ph ^= 1;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      const uint32_t idesc = tcg::idesc_tf32(128, 128);
+      uint32_t st = 0, ph = 0, acc = 0, aph = 0;
+      for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
+        const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const bool same = u.i0 == u.j0;
+        const int nch = (u.K + 31) / 32;
+        if (!tcg::mbar_wait(&tempty[acc], aph ^ 1)) {
+          fail();
+          break;
+        }
+        tcg::tc_fence_after();
+        const uint32_t d = tmem + acc * 128;
+        bool ok = true;
+        for (int c = 0; c < nch; c++) {
+          if (!tcg::mbar_wait(&full[st], ph)) {
+            ok = false;
+            break;
+          }
+          tcg::tc_fence_after();
+          const uint32_t aH = sbase + st * UW_STAGE, aL = aH + UW_OP;
+          const uint32_t bH = same ? aH : aH + 2 * UW_OP, bL = same ? aL : aH + 3 * UW_OP;
 #pragma unroll
-      for (int q = 0; q < 32; q++) S[r * 128 + ((cc + q) ^ (r & 31))] = v[q];
+          for (int kk = 0; kk < 4; kk++) {
+            const uint32_t o = kk * 32;
+            const uint64_t ah = tcg::smem_desc_sw128(aH + o), al = tcg::smem_desc_sw128(aL + o);
+            const uint64_t bh = tcg::smem_desc_sw128(bH + o), bl = tcg::smem_desc_sw128(bL + o);
+            tcg::mma_tf32(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            tcg::mma_tf32(d, ah, bl, idesc, 1u);
+            tcg::mma_tf32(d, ah, bh, idesc, 1u);
+          }
+          tcg::mma_commit(&empty[st]);
+          if (++st == UW_STAGES) {
+            st = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        tcg::mma_commit(&tfull[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          aph ^= 1;
+        }
+      }
+    }
+  } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [64 h, 64 h + 64)
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    float* slab = epi + (warp - 2) * 1024;
+    uint32_t acc = 0, aph = 0;
+    for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
+      const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+      if (!tcg::mbar_wait(&tfull[acc], aph)) {
+        fail();
+        break;
+      }
+      tcg::tc_fence_after();
+      float v1[32];
+      {
+        float v0[32];
+        const uint32_t ta = tmem + acc * 128 + ((uint32_t)(q * 32) << 16) + h * 64;
+        tcg::tmem_ld32(ta, v0);
+        tcg::tmem_ld32(ta + 32, v1);
+#pragma unroll
+        for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v0[e];
+      }
+      tcg::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tcg::mbar_arrive(&tempty[acc]);   // this warp's part of the accumulator is in registers
+      if (++acc == 2) {
+        acc = 0;
+        aph ^= 1;
+      }
+      float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
+      float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
+      double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
+      const int64_t ib = u.i0 + q * 32;
+      for (int sl = 0; sl < 2; sl++) {
+        if (sl == 1) {
+          __syncwarp();
+#pragma unroll
+          for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v1[e];
+        }
+        __syncwarp();
+        const int64_t j = u.j0 + h * 64 + sl * 32 + lane;
+        const bool colok = j < u.jlim;
+        float* cb;
+        int64_t cs;
+        if (j < u.w) {
+          cb = P + j;
+          cs = u.ldw;
+        } else {
+          cb = U + (j - u.w) - (int64_t)u.w * u.r;
+          cs = u.r;
+        }
+#pragma unroll
+        for (int r0 = 0; r0 < 32; r0 += 16) {
+          float old[16];
+#pragma unroll
+          for (int e = 0; e < 16; e++) {
+            const int64_t i = ib + r0 + e;
+            const bool ok = colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6));
+            old[e] = ok ? cb[i * cs] : 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; e++) {
+            const int64_t i = ib + r0 + e;
+            const bool ok = colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6));
+            const int rr = r0 + e;
+            if (ok) cb[i * cs] = old[e] - slab[rr * 32 + (lane ^ rr)];
+          }
+        }
+        if (ib < u.w && j < u.w) {   // entries of the FP64 diagonal tiles
+          for (int rr = 0; rr < 32; rr++) {
+            const int64_t i = ib + rr;
+            if (colok && i < u.w && j <= i && (i >> 6) == (j >> 6))
+              D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)] -= (double)slab[rr * 32 + (lane ^ rr)];
+          }
+        }
+      }
+      __syncwarp();
     }
   }
   tcg::tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) tcg::tmem_dealloc(tmem, 128);
-  if (!ok) return;
-  // two rows (r, r + 4) x 4 column groups per step: all 8 loads issued before any store
-  for (int r = warp; r < 128; r += 8) {
-    float* pf[8];
-    double* pd[8];
-    float of[8], av[8];
-    double od[8];
-#pragma unroll
-    for (int e = 0; e < 8; e++) {
-      const int rr = r + (e >> 2) * 4, c = (e & 3) * 32 + lane;
-      const int64_t i = i0 + rr, j = j0 + c;
-      pf[e] = nullptr;
-      pd[e] = nullptr;
-      if (i < fr.m && j <= i && j < jlim) {
-        av[e] = S[rr * 128 + (c ^ (rr & 31))];
-        if (j >= fr.w) pf[e] = fr.Uu + (i - fr.w) * fr.r + (j - fr.w);
-        else if (in_diag(fr, i, j)) pd[e] = diag_at(fr, i, j);
-        else pf[e] = fr.P + i * fr.ldw + j;
-        if (pf[e]) of[e] = *pf[e];
-        if (pd[e]) od[e] = *pd[e];
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 8; e++) {
-      if (pf[e]) *pf[e] = of[e] - av[e];
-      if (pd[e]) *pd[e] = od[e] - (double)av[e];
-    }
+  if (warp == 1) {
+    tcg::tc_fence_after();
+    tcg::tmem_dealloc(tmem, UW_TMEM_COLS);
   }
 }
 
@@ -422,7 +611,7 @@ void set_attrs() {
   if (g_attrs) return;
   GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES + 1024));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, UW_SMEM));
   GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   g_attrs = true;
 }
@@ -483,6 +672,75 @@ void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps) {
   GP_CHECK_LAUNCH(ctx);
 }
 
+namespace {
+void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
+                   int32_t nfront, int32_t kb, int mode) {
+  const SymPlan& sp = f->ps->sp;
+  const int64_t ntiles = total * f->B;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
+  k_update_ws<<<grid, UW_THREADS, UW_SMEM, ctx->stream>>>(fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp,
+                                                          f->op_maps, f->op_slot, f->panels32, f->diag, f->upd32,
+                                                          sp.panel32_entries, sp.diag_entries, sp.update_entries,
+                                                          f->tiles_err);
+  GP_CHECK_LAUNCH(ctx);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    GP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    GP_REQUIRE(q == cudaDriverEntryPointSuccess && p, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+}  // namespace
+
+// Tensor maps of the TF32 operand pair of every front that has tensor-core updates: per front two 3-D maps
+// (columns x rows x proposals) over op_hi and op_lo, 128 x 32 boxes with the 128-byte swizzle; rows past the
+// front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
+void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
+  const SymPlan& sp = f->ps->sp;
+  const int64_t ns = (int64_t)sp.sn_w.size();
+  std::vector<int32_t> slot(ns, -1);
+  std::vector<int32_t> order;
+  for (int32_t s : sp.upd_fronts)
+    if (slot[s] < 0) {
+      slot[s] = (int32_t)order.size();
+      order.push_back(s);
+    }
+  const size_t nmaps = std::max<size_t>(order.size(), 1);
+  std::vector<CUtensorMap> maps(2 * nmaps);
+  std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+  auto enc = tensor_map_encoder();
+  GP_REQUIRE(sp.panel32_entries % 4 == 0, "FP32 panel stride must be a multiple of 16 bytes");
+  for (size_t k = 0; k < order.size(); k++) {
+    const int32_t s = order[k];
+    const int64_t ldw = sp.sn_ldw[s], m = (int64_t)sp.sn_w[s] + sp.sn_r[s];
+    GP_REQUIRE(ldw % 4 == 0 && sp.sn_loff32[s] % 4 == 0, "FP32 panel rows must start on 16-byte boundaries");
+    for (int part = 0; part < 2; part++) {
+      float* base = (part == 0 ? f->op_hi : f->op_lo) + sp.sn_loff32[s];
+      cuuint64_t dims[3] = {(cuuint64_t)ldw, (cuuint64_t)m, (cuuint64_t)f->B};
+      cuuint64_t strides[2] = {(cuuint64_t)ldw * 4, (cuuint64_t)sp.panel32_entries * 4};
+      cuuint32_t box[3] = {32, 128, 1};
+      cuuint32_t es[3] = {1, 1, 1};
+      CUresult r = enc(&maps[2 * k + part], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      GP_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled rejected an operand map");
+    }
+  }
+  f->op_maps = dalloc<uint8_t>(ctx, f->bufs, maps.size() * sizeof(CUtensorMap));
+  f->op_slot = dalloc<int32_t>(ctx, f->bufs, (size_t)ns + 1);
+  GP_CUDA(cudaMemcpyAsync(f->op_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  GP_CUDA(cudaMemcpyAsync(f->op_slot, slot.data(), (size_t)ns * sizeof(int32_t), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  GP_CUDA(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
+}
+
 void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   gp_pointset* ps = f->ps;
   const SymPlan& sp = ps->sp;
@@ -520,7 +778,6 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
     for (const auto& stp : lv.steps) {
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
-      const int64_t* pre128 = dp.step_pre128 + stp.pre128_off;
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
         k_potrf64<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
@@ -530,23 +787,19 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       if (stp.trsm_total > 0) {
         ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
         k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 64, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
-                                                                   f->panels32, f->diag, P32E, DE);
+                                                                   f->panels32, f->op_hi, f->op_lo, f->diag, P32E,
+                                                                   DE);
         GP_CHECK_LAUNCH(ctx);
       }
-      (void)pre128;
       if (stp.intra_total > 0) {   // this block's update of the rest of its 256-column group
         ProfScope ps_(ctx, KC_UPDATE, B * stp.intra_flops);
-        k_update_tc<<<dim3((unsigned)stp.intra_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
-            dp.upd_fronts + stp.intra_off, dp.upd_pre + stp.intra_pre_off, stp.n_intra, stp.kb, 1, dp, f->panels32,
-            f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
-        GP_CHECK_LAUNCH(ctx);
+        launch_update(ctx, f, stp.intra_total, dp.upd_fronts + stp.intra_off, dp.upd_pre + stp.intra_pre_off,
+                      stp.n_intra, stp.kb, 1);
       }
       if (stp.group_total > 0) {   // fronts whose group ends here: the deferred update with K = group width
         ProfScope ps_(ctx, KC_UPDATE, B * stp.group_flops);
-        k_update_tc<<<dim3((unsigned)stp.group_total, B), 128, tcg::SMEM_BYTES + 1024, st>>>(
-            dp.upd_fronts + stp.group_off, dp.upd_pre + stp.group_pre_off, stp.n_group, stp.kb, 2, dp, f->panels32,
-            f->diag, f->upd32, P32E, DE, UE, f->tiles_err);
-        GP_CHECK_LAUNCH(ctx);
+        launch_update(ctx, f, stp.group_total, dp.upd_fronts + stp.group_off, dp.upd_pre + stp.group_pre_off,
+                      stp.n_group, stp.kb, 2);
       }
     }
   }

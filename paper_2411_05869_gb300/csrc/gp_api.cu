@@ -125,7 +125,11 @@ extern "C" gp_status gp_create(gp_ctx** out, int device, void* cuda_stream, size
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   ctx->budget = mem_budget_bytes;
-  gp_status st = guarded(ctx, [&] { GP_CUDA(cudaFree(nullptr)); });
+  gp_status st = guarded(ctx, [&] {
+    GP_CUDA(cudaSetDevice(device));
+    GP_CUDA(cudaFree(nullptr));
+    GP_CUDA(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device));
+  });
   if (st != GP_OK) {
     delete ctx;
     return st;
@@ -347,6 +351,12 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
       f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
+      f->op_hi = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
+      f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
+      // entries the TRSM never writes (padding columns) must read as zeros
+      GP_CUDA(cudaMemsetAsync(f->op_hi, 0, (size_t)B * sp.panel32_entries * sizeof(float), ctx->stream));
+      GP_CUDA(cudaMemsetAsync(f->op_lo, 0, (size_t)B * sp.panel32_entries * sizeof(float), ctx->stream));
+      build_update_maps(ctx, f);
     }
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
     f->notpd = dalloc<int32_t>(ctx, f->bufs, B);

@@ -59,6 +59,7 @@ enum KClass { KC_VALUES = 0, KC_EXTEND_ADD, KC_FRONT_SMALL, KC_POTRF, KC_TRSM, K
 
 struct gp_ctx {
   int device = 0;
+  int nsm = 1;           // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   size_t budget = 0;     // 0 = unlimited
   size_t held = 0;       // bytes currently held by this context's handles
@@ -245,6 +246,10 @@ struct gp_factor_s {
   int n1max = 0;
   double* panels = nullptr;     // FP64 panels, B x panel_entries
   float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
+  float* op_hi = nullptr;       // GP_MIXED: TF32 pair (hi, lo) of each panel entry below its diagonal tile,
+  float* op_lo = nullptr;       //   same layout as panels32: the tensor-core update operands
+  uint8_t* op_maps = nullptr;   // GP_MIXED: TMA maps of op_hi / op_lo, 2 x 128 bytes per updated front
+  int32_t* op_slot = nullptr;   // GP_MIXED: per supernode, its map pair (-1 = none)
   double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
   double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n
   double* dinv = nullptr;       // FP64 inverses of the 64 x 64 diagonal blocks (row-major), B x diag_entries
@@ -297,6 +302,7 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
 void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, const double* d_mu, double* d_mean);
 void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
+void build_update_maps(gp_ctx* ctx, gp_factor_t* f);
 #define DIAG_FLAG ((int64_t)1 << 62)
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
