@@ -187,7 +187,7 @@ __device__ __forceinline__ double pivot_recip(double* a, int32_t* notpd, int32_t
 
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
                                                            double* __restrict__ dg, int64_t DE,
-                                                           int32_t* __restrict__ notpd, double* __restrict__ dinv) {
+                                                           int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
   extern __shared__ double sm64[];
   double* A = sm64;                                      // T x PT
   float* Lf = reinterpret_cast<float*>(A + T * PT);     // T x PT, FP32 copy of L
@@ -200,7 +200,6 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  double* DI = dinv + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], bw = min(T, w - kb * T);
   const int32_t first = dp.sn_first[s] + kb * T;
   int32_t* flag = notpd + b;
@@ -269,9 +268,10 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
     }
   }
   __syncthreads();
+  float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   for (int t = tid; t < T * T; t += POTRF_THREADS) {
     D[t] = A[(t >> 6) * PT + (t & 63)];
-    DI[t] = (double)Inv[t];
+    DI[t] = Inv[t];
   }
 }
 
@@ -281,45 +281,57 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(u);
 }
 
-// FP32 TRSM of the rows below diagonal tile kb (one CTA per 64-row tile, one thread per row).
-__global__ void k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                         DevPlan dp, float* __restrict__ p32, float* __restrict__ oph, float* __restrict__ opl,
-                         const double* __restrict__ dg, int64_t P32E, int64_t DE) {
-  __shared__ float L[T * (T + 1)];
-  __shared__ float X[T * (T + 1)];   // X[row][col]
+// FP32 TRSM of the rows below diagonal tile kb as a product with the inverse the POTRF left behind:
+// X = B L^{-T}, X[r][j] = sum_{l <= j} B[r][l] Inv[j][l], one CTA of 256 threads per 64-row tile, each thread a
+// 4 x 4 block of X (no dependency chains, unlike a column-by-column substitution). The L entries are written
+// with their TF32 pair (hi = rn(x), lo = rn(x - hi)), the tensor-core operands of the updates.
+__global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                int nfront, int kb, DevPlan dp, float* __restrict__ p32,
+                                                float* __restrict__ oph, float* __restrict__ opl,
+                                                const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
+  __shared__ float Bs[T * (T + 1)];   // B[r][l]
+  __shared__ float Is[T * (T + 1)];   // Inv[j][l]
   int64_t t = blockIdx.x;
   int fi = find_front(pre, nfront, t);
   int32_t s = fronts[fi];
   int b = blockIdx.y;
   float* P = p32 + (int64_t)b * P32E + dp.loff32[s];
-  const double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], ldw = dp.ldw[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
   const int64_t r0 = c1 + (t - pre[fi]) * T;
   const int nr = (int)imin64(T, m - r0);
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
-    int i = q / T, j = q % T;
-    L[i * (T + 1) + j] = (i < bw && j <= i) ? (float)D[i * T + j] : 0.f;
-    X[i * (T + 1) + j] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
+    int i = q >> 6, j = q & 63;
+    Is[i * (T + 1) + j] = DI[q];   // zero outside the lower bw x bw triangle
+    Bs[i * (T + 1) + j] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
   }
   __syncthreads();
-  // X <- X L^{-T}: column j of X = (X[:, j] - sum_{l<j} X[:, l] L[j, l]) / L[j, j], row-parallel
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    if (i >= nr) continue;
-    for (int j = 0; j < bw; j++) {
-      float acc = X[i * (T + 1) + j];
-      for (int l = 0; l < j; l++) acc -= X[i * (T + 1) + l] * L[j * (T + 1) + l];
-      X[i * (T + 1) + j] = acc / L[j * (T + 1) + j];
+  const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+  float acc[4][4] = {};
+  for (int l = 0; l < bw; l++) {
+    float bv[4], iv[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      bv[e] = Bs[(tr + e) * (T + 1) + l];
+      iv[e] = Is[(tc + e) * (T + 1) + l];
     }
+#pragma unroll
+    for (int e = 0; e < 4; e++)
+#pragma unroll
+      for (int f = 0; f < 4; f++) acc[e][f] = fmaf(bv[e], iv[f], acc[e][f]);
   }
-  __syncthreads();
-  // the L entries and their TF32 pair (hi = rn(x), lo = rn(x - hi)), the tensor-core operands of the updates
   const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
-  for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
-    int i = q / T, j = q % T;
-    if (i < nr && j < bw) {
-      const float x = X[i * (T + 1) + j];
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const int i = tr + e;
+    if (i >= nr) continue;
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      const int j = tc + f;
+      if (j >= bw) continue;
+      const float x = acc[e][f];
       const int64_t o = (r0 + i) * ldw + c0 + j;
       P[o] = x;
       const float hi = tf32_rn(x);
@@ -527,6 +539,25 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     uint32_t acc = 0, aph = 0;
     for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
       const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+      float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
+      float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
+      double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
+      const int64_t ib = u.i0 + q * 32;
+      // while the tile's MMAs run: pull this warp's target rows (2 x 128 bytes each) into L2
+      {
+        const int64_t i = ib + lane;
+        const int64_t jc = u.j0 + h * 64;
+        if (i < u.m) {
+#pragma unroll
+          for (int half = 0; half < 2; half++) {
+            const int64_t j = jc + half * 32;
+            if (j <= i && j < u.jlim) {
+              const float* pa = j < u.w ? P + i * u.ldw + j : U + (i - u.w) * u.r + (j - u.w);
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+            }
+          }
+        }
+      }
       if (!tcg::mbar_wait(&tfull[acc], aph)) {
         fail();
         break;
@@ -548,10 +579,6 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         acc = 0;
         aph ^= 1;
       }
-      float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
-      float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
-      double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
-      const int64_t ib = u.i0 + q * 32;
       for (int sl = 0; sl < 2; sl++) {
         if (sl == 1) {
           __syncwarp();
@@ -570,23 +597,20 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           cb = U + (j - u.w) - (int64_t)u.w * u.r;
           cs = u.r;
         }
+        // entries (i, j) of this lane's column: lower triangle, inside the front, not in an FP64 tile;
+        // all 32 loads in flight before the first store
+        uint32_t okm = 0;
 #pragma unroll
-        for (int r0 = 0; r0 < 32; r0 += 16) {
-          float old[16];
-#pragma unroll
-          for (int e = 0; e < 16; e++) {
-            const int64_t i = ib + r0 + e;
-            const bool ok = colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6));
-            old[e] = ok ? cb[i * cs] : 0.f;
-          }
-#pragma unroll
-          for (int e = 0; e < 16; e++) {
-            const int64_t i = ib + r0 + e;
-            const bool ok = colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6));
-            const int rr = r0 + e;
-            if (ok) cb[i * cs] = old[e] - slab[rr * 32 + (lane ^ rr)];
-          }
+        for (int rr = 0; rr < 32; rr++) {
+          const int64_t i = ib + rr;
+          if (colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6))) okm |= 1u << rr;
         }
+        float old[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++) old[rr] = (okm >> rr & 1) ? cb[(ib + rr) * cs] : 0.f;
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++)
+          if (okm >> rr & 1) cb[(ib + rr) * cs] = old[rr] - slab[rr * 32 + (lane ^ rr)];
         if (ib < u.w && j < u.w) {   // entries of the FP64 diagonal tiles
           for (int rr = 0; rr < 32; rr++) {
             const int64_t i = ib + rr;
@@ -781,14 +805,14 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
         k_potrf64<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
-                                                                               f->notpd, f->dinv);
+                                                                               f->notpd, f->dinv32);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.trsm_total > 0) {
         ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
-        k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 64, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
-                                                                   f->panels32, f->op_hi, f->op_lo, f->diag, P32E,
-                                                                   DE);
+        k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
+                                                                    f->panels32, f->op_hi, f->op_lo, f->dinv32, P32E,
+                                                                    DE);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.intra_total > 0) {   // this block's update of the rest of its 256-column group

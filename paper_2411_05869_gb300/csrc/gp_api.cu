@@ -351,6 +351,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
       f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
+      f->dinv32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->op_hi = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
       f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
       // entries the TRSM never writes (padding columns) must read as zeros
@@ -361,7 +362,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
     f->notpd = dalloc<int32_t>(ctx, f->bufs, B);
     f->alpha = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
-    f->dinv = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
+    if (prec == GP_FP64) f->dinv = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
     f->rhs = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
     f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
     f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);

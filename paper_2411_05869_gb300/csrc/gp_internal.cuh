@@ -253,6 +253,7 @@ struct gp_factor_s {
   double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
   double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n
   double* dinv = nullptr;       // FP64 inverses of the 64 x 64 diagonal blocks (row-major), B x diag_entries
+  float* dinv32 = nullptr;      // GP_MIXED: the same inverses in FP32 (the TRSM's operand)
   double* rhs = nullptr;        // B x n copy of the caller's residual (the solve graph reads it from here)
   // CUDA graphs of the fixed launch sequences, captured on first use and replayed (launch counts per replay)
   cudaGraphExec_t gx_factor = nullptr, gx_solve = nullptr, gx_cor = nullptr;

@@ -8,12 +8,14 @@
 // child's relative indices (children in order), then x = L11^{-1} f_1 and f_2 -= L21 x; f_2 is the update
 // vector handed to the parent. Backward (levels descending): t = x - L21^T alpha'(rows below), then
 // L11^T z = t. Fronts of order <= 96 use one CTA; larger ones advance 64 columns per launch, every CTA
-// multiplying by the inverted 64 x 64 diagonal block (formed in FP64 by the factorization) and applying the
-// result to its own 64-row (or 64-column) tile.
+// multiplying by the inverted 64 x 64 diagonal block (formed by the factorization) and applying the result
+// to its own 64-row (or 64-column) tile.
 // The kernels read the factor through an accessor: FP64 column-major panels (GP_FP64) or FP32 row-major
-// panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the quadratic form is |L^{-1} P r|^2; in GP_MIXED
-// alpha is refined in FP64 (residual r - C alpha from the FP64 CSR values, correction through the same
-// factor) until |r - C alpha| / |r| <= 1e-12 or 10 sweeps, and the quadratic form is r^T alpha.
+// panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the solves run in FP64 and the quadratic form is
+// |L^{-1} P r|^2. In GP_MIXED the solves run in FP32 (FP32 inverses, FP32 vectors): they only precondition
+// the FP64 refinement of alpha (residual r - C alpha from the FP64 CSR values, correction through the same
+// factor) until |r - C alpha| / |r| <= 1e-12 or 10 sweeps; the quadratic form is r^T alpha in FP64 and the
+// log-determinant is summed in FP64 from the FP64 diagonal tiles.
 // Sums use fixed-shape trees, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
@@ -25,21 +27,30 @@ namespace {
 constexpr int T = GP_TILE;
 
 // ---------------------------------------------------------------------------------------- factor access
+// L(i, j) in the solve's working precision; Ld(i, j) in FP64 (the log-determinant).
 struct AccF64 {
   const double* P;
   int64_t m;
   __device__ __forceinline__ double L(int64_t i, int64_t j) const { return P[j * m + i]; }
+  __device__ __forceinline__ double Ld(int64_t i, int64_t j) const { return P[j * m + i]; }
 };
 struct AccMix {
   const float* P;
   const double* D;
   int w, ldw;
-  __device__ __forceinline__ double L(int64_t i, int64_t j) const {
+  __device__ __forceinline__ double Ld(int64_t i, int64_t j) const {
     if (i < w && (i >> 6) == (j >> 6)) return D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)];
     return (double)P[i * ldw + j];
   }
+  __device__ __forceinline__ float L(int64_t i, int64_t j) const {
+    if (i < w && (i >> 6) == (j >> 6)) return (float)D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)];
+    return P[i * ldw + j];
+  }
 };
+// The solve's working precision V: FP64 with the FP64 factor; FP32 with the mixed factor, whose solves only
+// precondition the FP64 refinement (the FP64 residual fixes the accuracy of alpha).
 struct StoreF64 {
+  using V = double;
   static constexpr bool kRowMajor = false;
   const double* P;
   int64_t PE;
@@ -54,12 +65,13 @@ struct StoreF64 {
   }
 };
 struct StoreMix {
+  using V = float;
   static constexpr bool kRowMajor = true;
   const float* P;
   const double* D;
   int64_t P32E, DE;
-  const double* DI;
-  __device__ __forceinline__ const double* inv(const DevPlan& dp, int32_t s, int b) const {
+  const float* DI;   // FP32 inverses of the 64 x 64 diagonal blocks
+  __device__ __forceinline__ const float* inv(const DevPlan& dp, int32_t s, int b) const {
     return DI + (int64_t)b * DE + dp.doff[s];
   }
   using Acc = AccMix;
@@ -68,23 +80,25 @@ struct StoreMix {
   }
 };
 
+template <class V>
 __global__ void k_rhs(const double* __restrict__ rhs, const int32_t* __restrict__ perm, int64_t n, DevPlan dp,
-                      double* __restrict__ work, int64_t ws) {
+                      V* __restrict__ work, int64_t ws) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (j >= n) return;
   int32_t s = dp.sn_of_col[j];
-  work[(int64_t)b * ws + dp.frow_off[s] + (j - dp.sn_first[s])] = rhs[(int64_t)b * n + perm[j]];
+  work[(int64_t)b * ws + dp.frow_off[s] + (j - dp.sn_first[s])] = (V)rhs[(int64_t)b * n + perm[j]];
 }
 
 // Children's update vectors into the front vector of each supernode of the list.
-__global__ void k_fwd_gather(const int32_t* __restrict__ list, DevPlan dp, double* __restrict__ work, int64_t ws) {
+template <class V>
+__global__ void k_fwd_gather(const int32_t* __restrict__ list, DevPlan dp, V* __restrict__ work, int64_t ws) {
   int32_t s = list[blockIdx.x];
-  double* W = work + (int64_t)blockIdx.y * ws;
-  double* fv = W + dp.frow_off[s];
+  V* W = work + (int64_t)blockIdx.y * ws;
+  V* fv = W + dp.frow_off[s];
   for (int32_t q = dp.ch_ptr[s]; q < dp.ch_ptr[s + 1]; q++) {
     int32_t c = dp.ch_idx[q];
-    const double* uc = W + dp.frow_off[c] + dp.w[c];
+    const V* uc = W + dp.frow_off[c] + dp.w[c];
     const int32_t* rel = dp.relidx + dp.relidx_off[c];
     for (int32_t a = threadIdx.x; a < dp.r[c]; a += blockDim.x) fv[rel[a]] += uc[a];
     __syncthreads();
@@ -93,24 +107,28 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ list, DevPlan dp, doubl
 
 // Forward elimination of a whole (small) front by one CTA.
 template <class St>
-__global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, St store, double* __restrict__ work,
+__global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, St store, typename St::V* __restrict__ work,
                             int64_t ws, int64_t xv_off) {
-  __shared__ double xs;
+  using V = typename St::V;
+  __shared__ V xs;
+  __shared__ V rdg[GP_SMALL_M];   // 1 / L_jj, formed in parallel ahead of the substitution
   int32_t s = list[blockIdx.x];
   int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
-  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
-  double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
+  V* fv = work + (int64_t)b * ws + dp.frow_off[s];
+  V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
+  for (int j = threadIdx.x; j < w; j += blockDim.x) rdg[j] = V(1) / A.L(j, j);
+  __syncthreads();
   for (int j = 0; j < w; j++) {
     if (threadIdx.x == 0) {
-      xs = fv[j] / A.L(j, j);
+      xs = fv[j] * rdg[j];
       fv[j] = xs;
       xv[j] = xs;
     }
     __syncthreads();
-    double x = xs;
+    V x = xs;
     for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) fv[i] -= A.L(i, j) * x;
     __syncthreads();
   }
@@ -127,7 +145,8 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
 }
 
 // Load the inverse of diagonal block kb (row-major 64 x 64, FP64) into shared memory with a padded stride.
-__device__ __forceinline__ void load_inverse(const double* Inv, double* Li) {
+template <class V>
+__device__ __forceinline__ void load_inverse(const V* Inv, V* Li) {
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) Li[(q / T) * (T + 1) + (q % T)] = Inv[q];
 }
 
@@ -137,30 +156,31 @@ __device__ __forceinline__ void load_inverse(const double* Inv, double* Li) {
 // Row-major panels: a half-warp reads one row's 64 entries as 16 float4; column-major: thread per row.
 template <class St>
 __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                           DevPlan dp, St store, double* __restrict__ work, int64_t ws, int64_t xv_off) {
-  __shared__ double Li[T * (T + 1)];
-  __shared__ double fb[T], x[T];
+                           DevPlan dp, St store, typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
+  using V = typename St::V;
+  __shared__ V Li[T * (T + 1)];
+  __shared__ V fb[T], x[T];
   const int64_t t = blockIdx.x;
   const bool writer = t < nfront;
   const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
   const int32_t s = fronts[fi];
   const int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
-  double* fv = work + (int64_t)b * ws + dp.frow_off[s];
+  V* fv = work + (int64_t)b * ws + dp.frow_off[s];
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
   load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) fb[q] = q < bw ? fv[c0 + q] : 0.0;
+  for (int q = threadIdx.x; q < T; q += blockDim.x) fb[q] = q < bw ? fv[c0 + q] : V(0);
   __syncthreads();
   for (int q = threadIdx.x; q < T; q += blockDim.x) {
-    double acc = 0.0;
+    V acc = 0;
     for (int l = 0; l <= q; l++) acc += Li[q * (T + 1) + l] * fb[l];
-    x[q] = q < bw ? acc : 0.0;
+    x[q] = q < bw ? acc : V(0);
   }
   __syncthreads();
   if (writer) {
-    double* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
+    V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
     for (int q = threadIdx.x; q < bw; q += blockDim.x) xv[c0 + q] = x[q];
     return;
   }
@@ -170,14 +190,14 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
     const int l = l16 * 4;
     for (int64_t base = r0 + 2 * warp; base < rend; base += 2 * nw) {
       const int64_t i = base + (lane >> 4);
-      double acc = 0.0;
+      V acc = 0;
       if (i < rend && l < bw) {
         const float* row = A.P + i * A.ldw + c0;
         if (l + 4 <= bw) {
           float4 v = *reinterpret_cast<const float4*>(row + l);
-          acc = (double)v.x * x[l] + (double)v.y * x[l + 1] + (double)v.z * x[l + 2] + (double)v.w * x[l + 3];
+          acc = (V)v.x * x[l] + (V)v.y * x[l + 1] + (V)v.z * x[l + 2] + (V)v.w * x[l + 3];
         } else {
-          for (int q = l; q < bw; q++) acc += (double)row[q] * x[q];
+          for (int q = l; q < bw; q++) acc += (V)row[q] * x[q];
         }
       }
       for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -185,7 +205,7 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
     }
   } else {
     for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
-      double acc = 0.0;
+      V acc = 0;
       for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
       fv[i] -= acc;
     }
@@ -196,34 +216,37 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
 // column), then L11^T z = t by substitution; z is written to alpha'.
 template <class St>
 __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, DevPlan dp, St store,
-                           double* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
-  __shared__ double zs;
+                           typename St::V* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
+  using V = typename St::V;
+  __shared__ V zs;
+  __shared__ V rdg[GP_SMALL_M];
   int32_t s = list[blockIdx.x];
   int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
-  double* W = work + (int64_t)b * ws;
-  double* fv = W + dp.frow_off[s];
-  double* apv = W + apv_off;
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
+  V* apv = W + apv_off;
   const int w = dp.w[s], r = dp.r[s];
   const int32_t* R = dp.frows + dp.frow_off[s] + w;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = warp; j < w; j += nw) {
-    double acc = 0.0;
+    V acc = 0;
     for (int a = lane; a < r; a += 32) acc += A.L(w + a, j) * apv[R[a]];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) fv[j] = W[xv_off + dp.sn_first[s] + j] - acc;
   }
-  __syncthreads();
   if (!solve_small) return;
+  for (int j = threadIdx.x; j < w; j += blockDim.x) rdg[j] = V(1) / A.L(j, j);
+  __syncthreads();
   const int32_t first = dp.sn_first[s];
   for (int j = w - 1; j >= 0; j--) {
     if (threadIdx.x == 0) {
-      zs = fv[j] / A.L(j, j);
+      zs = fv[j] * rdg[j];
       fv[j] = zs;
       apv[first + j] = zs;
     }
     __syncthreads();
-    double z = zs;
+    V z = zs;
     for (int k = threadIdx.x; k < j; k += blockDim.x) fv[k] -= A.L(j, k) * z;
     __syncthreads();
   }
@@ -234,24 +257,26 @@ __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, De
 // stripe's columns x 4 row groups, fixed-order combination; column-major: a warp per column.
 template <class St>
 __global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32_t* __restrict__ kbs, DevPlan dp,
-                                 St store, double* __restrict__ work, int64_t ws, int64_t apv_off, int64_t xv_off) {
-  __shared__ double part[4][T];
+                                 St store, typename St::V* __restrict__ work, int64_t ws, int64_t apv_off,
+                                 int64_t xv_off) {
+  using V = typename St::V;
+  __shared__ V part[4][T];
   int32_t s = fronts[blockIdx.x];
   const int j0 = kbs[blockIdx.x] * T;
   int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
-  double* W = work + (int64_t)b * ws;
-  double* fv = W + dp.frow_off[s];
-  const double* apv = W + apv_off;
-  const double* xv = W + xv_off + dp.sn_first[s];
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
+  const V* apv = W + apv_off;
+  const V* xv = W + xv_off + dp.sn_first[s];
   const int w = dp.w[s], r = dp.r[s];
   const int nj = min(T, w - j0);
   const int32_t* R = dp.frows + dp.frow_off[s] + w;
   if constexpr (St::kRowMajor) {
     const int c = threadIdx.x & 63, g = threadIdx.x >> 6;   // blockDim = 256
-    double acc = 0.0;
+    V acc = 0;
     if (c < nj)
-      for (int a = g; a < r; a += 4) acc += (double)A.P[(int64_t)(w + a) * A.ldw + j0 + c] * apv[R[a]];
+      for (int a = g; a < r; a += 4) acc += (V)A.P[(int64_t)(w + a) * A.ldw + j0 + c] * apv[R[a]];
     part[g][c] = acc;
     __syncthreads();
     if (g == 0 && c < nj) fv[j0 + c] = xv[j0 + c] - (((part[0][c] + part[1][c]) + part[2][c]) + part[3][c]);
@@ -259,7 +284,7 @@ __global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int jj = warp; jj < nj; jj += nw) {
       const int j = j0 + jj;
-      double acc = 0.0;
+      V acc = 0;
       for (int a = lane; a < r; a += 32) acc += A.L(w + a, j) * apv[R[a]];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) fv[j] = xv[j] - acc;
@@ -272,30 +297,31 @@ __global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32
 // one 64-column tile of the earlier columns k < c0.
 template <class St>
 __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
-                           double* __restrict__ work, int64_t ws, int64_t apv_off) {
-  __shared__ double Li[T * (T + 1)];   // the inverse block, then (column-major path) the block's rows
-  __shared__ double tb[T], z[T];
+                           typename St::V* __restrict__ work, int64_t ws, int64_t apv_off) {
+  using V = typename St::V;
+  __shared__ V Li[T * (T + 1)];   // the inverse block, then (column-major path) the block's rows
+  __shared__ V tb[T], z[T];
   const int64_t t = blockIdx.x;
   const int fi = (int)(t / (kb + 1));
   const int task = (int)(t % (kb + 1));
   const int32_t s = fronts[fi];
   const int b = blockIdx.y;
   auto A = store.acc(dp, s, b);
-  double* W = work + (int64_t)b * ws;
-  double* fv = W + dp.frow_off[s];
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
   const int w = dp.w[s];
   const int c0 = kb * T, bw = min(T, w - c0);
   load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) tb[q] = q < bw ? fv[c0 + q] : 0.0;
+  for (int q = threadIdx.x; q < T; q += blockDim.x) tb[q] = q < bw ? fv[c0 + q] : V(0);
   __syncthreads();
   for (int q = threadIdx.x; q < T; q += blockDim.x) {   // z_q = sum_{l >= q} inv[l][q] t_l
-    double acc = 0.0;
+    V acc = 0;
     for (int l = q; l < bw; l++) acc += Li[l * (T + 1) + q] * tb[l];
-    z[q] = q < bw ? acc : 0.0;
+    z[q] = q < bw ? acc : V(0);
   }
   __syncthreads();
   if (task == 0) {
-    double* apv = W + apv_off;
+    V* apv = W + apv_off;
     const int32_t first = dp.sn_first[s];
     for (int q = threadIdx.x; q < bw; q += blockDim.x) apv[first + c0 + q] = z[q];
     return;
@@ -303,12 +329,12 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
   const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
   if constexpr (St::kRowMajor) {
     for (int k = threadIdx.x; k < T; k += blockDim.x) {   // row c0 + l is contiguous over k
-      double acc = 0.0;
-      for (int l = 0; l < bw; l++) acc += (double)A.P[(int64_t)(c0 + l) * A.ldw + k0 + k] * z[l];
+      V acc = 0;
+      for (int l = 0; l < bw; l++) acc += (V)A.P[(int64_t)(c0 + l) * A.ldw + k0 + k] * z[l];
       fv[k0 + k] -= acc;
     }
   } else {
-    double* Lt = Li;   // reuse: the block's rows for the tile's columns, staged by columns (contiguous)
+    V* Lt = Li;   // reuse: the block's rows for the tile's columns, staged by columns (contiguous)
     __syncthreads();
     for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {
       int l = q % bw, k = q / bw;
@@ -316,7 +342,7 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
     }
     __syncthreads();
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
-      double acc = 0.0;
+      V acc = 0;
       for (int l = 0; l < bw; l++) acc += Lt[l * (T + 1) + k] * z[l];
       fv[k0 + k] -= acc;
     }
@@ -325,7 +351,7 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
 
 // Per-block partial sums: log L_jj and x_j^2 (x = forward solution on own columns).
 template <class St>
-__global__ void k_partials(int64_t n, DevPlan dp, St store, const double* __restrict__ work, int64_t ws,
+__global__ void k_partials(int64_t n, DevPlan dp, St store, const typename St::V* __restrict__ work, int64_t ws,
                            int64_t xv_off, double* __restrict__ red, int64_t rs, int nblk) {
   __shared__ double sa[1024], sb[1024];
   int b = blockIdx.y;
@@ -335,8 +361,8 @@ __global__ void k_partials(int64_t n, DevPlan dp, St store, const double* __rest
     int32_t s = dp.sn_of_col[j];
     int64_t jl = j - dp.sn_first[s];
     auto A = store.acc(dp, s, b);
-    la = log(A.L(jl, jl));
-    double x = work[(int64_t)b * ws + xv_off + j];
+    la = log(A.Ld(jl, jl));
+    double x = (double)work[(int64_t)b * ws + xv_off + j];
     lb = x * x;
   }
   sa[threadIdx.x] = la;
@@ -395,11 +421,12 @@ __global__ void k_finish(int B, int64_t n, const double* __restrict__ s_logdet, 
   out[b] = ll;
 }
 
-__global__ void k_alpha(const double* __restrict__ work, int64_t ws, int64_t apv_off, const int32_t* __restrict__ perm,
+template <class V>
+__global__ void k_alpha(const V* __restrict__ work, int64_t ws, int64_t apv_off, const int32_t* __restrict__ perm,
                         int64_t n, double* __restrict__ alpha) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
-  if (j < n) alpha[(int64_t)b * n + perm[j]] = work[(int64_t)b * ws + apv_off + j];
+  if (j < n) alpha[(int64_t)b * n + perm[j]] = (double)work[(int64_t)b * ws + apv_off + j];
 }
 
 // res = r - C alpha (warp per CSR row, fixed lane order) and per-block sums of res^2, r^2 and r . alpha.
@@ -490,54 +517,56 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
   const int64_t n = ps->n, ws = f->work_stride;
   const int64_t apv_off = sp.sn_frow[sp.ns];   // work layout: front vectors, alpha' (n), x (n)
   const int64_t xv_off = apv_off + n;
-  GP_CUDA(cudaMemsetAsync(f->work, 0, sizeof(double) * (size_t)B * ws, st));
-  k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(rhs, ps->perm, n, dp, f->work, ws);
+  using V = typename St::V;
+  V* work = reinterpret_cast<V*>(f->work);   // ws entries of V per proposal
+  GP_CUDA(cudaMemsetAsync(f->work, 0, sizeof(V) * (size_t)B * ws, st));
+  k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(rhs, ps->perm, n, dp, work, ws);
   GP_CHECK_LAUNCH(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
     int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
     if (L > 0) {
-      k_fwd_gather<<<dim3(nl, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->work, ws);
+      k_fwd_gather<<<dim3(nl, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, work, ws);
       GP_CHECK_LAUNCH(ctx);
     }
     if (lv.nsmall > 0) {
-      k_fwd_small<St><<<dim3(lv.nsmall, B), 128, 0, st>>>(dp.small_list + lv.small_off, dp, store, f->work, ws,
+      k_fwd_small<St><<<dim3(lv.nsmall, B), 128, 0, st>>>(dp.small_list + lv.small_off, dp, store, work, ws,
                                                           xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
     for (const auto& stp : lv.steps) {
       k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 128, 0, st>>>(
-          dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, f->work, ws,
+          dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, work, ws,
           xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
   }
   if (partials) {
     int nblk = (int)((n + 1023) / 1024);
-    k_partials<St><<<dim3(nblk, B), 1024, 0, st>>>(n, dp, store, f->work, ws, xv_off, f->red, f->red_stride, nblk);
+    k_partials<St><<<dim3(nblk, B), 1024, 0, st>>>(n, dp, store, work, ws, xv_off, f->red, f->red_stride, nblk);
     GP_CHECK_LAUNCH(ctx);
   }
   for (int32_t L = sp.nlevels - 1; L >= 0; L--) {
     const SymPlan::Level& lv = sp.levels[L];
     if (lv.nsmall > 0) {
-      k_bwd_prep<St><<<dim3(lv.nsmall, B), 256, 0, st>>>(dp.small_list + lv.small_off, 1, dp, store, f->work, ws,
+      k_bwd_prep<St><<<dim3(lv.nsmall, B), 256, 0, st>>>(dp.small_list + lv.small_off, 1, dp, store, work, ws,
                                                          apv_off, xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
     if (!lv.steps.empty()) {
       const auto& ll = sp.level_large[L];   // one task per (large front, 64-column stripe)
       k_bwd_prep_large<St><<<dim3((unsigned)ll.count, B), 256, 0, st>>>(
-          dp.large_fronts + ll.off, dp.large_kb + ll.off, dp, store, f->work, ws, apv_off, xv_off);
+          dp.large_fronts + ll.off, dp.large_kb + ll.off, dp, store, work, ws, apv_off, xv_off);
       GP_CHECK_LAUNCH(ctx);
       for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
         const auto& stp = lv.steps[q];
         k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 64, 0, st>>>(
-            dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, f->work, ws, apv_off);
+            dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, work, ws, apv_off);
         GP_CHECK_LAUNCH(ctx);
       }
     }
   }
-  k_alpha<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(f->work, ws, apv_off, ps->perm, n, alpha_out);
+  k_alpha<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(work, ws, apv_off, ps->perm, n, alpha_out);
   GP_CHECK_LAUNCH(ctx);
 }
 
@@ -594,7 +623,7 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
     if (d_err) residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err, nullptr);
     return;
   }
-  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries, f->dinv};
+  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries, f->dinv32};
   run_maybe_graph(ctx, &f->gx_solve, &f->n_solve, [&] {
     solve_impl(ctx, f, store, f->rhs, f->alpha, true);
     k_sum2<<<B, 256, 0, ctx->stream>>>(f->red, f->red_stride, nblk, s_log);
