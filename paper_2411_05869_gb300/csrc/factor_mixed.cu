@@ -163,26 +163,39 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
 }
 
 // FP64 POTRF of diagonal tile kb, right-looking in shared memory (row stride T + 1, so walks down a column are
-// free of bank conflicts). The pivots d_k = L_kk^2 stay unscaled during the elimination: step k forms the scaled
-// column s_j = a_jk / d_k once, then a_ij -= a_ik s_j over the trailing triangle k < j <= i. That triangle is
-// numbered column by column from the last column, so step k's work is a prefix of one fixed list, spread evenly
-// over all threads, and the entry (k + 1, k + 1) closes the prefix; its thread forms the next reciprocal 1 / d_{k+1}.
-// Square roots and the column scaling L_ik = a_ik / sqrt(d_k) follow in one parallel pass, then the FP32 inverse
-// of L for the solves. GB300 issues FP64 at a small fraction of its FP32 rate, so the kernel keeps FP64 to the
-// elimination itself.
+// free of bank conflicts), with a one-column lookahead. The pivots d_k = L_kk^2 stay unscaled during the
+// elimination and column k enters the update through its scaled copy s_j = a_jk / d_k: a_ij -= a_ik s_j.
+// In step k warp 0 updates column k + 1, forms 1 / d_{k+1} and the scaled copy of column k + 1 (the division is
+// the longest dependency of a step: FP64 latencies on GB300 are some 64 cycles per DFMA and 440 per divide),
+// while warps 1-7 update the entries (i, j), k + 2 <= j <= i; one barrier per step. Those entries are numbered
+// column by column from the last column, so each step's work is a prefix of one fixed list, spread evenly,
+// four loads in flight per thread. Square roots and the column scaling L_ik = a_ik / sqrt(d_k) follow in one
+// parallel pass, then the FP32 inverse of L for the TRSM and the solves.
 constexpr int PT = T + 1;
 constexpr int POTRF_THREADS = 256;
 constexpr size_t POTRF_SMEM = (size_t)T * PT * sizeof(double) + (size_t)T * PT * sizeof(float) +
-                              (size_t)T * T * sizeof(float) + (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
+                              (size_t)T * T * sizeof(float) + (size_t)T * T / 2 * sizeof(float) +
+                              (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
 
-__device__ __forceinline__ double pivot_recip(double* a, int32_t* notpd, int32_t col) {
-  double d = *a;
+// 1 / d by Newton's iteration r <- r + r (1 - d r) from the hardware's approximate FP64 reciprocal; two steps
+// take its ~23 correct bits past 53 (error within an ulp or two; the pivot only needs FP64 accuracy, not
+// correct rounding). Shorter than an IEEE divide, and this sits on the critical path of every step.
+__device__ __forceinline__ double recip_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ double pivot_recip(double d, double* a, int32_t* notpd, int32_t col) {
   if (!(d > 0.0)) {
     atomicMin(notpd, col);
     d = 1.0;
     *a = d;
   }
-  return 1.0 / d;
+  return recip_nr(d);
 }
 
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
@@ -192,19 +205,24 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   double* A = sm64;                                      // T x PT
   float* Lf = reinterpret_cast<float*>(A + T * PT);     // T x PT, FP32 copy of L
   float* Inv = Lf + T * PT;                              // T x T, row-major
-  uint16_t* tab = reinterpret_cast<uint16_t*>(Inv + T * T);
-  __shared__ double rd[T];   // 1 / d_k
-  __shared__ double sc[T];   // scaled column of the current step; later 1 / L_kk
-  __shared__ float rf[T];    // 1 / L_kk in FP32
-  const int tid = threadIdx.x;
+  float* Mt = Inv + T * T;                               // T x T / 2 scratch of the block inversion
+  uint16_t* tab = reinterpret_cast<uint16_t*>(Mt + T * T / 2);
+  __shared__ double rd[T];      // 1 / d_k
+  __shared__ double sc[2][T];   // scaled copy of the current column (double-buffered); later 1 / L_kk
+  __shared__ float rf[T];       // 1 / L_kk in FP32
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], bw = min(T, w - kb * T);
   const int32_t first = dp.sn_first[s] + kb * T;
   int32_t* flag = notpd + b;
-  for (int t = tid; t < T * T; t += POTRF_THREADS) A[(t >> 6) * PT + (t & 63)] = D[t];
-  // trailing-entry list for this bw: column j = bw - 1 - c holds rows j .. bw - 1 at offsets c (c + 1) / 2 ..
+#pragma unroll
+  for (int u = 0; u < T * T / POTRF_THREADS; u++) {
+    const int t = tid + u * POTRF_THREADS;
+    A[(t >> 6) * PT + (t & 63)] = D[t];
+  }
+  // entry list for this bw: column j = bw - 1 - c holds rows j .. bw - 1 at offsets c (c + 1) / 2 ..
   const int ne = bw * (bw - 1) / 2;
   for (int e = tid; e < ne; e += POTRF_THREADS) {
     int c = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
@@ -214,25 +232,63 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
     tab[e] = (uint16_t)((i << 8) | j);
   }
   __syncthreads();
-  if (tid == 0) rd[0] = pivot_recip(A, flag, first);
+  if (warp == 0) {   // column 0: reciprocal and scaled copy
+    double r = 0.0;
+    if (lane == 0) r = rd[0] = pivot_recip(A[0], A, flag, first);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int i = 1 + lane; i < bw; i += 32) sc[0][i] = A[i * PT] * r;
+  }
   __syncthreads();
+  constexpr int NB = POTRF_THREADS - 32;
   for (int k = 0; k + 1 < bw; k++) {
-    if (tid < bw - 1 - k) sc[k + 1 + tid] = A[(k + 1 + tid) * PT + k] * rd[k];
-    __syncthreads();
-    const int cnt = (bw - 1 - k) * (bw - k) / 2;
-    for (int e = tid; e < cnt; e += POTRF_THREADS) {
-      const int ij = tab[e], i = ij >> 8, j = ij & 255;
-      const double v = A[i * PT + j] - A[i * PT + k] * sc[j];
-      A[i * PT + j] = v;
-      if (j == k + 1 && i == j) rd[k + 1] = pivot_recip(A + i * PT + j, flag, first + k + 1);
+    const double* scur = sc[k & 1];
+    const int k1 = k + 1;
+    if (warp == 0) {
+      double* snxt = sc[(k & 1) ^ 1];
+      const double s1 = scur[k1];
+      const int i0 = k1 + lane, i1 = k1 + 32 + lane;
+      double v0 = 0.0, v1 = 0.0;
+      if (i0 < bw) v0 = A[i0 * PT + k1] - A[i0 * PT + k] * s1;
+      if (i1 < bw) v1 = A[i1 * PT + k1] - A[i1 * PT + k] * s1;
+      if (i0 < bw) A[i0 * PT + k1] = v0;
+      if (i1 < bw) A[i1 * PT + k1] = v1;
+      double r = 0.0;
+      if (lane == 0) r = rd[k1] = pivot_recip(v0, A + k1 * PT + k1, flag, first + k1);
+      r = __shfl_sync(0xffffffffu, r, 0);
+      if (i0 > k1 && i0 < bw) snxt[i0] = v0 * r;
+      if (i1 < bw) snxt[i1] = v1 * r;
+    } else {
+      const int cnt = (bw - 2 - k) * (bw - 1 - k) / 2;   // entries (i, j), k + 2 <= j <= i
+      for (int e0 = tid - 32; e0 < cnt; e0 += 4 * NB) {
+        int ij[4];
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int e = e0 + q * NB;
+          ij[q] = e < cnt ? tab[e] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int i = ij[q] >> 8, j = ij[q] & 255;
+          v[q] = A[i * PT + j] - A[i * PT + k] * scur[j];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (e0 + q * NB < cnt) A[(ij[q] >> 8) * PT + (ij[q] & 255)] = v[q];
+      }
     }
     __syncthreads();
   }
-  if (tid < bw) {
-    const double l = sqrt(A[tid * PT + tid]);
-    A[tid * PT + tid] = l;
-    sc[tid] = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
-    rf[tid] = (float)(1.0 / l);
+  if (tid < T) {
+    if (tid < bw) {
+      const double l = sqrt(A[tid * PT + tid]);
+      A[tid * PT + tid] = l;
+      const double il = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
+      sc[0][tid] = il;
+      rf[tid] = (float)il;
+    } else {
+      rf[tid] = 1.f;   // rows past bw: identity, so the block inversion below stays finite
+    }
   }
   __syncthreads();
   for (int t = tid; t < T * T; t += POTRF_THREADS) {
@@ -241,37 +297,60 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
     if (i < bw && j <= i) {
       double v = A[i * PT + j];
       if (j < i) {
-        v *= sc[j];
+        v *= sc[0][j];
         A[i * PT + j] = v;
       }
       lf = (float)v;
+    } else if (i == j) {
+      lf = 1.f;
     }
     Lf[i * PT + j] = lf;
     Inv[t] = 0.f;
   }
   __syncthreads();
-  // FP32 inverse of L, one thread per column: Inv[i][j] = -(sum_{j <= l < i} L[i][l] Inv[l][j]) / L[i][i]
-  if (tid < bw) {
-    const int j = tid;
-    Inv[j * T + j] = rf[j];
-    for (int i = j + 1; i < bw; i++) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int l = j;
-      for (; l + 3 < i; l += 4) {
-        s0 = fmaf(Lf[i * PT + l], Inv[l * T + j], s0);
-        s1 = fmaf(Lf[i * PT + l + 1], Inv[(l + 1) * T + j], s1);
-        s2 = fmaf(Lf[i * PT + l + 2], Inv[(l + 2) * T + j], s2);
-        s3 = fmaf(Lf[i * PT + l + 3], Inv[(l + 3) * T + j], s3);
-      }
-      for (; l < i; l++) s0 = fmaf(Lf[i * PT + l], Inv[l * T + j], s0);
-      Inv[i * T + j] = -((s0 + s1) + (s2 + s3)) * rf[i];
+  // FP32 inverse of L by recursive 2 x 2 block inversion: inv([A 0; B C]) = [inv(A) 0; -inv(C) B inv(A) inv(C)].
+  // 4 x 4 diagonal blocks by substitution (thread per block column), then four doublings, each two parallel
+  // products (M = B inv(A), then -inv(C) M) over all pairs of blocks.
+  if (tid < T) {
+    const int o = tid & ~3, c = tid & 3;
+    float x[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      float acc = r == c ? 1.f : 0.f;
+#pragma unroll
+      for (int l = 0; l < r; l++)
+        if (l >= c) acc = fmaf(-Lf[(o + r) * PT + o + l], x[l], acc);
+      x[r] = r < c ? 0.f : acc * rf[o + r];
     }
+#pragma unroll
+    for (int r = 0; r < 4; r++) Inv[(o + r) * T + o + c] = x[r];
   }
   __syncthreads();
+  for (int h = 4; h < T; h *= 2) {
+    const int nq = (T / 2) * h;   // outputs per product over all pairs
+    for (int q = tid; q < nq; q += POTRF_THREADS) {   // M[r][c] = sum_{l >= c} B[r][l] inv(A)[l][c]
+      const int p = q / (h * h), rem = q - p * h * h, r = rem / h, c = rem - r * h, o = p * 2 * h;
+      float acc = 0.f;
+      for (int l = c; l < h; l++) acc = fmaf(Lf[(o + h + r) * PT + o + l], Inv[(o + l) * T + o + c], acc);
+      Mt[q] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < nq; q += POTRF_THREADS) {   // X21[r][c] = -sum_{l <= r} inv(C)[r][l] M[l][c]
+      const int p = q / (h * h), rem = q - p * h * h, r = rem / h, c = rem - r * h, o = p * 2 * h;
+      const float* Mp = Mt + p * h * h;
+      float acc = 0.f;
+      for (int l = 0; l <= r; l++) acc = fmaf(Inv[(o + h + r) * T + o + h + l], Mp[l * h + c], acc);
+      Inv[(o + h + r) * T + o + c] = -acc;
+    }
+    __syncthreads();
+  }
   float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  for (int t = tid; t < T * T; t += POTRF_THREADS) {
-    D[t] = A[(t >> 6) * PT + (t & 63)];
-    DI[t] = Inv[t];
+#pragma unroll
+  for (int u = 0; u < T * T / POTRF_THREADS; u++) {
+    const int t = tid + u * POTRF_THREADS;
+    const int i = t >> 6, j = t & 63;
+    D[t] = A[i * PT + j];
+    DI[t] = (i < bw && j < bw) ? Inv[t] : 0.f;
   }
 }
 

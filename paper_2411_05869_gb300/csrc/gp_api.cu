@@ -366,6 +366,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->rhs = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n);
     f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
     f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);
+    f->bwd_part = dalloc<double>(ctx, f->bufs, (size_t)B * bwd_part_entries(sp));
     f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
     f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride + 4 * (size_t)B + 8);
     pack_thetas(f, thetas);

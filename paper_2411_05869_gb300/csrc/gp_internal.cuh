@@ -265,6 +265,7 @@ struct gp_factor_s {
   int32_t* notpd = nullptr;     // B: smallest failing permuted column (INT_MAX = none)
   double* alpha = nullptr;      // B x n
   double* work = nullptr;       // solve workspace
+  double* bwd_part = nullptr;   // backward partial sums over row chunks (B x bwd_part_entries)
   double* red = nullptr;        // reduction partials, B x red_stride
   int64_t red_stride = 0;
   int64_t work_stride = 0;
@@ -304,6 +305,7 @@ void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t
 void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f);
+int64_t bwd_part_entries(const SymPlan& sp);
 #define DIAG_FLAG ((int64_t)1 << 62)
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }

@@ -144,22 +144,19 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// Load the inverse of diagonal block kb (row-major 64 x 64, FP64) into shared memory with a padded stride.
-template <class V>
-__device__ __forceinline__ void load_inverse(const V* Inv, V* Li) {
-  for (int q = threadIdx.x; q < T * T; q += blockDim.x) Li[(q / T) * (T + 1) + (q % T)] = Inv[q];
-}
-
 // Forward, block column kb of every large front of a step, one launch: every CTA forms x_J = inv(L_JJ) f_J
 // (a 64 x 64 product with the inverted diagonal block); tasks [0, nfront) write x_J to x (the front vector's
 // block stays untouched, others read it), the rest (64-row tile prefix) apply f_i -= L[i, J] x_J to one tile.
-// Row-major panels: a half-warp reads one row's 64 entries as 16 float4; column-major: thread per row.
+// 256 threads: the inverse arrives transposed through unrolled coalesced loads, the product is split four
+// ways over l and combined in a fixed order; row-major panels: a half-warp reads one row's 64 entries as 16
+// float4, four rows per half-warp with all loads in flight; column-major: thread per row.
 template <class St>
-__global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int kb,
-                           DevPlan dp, St store, typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
+__global__ void __launch_bounds__(256) k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                  int nfront, int kb, DevPlan dp, St store,
+                                                  typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
   using V = typename St::V;
-  __shared__ V Li[T * (T + 1)];
-  __shared__ V fb[T], x[T];
+  __shared__ V LiT[T * (T + 1)];   // LiT[l][q] = inv[q][l]
+  __shared__ V fb[T], x[T], part[4][T];
   const int64_t t = blockIdx.x;
   const bool writer = t < nfront;
   const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
@@ -170,38 +167,49 @@ __global__ void k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
-  load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) fb[q] = q < bw ? fv[c0 + q] : V(0);
+  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
+#pragma unroll
+  for (int u = 0; u < T * T / 256; u++) {
+    const int q = threadIdx.x + u * 256;
+    LiT[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
+  }
+  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
   __syncthreads();
-  for (int q = threadIdx.x; q < T; q += blockDim.x) {
+  {   // the inverse is lower triangular with zeros above (and past bw), so every l enters
+    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
     V acc = 0;
-    for (int l = 0; l <= q; l++) acc += Li[q * (T + 1) + l] * fb[l];
-    x[q] = q < bw ? acc : V(0);
+#pragma unroll
+    for (int l = g * 16; l < g * 16 + 16; l++) acc += LiT[l * (T + 1) + q] * fb[l];
+    part[g][q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const int q = threadIdx.x;
+    x[q] = q < bw ? (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]) : V(0);
   }
   __syncthreads();
   if (writer) {
     V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
-    for (int q = threadIdx.x; q < bw; q += blockDim.x) xv[c0 + q] = x[q];
+    if (threadIdx.x < bw) xv[c0 + threadIdx.x] = x[threadIdx.x];
     return;
   }
   const int64_t r0 = c1 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
   if constexpr (St::kRowMajor) {
-    const int lane = threadIdx.x & 31, l16 = lane & 15, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int l = l16 * 4;
-    for (int64_t base = r0 + 2 * warp; base < rend; base += 2 * nw) {
-      const int64_t i = base + (lane >> 4);
-      V acc = 0;
-      if (i < rend && l < bw) {
-        const float* row = A.P + i * A.ldw + c0;
-        if (l + 4 <= bw) {
-          float4 v = *reinterpret_cast<const float4*>(row + l);
-          acc = (V)v.x * x[l] + (V)v.y * x[l + 1] + (V)v.z * x[l + 2] + (V)v.w * x[l + 3];
-        } else {
-          for (int q = l; q < bw; q++) acc += (V)row[q] * x[q];
-        }
-      }
+    // columns past bw are zero in x and the row is padded to ldw (a multiple of 4): whole float4 reads are safe
+    const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int64_t i = r0 + hw + 16 * u;
+      v[u] = (i < rend && l < bw) ? *reinterpret_cast<const float4*>(A.P + i * A.ldw + c0 + l)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      V acc = (V)v[u].x * x[l] + (V)v[u].y * x[l + 1] + (V)v[u].z * x[l + 2] + (V)v[u].w * x[l + 3];
       for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (i < rend && l16 == 0) fv[i] -= acc;
+      const int64_t i = r0 + hw + 16 * u;
+      if (i < rend && (threadIdx.x & 15) == 0) fv[i] -= acc;
     }
   } else {
     for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
@@ -252,55 +260,91 @@ __global__ void k_bwd_prep(const int32_t* __restrict__ list, int solve_small, De
   }
 }
 
-// Backward, large fronts: t_j = x_j - sum_a L[w + a, j] alpha'(R_s[a]) for the 64-column stripe of one
-// task (a task per (front, stripe) over all of a level's large fronts). Row-major: 64 threads across the
-// stripe's columns x 4 row groups, fixed-order combination; column-major: a warp per column.
+// Backward, large fronts: t_j = x_j - sum_a L[w + a, j] alpha'(R_s[a]) for the 64-column stripe of each task
+// (a task per (front, stripe) over all of a level's large fronts), in two launches: partial sums over chunks of
+// BP_CH rows (grid: task x chunk), then a fixed-order sum of the chunks per task.
+// Row-major: 64 threads across the stripe's columns x 4 row groups, eight loads in flight per thread;
+// column-major: a warp per column.
+constexpr int BP_CH = 128;
+
 template <class St>
-__global__ void k_bwd_prep_large(const int32_t* __restrict__ fronts, const int32_t* __restrict__ kbs, DevPlan dp,
-                                 St store, typename St::V* __restrict__ work, int64_t ws, int64_t apv_off,
-                                 int64_t xv_off) {
+__global__ void __launch_bounds__(256) k_bwd_prep_part(const int32_t* __restrict__ fronts,
+                                                       const int32_t* __restrict__ kbs, int ntask, int nch,
+                                                       DevPlan dp, St store, const typename St::V* __restrict__ work,
+                                                       int64_t ws, int64_t apv_off, typename St::V* __restrict__ part) {
   using V = typename St::V;
-  __shared__ V part[4][T];
-  int32_t s = fronts[blockIdx.x];
-  const int j0 = kbs[blockIdx.x] * T;
-  int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  V* W = work + (int64_t)b * ws;
-  V* fv = W + dp.frow_off[s];
-  const V* apv = W + apv_off;
-  const V* xv = W + xv_off + dp.sn_first[s];
+  __shared__ V ps[4][T];
+  const int task = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
+  const int32_t s = fronts[task];
+  const int j0 = kbs[task] * T;
   const int w = dp.w[s], r = dp.r[s];
+  const int a0 = chunk * BP_CH;
+  if (a0 >= r) return;
+  const int a1 = min(r, a0 + BP_CH);
+  auto A = store.acc(dp, s, b);
+  const V* apv = work + (int64_t)b * ws + apv_off;
   const int nj = min(T, w - j0);
   const int32_t* R = dp.frows + dp.frow_off[s] + w;
+  V* out = part + (((int64_t)b * ntask + task) * nch + chunk) * T;
   if constexpr (St::kRowMajor) {
-    const int c = threadIdx.x & 63, g = threadIdx.x >> 6;   // blockDim = 256
+    const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
     V acc = 0;
-    if (c < nj)
-      for (int a = g; a < r; a += 4) acc += (V)A.P[(int64_t)(w + a) * A.ldw + j0 + c] * apv[R[a]];
-    part[g][c] = acc;
+    if (c < nj) {
+      for (int a = a0 + g; a < a1; a += 32) {
+        V lv[8], av[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          const int aa = a + 4 * e;
+          lv[e] = aa < a1 ? (V)A.P[(int64_t)(w + aa) * A.ldw + j0 + c] : V(0);
+          av[e] = aa < a1 ? apv[R[aa]] : V(0);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e++) acc += lv[e] * av[e];
+      }
+    }
+    ps[g][c] = acc;
     __syncthreads();
-    if (g == 0 && c < nj) fv[j0 + c] = xv[j0 + c] - (((part[0][c] + part[1][c]) + part[2][c]) + part[3][c]);
+    if (g == 0) out[c] = ((ps[0][c] + ps[1][c]) + ps[2][c]) + ps[3][c];
   } else {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int jj = warp; jj < nj; jj += nw) {
-      const int j = j0 + jj;
+    for (int jj = warp; jj < T; jj += nw) {
       V acc = 0;
-      for (int a = lane; a < r; a += 32) acc += A.L(w + a, j) * apv[R[a]];
+      if (jj < nj)
+        for (int a = a0 + lane; a < a1; a += 32) acc += A.L(w + a, j0 + jj) * apv[R[a]];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) fv[j] = xv[j] - acc;
+      if (lane == 0) out[jj] = acc;
     }
   }
 }
 
+template <class V>
+__global__ void k_bwd_prep_sum(const int32_t* __restrict__ fronts, const int32_t* __restrict__ kbs, int ntask,
+                               int nch, DevPlan dp, V* __restrict__ work, int64_t ws, int64_t xv_off,
+                               const V* __restrict__ part) {
+  const int task = blockIdx.x, b = blockIdx.y, c = threadIdx.x;
+  const int32_t s = fronts[task];
+  const int j0 = kbs[task] * T;
+  const int nj = min(T, dp.w[s] - j0);
+  if (c >= nj) return;
+  const int nc = (dp.r[s] + BP_CH - 1) / BP_CH;
+  const V* p = part + ((int64_t)b * ntask + task) * nch * T + c;
+  V acc = 0;
+  for (int k = 0; k < nc; k++) acc += p[(int64_t)k * T];
+  V* W = work + (int64_t)b * ws;
+  W[dp.frow_off[s] + j0 + c] = W[xv_off + dp.sn_first[s] + j0 + c] - acc;
+}
+
 // Backward, block column kb of every large front of a step, one launch: every CTA forms
 // z_J = inv(L_JJ)^T t_J; task 0 of a front writes z_J to alpha', tasks 1..kb apply t_k -= L[J, k]^T z_J to
-// one 64-column tile of the earlier columns k < c0.
+// one 64-column tile of the earlier columns k < c0. 256 threads; the product and the tile update are split
+// four ways over l (16 independent loads per thread in flight) and combined in a fixed order.
 template <class St>
-__global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp, St store,
-                           typename St::V* __restrict__ work, int64_t ws, int64_t apv_off) {
+__global__ void __launch_bounds__(256) k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp,
+                                                  St store, typename St::V* __restrict__ work, int64_t ws,
+                                                  int64_t apv_off) {
   using V = typename St::V;
-  __shared__ V Li[T * (T + 1)];   // the inverse block, then (column-major path) the block's rows
-  __shared__ V tb[T], z[T];
+  __shared__ V Li[T * (T + 1)];   // the inverse block (row-major), then (column-major path) the block's rows
+  __shared__ V tb[T], z[T], part[4][T];
   const int64_t t = blockIdx.x;
   const int fi = (int)(t / (kb + 1));
   const int task = (int)(t % (kb + 1));
@@ -311,41 +355,56 @@ __global__ void k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int k
   V* fv = W + dp.frow_off[s];
   const int w = dp.w[s];
   const int c0 = kb * T, bw = min(T, w - c0);
-  load_inverse(store.inv(dp, s, b) + (int64_t)kb * T * T, Li);
-  for (int q = threadIdx.x; q < T; q += blockDim.x) tb[q] = q < bw ? fv[c0 + q] : V(0);
+  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
+#pragma unroll
+  for (int u = 0; u < T * T / 256; u++) {
+    const int q = threadIdx.x + u * 256;
+    Li[(q >> 6) * (T + 1) + (q & 63)] = inv[q];
+  }
+  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
   __syncthreads();
-  for (int q = threadIdx.x; q < T; q += blockDim.x) {   // z_q = sum_{l >= q} inv[l][q] t_l
+  const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+  {   // z_q = sum_{l >= q} inv[l][q] t_l (zeros above the diagonal and past bw)
     V acc = 0;
-    for (int l = q; l < bw; l++) acc += Li[l * (T + 1) + q] * tb[l];
-    z[q] = q < bw ? acc : V(0);
+#pragma unroll
+    for (int l = g * 16; l < g * 16 + 16; l++) acc += Li[l * (T + 1) + q] * tb[l];
+    part[g][q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const int k = threadIdx.x;
+    z[k] = k < bw ? (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]) : V(0);
   }
   __syncthreads();
   if (task == 0) {
     V* apv = W + apv_off;
     const int32_t first = dp.sn_first[s];
-    for (int q = threadIdx.x; q < bw; q += blockDim.x) apv[first + c0 + q] = z[q];
+    if (threadIdx.x < bw) apv[first + c0 + threadIdx.x] = z[threadIdx.x];
     return;
   }
   const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
-  if constexpr (St::kRowMajor) {
-    for (int k = threadIdx.x; k < T; k += blockDim.x) {   // row c0 + l is contiguous over k
-      V acc = 0;
-      for (int l = 0; l < bw; l++) acc += (V)A.P[(int64_t)(c0 + l) * A.ldw + k0 + k] * z[l];
-      fv[k0 + k] -= acc;
+  V acc = 0;
+  if constexpr (St::kRowMajor) {   // row c0 + l is contiguous over the tile's columns
+    V v[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      const int l = g * 16 + e;
+      v[e] = l < bw ? (V)A.P[(int64_t)(c0 + l) * A.ldw + k0 + q] : V(0);
     }
+#pragma unroll
+    for (int e = 0; e < 16; e++) acc += v[e] * z[g * 16 + e];
   } else {
-    V* Lt = Li;   // reuse: the block's rows for the tile's columns, staged by columns (contiguous)
-    __syncthreads();
-    for (int q = threadIdx.x; q < T * bw; q += blockDim.x) {
-      int l = q % bw, k = q / bw;
-      Lt[l * (T + 1) + k] = A.L(c0 + l, k0 + k);
+    for (int e = 0; e < 16; e++) {
+      const int l = g * 16 + e;
+      if (l < bw) acc += A.L(c0 + l, k0 + q) * z[l];
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < T; k += blockDim.x) {
-      V acc = 0;
-      for (int l = 0; l < bw; l++) acc += Lt[l * (T + 1) + k] * z[l];
-      fv[k0 + k] -= acc;
-    }
+  }
+  __syncthreads();   // part is reused
+  part[g][q] = acc;
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const int k = threadIdx.x;
+    fv[k0 + k] -= (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]);
   }
 }
 
@@ -507,6 +566,17 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int
   if (i < cnt) y[i] += x[i];
 }
 
+// Row chunks of the widest front among level L's large-front tasks (the backward partial-sum grid).
+int bwd_chunks(const SymPlan& sp, int32_t L) {
+  const auto& ll = sp.level_large[L];
+  int nch = 1;
+  for (int64_t q = 0; q < ll.count; q++) {
+    const int32_t s = sp.large_fronts[ll.off + q];
+    nch = std::max(nch, (int)((sp.sn_r[s] + BP_CH - 1) / BP_CH));
+  }
+  return nch;
+}
+
 template <class St>
 void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs, double* alpha_out, bool partials) {
   gp_pointset* ps = f->ps;
@@ -535,7 +605,7 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       GP_CHECK_LAUNCH(ctx);
     }
     for (const auto& stp : lv.steps) {
-      k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 128, 0, st>>>(
+      k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 256, 0, st>>>(
           dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, work, ws,
           xv_off);
       GP_CHECK_LAUNCH(ctx);
@@ -555,12 +625,17 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
     }
     if (!lv.steps.empty()) {
       const auto& ll = sp.level_large[L];   // one task per (large front, 64-column stripe)
-      k_bwd_prep_large<St><<<dim3((unsigned)ll.count, B), 256, 0, st>>>(
-          dp.large_fronts + ll.off, dp.large_kb + ll.off, dp, store, work, ws, apv_off, xv_off);
+      const int nch = bwd_chunks(sp, L);
+      V* part = reinterpret_cast<V*>(f->bwd_part);
+      k_bwd_prep_part<St><<<dim3((unsigned)ll.count, nch, B), 256, 0, st>>>(
+          dp.large_fronts + ll.off, dp.large_kb + ll.off, (int)ll.count, nch, dp, store, work, ws, apv_off, part);
+      GP_CHECK_LAUNCH(ctx);
+      k_bwd_prep_sum<V><<<dim3((unsigned)ll.count, B), T, 0, st>>>(dp.large_fronts + ll.off, dp.large_kb + ll.off,
+                                                                   (int)ll.count, nch, dp, work, ws, xv_off, part);
       GP_CHECK_LAUNCH(ctx);
       for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
         const auto& stp = lv.steps[q];
-        k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 64, 0, st>>>(
+        k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
             dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, work, ws, apv_off);
         GP_CHECK_LAUNCH(ctx);
       }
@@ -650,4 +725,12 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
   k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
   GP_CHECK_LAUNCH(ctx);
+}
+
+// Entries (per proposal) of the backward partial-sum scratch: the largest level's tasks x row chunks x 64.
+int64_t bwd_part_entries(const SymPlan& sp) {
+  int64_t e = 64;
+  for (int32_t L = 0; L < sp.nlevels; L++)
+    if (sp.level_large[L].count > 0) e = std::max<int64_t>(e, sp.level_large[L].count * bwd_chunks(sp, L) * T);
+  return e;
 }
