@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 
 // ---------------------------------------------------------------------------------------------------------
 // Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x 128 tiles, j <= i.
-// Modes (block column kb, 256-column group [g0, gend) containing it):
+// Modes (block column kb, (64 GP_GROUP)-column group [g0, gend) containing it):
 //   1: intra-group: rows >= c1 x columns [c1, gend), rectangular tiles, K = the block column;
 //   2: group end: rows/columns >= gend, lower-triangular tiles, K = the whole group [g0, gend).
 // The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
@@ -445,6 +445,9 @@ constexpr int UW_EPI = 8 * 32 * 32 * 4;  // a 32 x 32 FP32 slab per epilogue war
 constexpr int UW_BAR = 256;
 constexpr int UW_SMEM = UW_STAGES * UW_STAGE + UW_EPI + UW_BAR + 1024;
 constexpr uint32_t UW_TMEM_COLS = 256;   // two 128-column FP32 accumulators
+
+// Bit mask of the integers below x, 0 <= x <= 32.
+__device__ __forceinline__ uint32_t below32(int x) { return x >= 32 ? 0xffffffffu : ((1u << x) - 1u); }
 
 struct UTile {
   int32_t s, slot;
@@ -676,26 +679,32 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           cb = U + (j - u.w) - (int64_t)u.w * u.r;
           cs = u.r;
         }
-        // entries (i, j) of this lane's column: lower triangle, inside the front, not in an FP64 tile;
+        // rows of this lane's column in the warp's 32: [lo, hi) = lower triangle inside the front (and inside
+        // the update's column range), minus [dlo, dhi) = rows whose entry lives in an FP64 diagonal tile;
         // all 32 loads in flight before the first store
-        uint32_t okm = 0;
-#pragma unroll
-        for (int rr = 0; rr < 32; rr++) {
-          const int64_t i = ib + rr;
-          if (colok && i < u.m && j <= i && !(i < u.w && (i >> 6) == (j >> 6))) okm |= 1u << rr;
+        int lo = 32, hi = 0, dlo = 0, dhi = 0;
+        if (colok) {
+          lo = (int)imin64(32, j > ib ? j - ib : 0);
+          hi = (int)imin64(32, u.m > ib ? u.m - ib : 0);
+          if (j < u.w) {
+            const int64_t b0 = j & ~(int64_t)63, b1 = imin64(b0 + 64, u.w);
+            dlo = (int)imin64(32, b0 > ib ? b0 - ib : 0);
+            dhi = (int)imin64(32, b1 > ib ? b1 - ib : 0);
+          }
         }
+        const uint32_t okm = lo < hi ? (below32(hi) & ~below32(lo)) & ~(below32(dhi) & ~below32(dlo)) : 0u;
+        float* base = cb + ib * cs;   // dereferenced only at valid rows
+        const int csi = (int)cs;
         float old[32];
 #pragma unroll
-        for (int rr = 0; rr < 32; rr++) old[rr] = (okm >> rr & 1) ? cb[(ib + rr) * cs] : 0.f;
+        for (int rr = 0; rr < 32; rr++) old[rr] = (okm >> rr & 1) ? base[rr * csi] : 0.f;
 #pragma unroll
         for (int rr = 0; rr < 32; rr++)
-          if (okm >> rr & 1) cb[(ib + rr) * cs] = old[rr] - slab[rr * 32 + (lane ^ rr)];
-        if (ib < u.w && j < u.w) {   // entries of the FP64 diagonal tiles
-          for (int rr = 0; rr < 32; rr++) {
-            const int64_t i = ib + rr;
-            if (colok && i < u.w && j <= i && (i >> 6) == (j >> 6))
-              D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)] -= (double)slab[rr * 32 + (lane ^ rr)];
-          }
+          if (okm >> rr & 1) base[rr * csi] = old[rr] - slab[rr * 32 + (lane ^ rr)];
+        const int d0 = max(dlo, lo), d1 = min(dhi, hi);
+        for (int rr = d0; rr < d1; rr++) {   // entries of the FP64 diagonal tiles
+          const int64_t i = ib + rr;
+          D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)] -= (double)slab[rr * 32 + (lane ^ rr)];
         }
       }
       __syncwarp();
@@ -894,7 +903,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                                                                     DE);
         GP_CHECK_LAUNCH(ctx);
       }
-      if (stp.intra_total > 0) {   // this block's update of the rest of its 256-column group
+      if (stp.intra_total > 0) {   // this block's update of the rest of its column group
         ProfScope ps_(ctx, KC_UPDATE, B * stp.intra_flops);
         launch_update(ctx, f, stp.intra_total, dp.upd_fronts + stp.intra_off, dp.upd_pre + stp.intra_pre_off,
                       stp.n_intra, stp.kb, 1);

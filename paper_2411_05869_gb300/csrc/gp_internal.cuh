@@ -159,7 +159,7 @@ struct SymPlan {
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
   struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
                       int64_t pre128_off; int64_t upd128_total;
-                      // mixed path, 256-column groups: intra-group update (rows >= c1 x the group's remaining
+                      // mixed path, (64 GP_GROUP)-column groups: intra-group update (rows >= c1 x the group's remaining
                       // columns, K = this block) and, at a group's last block, the deferred group update
                       // (rows/columns after the group, K = the group's width); fronts and tile prefixes of each
                       int64_t intra_off, intra_pre_off, intra_total; int32_t n_intra;
@@ -204,7 +204,7 @@ struct DevPlan {
   int32_t* upd_fronts;
   int64_t* upd_pre;
 };
-#define GP_GROUP 4   // 64-column blocks per deferred-update group of the mixed path
+#define GP_GROUP 8   // 64-column blocks per deferred-update group of the mixed path
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
 
