@@ -381,10 +381,19 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
   const int64_t r0 = c1 + (t - pre[fi]) * T;
   const int nr = (int)imin64(T, m - r0);
-  for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
-    int i = q >> 6, j = q & 63;
-    Is[i * (T + 1) + j] = DI[q];   // zero outside the lower bw x bw triangle
-    Bs[i * (T + 1) + j] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
+  // all 32 loads of a thread in flight at once (the rows of B are 64 contiguous FP32 at stride ldw)
+  float bv[16], iv[16];
+#pragma unroll
+  for (int u = 0; u < 16; u++) {
+    const int q = threadIdx.x + u * 256, i = q >> 6, j = q & 63;
+    iv[u] = DI[q];   // zero outside the lower bw x bw triangle
+    bv[u] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < 16; u++) {
+    const int q = threadIdx.x + u * 256, i = q >> 6, j = q & 63;
+    Is[i * (T + 1) + j] = iv[u];
+    Bs[i * (T + 1) + j] = bv[u];
   }
   __syncthreads();
   const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
@@ -868,7 +877,13 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
     int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
-    k_zero_updates32<<<dim3(nl, 8, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd32, UE);
+    int64_t r2max = 1;   // CTAs per front sized by the level's largest update matrix
+    for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
+      const int64_t r = sp.sn_r[sp.lev_sn[q]];
+      r2max = std::max(r2max, r * r);
+    }
+    const unsigned zy = (unsigned)std::min<int64_t>(2048, (r2max + 8191) / 8192);
+    k_zero_updates32<<<dim3(nl, zy, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd32, UE);
     GP_CHECK_LAUNCH(ctx);
     for (const auto& ea : lv.ea) {
       ProfScope ps_(ctx, KC_EXTEND_ADD);
