@@ -430,30 +430,36 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 }
 
 // ---------------------------------------------------------------------------------------------------------
-// Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x 128 tiles, j <= i.
+// Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x TN tiles, j <= i.
 // Modes (block column kb, (64 GP_GROUP)-column group [g0, gend) containing it):
-//   1: intra-group: rows >= c1 x columns [c1, gend), rectangular tiles, K = the block column;
-//   2: group end: rows/columns >= gend, lower-triangular tiles, K = the whole group [g0, gend).
+//   1: intra-group: rows >= c1 x columns [c1, gend), rectangular 128 x 128 tiles, K = the block column;
+//   2: group end: rows/columns >= gend, 128 x 256 tiles on and below the diagonal, K = the whole group [g0, gend).
 // The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
 // tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
-// significant bits survive the products instead of the 11 of one TF32 pass).
+// significant bits survive the products instead of the 11 of one TF32 pass). The wide tiles of mode 2 halve
+// the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
+// bounds this kernel).
 //
 // One persistent CTA per SM walks the launch's tiles (all fronts, all proposals) with three roles:
-//   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a 3-stage ring of 128-byte-swizzled tiles;
+//   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a ring of 128-byte-swizzled tiles;
 //   warp 1 (one lane): tcgen05.mma, 12 instructions per chunk, into one of two TMEM accumulators;
 //   warps 2-9: the epilogue, which drains the other accumulator (tcgen05.ld -> swizzled 32 x 32 shared slab ->
-//              coalesced read-modify-write of the front, 16 loads in flight per lane) while the next tile's
+//              coalesced read-modify-write of the front, 32 loads in flight per lane) while the next tile's
 //              MMAs run.
-// Diagonal tiles (same rows for A and B) load one operand pair. Waits are bounded; a wait that runs out sets
-// *err and the CTA winds down.
+// A tile whose A rows are a block of its B rows (on the diagonal) loads only B. Waits are bounded; a wait that
+// runs out sets *err and the CTA winds down.
 constexpr int UW_THREADS = 320;
-constexpr int UW_STAGES = 3;
-constexpr int UW_OP = 128 * 32 * 4;      // one operand chunk: 128 rows x 32 FP32 (128-byte rows)
-constexpr int UW_STAGE = 4 * UW_OP;      // A_hi, A_lo, B_hi, B_lo
 constexpr int UW_EPI = 8 * 32 * 32 * 4;  // a 32 x 32 FP32 slab per epilogue warp
 constexpr int UW_BAR = 256;
-constexpr int UW_SMEM = UW_STAGES * UW_STAGE + UW_EPI + UW_BAR + 1024;
-constexpr uint32_t UW_TMEM_COLS = 256;   // two 128-column FP32 accumulators
+template <int TN>
+struct UW {
+  static constexpr int STAGES = TN == 256 ? 2 : 3;
+  static constexpr int OPA = 128 * 32 * 4;        // A operand chunk: 128 rows x 32 FP32 (128-byte rows)
+  static constexpr int OPB = TN * 32 * 4;         // B operand chunk
+  static constexpr int STAGE = 2 * OPA + 2 * OPB; // A_hi, A_lo, B_hi, B_lo
+  static constexpr int SMEM = STAGES * STAGE + UW_EPI + UW_BAR + 1024;
+  static constexpr uint32_t TMEM_COLS = 2 * TN;   // two FP32 accumulators of TN columns
+};
 
 // Bit mask of the integers below x, 0 <= x <= 32.
 __device__ __forceinline__ uint32_t below32(int x) { return x >= 32 ? 0xffffffffu : ((1u << x) - 1u); }
@@ -464,6 +470,9 @@ struct UTile {
   int64_t m, i0, j0, jlim;
 };
 
+// Tile tt of a launch: proposal, front (prefix search), then its position. Mode 2 with TN = 256: row I (128
+// rows) holds floor(I / 2) + 1 tiles of 256 columns, rows 2p and 2p + 1 starting at p (p + 1).
+template <int TN>
 __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                              int nfront, int64_t total, int kb, int mode, const DevPlan& dp,
                                              const int32_t* __restrict__ slot_of, int64_t tt) {
@@ -482,7 +491,7 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   const int64_t loc = t - pre[fi];
   int64_t I, J, base;
   if (mode == 1) {
-    const int64_t ntc = (gend - c1 + 127) / 128;
+    const int64_t ntc = (gend - c1 + TN - 1) / TN;
     I = loc / ntc;
     J = loc - I * ntc;
     base = c1;
@@ -490,39 +499,51 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
     u.K = bw;
     u.kc = c0;
   } else {
-    I = (int64_t)((sqrtf(8.f * (float)loc + 1.f) - 1.f) * 0.5f);
-    while ((I + 1) * (I + 2) / 2 <= loc) I++;
-    while (I * (I + 1) / 2 > loc) I--;
-    J = loc - I * (I + 1) / 2;
+    if (TN == 128) {
+      I = (int64_t)((sqrtf(8.f * (float)loc + 1.f) - 1.f) * 0.5f);
+      while ((I + 1) * (I + 2) / 2 <= loc) I++;
+      while (I * (I + 1) / 2 > loc) I--;
+      J = loc - I * (I + 1) / 2;
+    } else {
+      int64_t p = (int64_t)((sqrtf(4.f * (float)loc + 1.f) - 1.f) * 0.5f);
+      while ((p + 1) * (p + 2) <= loc) p++;
+      while (p * (p + 1) > loc) p--;
+      const int64_t rem = loc - p * (p + 1);
+      I = 2 * p + (rem > p ? 1 : 0);
+      J = rem > p ? rem - (p + 1) : rem;
+    }
     base = gend;
     u.jlim = u.m;
     u.K = gend - g0;
     u.kc = g0;
   }
   u.i0 = base + I * 128;
-  u.j0 = base + J * 128;
+  u.j0 = base + J * TN;
   return u;
 }
 
+template <int TN>
 __global__ void __launch_bounds__(UW_THREADS, 1)
     k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
                 int64_t ntiles, int kb, int mode, DevPlan dp, const uint8_t* __restrict__ tmaps,
                 const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
                 float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err) {
+  using C = UW<TN>;
+  constexpr int NS = C::STAGES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* epi = reinterpret_cast<float*>(smem + UW_STAGES * UW_STAGE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + UW_STAGES * UW_STAGE + UW_EPI);
-  uint64_t* full = bars;                       // [UW_STAGES] operands landed
-  uint64_t* empty = bars + UW_STAGES;          // [UW_STAGES] MMAs done reading
-  uint64_t* tfull = bars + 2 * UW_STAGES;      // [2] accumulator complete
-  uint64_t* tempty = bars + 2 * UW_STAGES + 2; // [2] accumulator drained
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * UW_STAGES + 4);
+  float* epi = reinterpret_cast<float*>(smem + NS * C::STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * C::STAGE + UW_EPI);
+  uint64_t* full = bars;                // [NS] operands landed
+  uint64_t* empty = bars + NS;          // [NS] MMAs done reading
+  uint64_t* tfull = bars + 2 * NS;      // [2] accumulator complete
+  uint64_t* tempty = bars + 2 * NS + 2; // [2] accumulator drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = tcg::smem_u32(smem);
   if (threadIdx.x == 0) {
-    for (int q = 0; q < UW_STAGES; q++) {
+    for (int q = 0; q < NS; q++) {
       tcg::mbar_init(&full[q], 1);
       tcg::mbar_init(&empty[q], 1);
     }
@@ -533,7 +554,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 1) tcg::tmem_alloc(tslot, UW_TMEM_COLS);
+  if (warp == 1) tcg::tmem_alloc(tslot, C::TMEM_COLS);
   tcg::tc_fence_before();
   __syncthreads();
   tcg::tc_fence_after();
@@ -542,33 +563,42 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     *abort_flag = 1;
     atomicExch(err, 1);
   };
+  // which 128-row block of B holds the A rows (-1: none, A is loaded)
+  auto a_in_b = [](const UTile& u) -> int {
+    if (u.i0 == u.j0) return 0;
+    if (TN == 256 && u.i0 == u.j0 + 128) return 1;
+    return -1;
+  };
 
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
       uint32_t st = 0, ph = 0;
       for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
         const uint8_t* mh = tmaps + (int64_t)u.slot * 256;
         const uint8_t* ml = mh + 128;
         tcg::tmap_acquire(mh);
         tcg::tmap_acquire(ml);
-        const bool same = u.i0 == u.j0;
+        const bool shared_a = a_in_b(u) >= 0;
         const int nch = (u.K + 31) / 32;
         for (int c = 0; c < nch; c++) {
           if (!tcg::mbar_wait(&empty[st], ph ^ 1)) {
             fail();
             break;
           }
-          const uint32_t sa = sbase + st * UW_STAGE;
-          tcg::mbar_arrive_expect_tx(&full[st], same ? 2 * UW_OP : 4 * UW_OP);
+          const uint32_t sa = sbase + st * C::STAGE, sb = sa + 2 * C::OPA;
+          tcg::mbar_arrive_expect_tx(&full[st], (shared_a ? 0 : 2 * C::OPA) + 2 * C::OPB);
           const int x = u.kc + c * 32;
-          tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
-          tcg::tma_load_3d(sa + UW_OP, ml, x, (int)u.i0, u.b, &full[st]);
-          if (!same) {
-            tcg::tma_load_3d(sa + 2 * UW_OP, mh, x, (int)u.j0, u.b, &full[st]);
-            tcg::tma_load_3d(sa + 3 * UW_OP, ml, x, (int)u.j0, u.b, &full[st]);
+          if (!shared_a) {
+            tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
+            tcg::tma_load_3d(sa + C::OPA, ml, x, (int)u.i0, u.b, &full[st]);
           }
-          if (++st == UW_STAGES) {
+#pragma unroll
+          for (int hb = 0; hb < TN / 128; hb++) {
+            tcg::tma_load_3d(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
+            tcg::tma_load_3d(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
+          }
+          if (++st == NS) {
             st = 0;
             ph ^= 1;
           }
@@ -577,18 +607,18 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
-      const uint32_t idesc = tcg::idesc_tf32(128, 128);
+      const uint32_t idesc = tcg::idesc_tf32(128, TN);
       uint32_t st = 0, ph = 0, acc = 0, aph = 0;
       for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
-        const bool same = u.i0 == u.j0;
+        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const int ab = a_in_b(u);
         const int nch = (u.K + 31) / 32;
         if (!tcg::mbar_wait(&tempty[acc], aph ^ 1)) {
           fail();
           break;
         }
         tcg::tc_fence_after();
-        const uint32_t d = tmem + acc * 128;
+        const uint32_t d = tmem + acc * TN;
         bool ok = true;
         for (int c = 0; c < nch; c++) {
           if (!tcg::mbar_wait(&full[st], ph)) {
@@ -596,8 +626,9 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             break;
           }
           tcg::tc_fence_after();
-          const uint32_t aH = sbase + st * UW_STAGE, aL = aH + UW_OP;
-          const uint32_t bH = same ? aH : aH + 2 * UW_OP, bL = same ? aL : aH + 3 * UW_OP;
+          const uint32_t bH = sbase + st * C::STAGE + 2 * C::OPA, bL = bH + C::OPB;
+          const uint32_t aH = ab >= 0 ? bH + ab * C::OPA : bH - 2 * C::OPA;
+          const uint32_t aL = ab >= 0 ? bL + ab * C::OPA : bH - C::OPA;
 #pragma unroll
           for (int kk = 0; kk < 4; kk++) {
             const uint32_t o = kk * 32;
@@ -608,7 +639,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             tcg::mma_tf32(d, ah, bh, idesc, 1u);
           }
           tcg::mma_commit(&empty[st]);
-          if (++st == UW_STAGES) {
+          if (++st == NS) {
             st = 0;
             ph ^= 1;
           }
@@ -624,24 +655,25 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         }
       }
     }
-  } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [64 h, 64 h + 64)
+  } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [h TN / 2, (h + 1) TN / 2)
+    constexpr int NSL = TN / 64;   // 32-column slabs per warp
     const int q = warp & 3, h = (warp - 2) >> 2;
     float* slab = epi + (warp - 2) * 1024;
     uint32_t acc = 0, aph = 0;
     for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-      const UTile u = decode_tile(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+      const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
       float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
       float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
       double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
       const int64_t ib = u.i0 + q * 32;
-      // while the tile's MMAs run: pull this warp's target rows (2 x 128 bytes each) into L2
+      const int64_t jc = u.j0 + h * (TN / 2);
+      // while the tile's MMAs run: pull this warp's target rows (NSL x 128 bytes each) into L2
       {
         const int64_t i = ib + lane;
-        const int64_t jc = u.j0 + h * 64;
         if (i < u.m) {
 #pragma unroll
-          for (int half = 0; half < 2; half++) {
-            const int64_t j = jc + half * 32;
+          for (int sl = 0; sl < NSL; sl++) {
+            const int64_t j = jc + sl * 32;
             if (j <= i && j < u.jlim) {
               const float* pa = j < u.w ? P + i * u.ldw + j : U + (i - u.w) * u.r + (j - u.w);
               asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
@@ -654,30 +686,22 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         break;
       }
       tcg::tc_fence_after();
-      float v1[32];
-      {
-        float v0[32];
-        const uint32_t ta = tmem + acc * 128 + ((uint32_t)(q * 32) << 16) + h * 64;
-        tcg::tmem_ld32(ta, v0);
-        tcg::tmem_ld32(ta + 32, v1);
-#pragma unroll
-        for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v0[e];
-      }
-      tcg::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tcg::mbar_arrive(&tempty[acc]);   // this warp's part of the accumulator is in registers
-      if (++acc == 2) {
-        acc = 0;
-        aph ^= 1;
-      }
-      for (int sl = 0; sl < 2; sl++) {
-        if (sl == 1) {
+      const uint32_t ta = tmem + acc * TN + ((uint32_t)(q * 32) << 16) + h * (TN / 2);
+      for (int sl = 0; sl < NSL; sl++) {
+        {
+          float v[32];
+          tcg::tmem_ld32(ta + sl * 32, v);
+          if (sl == NSL - 1) {   // this warp's part of the accumulator has been read
+            tcg::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tcg::mbar_arrive(&tempty[acc]);
+          }
           __syncwarp();
 #pragma unroll
-          for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v1[e];
+          for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v[e];
         }
         __syncwarp();
-        const int64_t j = u.j0 + h * 64 + sl * 32 + lane;
+        const int64_t j = jc + sl * 32 + lane;
         const bool colok = j < u.jlim;
         float* cb;
         int64_t cs;
@@ -715,15 +739,19 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           const int64_t i = ib + rr;
           D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)] -= (double)slab[rr * 32 + (lane ^ rr)];
         }
+        __syncwarp();
       }
-      __syncwarp();
+      if (++acc == 2) {
+        acc = 0;
+        aph ^= 1;
+      }
     }
   }
   tcg::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tcg::tc_fence_after();
-    tcg::tmem_dealloc(tmem, UW_TMEM_COLS);
+    tcg::tmem_dealloc(tmem, C::TMEM_COLS);
   }
 }
 
@@ -732,7 +760,10 @@ void set_attrs() {
   if (g_attrs) return;
   GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, UW_SMEM));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_INTRA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<GP_TN_INTRA>::SMEM));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<GP_TN_GROUP>::SMEM));
   GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   g_attrs = true;
 }
@@ -799,10 +830,14 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
   const SymPlan& sp = f->ps->sp;
   const int64_t ntiles = total * f->B;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
-  k_update_ws<<<grid, UW_THREADS, UW_SMEM, ctx->stream>>>(fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp,
-                                                          f->op_maps, f->op_slot, f->panels32, f->diag, f->upd32,
-                                                          sp.panel32_entries, sp.diag_entries, sp.update_entries,
-                                                          f->tiles_err);
+  if (mode == 1)
+    k_update_ws<GP_TN_INTRA><<<grid, UW_THREADS, UW<GP_TN_INTRA>::SMEM, ctx->stream>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp, f->op_maps, f->op_slot, f->panels32, f->diag,
+        f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+  else
+    k_update_ws<GP_TN_GROUP><<<grid, UW_THREADS, UW<GP_TN_GROUP>::SMEM, ctx->stream>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp, f->op_maps, f->op_slot, f->panels32, f->diag,
+        f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
   GP_CHECK_LAUNCH(ctx);
 }
 

@@ -205,6 +205,8 @@ struct DevPlan {
   int64_t* upd_pre;
 };
 #define GP_GROUP 8   // 64-column blocks per deferred-update group of the mixed path
+#define GP_TN_INTRA 128   // tensor-core tile width (columns) of the mixed path's intra-group updates
+#define GP_TN_GROUP 256   // ... and of its group-end updates (rows stay 128 per tile)
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
 

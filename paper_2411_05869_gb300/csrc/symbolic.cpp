@@ -68,6 +68,12 @@ struct FirstFit {
 };
 
 inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
+// Tiles of 128 rows x 256 columns on and below the diagonal of a square of nt 128-row tile rows: row I holds
+// I / 2 + 1 of them (rows 2p and 2p + 1 hold p + 1 each).
+inline int64_t stair(int64_t nt) {
+  const int64_t p = nt / 2;
+  return p * (p + 1) + (nt & 1) * (p + 1);
+}
 
 }  // namespace
 
@@ -503,7 +509,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, w);
           int64_t gend = std::min<int64_t>((int64_t)(kb / GP_GROUP + 1) * GP_GROUP * GP_TILE, w);
           if (c1 >= gend) continue;   // this block ends its group
-          int64_t ntr = (m - c1 + 127) / 128, ntc = (gend - c1 + 127) / 128;
+          int64_t ntr = (m - c1 + 127) / 128, ntc = (gend - c1 + GP_TN_INTRA - 1) / GP_TN_INTRA;
           sp.upd_fronts.push_back(s);
           acc += ntr * ntc;
           sp.upd_pre.push_back(acc);
@@ -526,9 +532,9 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           int64_t g0 = (int64_t)(kb / GP_GROUP) * GP_GROUP * GP_TILE;
           int64_t gend = std::min<int64_t>(g0 + GP_GROUP * GP_TILE, w);
           if (c1 < gend || gend >= m) continue;   // not a group end, or nothing after the group
-          int64_t nt = (m - gend + 127) / 128;
+          int64_t nt = (m - gend + 127) / 128;   // 128-row tile rows; row I holds I / 2 + 1 tiles of 256 columns
           sp.upd_fronts.push_back(s);
-          acc += tri(nt);
+          acc += stair(nt);
           sp.upd_pre.push_back(acc);
           stp.n_group++;
           double M = (double)(m - gend);
