@@ -431,8 +431,9 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 
 // ---------------------------------------------------------------------------------------------------------
 // Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x TN tiles, j <= i.
-// Modes (block column kb, (64 GP_GROUP)-column group [g0, gend) containing it):
-//   1: intra-group: rows >= c1 x columns [c1, gend), rectangular 128 x 128 tiles, K = the block column;
+// Modes (block column kb = columns [c0, c1), in the (64 GP_GROUP)-column group [g0, gend)):
+//   3: left-looking, before the block's POTRF: rows >= c0 x the block's columns, 128 x 64 tiles, K = [g0, c0)
+//      (the group's earlier blocks);
 //   2: group end: rows/columns >= gend, 128 x 256 tiles on and below the diagonal, K = the whole group [g0, gend).
 // The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
 // tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
@@ -455,7 +456,8 @@ template <int TN>
 struct UW {
   static constexpr int STAGES = TN == 256 ? 2 : 3;
   static constexpr int OPA = 128 * 32 * 4;        // A operand chunk: 128 rows x 32 FP32 (128-byte rows)
-  static constexpr int OPB = TN * 32 * 4;         // B operand chunk
+  static constexpr int BROWS = TN < 128 ? 128 : TN;   // B rows loaded (whole 128-row boxes; N = TN are used)
+  static constexpr int OPB = BROWS * 32 * 4;      // B operand chunk
   static constexpr int STAGE = 2 * OPA + 2 * OPB; // A_hi, A_lo, B_hi, B_lo
   static constexpr int SMEM = STAGES * STAGE + UW_EPI + UW_BAR + 1024;
   static constexpr uint32_t TMEM_COLS = 2 * TN;   // two FP32 accumulators of TN columns
@@ -488,16 +490,16 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   u.m = (int64_t)u.w + u.r;
   const int c0 = kb * T, bw = min(T, u.w - c0), c1 = c0 + bw;
   const int g0 = (kb / GP_GROUP) * GP_GROUP * T, gend = min(g0 + GP_GROUP * T, u.w);
+  (void)bw;
   const int64_t loc = t - pre[fi];
   int64_t I, J, base;
-  if (mode == 1) {
-    const int64_t ntc = (gend - c1 + TN - 1) / TN;
-    I = loc / ntc;
-    J = loc - I * ntc;
-    base = c1;
-    u.jlim = gend;
-    u.K = bw;
-    u.kc = c0;
+  if (mode == 3) {
+    I = loc;
+    J = 0;
+    base = c0;
+    u.jlim = c1;
+    u.K = c0 - g0;
+    u.kc = g0;
   } else {
     if (TN == 128) {
       I = (int64_t)((sqrtf(8.f * (float)loc + 1.f) - 1.f) * 0.5f);
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             tcg::tma_load_3d(sa + C::OPA, ml, x, (int)u.i0, u.b, &full[st]);
           }
 #pragma unroll
-          for (int hb = 0; hb < TN / 128; hb++) {
+          for (int hb = 0; hb < C::BROWS / 128; hb++) {
             tcg::tma_load_3d(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
             tcg::tma_load_3d(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
           }
@@ -760,8 +762,8 @@ void set_attrs() {
   if (g_attrs) return;
   GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_INTRA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               UW<GP_TN_INTRA>::SMEM));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<GP_TN_LEFT>::SMEM));
   GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                UW<GP_TN_GROUP>::SMEM));
   GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
@@ -830,8 +832,8 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
   const SymPlan& sp = f->ps->sp;
   const int64_t ntiles = total * f->B;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
-  if (mode == 1)
-    k_update_ws<GP_TN_INTRA><<<grid, UW_THREADS, UW<GP_TN_INTRA>::SMEM, ctx->stream>>>(
+  if (mode == 3)
+    k_update_ws<GP_TN_LEFT><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp, f->op_maps, f->op_slot, f->panels32, f->diag,
         f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
   else
@@ -940,6 +942,11 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
     for (const auto& stp : lv.steps) {
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
+      if (stp.left_total > 0) {   // this block column from the earlier blocks of its group
+        ProfScope ps_(ctx, KC_UPDATE, B * stp.left_flops);
+        launch_update(ctx, f, stp.left_total, dp.upd_fronts + stp.left_off, dp.upd_pre + stp.left_pre_off,
+                      stp.n_left, stp.kb, 3);
+      }
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
         k_potrf64<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
@@ -952,11 +959,6 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                                                                     f->panels32, f->op_hi, f->op_lo, f->dinv32, P32E,
                                                                     DE);
         GP_CHECK_LAUNCH(ctx);
-      }
-      if (stp.intra_total > 0) {   // this block's update of the rest of its column group
-        ProfScope ps_(ctx, KC_UPDATE, B * stp.intra_flops);
-        launch_update(ctx, f, stp.intra_total, dp.upd_fronts + stp.intra_off, dp.upd_pre + stp.intra_pre_off,
-                      stp.n_intra, stp.kb, 1);
       }
       if (stp.group_total > 0) {   // fronts whose group ends here: the deferred update with K = group width
         ProfScope ps_(ctx, KC_UPDATE, B * stp.group_flops);

@@ -152,19 +152,20 @@ struct SymPlan {
   std::vector<int64_t> sn_loff32, sn_doff;
   int64_t panel32_entries = 0, diag_entries = 0;
   std::vector<int64_t> step_pre128;  // per step: prefix of 128 x 128 update tiles (nfront + 1 entries)
-  std::vector<int32_t> upd_fronts;   // per step: fronts of the intra-group and of the group update
-  std::vector<int64_t> upd_pre;      // their 128 x 128 tile prefixes
+  std::vector<int32_t> upd_fronts;   // per step: fronts of the left-looking and of the group update
+  std::vector<int64_t> upd_pre;      // their tile prefixes
 
   // schedule for the numeric factorization, per level
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
   struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
                       int64_t pre128_off; int64_t upd128_total;
-                      // mixed path, (64 GP_GROUP)-column groups: intra-group update (rows >= c1 x the group's remaining
-                      // columns, K = this block) and, at a group's last block, the deferred group update
-                      // (rows/columns after the group, K = the group's width); fronts and tile prefixes of each
-                      int64_t intra_off, intra_pre_off, intra_total; int32_t n_intra;
+                      // mixed path, (64 GP_GROUP)-column groups: left-looking update of this block column
+                      // (rows >= c0 x its 64 columns, K = the group's earlier blocks) and, at a group's last block,
+                      // the deferred group update (rows/columns after the group, K = the group's width); fronts
+                      // and tile prefixes of each
+                      int64_t left_off, left_pre_off, left_total; int32_t n_left;
                       int64_t group_off, group_pre_off, group_total; int32_t n_group;
-                      double intra_flops, group_flops;
+                      double left_flops, group_flops;
                       double potrf_flops, trsm_flops, upd_flops; };   // useful flops of the step's launches
   struct Level {
     std::vector<EaLaunch> ea;        // one per child slot
@@ -205,7 +206,7 @@ struct DevPlan {
   int64_t* upd_pre;
 };
 #define GP_GROUP 8   // 64-column blocks per deferred-update group of the mixed path
-#define GP_TN_INTRA 128   // tensor-core tile width (columns) of the mixed path's intra-group updates
+#define GP_TN_LEFT 64     // tensor-core tile width (columns) of the mixed path's left-looking block updates
 #define GP_TN_GROUP 256   // ... and of its group-end updates (rows stay 128 per tile)
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);

@@ -497,28 +497,26 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
         }
         stp.upd128_total = acc;
         // group-deferred updates of the mixed path
-        stp.intra_off = (int64_t)sp.upd_fronts.size();
-        stp.intra_pre_off = (int64_t)sp.upd_pre.size();
-        stp.n_intra = 0;
-        stp.intra_flops = 0.0;
+        stp.left_off = (int64_t)sp.upd_fronts.size();
+        stp.left_pre_off = (int64_t)sp.upd_pre.size();
+        stp.n_left = 0;
+        stp.left_flops = 0.0;
         acc = 0;
         sp.upd_pre.push_back(0);
-        for (int32_t t = 0; t < cnt; t++) {
+        for (int32_t t = 0; t < cnt; t++) {   // block column kb from the earlier blocks of its group
           int32_t s = sp.large_fronts[stp.fr_off + t];
           int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
-          int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, w);
-          int64_t gend = std::min<int64_t>((int64_t)(kb / GP_GROUP + 1) * GP_GROUP * GP_TILE, w);
-          if (c1 >= gend) continue;   // this block ends its group
-          int64_t ntr = (m - c1 + 127) / 128, ntc = (gend - c1 + GP_TN_INTRA - 1) / GP_TN_INTRA;
+          int64_t c0 = (int64_t)kb * GP_TILE, c1 = std::min<int64_t>(c0 + GP_TILE, w);
+          int64_t g0 = (int64_t)(kb / GP_GROUP) * GP_GROUP * GP_TILE;
+          if (c0 == g0) continue;   // the first block of its group
           sp.upd_fronts.push_back(s);
-          acc += ntr * ntc;
+          acc += (m - c0 + 127) / 128;
           sp.upd_pre.push_back(acc);
-          stp.n_intra++;
-          double bw = std::min<double>(GP_TILE, (double)w - (double)kb * GP_TILE);
-          double M = (double)(m - c1), N = (double)(gend - c1);
-          stp.intra_flops += 2.0 * bw * (M * N - N * (N - 1.0) / 2.0);
+          stp.n_left++;
+          double bw = (double)(c1 - c0);
+          stp.left_flops += 2.0 * (double)(c0 - g0) * (bw * (bw + 1.0) / 2.0 + (double)(m - c1) * bw);
         }
-        stp.intra_total = acc;
+        stp.left_total = acc;
         stp.group_off = (int64_t)sp.upd_fronts.size();
         stp.group_pre_off = (int64_t)sp.upd_pre.size();
         stp.n_group = 0;
