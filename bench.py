@@ -44,6 +44,8 @@ def make_workload(name: str):
     from paper_2411_05869_gb300 import synth
     if name == "station_1.2M":
         return synth.config(5, with_test=False)
+    if name == "station_120k":   # the same field over the first 24 days: a profiling-size case
+        return synth.station_spacetime(nsites=5000, ndays=24, with_test=False)
     if name == "spacetime_100k":
         return synth.config(2, m=0)
     if name == "batched_200k":
