@@ -186,6 +186,77 @@ GP_API gp_status gp_pattern_counts_noalloc(gp_ctx* ctx, const double* d_X, int64
 /* Number of kernel launches this context has issued (a counter for launch accounting). */
 GP_API int64_t gp_launch_count(const gp_ctx* ctx);
 
+/* Device bytes gp_factor allocates for B settings of `theta`'s shape on point set ps in precision prec (the
+ * memory a caller or a server admits against). Host-only. Errors: GP_ERR_ARG. */
+GP_API gp_status gp_factor_bytes(const gp_pointset* ps, const gp_hyper* theta, int B, gp_precision prec,
+                                 size_t* bytes);
+
+/* Build the per-precision maps of a point set (GP_MIXED: the CSR -> FP32 panel / FP64 tile map) now, on the
+ * point set's context, instead of inside the first gp_factor of that precision. A point set may serve
+ * factors created on other contexts of the same device (each context its own stream and host thread); prepare
+ * it first when such factors can be created concurrently. Synchronous. Errors: GP_ERR_ARG, GP_ERR_NOMEM. */
+GP_API gp_status gp_pointset_prepare(gp_ctx* ctx, gp_pointset* ps, gp_precision prec);
+
+/* ----------------------------------------------------------------------------------------- request server
+ * A continuous-batching server of log-likelihood (Sec. 3.3) and predictive-mean (Sec. 3.2) requests on one GPU.
+ * The paper has no counterpart (it evaluates one likelihood at a time across many GPUs); this is the serving
+ * layer over the same hot path. Point sets are added once (A1, A2, A5, A6 cached). Requests of uneven sizes
+ * queue in arrival order; `slots` worker threads, each with its own context and CUDA stream, admit the head
+ * request when it fits: a slot re-uses an idle factor it holds for the same point set and precision (values
+ * and factorization recomputed for the new theta, no allocation), or creates one if its bytes
+ * (gp_factor_bytes) fit mem_budget_bytes after evicting idle cached factors, least recently used first.
+ * Requests run concurrently on the slots' streams; a result does not depend on what else runs.
+ * All device buffers of a request are the caller's and must stay valid until its completion is polled. */
+typedef struct gp_server_s gp_server_t;
+
+typedef enum { GP_REQ_LOGLIK = 0, GP_REQ_PREDICT = 1 } gp_request_kind;
+
+typedef struct {
+  int kind;                 /* gp_request_kind */
+  int32_t pointset;         /* id from gp_server_add_pointset */
+  gp_precision precision;
+  const gp_hyper* theta;    /* host; copied at submission */
+  const double* d_resid;    /* n (device): r = z - mu of the point set's points */
+  const double* d_Xtest;    /* m x d (device), GP_REQ_PREDICT */
+  int64_t m;                /* test points, GP_REQ_PREDICT */
+  const double* d_mu_test;  /* m (device) or NULL, GP_REQ_PREDICT */
+  double* d_out;            /* device: 1 log-likelihood (GP_REQ_LOGLIK) or m predictive means (GP_REQ_PREDICT) */
+  double* d_err;            /* device or NULL: 1 relative residual |r - C alpha| / |r| */
+} gp_request;
+
+typedef struct {
+  int64_t id;               /* from gp_server_submit */
+  gp_status status;
+  int32_t slot;             /* worker that ran it */
+  double t_submit, t_start, t_done;   /* seconds on the host's monotonic clock */
+} gp_completion;
+
+typedef struct {
+  size_t budget, held, peak;          /* factor bytes: budget, reserved or held now, largest held */
+  int32_t cached_factors, queued, running, max_running;
+  int64_t completed;
+} gp_server_stats_t;
+
+/* slots in 1..64; mem_budget_bytes caps the bytes of the factors the server holds (point sets not included).
+ * Errors: GP_ERR_ARG, GP_ERR_CUDA. */
+GP_API gp_status gp_server_create(int device, int slots, size_t mem_budget_bytes, gp_server_t** out);
+/* gp_assemble + gp_pointset_prepare(GP_MIXED) on the server's own context; *id numbers point sets from 0.
+ * Synchronous. Errors as gp_assemble. */
+GP_API gp_status gp_server_add_pointset(gp_server_t* s, const double* d_X, int64_t n, int d,
+                                        const double* core_radius, int32_t* id);
+/* Queue a request (non-blocking). Errors: GP_ERR_ARG (bad fields or point set id), GP_ERR_NOMEM (its factor
+ * alone exceeds the budget: it could never run). */
+GP_API gp_status gp_server_submit(gp_server_t* s, const gp_request* req, int64_t* id);
+/* Move up to max completions (in completion order) to out; returns how many (non-blocking). */
+GP_API int gp_server_poll(gp_server_t* s, gp_completion* out, int max);
+/* Block until the queue is empty and no request runs; timeout_s <= 0 waits without limit.
+ * Errors: GP_ERR_TIMEOUT. */
+GP_API gp_status gp_server_wait(gp_server_t* s, double timeout_s);
+GP_API gp_status gp_server_stats(gp_server_t* s, gp_server_stats_t* stats);
+GP_API const char* gp_server_last_error(const gp_server_t* s);
+/* Stops the workers after their current requests (queued requests are dropped) and frees everything. */
+GP_API void gp_server_destroy(gp_server_t* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -277,15 +277,18 @@ __global__ void __launch_bounds__(256) k_update(const int32_t* __restrict__ fron
   }
 }
 
-bool g_attrs_set = false;
-void set_attrs() {
-  if (g_attrs_set) return;
-  GP_CUDA(cudaFuncSetAttribute(k_small_front, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T * T * (int)sizeof(double)));
-  g_attrs_set = true;
+std::once_flag g_attrs_once;
+void set_attrs() {   // once per process (contexts may run on several host threads)
+  std::call_once(g_attrs_once, [] {
+    GP_CUDA(cudaFuncSetAttribute(k_small_front, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
+    GP_CUDA(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * T * T * (int)sizeof(double)));
+    GP_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * T * T * (int)sizeof(double)));
+    GP_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * T * T * (int)sizeof(double)));
+  });
 }
 
 __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {

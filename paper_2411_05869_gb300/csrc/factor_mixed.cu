@@ -757,17 +757,17 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   }
 }
 
-bool g_attrs = false;
-void set_attrs() {
-  if (g_attrs) return;
-  GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               UW<GP_TN_LEFT>::SMEM));
-  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               UW<GP_TN_GROUP>::SMEM));
-  GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
-  g_attrs = true;
+std::once_flag g_attrs_once;
+void set_attrs() {   // once per process (contexts may run on several host threads)
+  std::call_once(g_attrs_once, [] {
+    GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 UW<GP_TN_LEFT>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 UW<GP_TN_GROUP>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
+  });
 }
 
 __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
@@ -844,14 +844,15 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     GP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
     GP_REQUIRE(q == cudaDriverEntryPointSuccess && p, "cuTensorMapEncodeTiled is not available from the driver");
     fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+  });
   return fn;
 }
 }  // namespace

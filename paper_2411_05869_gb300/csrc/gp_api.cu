@@ -10,9 +10,9 @@
 void* dev_alloc(gp_ctx* ctx, std::vector<DevBuf>& owner, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
-  if (ctx->budget && ctx->held + bytes > ctx->budget)
-    throw GpError{GP_ERR_NOMEM, "device memory budget exceeded (" + std::to_string(ctx->held + bytes) + " > " +
-                                    std::to_string(ctx->budget) + " bytes)"};
+  if (ctx->budget && ctx->held.load() + bytes > ctx->budget)
+    throw GpError{GP_ERR_NOMEM, "device memory budget exceeded (" + std::to_string(ctx->held.load() + bytes) +
+                                    " > " + std::to_string(ctx->budget) + " bytes)"};
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
@@ -28,7 +28,7 @@ void dev_free_all(gp_ctx* ctx, std::vector<DevBuf>& owner) {
   if (!owner.empty()) cudaStreamSynchronize(ctx->stream);
   for (auto& b : owner) {
     cudaFree(b.p);
-    ctx->held -= std::min(ctx->held, b.bytes);
+    ctx->held.fetch_sub(std::min(ctx->held.load(), b.bytes));
   }
   owner.clear();
 }
@@ -328,7 +328,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
   *out = nullptr;
   gp_factor_t* f = new gp_factor_t();
   gp_status st = guarded(ctx, [&] {
-    GP_REQUIRE(ps && ps->ctx == ctx, "point set missing or from another context");
+    GP_REQUIRE(ps && ps->ctx && ps->ctx->device == ctx->device, "point set missing or on another device");
     GP_REQUIRE(thetas && B >= 1, "B >= 1 settings are required");
     GP_REQUIRE(prec == GP_FP64 || prec == GP_MIXED, "unknown precision");
     const SymPlan& sp = ps->sp;
@@ -345,7 +345,10 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
       f->panels = dalloc<double>(ctx, f->bufs, (size_t)B * sp.panel_entries);
       f->upd = dalloc<double>(ctx, f->bufs, (size_t)B * sp.update_entries);
     } else {
-      if (!ps->dest32) compute_dest_map_mixed(ctx, ps);
+      if (!ps->dest32) {   // the point set's own context owns (and stream-orders) its per-precision map
+        compute_dest_map_mixed(ps->ctx, ps);
+        GP_CUDA(cudaStreamSynchronize(ps->ctx->stream));
+      }
       f->panels32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
       f->diag = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
@@ -382,6 +385,57 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
   ctx->live++;
   *out = f;
   return GP_OK;
+}
+
+namespace {
+size_t alloc_bytes(size_t b) { return ((b == 0 ? 16 : b) + 255) & ~size_t(255); }
+}  // namespace
+
+// Device bytes gp_factor allocates for (ps, prec, B): the same list of buffers, rounded as dev_alloc rounds.
+size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const ThetaDims& td) {
+  const SymPlan& sp = ps->sp;
+  const size_t b = (size_t)B, n = (size_t)ps->n;
+  size_t t = alloc_bytes((size_t)theta_stride_of(td) * b * 8) + alloc_bytes((b * n * td.n1 + 1) * 8);
+  if (prec == GP_FP64) {
+    t += alloc_bytes(b * sp.panel_entries * 8) + alloc_bytes(b * sp.update_entries * 8);
+  } else {
+    std::vector<char> seen(sp.sn_w.size(), 0);
+    size_t nmaps = 0;
+    for (int32_t s : sp.upd_fronts)
+      if (!seen[s]) {
+        seen[s] = 1;
+        nmaps++;
+      }
+    nmaps = std::max<size_t>(nmaps, 1);
+    t += alloc_bytes(b * sp.panel32_entries * 4) + alloc_bytes(b * sp.diag_entries * 8) +
+         alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
+         alloc_bytes(b * sp.diag_entries * 4) + 2 * alloc_bytes(b * sp.panel32_entries * 4) +
+         alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
+  }
+  t += alloc_bytes(b * ps->nnz * 8) + alloc_bytes(b * 4) + alloc_bytes(b * n * 8);
+  if (prec == GP_FP64) t += alloc_bytes(b * sp.diag_entries * 8);
+  t += alloc_bytes(b * n * 8) + alloc_bytes(b * (3 * n + sp.vec_update_entries + 64) * 8) +
+       alloc_bytes(b * (size_t)bwd_part_entries(sp) * 8) +
+       alloc_bytes((b * (2 * ((n + 1023) / 1024) + 8) + 4 * b + 8) * 8);
+  return t;
+}
+
+extern "C" gp_status gp_factor_bytes(const gp_pointset* ps, const gp_hyper* theta, int B, gp_precision prec,
+                                     size_t* bytes) {
+  if (!ps || !theta || !bytes || B < 1 || (prec != GP_FP64 && prec != GP_MIXED)) return GP_ERR_ARG;
+  if (theta->n1 < 0 || theta->n1 > GP_MAX_N1 || theta->d != ps->d) return GP_ERR_ARG;
+  *bytes = factor_bytes(ps, prec, B, ThetaDims{theta->d, theta->n1, theta->n2, theta->bump_dims});
+  return GP_OK;
+}
+
+extern "C" gp_status gp_pointset_prepare(gp_ctx* ctx, gp_pointset* ps, gp_precision prec) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(ps && ps->ctx == ctx, "point set missing or from another context");
+    GP_REQUIRE(prec == GP_FP64 || prec == GP_MIXED, "unknown precision");
+    if (prec == GP_MIXED && !ps->dest32) compute_dest_map_mixed(ctx, ps);
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
 }
 
 extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas) {

@@ -10,6 +10,8 @@
 //   A8-A11 solves           solve.cu     (forward/backward supernodal solves, log-det, refinement)
 //   A12 predictive mean     predict.cu
 #pragma once
+#include <atomic>
+#include <mutex>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -62,10 +64,10 @@ struct gp_ctx {
   int nsm = 1;           // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   size_t budget = 0;     // 0 = unlimited
-  size_t held = 0;       // bytes currently held by this context's handles
+  std::atomic<size_t> held{0};   // bytes currently held by this context's handles
   int64_t launches = 0;
   std::string err;
-  int64_t live = 0;          // point sets and factors still holding this context
+  std::atomic<int64_t> live{0};  // point sets and factors still holding this context
   bool destroyed = false;    // gp_destroy was called; the context goes with its last handle
   // launch profiler: CUDA events around every launch of a class, on the context stream
   bool prof = false;
@@ -309,6 +311,7 @@ void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f);
 int64_t bwd_part_entries(const SymPlan& sp);
+size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const ThetaDims& td);
 #define DIAG_FLAG ((int64_t)1 << 62)
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }

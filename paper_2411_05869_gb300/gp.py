@@ -45,23 +45,44 @@ class FactorInfo(ctypes.Structure):
     _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32)]
 
 
+class GpRequest(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("pointset", ctypes.c_int32), ("precision", c_int), ("theta", ctypes.POINTER(GpHyper)),
+                ("d_resid", P), ("d_Xtest", P), ("m", c_i64), ("d_mu_test", P), ("d_out", P), ("d_err", P)]
+
+
+class GpCompletion(ctypes.Structure):
+    _fields_ = [("id", c_i64), ("status", c_int), ("slot", ctypes.c_int32), ("t_submit", c_dbl), ("t_start", c_dbl),
+                ("t_done", c_dbl)]
+
+
+class GpServerStats(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_size_t), ("held", ctypes.c_size_t), ("peak", ctypes.c_size_t),
+                ("cached_factors", ctypes.c_int32), ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
+                ("max_running", ctypes.c_int32), ("completed", c_i64)]
+
+
+GP_REQ_LOGLIK, GP_REQ_PREDICT = 0, 1
+
 SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_pointset_free", "gp_pointset_info",
            "gp_pointset_export", "gp_factor", "gp_factor_update", "gp_factor_free", "gp_factor_info", "gp_loglik",
-           "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read"]
+           "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read", "gp_factor_bytes",
+           "gp_pointset_prepare", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
+           "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7}
 
 _lib = None
-_LIVE = {"factor": weakref.WeakSet(), "pointset": weakref.WeakSet(), "context": weakref.WeakSet()}
+_LIVE = {"server": weakref.WeakSet(), "factor": weakref.WeakSet(), "pointset": weakref.WeakSet(),
+         "context": weakref.WeakSet()}
 _EXIT_HOOKED = False
 
 
 def _free_all():
     """Free the library handles still alive at interpreter exit, factors first, while CUDA is still up."""
-    for kind in ("factor", "pointset", "context"):
+    for kind in ("server", "factor", "pointset", "context"):
         for obj in list(_LIVE[kind]):
             try:
-                obj.close() if kind == "context" else obj.free()
+                obj.close() if kind in ("context", "server") else obj.free()
             except Exception:
                 pass
 
@@ -119,6 +140,26 @@ def load(build_if_missing: bool = True):
     L.gp_profile.argtypes = [P, c_int]
     L.gp_profile_read.restype = c_int
     L.gp_profile_read.argtypes = [P, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]
+    L.gp_factor_bytes.restype = c_int
+    L.gp_factor_bytes.argtypes = [P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gp_pointset_prepare.restype = c_int
+    L.gp_pointset_prepare.argtypes = [P, P, c_int]
+    L.gp_server_create.restype = c_int
+    L.gp_server_create.argtypes = [c_int, c_int, ctypes.c_size_t, ctypes.POINTER(P)]
+    L.gp_server_add_pointset.restype = c_int
+    L.gp_server_add_pointset.argtypes = [P, P, c_i64, c_int, DP, ctypes.POINTER(ctypes.c_int32)]
+    L.gp_server_submit.restype = c_int
+    L.gp_server_submit.argtypes = [P, ctypes.POINTER(GpRequest), ctypes.POINTER(c_i64)]
+    L.gp_server_poll.restype = c_int
+    L.gp_server_poll.argtypes = [P, ctypes.POINTER(GpCompletion), c_int]
+    L.gp_server_wait.restype = c_int
+    L.gp_server_wait.argtypes = [P, c_dbl]
+    L.gp_server_stats.restype = c_int
+    L.gp_server_stats.argtypes = [P, ctypes.POINTER(GpServerStats)]
+    L.gp_server_last_error.restype = ctypes.c_char_p
+    L.gp_server_last_error.argtypes = [P]
+    L.gp_server_destroy.restype = None
+    L.gp_server_destroy.argtypes = [P]
     _lib = L
     return L
 
@@ -245,6 +286,13 @@ class PointSet:
         self.ctx.check(self.ctx.lib.gp_pointset_export(self.h, what, out.ctypes.data_as(P), out.nbytes))
         return out
 
+    def factor_bytes(self, theta, B: int = 1, precision: int = GP_FP64) -> int:
+        """Device bytes a factor of B settings of theta's shape takes (gp_factor_bytes)."""
+        pack = _HyperPack([theta])
+        out = ctypes.c_size_t()
+        self.ctx.check(self.ctx.lib.gp_factor_bytes(self.h, pack.arr, B, precision, ctypes.byref(out)))
+        return int(out.value)
+
     def free(self):
         if self.h:
             self.ctx.lib.gp_pointset_free(self.h)
@@ -307,5 +355,82 @@ class Factor:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """The continuous-batching request server (gp_server_*): cached point sets, `slots` concurrent workers,
+    admission by a device-memory budget. Device buffers passed to submit() must stay alive until their
+    completion has been polled; the server keeps a reference to them until then."""
+
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget_bytes: int = 0):
+        self.lib = load()
+        h = P()
+        st = self.lib.gp_server_create(device, slots, mem_budget_bytes, ctypes.byref(h))
+        if st != 0:
+            raise GpError(st, "gp_server_create failed")
+        self.h = h
+        self._keep = {}
+        _hook_exit()
+        _LIVE["server"].add(self)
+
+    def check(self, st: int):
+        if st != 0:
+            raise GpError(st, self.lib.gp_server_last_error(self.h).decode())
+
+    def add_pointset(self, X, core_radius) -> int:
+        import torch
+        assert X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+        X = X.contiguous()
+        rad = np.ascontiguousarray(np.asarray(core_radius, dtype=np.float64))
+        pid = ctypes.c_int32()
+        self.check(self.lib.gp_server_add_pointset(self.h, P(X.data_ptr()), X.shape[0], X.shape[1], _dp(rad),
+                                                   ctypes.byref(pid)))
+        return int(pid.value)
+
+    def submit(self, pointset: int, theta, resid, out, precision: int = GP_MIXED, Xtest=None, mu_test=None,
+               err=None) -> int:
+        """Queue a log-likelihood request (Xtest None: out holds 1 value) or a predictive-mean request
+        (out holds Xtest.shape[0] values)."""
+        pack = _HyperPack([theta])
+        req = GpRequest(GP_REQ_PREDICT if Xtest is not None else GP_REQ_LOGLIK, pointset, precision, pack.arr,
+                        P(resid.data_ptr()), P(Xtest.data_ptr()) if Xtest is not None else None,
+                        0 if Xtest is None else Xtest.shape[0],
+                        P(mu_test.data_ptr()) if mu_test is not None else None, P(out.data_ptr()),
+                        P(err.data_ptr()) if err is not None else None)
+        rid = c_i64()
+        self.check(self.lib.gp_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid)))
+        self._keep[int(rid.value)] = (resid, out, Xtest, mu_test, err)
+        return int(rid.value)
+
+    def poll(self, max_n: int = 256) -> list:
+        buf = (GpCompletion * max_n)()
+        k = self.lib.gp_server_poll(self.h, buf, max_n)
+        out = []
+        for i in range(k):
+            c = buf[i]
+            out.append({"id": c.id, "status": c.status, "slot": c.slot, "t_submit": c.t_submit,
+                        "t_start": c.t_start, "t_done": c.t_done})
+            self._keep.pop(int(c.id), None)
+        return out
+
+    def wait(self, timeout_s: float = 0.0):
+        self.check(self.lib.gp_server_wait(self.h, timeout_s))
+
+    def stats(self) -> dict:
+        st = GpServerStats()
+        self.check(self.lib.gp_server_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in GpServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
