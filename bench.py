@@ -187,13 +187,22 @@ def run_gpu(args, rank, world, local_rank):
     info = ps.info()
     rng = np.random.default_rng(1234 + rank)
     from paper_2411_05869_gb300 import synth
-    thetas = [synth.perturb(rng, hp, 0.05) for _ in range(max(args.steps, 1) + args.warmup + 8)]
-    f = ctx.factor(ps, [hp], prec)
-    out = torch.empty(1, dtype=torch.float64, device=dev)
+    B = max(1, args.batch)
+    # proposals per factorization: all B when they fit, else the largest chunk that fits in 80 % of free memory
+    per = ps.factor_bytes(hp, 1, prec)
+    free = torch.cuda.mem_get_info(dev)[0]
+    Bc = max(1, min(B, int(0.8 * free) // per))
+    nchunk = (B + Bc - 1) // Bc
+    thetas = [synth.perturb(rng, hp, 0.05 if B == 1 else 0.1) for _ in range(B * (args.steps + args.warmup + 2))]
+    f = ctx.factor(ps, thetas[:Bc], prec)
+    out = torch.empty(Bc, dtype=torch.float64, device=dev)
+    resid_b = resid.expand(Bc, -1).contiguous() if Bc > 1 else resid
 
-    def step(i):
-        f.update([thetas[i % len(thetas)]])
-        f.loglik(resid, out=out)
+    def step(i):   # one evaluation of each of the B proposals of step i
+        for c in range(nchunk):
+            k0 = (i * B + c * Bc) % len(thetas)
+            f.update([thetas[(k0 + j) % len(thetas)] for j in range(Bc)])
+            f.loglik(resid_b, out=out)
 
     # warm-up
     for i in range(args.warmup):
@@ -214,25 +223,26 @@ def run_gpu(args, rank, world, local_rank):
     stream.synchronize()
     clk = clocks.stop()
     launches = ctx.launches() - launches0
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    per_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[args.steps])
     ll_last = float(out.cpu()[0])
 
     # end to end through the public API from host buffers: H2D of r from pinned memory, theta structs from
     # the host, D2H of the log-likelihood, every step
-    r_host = torch.from_numpy(np.ascontiguousarray(w.resid)).pin_memory()
-    out_host = torch.empty(1, dtype=torch.float64).pin_memory()
-    r_dev = torch.empty_like(resid)
+    r_host = torch.from_numpy(np.tile(w.resid, (Bc, 1)).reshape(tuple(resid_b.shape))).pin_memory()
+    out_host = torch.empty(Bc, dtype=torch.float64).pin_memory()
+    r_dev = torch.empty_like(resid_b)
     e2e_steps = max(1, min(args.steps, 5))
     stream.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for k in range(e2e_steps):
-            r_dev.copy_(r_host, non_blocking=True)
-            f.update([thetas[k]])
-            f.loglik(r_dev, out=out)
-            out_host.copy_(out, non_blocking=True)
-            stream.synchronize()
+            for c in range(nchunk):
+                r_dev.copy_(r_host, non_blocking=True)
+                f.update([thetas[(k * B + c * Bc + j) % len(thetas)] for j in range(Bc)])
+                f.loglik(r_dev, out=out)
+                out_host.copy_(out, non_blocking=True)
+                stream.synchronize()
     e2e_s = time.perf_counter() - t0
 
     # per-kernel-class profile of one more step (not part of the timed region)
@@ -242,33 +252,116 @@ def run_gpu(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
 
-    res = dict(total_ms=total_ms, per=per, launches=launches, clk=clk, info=info, t_assemble=t_assemble,
+    res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
-               h2d=int(w.resid.nbytes), d2h=8, w=w)
+               h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
     # FP64 comparison (mixed runs only): one evaluation of the same setting through the FP64 path, timed from
     # the call that creates (allocates and factors) the FP64 factor to its log-likelihood
     if prec == gp.GP_MIXED and args.fp64_steps > 0:
-        th = thetas[0]
-        f.update([th])
-        f.loglik(resid, out=out)
-        ll_mixed = float(out.cpu()[0])
+        nb = min(Bc, args.fp64_proposals)
+        ths = thetas[:Bc]
+        f.update(ths)
+        f.loglik(resid_b, out=out)
+        stream.synchronize()   # out is written on the library's stream
+        ll_mixed = out.cpu().numpy()[:nb].copy()
+        f.free()   # room for the FP64 factor
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream.synchronize()
         with torch.cuda.stream(stream):
             e0.record(stream)
-            f64 = ctx.factor(ps, [th], gp.GP_FP64)
-            f64.loglik(resid, out=out)
+            f64 = ctx.factor(ps, ths[:nb], gp.GP_FP64)
+            out64 = f64.loglik(resid_b[:nb] if nb > 1 else resid)
             e1.record(stream)
         stream.synchronize()
-        ll64 = float(out.cpu()[0])
-        res["fp64"] = {"ms_per_step": e0.elapsed_time(e1), "evals_per_s": 1e3 / e0.elapsed_time(e1),
-                       "loglik": ll64, "mixed_loglik": ll_mixed,
-                       "mixed_rel_diff": abs(ll_mixed - ll64) / abs(ll64),
-                       "note": "one evaluation of the FP64 path (creation, first factorization and loglik)"}
+        ll64 = out64.cpu().numpy()
+        rel = np.abs(ll_mixed - ll64) / np.abs(ll64)
+        res["fp64"] = {"ms_per_step": e0.elapsed_time(e1) / nb, "evals_per_s": nb * 1e3 / e0.elapsed_time(e1),
+                       "loglik": float(ll64[0]), "mixed_loglik": float(ll_mixed[0]),
+                       "mixed_rel_diff": float(rel.max()), "proposals_compared": int(nb),
+                       "mixed_rel_diff_per_proposal": [float(x) for x in rel] if nb > 1 else None,
+                       "note": f"FP64 path on {nb} of the settings (one factor creation, first factorization "
+                               "and loglik), per-evaluation time; mixed_rel_diff is the largest over them"}
         f64.free()
-    f.free()
+        f = None
+    if f is not None:
+        f.free()
     ps.free()
     return res
+
+
+# ------------------------------------------------------------------------------------------------ serving leg
+
+def run_serving(args):
+    """The serving mix: 20 cached point sets (n log-uniform in [5k, 500k], ~60 nnz/row, 16 bumps), requests of
+    70 % log-likelihood and 30 % predictive mean (m uniform in 1000..50000 test points), Poisson arrivals at
+    rates swept around the measured saturation rate, through the library's request server."""
+    import torch
+    from paper_2411_05869_gb300 import gp, synth
+    sets = synth.serving_pointsets(count=args.serve_sets)
+    srv_budget = int(args.serve_budget_gb * 1e9)
+    rng = np.random.default_rng(4242)
+
+    def requests(count, prec):
+        out = []
+        for _ in range(count):
+            i = int(rng.integers(len(sets)))
+            th = synth.perturb(rng, sets[i].hyper, 0.1)
+            m = int(rng.integers(1000, 50001)) if rng.random() < 0.3 else 0
+            out.append((i, th, m, prec))
+        return out
+
+    def run(srv, ids, resid, reqs, rate):
+        """Submit at Poisson arrival times (rate None: all at once); per-request latency from submission."""
+        keep, lat = {}, []
+        t0 = time.perf_counter()
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs))) if rate else np.zeros(len(reqs))
+        for (i, th, m, prec), ta in zip(reqs, arrivals):
+            wait = t0 + ta - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            if m:
+                xt = torch.rand(m, 3, dtype=torch.float64, device="cuda")
+                out = torch.empty(m, dtype=torch.float64, device="cuda")
+                rid = srv.submit(ids[i], th, resid[i], out, prec, Xtest=xt)
+                keep[rid] = (xt, out)
+            else:
+                out = torch.empty(1, dtype=torch.float64, device="cuda")
+                rid = srv.submit(ids[i], th, resid[i], out, prec)
+                keep[rid] = (out,)
+        srv.wait(0.0)
+        done = srv.poll(4096)
+        bad = sum(1 for c in done if c["status"] != 0)
+        lat = np.array([c["t_done"] - c["t_submit"] for c in done])
+        span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
+        return {"requests": len(done), "failed": bad, "req_per_s": len(done) / span,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+    result = {}
+    for prec, name in ((gp.GP_MIXED, "mixed"), (gp.GP_FP64, "fp64")):
+        if name == "fp64" and args.serve_fp64_requests <= 0:
+            continue
+        srv = gp.Server(0, slots=args.serve_slots, mem_budget_bytes=srv_budget)
+        ids = [srv.add_pointset(torch.as_tensor(w.X, device="cuda"), w.hyper.core_radius) for w in sets]
+        resid = [torch.as_tensor(w.resid, device="cuda") for w in sets]
+        count = args.serve_requests if name == "mixed" else args.serve_fp64_requests
+        run(srv, ids, resid, requests(min(count, 2 * len(sets)), prec), None)   # warm the factor cache
+        sat = run(srv, ids, resid, requests(count, prec), None)
+        sweep = {"saturation": sat}
+        if name == "mixed":
+            for f in args.serve_rates:
+                sweep[f"{f:g}x"] = run(srv, ids, resid, requests(count, prec), f * sat["req_per_s"])
+        sweep["server"] = srv.stats()
+        result[name] = sweep
+        srv.close()
+    ns = [int(w.X.shape[0]) for w in sets]
+    line = {"metric": "serving mix requests/s and p50/p99 latency (mixed vs FP64)",
+            "value": result["mixed"]["saturation"]["req_per_s"], "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "tf32+f64",
+            "config": {"workload": "serving", "sets": len(sets), "n_min": min(ns), "n_max": max(ns),
+                       "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+                       "mix": "70% loglik, 30% predict (m ~ U{1000..50000})"},
+            "serving": result}
+    print(json.dumps(line))
 
 
 def main():
@@ -280,9 +373,19 @@ def main():
     ap.add_argument("--workload", default=os.environ.get("GP_BENCH_WORKLOAD", "station_1.2M"))
     ap.add_argument("--precision", default=os.environ.get("GP_BENCH_PRECISION", "mixed"), choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-proposals", type=int, default=8, help="batched runs: proposals compared with FP64")
+    ap.add_argument("--batch", type=int, default=0, help="proposals per step (default: 64 for batched_200k, else 1)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-sets", type=int, default=20)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-fp64-requests", type=int, default=12)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 1.0, 1.5])
     args = ap.parse_args()
+    if args.batch <= 0:
+        args.batch = 64 if args.workload == "batched_200k" else 1
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -317,6 +420,11 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args)
+        return
+
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -330,7 +438,7 @@ def main():
         tot_s = float(t.item())
     if rank != 0:
         return
-    value = args.steps * world / tot_s
+    value = args.steps * res["B"] * world / tot_s
     per = np.array(res["per"])
     info = res["info"]
     prof = res["prof"]
@@ -355,7 +463,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "tf32+f64",
         "data": "synthetic (seeded; shapes of the paper's space-time temperature workload)",
         "config": workload_config(res["w"], args.workload, args.precision,
-                                  {"parallelism": f"replicas{world}", "nnz": info["nnz"], "nnzL": info["nnzL"],
+                                  {"parallelism": f"replicas{world}", "B": res["B"],
+                                   "proposals_per_factorization": res["Bc"], "factorizations_per_step": res["nchunk"],
+                                   "nnz": info["nnz"], "nnzL": info["nnzL"],
                                    "supernodes": info["nsuper"], "levels": info["nlevels"],
                                    "max_front": info["max_front"], "assemble_s": round(res["t_assemble"], 3)}),
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
@@ -368,7 +478,7 @@ def main():
                      "peak_source": peak_note,
                      "a7_total": {"ms": t_a7, "achieved": flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
         "kernels": kernels,
-        "e2e": {"value": res["e2e_steps"] / res["e2e_s"], "unit": "evals/s", "h2d_bytes_per_step": res["h2d"],
+        "e2e": {"value": res["e2e_steps"] * res["B"] / res["e2e_s"], "unit": "evals/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": int(res["launches"]),
         "clocks": res["clk"],
