@@ -42,8 +42,8 @@ def load_peaks():
 
 def make_workload(name: str):
     from paper_2411_05869_gb300 import synth
-    if name == "station_1.2M":
-        return synth.config(5, with_test=False)
+    if name == "station_1.2M":   # with the 200 x 200 x 30 prediction grid
+        return synth.config(5, with_test=True)
     if name == "station_120k":   # the same field over the first 24 days: a profiling-size case
         return synth.station_spacetime(nsites=5000, ndays=24, with_test=False)
     if name == "spacetime_100k":
@@ -245,6 +245,26 @@ def run_gpu(args, rank, world, local_rank):
                 stream.synchronize()
     e2e_s = time.perf_counter() - t0
 
+    # A12 predictive mean on the workload's test points (the 200 x 200 x 30 grid at 1.2M) for the last setting,
+    # timed separately from the log-likelihood steps
+    if w.Xtest is not None and w.Xtest.shape[0] > 0:
+        Xt = torch.as_tensor(w.Xtest, dtype=torch.float64, device=dev)
+        mut = torch.as_tensor(w.mu_test, dtype=torch.float64, device=dev)
+        mean = torch.empty(Xt.shape[0], dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            f.predict(Xt, mut, out=mean)   # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                f.predict(Xt, mut, out=mean)
+            e1.record(stream)
+        stream.synchronize()
+        pms = e0.elapsed_time(e1) / 3
+        predict_info = {"m": int(Xt.shape[0]), "ms": pms, "points_per_s": Xt.shape[0] / (pms * 1e-3),
+                        "finite": bool(torch.isfinite(mean).all().item())}
+    else:
+        predict_info = None
+
     # per-kernel-class profile of one more step (not part of the timed region)
     ctx.profile(True)
     step(0)
@@ -252,7 +272,7 @@ def run_gpu(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
 
-    res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, clk=clk, info=info, t_assemble=t_assemble,
+    res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, predict=predict_info, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
                h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
     # FP64 comparison (mixed runs only): one evaluation of the same setting through the FP64 path, timed from
@@ -486,6 +506,8 @@ def main():
     }
     if "fp64" in res:
         line["fp64"] = res["fp64"]
+    if res.get("predict"):
+        line["predict"] = res["predict"]
     if world == 1 and not args.no_cpu_baseline:
         try:
             leg = OracleLeg(res["w"], args.oracle_points, flops)
