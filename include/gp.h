@@ -197,6 +197,27 @@ GP_API gp_status gp_factor_bytes(const gp_pointset* ps, const gp_hyper* theta, i
  * it first when such factors can be created concurrently. Synchronous. Errors: GP_ERR_ARG, GP_ERR_NOMEM. */
 GP_API gp_status gp_pointset_prepare(gp_ctx* ctx, gp_pointset* ps, gp_precision prec);
 
+/* Autotuner of the mixed path's supernode update tiles (the paper has no counterpart: it is a performance choice
+ * of this implementation, not of the method). Large fronts are factored 64 columns at a time; the trailing
+ * updates of a group of G such blocks are deferred and applied at the group's end as 128 x TN tensor-core
+ * tiles with K = 64 G. For each candidate (G, TN) in {4, 8, 16} x {128, 256} the point set's update schedule is
+ * re-planned, a GP_MIXED factor of B settings is created and gp_factor_update timed `reps` times (CUDA events on
+ * the context stream); the fastest candidate stays planned for the point set's later factors (results differ
+ * between candidates only by the order of FP32 sums). tried (nullable, room for 6) receives the candidates with
+ * their mean time per factorization, *ntried their count. Must run before any factor of the point set exists;
+ * on failure the default blocking (G = 8, TN = 256) is planned again.
+ * Errors: GP_ERR_ARG, GP_ERR_STATE (factors exist), GP_ERR_NOMEM, GP_ERR_CUDA. */
+typedef struct {
+  int32_t group_blocks;   /* G */
+  int32_t group_tile_n;   /* TN */
+  double ms;              /* mean time of one factorization (A3, A4, A7) */
+} gp_tune_candidate;
+GP_API gp_status gp_autotune(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, int reps,
+                             gp_tune_candidate* tried, int* ntried);
+/* Plan a given update blocking (G in 1..64, TN in {128, 256}) for the point set's later GP_MIXED factors
+ * (what gp_autotune does with its choice). Errors: GP_ERR_ARG, GP_ERR_STATE (factors exist). */
+GP_API gp_status gp_pointset_set_blocking(gp_ctx* ctx, gp_pointset* ps, int group_blocks, int group_tile_n);
+
 /* ----------------------------------------------------------------------------------------- request server
  * A continuous-batching server of log-likelihood (Sec. 3.3) and predictive-mean (Sec. 3.2) requests on one GPU.
  * The paper has no counterpart (it evaluates one likelihood at a time across many GPUs); this is the serving

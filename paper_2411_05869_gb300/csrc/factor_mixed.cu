@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 
 // ---------------------------------------------------------------------------------------------------------
 // Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x TN tiles, j <= i.
-// Modes (block column kb = columns [c0, c1), in the (64 GP_GROUP)-column group [g0, gend)):
+// Modes (block column kb = columns [c0, c1), in the (64 G)-column group [g0, gend), G = the plan's group):
 //   3: left-looking, before the block's POTRF: rows >= c0 x the block's columns, 128 x 64 tiles, K = [g0, c0)
 //      (the group's earlier blocks);
 //   2: group end: rows/columns >= gend, 128 x 256 tiles on and below the diagonal, K = the whole group [g0, gend).
@@ -476,8 +476,8 @@ struct UTile {
 // rows) holds floor(I / 2) + 1 tiles of 256 columns, rows 2p and 2p + 1 starting at p (p + 1).
 template <int TN>
 __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                             int nfront, int64_t total, int kb, int mode, const DevPlan& dp,
-                                             const int32_t* __restrict__ slot_of, int64_t tt) {
+                                             int nfront, int64_t total, int kb, int mode, int group,
+                                             const DevPlan& dp, const int32_t* __restrict__ slot_of, int64_t tt) {
   UTile u;
   u.b = (int)(tt / total);
   const int64_t t = tt - (int64_t)u.b * total;
@@ -489,7 +489,7 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   u.ldw = dp.ldw[u.s];
   u.m = (int64_t)u.w + u.r;
   const int c0 = kb * T, bw = min(T, u.w - c0), c1 = c0 + bw;
-  const int g0 = (kb / GP_GROUP) * GP_GROUP * T, gend = min(g0 + GP_GROUP * T, u.w);
+  const int g0 = (kb / group) * group * T, gend = min(g0 + group * T, u.w);
   (void)bw;
   const int64_t loc = t - pre[fi];
   int64_t I, J, base;
@@ -527,7 +527,7 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
 template <int TN>
 __global__ void __launch_bounds__(UW_THREADS, 1)
     k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
-                int64_t ntiles, int kb, int mode, DevPlan dp, const uint8_t* __restrict__ tmaps,
+                int64_t ntiles, int kb, int mode, int group, DevPlan dp, const uint8_t* __restrict__ tmaps,
                 const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
                 float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err) {
   using C = UW<TN>;
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     if (lane == 0) {   // TMA producer
       uint32_t st = 0, ph = 0;
       for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
         const uint8_t* mh = tmaps + (int64_t)u.slot * 256;
         const uint8_t* ml = mh + 128;
         tcg::tmap_acquire(mh);
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       const uint32_t idesc = tcg::idesc_tf32(128, TN);
       uint32_t st = 0, ph = 0, acc = 0, aph = 0;
       for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
         const int ab = a_in_b(u);
         const int nch = (u.K + 31) / 32;
         if (!tcg::mbar_wait(&tempty[acc], aph ^ 1)) {
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     float* slab = epi + (warp - 2) * 1024;
     uint32_t acc = 0, aph = 0;
     for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-      const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, dp, slot_of, tt);
+      const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
       float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
       float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
       double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
@@ -764,8 +764,8 @@ void set_attrs() {   // once per process (contexts may run on several host threa
                                  GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
     GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  UW<GP_TN_LEFT>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 UW<GP_TN_GROUP>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, UW<128>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, UW<256>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   });
 }
@@ -834,12 +834,16 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
   if (mode == 3)
     k_update_ws<GP_TN_LEFT><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
-        fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp, f->op_maps, f->op_slot, f->panels32, f->diag,
-        f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+  else if (sp.tn_group == 256)
+    k_update_ws<256><<<grid, UW_THREADS, UW<256>::SMEM, ctx->stream>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
   else
-    k_update_ws<GP_TN_GROUP><<<grid, UW_THREADS, UW<GP_TN_GROUP>::SMEM, ctx->stream>>>(
-        fronts, pre, nfront, total, ntiles, kb, mode, f->ps->dp, f->op_maps, f->op_slot, f->panels32, f->diag,
-        f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+    k_update_ws<128><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
   GP_CHECK_LAUNCH(ctx);
 }
 
@@ -857,7 +861,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
-// Tensor maps of the TF32 operand pair of every front that has tensor-core updates: per front two 3-D maps
+// Tensor maps of the TF32 operand pair of every large front (those with tensor-core updates under any
+// blocking of plan_mixed_updates): per front two 3-D maps
 // (columns x rows x proposals) over op_hi and op_lo, 128 x 32 boxes with the 128-byte swizzle; rows past the
 // front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
@@ -865,7 +870,7 @@ void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
   const int64_t ns = (int64_t)sp.sn_w.size();
   std::vector<int32_t> slot(ns, -1);
   std::vector<int32_t> order;
-  for (int32_t s : sp.upd_fronts)
+  for (int32_t s : sp.large_fronts)
     if (slot[s] < 0) {
       slot[s] = (int32_t)order.size();
       order.push_back(s);

@@ -242,14 +242,13 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     dp.ldw = upload(ctx, ps->bufs, sp.sn_ldw);
     dp.loff32 = upload(ctx, ps->bufs, sp.sn_loff32);
     dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
-    dp.step_pre128 = upload(ctx, ps->bufs, sp.step_pre128);
     dp.large_kb = upload(ctx, ps->bufs, sp.large_kb);
-    dp.upd_fronts = upload(ctx, ps->bufs, sp.upd_fronts);
-    dp.upd_pre = upload(ctx, ps->bufs, sp.upd_pre);
+    upload_schedule(ctx, ps);
     compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != GP_OK) {
+    dev_free_all(ctx, ps->sched_bufs);
     dev_free_all(ctx, ps->bufs);
     delete ps;
     return st;
@@ -264,6 +263,7 @@ extern "C" void gp_pointset_free(gp_pointset* ps) {
   gp_ctx* ctx = ps->ctx;
   if (ctx) {
     cudaSetDevice(ctx->device);
+    dev_free_all(ctx, ps->sched_bufs);
     dev_free_all(ctx, ps->bufs);
   }
   delete ps;
@@ -318,6 +318,14 @@ extern "C" gp_status gp_pointset_export(const gp_pointset* ps, int what, void* d
     case 10: return dev(ps->cell_perm, n * 4);
     default: return fail(ctx, GpError{GP_ERR_ARG, "unknown export"});
   }
+}
+
+// The mixed-path update schedule on the device (replaced when it is re-planned).
+void upload_schedule(gp_ctx* ctx, gp_pointset* ps) {
+  dev_free_all(ctx, ps->sched_bufs);
+  ps->dp.upd_fronts = upload(ctx, ps->sched_bufs, ps->sp.upd_fronts);
+  ps->dp.upd_pre = upload(ctx, ps->sched_bufs, ps->sp.upd_pre);
+  GP_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
 // ------------------------------------------------------------------------------------------ factors
@@ -383,6 +391,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     return st;
   }
   ctx->live++;
+  ps->nfactors++;
   *out = f;
   return GP_OK;
 }
@@ -401,7 +410,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
   } else {
     std::vector<char> seen(sp.sn_w.size(), 0);
     size_t nmaps = 0;
-    for (int32_t s : sp.upd_fronts)
+    for (int32_t s : sp.large_fronts)
       if (!seen[s]) {
         seen[s] = 1;
         nmaps++;
@@ -438,6 +447,70 @@ extern "C" gp_status gp_pointset_prepare(gp_ctx* ctx, gp_pointset* ps, gp_precis
   });
 }
 
+extern "C" gp_status gp_pointset_set_blocking(gp_ctx* ctx, gp_pointset* ps, int group_blocks, int group_tile_n) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(ps && ps->ctx == ctx, "point set missing or from another context");
+    GP_REQUIRE(group_blocks >= 1 && group_blocks <= 64, "group_blocks must be in 1..64");
+    GP_REQUIRE(group_tile_n == 128 || group_tile_n == 256, "group_tile_n must be 128 or 256");
+    if (ps->nfactors.load() != 0) throw GpError{GP_ERR_STATE, "set the blocking before creating factors"};
+    plan_mixed_updates(ps->sp, group_blocks, group_tile_n);
+    upload_schedule(ctx, ps);
+  });
+}
+
+extern "C" gp_status gp_autotune(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, int reps,
+                                 gp_tune_candidate* tried, int* ntried) {
+  if (!ctx) return GP_ERR_ARG;
+  static const int cand[][2] = {{4, 128}, {4, 256}, {8, 128}, {8, 256}, {16, 128}, {16, 256}};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gp_status st = guarded(ctx, [&] {
+    GP_REQUIRE(ps && ps->ctx == ctx, "point set missing or from another context");
+    if (ps->nfactors.load() != 0) throw GpError{GP_ERR_STATE, "tune a point set before creating its factors"};
+    GP_REQUIRE(thetas && B >= 1 && reps >= 1, "B >= 1 settings and reps >= 1 are required");
+    GP_CUDA(cudaEventCreate(&e0));
+    GP_CUDA(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.f;
+    for (int c = 0; c < nc; c++) {
+      plan_mixed_updates(ps->sp, cand[c][0], cand[c][1]);
+      upload_schedule(ctx, ps);
+      gp_factor_t* f = nullptr;
+      gp_status fs = gp_factor(ctx, ps, thetas, B, GP_MIXED, &f);   // allocates and factors once (graph capture)
+      if (fs != GP_OK) throw GpError{fs, ctx->err};
+      GP_CUDA(cudaEventRecord(e0, ctx->stream));
+      for (int r = 0; r < reps && fs == GP_OK; r++) fs = gp_factor_update(ctx, f, thetas);
+      GP_CUDA(cudaEventRecord(e1, ctx->stream));
+      GP_CUDA(cudaEventSynchronize(e1));
+      gp_factor_free(f);
+      if (fs != GP_OK) throw GpError{fs, ctx->err};
+      float ms = 0.f;
+      GP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= (float)reps;
+      if (tried) tried[c] = gp_tune_candidate{cand[c][0], cand[c][1], (double)ms};
+      if (best < 0 || ms < best_ms) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+    plan_mixed_updates(ps->sp, cand[best][0], cand[best][1]);
+    upload_schedule(ctx, ps);
+    if (ntried) *ntried = nc;
+  });
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != GP_OK && ps && ps->ctx == ctx && ps->nfactors.load() == 0) {   // leave the default blocking behind
+    const std::string msg = ctx->err;
+    guarded(ctx, [&] {
+      plan_mixed_updates(ps->sp, GP_GROUP, GP_TN_GROUP);
+      upload_schedule(ctx, ps);
+    });
+    ctx->err = msg;
+  }
+  return st;
+}
+
 extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas) {
   if (!ctx) return GP_ERR_ARG;
   return guarded(ctx, [&] {
@@ -452,6 +525,7 @@ extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hype
 
 extern "C" void gp_factor_free(gp_factor_t* f) {
   if (!f) return;
+  if (f->ps) f->ps->nfactors--;
   gp_ctx* ctx = f->ctx;
   if (ctx) {
     cudaSetDevice(ctx->device);

@@ -122,6 +122,10 @@ void d2h(gp_ctx* ctx, T* dst, const T* src, size_t count) {
 
 // ------------------------------------------------------------------------------------------ symbolic plan
 // Host-side result of A6, plus the device copies the numeric kernels read.
+#define GP_GROUP 8   // default 64-column blocks per deferred-update group of the mixed path
+#define GP_TN_LEFT 64     // tensor-core tile width (columns) of the mixed path's left-looking block updates
+#define GP_TN_GROUP 256   // default tile width of its group-end updates (rows stay 128 per tile)
+
 struct SymPlan {
   int64_t n = 0;
   int64_t ns = 0;                    // supernodes
@@ -153,14 +157,13 @@ struct SymPlan {
   std::vector<int32_t> sn_ldw;
   std::vector<int64_t> sn_loff32, sn_doff;
   int64_t panel32_entries = 0, diag_entries = 0;
-  std::vector<int64_t> step_pre128;  // per step: prefix of 128 x 128 update tiles (nfront + 1 entries)
+  int group = GP_GROUP, tn_group = GP_TN_GROUP;   // mixed-path update blocking (plan_mixed_updates)
   std::vector<int32_t> upd_fronts;   // per step: fronts of the left-looking and of the group update
   std::vector<int64_t> upd_pre;      // their tile prefixes
 
   // schedule for the numeric factorization, per level
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
   struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
-                      int64_t pre128_off; int64_t upd128_total;
                       // mixed path, (64 GP_GROUP)-column groups: left-looking update of this block column
                       // (rows >= c0 x its 64 columns, K = the group's earlier blocks) and, at a group's last block,
                       // the deferred group update (rows/columns after the group, K = the group's width); fronts
@@ -202,14 +205,10 @@ struct DevPlan {
   int32_t* sn_parent;
   int32_t* ldw;
   int64_t *loff32, *doff;
-  int64_t* step_pre128;
   int32_t* large_kb;
   int32_t* upd_fronts;
   int64_t* upd_pre;
 };
-#define GP_GROUP 8   // 64-column blocks per deferred-update group of the mixed path
-#define GP_TN_LEFT 64     // tensor-core tile width (columns) of the mixed path's left-looking block updates
-#define GP_TN_GROUP 256   // ... and of its group-end updates (rows stay 128 per tile)
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
 
@@ -217,6 +216,8 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
 struct gp_pointset {
   gp_ctx* ctx = nullptr;
   std::vector<DevBuf> bufs;
+  std::vector<DevBuf> sched_bufs;     // the mixed-path update schedule (re-planned by gp_autotune)
+  std::atomic<int64_t> nfactors{0};   // live factors on this point set
   int64_t n = 0;
   int d = 0;
   double rho[GP_MAX_D] = {1, 1, 1};
@@ -311,6 +312,8 @@ void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f);
 int64_t bwd_part_entries(const SymPlan& sp);
+void plan_mixed_updates(SymPlan& sp, int group, int tn);
+void upload_schedule(gp_ctx* ctx, gp_pointset* ps);
 size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const ThetaDims& td);
 #define DIAG_FLAG ((int64_t)1 << 62)
 

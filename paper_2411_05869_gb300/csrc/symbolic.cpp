@@ -483,65 +483,66 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           stp.trsm_flops += M * bw * bw;
           stp.upd_flops += 2.0 * bw * M * (M + 1.0) / 2.0;
         }
-        // 128 x 128 tiles of the trailing lower triangle (tensor-core update of the mixed path)
-        stp.pre128_off = (int64_t)sp.step_pre128.size();
-        acc = 0;
-        sp.step_pre128.push_back(0);
-        for (int32_t t = 0; t < cnt; t++) {
-          int32_t s = sp.large_fronts[stp.fr_off + t];
-          int64_t m = sp.sn_w[s] + sp.sn_r[s];
-          int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, sp.sn_w[s]);
-          int64_t nt = (m - c1 + 127) / 128;
-          acc += tri(nt);
-          sp.step_pre128.push_back(acc);
-        }
-        stp.upd128_total = acc;
-        // group-deferred updates of the mixed path
-        stp.left_off = (int64_t)sp.upd_fronts.size();
-        stp.left_pre_off = (int64_t)sp.upd_pre.size();
-        stp.n_left = 0;
-        stp.left_flops = 0.0;
-        acc = 0;
-        sp.upd_pre.push_back(0);
-        for (int32_t t = 0; t < cnt; t++) {   // block column kb from the earlier blocks of its group
-          int32_t s = sp.large_fronts[stp.fr_off + t];
-          int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
-          int64_t c0 = (int64_t)kb * GP_TILE, c1 = std::min<int64_t>(c0 + GP_TILE, w);
-          int64_t g0 = (int64_t)(kb / GP_GROUP) * GP_GROUP * GP_TILE;
-          if (c0 == g0) continue;   // the first block of its group
-          sp.upd_fronts.push_back(s);
-          acc += (m - c0 + 127) / 128;
-          sp.upd_pre.push_back(acc);
-          stp.n_left++;
-          double bw = (double)(c1 - c0);
-          stp.left_flops += 2.0 * (double)(c0 - g0) * (bw * (bw + 1.0) / 2.0 + (double)(m - c1) * bw);
-        }
-        stp.left_total = acc;
-        stp.group_off = (int64_t)sp.upd_fronts.size();
-        stp.group_pre_off = (int64_t)sp.upd_pre.size();
-        stp.n_group = 0;
-        stp.group_flops = 0.0;
-        acc = 0;
-        sp.upd_pre.push_back(0);
-        for (int32_t t = 0; t < cnt; t++) {
-          int32_t s = sp.large_fronts[stp.fr_off + t];
-          int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
-          int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, w);
-          int64_t g0 = (int64_t)(kb / GP_GROUP) * GP_GROUP * GP_TILE;
-          int64_t gend = std::min<int64_t>(g0 + GP_GROUP * GP_TILE, w);
-          if (c1 < gend || gend >= m) continue;   // not a group end, or nothing after the group
-          int64_t nt = (m - gend + 127) / 128;   // 128-row tile rows; row I holds I / 2 + 1 tiles of 256 columns
-          sp.upd_fronts.push_back(s);
-          acc += stair(nt);
-          sp.upd_pre.push_back(acc);
-          stp.n_group++;
-          double M = (double)(m - gend);
-          stp.group_flops += 2.0 * (double)(gend - g0) * M * (M + 1.0) / 2.0;
-        }
-        stp.group_total = acc;
         lv.steps.push_back(stp);
       }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
   }
+  plan_mixed_updates(sp, GP_GROUP, GP_TN_GROUP);
+}
+
+// The tensor-core update schedule of the mixed path for a given blocking: per step, the fronts (and tile
+// prefixes) of the left-looking block-column update and, at a group's last block, of the group update.
+//   group: 64-column blocks per group; tn: tile width (columns) of the group update, 128 or 256.
+void plan_mixed_updates(SymPlan& sp, int group, int tn) {
+  sp.group = group;
+  sp.tn_group = tn;
+  sp.upd_fronts.clear();
+  sp.upd_pre.clear();
+  for (auto& lv : sp.levels)
+    for (auto& stp : lv.steps) {
+      const int32_t kb = stp.kb, cnt = stp.nfront;
+      stp.left_off = (int64_t)sp.upd_fronts.size();
+      stp.left_pre_off = (int64_t)sp.upd_pre.size();
+      stp.n_left = 0;
+      stp.left_flops = 0.0;
+      int64_t acc = 0;
+      sp.upd_pre.push_back(0);
+      for (int32_t t = 0; t < cnt; t++) {   // block column kb from the earlier blocks of its group
+        int32_t s = sp.large_fronts[stp.fr_off + t];
+        int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
+        int64_t c0 = (int64_t)kb * GP_TILE, c1 = std::min<int64_t>(c0 + GP_TILE, w);
+        int64_t g0 = (int64_t)(kb / group) * group * GP_TILE;
+        if (c0 == g0) continue;   // the first block of its group
+        sp.upd_fronts.push_back(s);
+        acc += (m - c0 + 127) / 128;
+        sp.upd_pre.push_back(acc);
+        stp.n_left++;
+        double bw = (double)(c1 - c0);
+        stp.left_flops += 2.0 * (double)(c0 - g0) * (bw * (bw + 1.0) / 2.0 + (double)(m - c1) * bw);
+      }
+      stp.left_total = acc;
+      stp.group_off = (int64_t)sp.upd_fronts.size();
+      stp.group_pre_off = (int64_t)sp.upd_pre.size();
+      stp.n_group = 0;
+      stp.group_flops = 0.0;
+      acc = 0;
+      sp.upd_pre.push_back(0);
+      for (int32_t t = 0; t < cnt; t++) {   // fronts whose group ends at block kb: rows/columns after it
+        int32_t s = sp.large_fronts[stp.fr_off + t];
+        int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
+        int64_t c1 = std::min<int64_t>((int64_t)(kb + 1) * GP_TILE, w);
+        int64_t g0 = (int64_t)(kb / group) * group * GP_TILE;
+        int64_t gend = std::min<int64_t>(g0 + (int64_t)group * GP_TILE, w);
+        if (c1 < gend || gend >= m) continue;   // not a group end, or nothing after the group
+        int64_t nt = (m - gend + 127) / 128;   // 128-row tile rows
+        sp.upd_fronts.push_back(s);
+        acc += tn == 256 ? stair(nt) : tri(nt);
+        sp.upd_pre.push_back(acc);
+        stp.n_group++;
+        double M = (double)(m - gend);
+        stp.group_flops += 2.0 * (double)(gend - g0) * M * (M + 1.0) / 2.0;
+      }
+      stp.group_total = acc;
+    }
 }

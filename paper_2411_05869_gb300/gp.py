@@ -61,12 +61,16 @@ class GpServerStats(ctypes.Structure):
                 ("max_running", ctypes.c_int32), ("completed", c_i64)]
 
 
+class GpTuneCandidate(ctypes.Structure):
+    _fields_ = [("group_blocks", ctypes.c_int32), ("group_tile_n", ctypes.c_int32), ("ms", c_dbl)]
+
+
 GP_REQ_LOGLIK, GP_REQ_PREDICT = 0, 1
 
 SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_pointset_free", "gp_pointset_info",
            "gp_pointset_export", "gp_factor", "gp_factor_update", "gp_factor_free", "gp_factor_info", "gp_loglik",
            "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read", "gp_factor_bytes",
-           "gp_pointset_prepare", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
+           "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
            "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7}
@@ -142,6 +146,11 @@ def load(build_if_missing: bool = True):
     L.gp_profile_read.argtypes = [P, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]
     L.gp_factor_bytes.restype = c_int
     L.gp_factor_bytes.argtypes = [P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gp_autotune.restype = c_int
+    L.gp_autotune.argtypes = [P, P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(GpTuneCandidate),
+                              ctypes.POINTER(c_int)]
+    L.gp_pointset_set_blocking.restype = c_int
+    L.gp_pointset_set_blocking.argtypes = [P, P, c_int, c_int]
     L.gp_pointset_prepare.restype = c_int
     L.gp_pointset_prepare.argtypes = [P, P, c_int]
     L.gp_server_create.restype = c_int
@@ -285,6 +294,21 @@ class PointSet:
         out = np.empty(size, dtype=dt)
         self.ctx.check(self.ctx.lib.gp_pointset_export(self.h, what, out.ctypes.data_as(P), out.nbytes))
         return out
+
+    def autotune(self, thetas: Sequence, reps: int = 2) -> list:
+        """gp_autotune: time the mixed factorization under each update blocking and keep the fastest; returns
+        [{"group_blocks", "group_tile_n", "ms"}] in candidate order."""
+        pack = _HyperPack(thetas)
+        tried = (GpTuneCandidate * 16)()
+        nt = c_int()
+        self.ctx.check(self.ctx.lib.gp_autotune(self.ctx.h, self.h, pack.arr, len(thetas), reps, tried,
+                                                ctypes.byref(nt)))
+        return [{"group_blocks": tried[i].group_blocks, "group_tile_n": tried[i].group_tile_n, "ms": tried[i].ms}
+                for i in range(nt.value)]
+
+    def set_blocking(self, group_blocks: int, group_tile_n: int):
+        """gp_pointset_set_blocking: plan a given mixed-path update blocking."""
+        self.ctx.check(self.ctx.lib.gp_pointset_set_blocking(self.ctx.h, self.h, group_blocks, group_tile_n))
 
     def factor_bytes(self, theta, B: int = 1, precision: int = GP_FP64) -> int:
         """Device bytes a factor of B settings of theta's shape takes (gp_factor_bytes)."""

@@ -211,3 +211,34 @@ def test_graph_replay_matches_direct_launches(case, ctx, precision):
     assert a.tobytes() == direct.tobytes() and b.tobytes() == direct.tobytes()
     f2.free()
     f0.free()
+
+
+def test_every_update_blocking_and_the_autotuner_match_oracle(ctx):
+    """The mixed path's update blocking (G blocks of 64 columns per deferred group, 128 x TN group tiles) only
+    reorders FP32 sums: every blocking, and the autotuner's choice, must give the oracle's log-likelihood to
+    1e-6. Fronts here span many 64-column blocks, so the left-looking and group-end updates all occur."""
+    from paper_2411_05869_gb300 import gp
+    w = synth.uniform_spacetime(20000, 0, 60.0, 8, seed=79, ndays=120)
+    hp = w.hyper
+    rp, col = oracle.pattern(w.X, hp.core_radius)
+    perm = oracle.fill_order(w.X, hp.core_radius, rp, col)
+    ref = oracle.sparse_loglik(hp, w.X, rp, col, perm, w.resid)["loglik"]
+    ps = ctx.assemble(_dev(w.X), hp.core_radius)
+    assert ps.info()["max_front"] > 8 * 64
+    r = _dev(w.resid)
+    for G in (1, 4, 8, 16):
+        for TN in (128, 256):
+            ps.set_blocking(G, TN)
+            f = ctx.factor(ps, [hp], gp.GP_MIXED)
+            ll = float(f.loglik(r).cpu()[0])
+            f.free()
+            assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (G, TN, ll, ref)
+    tried = ps.autotune([hp], reps=1)
+    assert len(tried) == 6 and all(t["ms"] > 0 for t in tried)
+    f = ctx.factor(ps, [hp], gp.GP_MIXED)
+    ll = float(f.loglik(r).cpu()[0])
+    assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (ll, ref)
+    with pytest.raises(gp.GpError):   # the schedule of live factors is not re-planned under them
+        ps.autotune([hp], reps=1)
+    f.free()
+    ps.free()
