@@ -194,6 +194,13 @@ def run_gpu(args, rank, world, local_rank):
     Bc = max(1, min(B, int(0.8 * free) // per))
     nchunk = (B + Bc - 1) // Bc
     thetas = [synth.perturb(rng, hp, 0.05 if B == 1 else 0.1) for _ in range(B * (args.steps + args.warmup + 2))]
+    tune = None
+    if prec == gp.GP_MIXED and args.autotune:   # update blocking chosen by timing factorizations of Bc settings
+        t0 = time.perf_counter()
+        tried = ps.autotune(thetas[:Bc], reps=1)
+        best = min(tried, key=lambda t: t["ms"])
+        tune = {"chosen": {"group_blocks": best["group_blocks"], "group_tile_n": best["group_tile_n"]},
+                "candidates": tried, "seconds": round(time.perf_counter() - t0, 2)}
     f = ctx.factor(ps, thetas[:Bc], prec)
     out = torch.empty(Bc, dtype=torch.float64, device=dev)
     resid_b = resid.expand(Bc, -1).contiguous() if Bc > 1 else resid
@@ -272,7 +279,8 @@ def run_gpu(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
 
-    res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, predict=predict_info, clk=clk, info=info, t_assemble=t_assemble,
+    res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, predict=predict_info,
+               autotune=tune, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
                h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
     # FP64 comparison (mixed runs only): one evaluation of the same setting through the FP64 path, timed from
@@ -395,6 +403,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fp64-proposals", type=int, default=8, help="batched runs: proposals compared with FP64")
     ap.add_argument("--batch", type=int, default=0, help="proposals per step (default: 64 for batched_200k, else 1)")
+    ap.add_argument("--autotune", type=int, default=-1, help="1/0: tune the update blocking first (default: "
+                                                              "on in mixed precision)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-sets", type=int, default=20)
@@ -406,6 +416,8 @@ def main():
     args = ap.parse_args()
     if args.batch <= 0:
         args.batch = 64 if args.workload == "batched_200k" else 1
+    if args.autotune < 0:   # the library's autotuner picks the update blocking of mixed runs
+        args.autotune = 1 if args.precision == "mixed" else 0
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -508,6 +520,8 @@ def main():
         line["fp64"] = res["fp64"]
     if res.get("predict"):
         line["predict"] = res["predict"]
+    if res.get("autotune"):
+        line["autotune"] = res["autotune"]
     if world == 1 and not args.no_cpu_baseline:
         try:
             leg = OracleLeg(res["w"], args.oracle_points, flops)
