@@ -50,8 +50,10 @@ def make_workload(name: str):
         return synth.config(2, m=0)
     if name == "batched_200k":
         return synth.uniform_spacetime(200_000, 0, 80.0, 8, seed=synth.SEED_BASE + 3, name="spacetime_200k")
-    if name == "spatial_2k":
-        return synth.spatial_2d(n=2000, m=0, seed=synth.SEED_BASE + 1)
+    if name == "spatial_2k":   # the residual is the workload's seeded normals (its GP draw is left to the caller)
+        w = synth.spatial_2d(n=2000, m=0, seed=synth.SEED_BASE + 1)
+        w.resid = w.normals.copy()
+        return w
     raise SystemExit(f"unknown workload {name}")
 
 
