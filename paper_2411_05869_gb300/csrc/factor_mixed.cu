@@ -439,7 +439,10 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 // tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
 // significant bits survive the products instead of the 11 of one TF32 pass). The wide tiles of mode 2 halve
 // the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
-// bounds this kernel).
+// bounds this kernel). Mode 2 runs in clusters of two CTAs on the tile pairs (rows 2p and 2p + 1 of 128, the same
+// 256 columns): each CTA loads its own A and half of the shared B, multicast into both CTAs' shared memory, so a
+// stage costs each CTA two thirds of the TMA requests of an unpaired tile; both MMAs' commits free a stage in
+// both CTAs.
 //
 // One persistent CTA per SM walks the launch's tiles (all fronts, all proposals) with three roles:
 //   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a ring of 128-byte-swizzled tiles;
@@ -472,12 +475,13 @@ struct UTile {
   int64_t m, i0, j0, jlim;
 };
 
-// Tile tt of a launch: proposal, front (prefix search), then its position. Mode 2 with TN = 256: row I (128
-// rows) holds floor(I / 2) + 1 tiles of 256 columns, rows 2p and 2p + 1 starting at p (p + 1).
-template <int TN>
+// Tile tt of a launch: proposal, front (prefix search), then its position. Mode 2 with TN = 256 (paired): tile
+// pair p (rows 2p and 2p + 1 of 128) holds p + 1 tiles of 256 columns; CTA `rank` of the pair takes row 2p + rank.
+template <int TN, bool PAIR>
 __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                              int nfront, int64_t total, int kb, int mode, int group,
-                                             const DevPlan& dp, const int32_t* __restrict__ slot_of, int64_t tt) {
+                                             const DevPlan& dp, const int32_t* __restrict__ slot_of, int64_t tt,
+                                             int rank) {
   UTile u;
   u.b = (int)(tt / total);
   const int64_t t = tt - (int64_t)u.b * total;
@@ -506,6 +510,12 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
       while ((I + 1) * (I + 2) / 2 <= loc) I++;
       while (I * (I + 1) / 2 > loc) I--;
       J = loc - I * (I + 1) / 2;
+    } else if (PAIR) {
+      int64_t p = (int64_t)((sqrtf(8.f * (float)loc + 1.f) - 1.f) * 0.5f);
+      while ((p + 1) * (p + 2) / 2 <= loc) p++;
+      while (p * (p + 1) / 2 > loc) p--;
+      J = loc - p * (p + 1) / 2;
+      I = 2 * p + rank;
     } else {
       int64_t p = (int64_t)((sqrtf(4.f * (float)loc + 1.f) - 1.f) * 0.5f);
       while ((p + 1) * (p + 2) <= loc) p++;
@@ -524,7 +534,7 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   return u;
 }
 
-template <int TN>
+template <int TN, bool PAIR>
 __global__ void __launch_bounds__(UW_THREADS, 1)
     k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
                 int64_t ntiles, int kb, int mode, int group, DevPlan dp, const uint8_t* __restrict__ tmaps,
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; q++) {
       tcg::mbar_init(&full[q], 1);
-      tcg::mbar_init(&empty[q], 1);
+      tcg::mbar_init(&empty[q], PAIR ? 2 : 1);   // paired: both CTAs' MMAs must be done with the stage
     }
     for (int q = 0; q < 2; q++) {
       tcg::mbar_init(&tfull[q], 1);
@@ -558,9 +568,13 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   }
   if (warp == 1) tcg::tmem_alloc(tslot, C::TMEM_COLS);
   tcg::tc_fence_before();
-  __syncthreads();
+  if (PAIR) tcg::cluster_sync();   // the peer's barriers are initialised before anything reaches them
+  else __syncthreads();
   tcg::tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int rank = PAIR ? (int)tcg::cluster_ctarank() : 0;
+  const int64_t t_first = PAIR ? (int64_t)tcg::cluster_id_x() : (int64_t)blockIdx.x;
+  const int64_t t_step = PAIR ? (int64_t)tcg::cluster_count_x() : (int64_t)gridDim.x;
   auto fail = [&]() {
     *abort_flag = 1;
     atomicExch(err, 1);
@@ -575,8 +589,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
       uint32_t st = 0, ph = 0;
-      for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
+      for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
+        const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
         const uint8_t* mh = tmaps + (int64_t)u.slot * 256;
         const uint8_t* ml = mh + 128;
         tcg::tmap_acquire(mh);
@@ -595,10 +609,16 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
             tcg::tma_load_3d(sa + C::OPA, ml, x, (int)u.i0, u.b, &full[st]);
           }
+          if (PAIR) {   // this CTA's half of B, into both CTAs
+            const int hb = rank;
+            tcg::tma_load_3d_mc(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st], 3);
+            tcg::tma_load_3d_mc(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st], 3);
+          } else {
 #pragma unroll
-          for (int hb = 0; hb < C::BROWS / 128; hb++) {
-            tcg::tma_load_3d(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
-            tcg::tma_load_3d(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
+            for (int hb = 0; hb < C::BROWS / 128; hb++) {
+              tcg::tma_load_3d(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
+              tcg::tma_load_3d(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
+            }
           }
           if (++st == NS) {
             st = 0;
@@ -611,8 +631,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     if (lane == 0) {   // MMA issuer
       const uint32_t idesc = tcg::idesc_tf32(128, TN);
       uint32_t st = 0, ph = 0, acc = 0, aph = 0;
-      for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-        const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
+      for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
+        const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
         const int ab = a_in_b(u);
         const int nch = (u.K + 31) / 32;
         if (!tcg::mbar_wait(&tempty[acc], aph ^ 1)) {
@@ -640,7 +660,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             tcg::mma_tf32(d, ah, bl, idesc, 1u);
             tcg::mma_tf32(d, ah, bh, idesc, 1u);
           }
-          tcg::mma_commit(&empty[st]);
+          if (PAIR) tcg::mma_commit_mc(&empty[st], 3);
+          else tcg::mma_commit(&empty[st]);
           if (++st == NS) {
             st = 0;
             ph ^= 1;
@@ -662,8 +683,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     const int q = warp & 3, h = (warp - 2) >> 2;
     float* slab = epi + (warp - 2) * 1024;
     uint32_t acc = 0, aph = 0;
-    for (int64_t tt = blockIdx.x; tt < ntiles && !*abort_flag; tt += gridDim.x) {
-      const UTile u = decode_tile<TN>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt);
+    for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
+      const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
       float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
       float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
       double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
@@ -750,7 +771,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     }
   }
   tcg::tc_fence_before();
-  __syncthreads();
+  if (PAIR) tcg::cluster_sync();   // no multicast or remote arrive may still target this CTA
+  else __syncthreads();
   if (warp == 1) {
     tcg::tc_fence_after();
     tcg::tmem_dealloc(tmem, C::TMEM_COLS);
@@ -762,10 +784,12 @@ void set_attrs() {   // once per process (contexts may run on several host threa
   std::call_once(g_attrs_once, [] {
     GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  UW<GP_TN_LEFT>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, UW<128>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, UW<256>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 UW<128>::SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 UW<256>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   });
 }
@@ -832,18 +856,32 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
   const SymPlan& sp = f->ps->sp;
   const int64_t ntiles = total * f->B;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
-  if (mode == 3)
-    k_update_ws<GP_TN_LEFT><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
+  if (mode == 3) {
+    k_update_ws<GP_TN_LEFT, false><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
         f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
-  else if (sp.tn_group == 256)
-    k_update_ws<256><<<grid, UW_THREADS, UW<256>::SMEM, ctx->stream>>>(
+  } else if (sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
+    cfg.blockDim = dim3(UW_THREADS);
+    cfg.dynamicSmemBytes = UW<256>::SMEM;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true>, fronts, pre, nfront, total, ntiles, kb, mode, sp.group,
+                               f->ps->dp, (const uint8_t*)f->op_maps, (const int32_t*)f->op_slot, f->panels32,
+                               f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries,
+                               f->tiles_err));
+  } else {
+    k_update_ws<128, false><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
         f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
-  else
-    k_update_ws<128><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
-        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
-        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+  }
   GP_CHECK_LAUNCH(ctx);
 }
 

@@ -68,12 +68,6 @@ struct FirstFit {
 };
 
 inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
-// Tiles of 128 rows x 256 columns on and below the diagonal of a square of nt 128-row tile rows: row I holds
-// I / 2 + 1 of them (rows 2p and 2p + 1 hold p + 1 each).
-inline int64_t stair(int64_t nt) {
-  const int64_t p = nt / 2;
-  return p * (p + 1) + (nt & 1) * (p + 1);
-}
 
 }  // namespace
 
@@ -537,7 +531,7 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
         if (c1 < gend || gend >= m) continue;   // not a group end, or nothing after the group
         int64_t nt = (m - gend + 127) / 128;   // 128-row tile rows
         sp.upd_fronts.push_back(s);
-        acc += tn == 256 ? stair(nt) : tri(nt);
+        acc += tn == 256 ? tri((nt + 1) / 2) : tri(nt);   // 256 wide: tile pairs (rows 2p, 2p + 1)
         sp.upd_pre.push_back(acc);
         stp.n_group++;
         double M = (double)(m - gend);
