@@ -368,8 +368,9 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
                                                 int nfront, int kb, DevPlan dp, float* __restrict__ p32,
                                                 float* __restrict__ oph, float* __restrict__ opl,
                                                 const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
-  __shared__ float Bs[T * (T + 1)];   // B[r][l]
-  __shared__ float Is[T * (T + 1)];   // Inv[j][l]
+  constexpr int S = T + 4;            // transposed tiles, rows 16-byte aligned for vector reads
+  __shared__ __align__(16) float BsT[T * S];   // BsT[l][r] = B[r][l]
+  __shared__ __align__(16) float IsT[T * S];   // IsT[l][j] = Inv[j][l]
   int64_t t = blockIdx.x;
   int fi = find_front(pre, nfront, t);
   int32_t s = fronts[fi];
@@ -392,39 +393,46 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 #pragma unroll
   for (int u = 0; u < 16; u++) {
     const int q = threadIdx.x + u * 256, i = q >> 6, j = q & 63;
-    Is[i * (T + 1) + j] = iv[u];
-    Bs[i * (T + 1) + j] = bv[u];
+    IsT[j * S + i] = iv[u];
+    BsT[j * S + i] = bv[u];
   }
   __syncthreads();
+  // thread: rows tr..tr+3 x columns tc..tc+3 of X, one 16-byte read of each operand per l
   const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
   float acc[4][4] = {};
   for (int l = 0; l < bw; l++) {
-    float bv[4], iv[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      bv[e] = Bs[(tr + e) * (T + 1) + l];
-      iv[e] = Is[(tc + e) * (T + 1) + l];
-    }
+    const float4 bq = *reinterpret_cast<const float4*>(BsT + l * S + tr);
+    const float4 iq = *reinterpret_cast<const float4*>(IsT + l * S + tc);
+    const float bv4[4] = {bq.x, bq.y, bq.z, bq.w}, iv4[4] = {iq.x, iq.y, iq.z, iq.w};
 #pragma unroll
     for (int e = 0; e < 4; e++)
 #pragma unroll
-      for (int f = 0; f < 4; f++) acc[e][f] = fmaf(bv[e], iv[f], acc[e][f]);
+      for (int f = 0; f < 4; f++) acc[e][f] = fmaf(bv4[e], iv4[f], acc[e][f]);
   }
   const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int i = tr + e;
     if (i >= nr) continue;
+    const int64_t o = (r0 + i) * ldw + c0 + tc;   // 16-byte aligned: ldw, c0, tc and the panel offset are x4
+    if (tc + 4 <= bw) {
+      float4 x, hi, lo;
+      x = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+      hi = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+      lo = make_float4(tf32_rn(x.x - hi.x), tf32_rn(x.y - hi.y), tf32_rn(x.z - hi.z), tf32_rn(x.w - hi.w));
+      *reinterpret_cast<float4*>(P + o) = x;
+      *reinterpret_cast<float4*>(oph + ob + o) = hi;
+      *reinterpret_cast<float4*>(opl + ob + o) = lo;
+    } else {
 #pragma unroll
-    for (int f = 0; f < 4; f++) {
-      const int j = tc + f;
-      if (j >= bw) continue;
-      const float x = acc[e][f];
-      const int64_t o = (r0 + i) * ldw + c0 + j;
-      P[o] = x;
-      const float hi = tf32_rn(x);
-      oph[ob + o] = hi;
-      opl[ob + o] = tf32_rn(x - hi);
+      for (int f = 0; f < 4; f++) {
+        if (tc + f >= bw) continue;
+        const float x = acc[e][f];
+        P[o + f] = x;
+        const float hi = tf32_rn(x);
+        oph[ob + o + f] = hi;
+        opl[ob + o + f] = tf32_rn(x - hi);
+      }
     }
   }
 }
