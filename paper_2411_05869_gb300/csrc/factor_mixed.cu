@@ -107,9 +107,27 @@ __global__ void k_extend_add32(const int2* __restrict__ tab, DevPlan dp, float* 
   const int32_t* rel = dp.relidx + dp.relidx_off[c];
   MixFront fp = mix_front(dp, p, pp, pd, pu);
   int32_t a1 = min(a0 + 8, rc);
+  // two entries per thread per round, both loads of the targets in flight before either store (the targets of
+  // one row are distinct: rel is increasing)
   for (int32_t a = a0; a < a1; a++) {
-    int32_t tr = rel[a];
-    for (int32_t bc = threadIdx.x; bc <= a; bc += blockDim.x) mix_add(fp, tr, rel[bc], Uc[(int64_t)a * rc + bc]);
+    const int32_t tr = rel[a];
+    const float* ur = Uc + (int64_t)a * rc;
+    for (int32_t b0 = threadIdx.x; b0 <= a; b0 += 2 * blockDim.x) {
+      const int32_t b1 = b0 + blockDim.x;
+      const bool two = b1 <= a;
+      const int32_t c0 = rel[b0], c1 = two ? rel[b1] : 0;
+      const float v0 = ur[b0], v1 = two ? ur[b1] : 0.f;
+      if (two && c1 >= fp.w && c0 >= fp.w) {   // both in the update matrix (the common case below the front)
+        float* t0 = fp.Uu + (int64_t)(tr - fp.w) * fp.r + (c0 - fp.w);
+        float* t1 = fp.Uu + (int64_t)(tr - fp.w) * fp.r + (c1 - fp.w);
+        const float o0 = *t0, o1 = *t1;
+        *t0 = o0 + v0;
+        *t1 = o1 + v1;
+      } else {
+        mix_add(fp, tr, c0, v0);
+        if (two) mix_add(fp, tr, c1, v1);
+      }
+    }
   }
 }
 
