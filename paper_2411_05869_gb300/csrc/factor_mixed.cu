@@ -466,9 +466,10 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 // significant bits survive the products instead of the 11 of one TF32 pass). The wide tiles of mode 2 halve
 // the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
 // bounds this kernel). Mode 2 runs in clusters of two CTAs on the tile pairs (rows 2p and 2p + 1 of 128, the same
-// 256 columns): each CTA loads its own A and half of the shared B, multicast into both CTAs' shared memory, so a
-// stage costs each CTA two thirds of the TMA requests of an unpaired tile; both MMAs' commits free a stage in
-// both CTAs.
+// 256 columns) as one 256 x 256 CTA-pair MMA: each CTA loads its own 128 A rows and its half of the 256 B rows,
+// so a stage costs each CTA two thirds of the operand bytes of an unpaired 128 x 256 tile and holds 64 KB, which
+// leaves room for a three-stage ring; the even CTA issues the MMAs once both CTAs' bytes have landed on its
+// barrier, and its commits free the stage and hand the accumulator halves to both CTAs.
 //
 // One persistent CTA per SM walks the launch's tiles (all fronts, all proposals) with three roles:
 //   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a ring of 128-byte-swizzled tiles;
@@ -481,11 +482,12 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 constexpr int UW_THREADS = 320;
 constexpr int UW_EPI = 8 * 32 * 32 * 4;  // a 32 x 32 FP32 slab per epilogue warp
 constexpr int UW_BAR = 256;
-template <int TN>
+template <int TN, bool PAIR = false>
 struct UW {
-  static constexpr int STAGES = TN == 256 ? 2 : 3;
+  static constexpr int STAGES = TN == 256 && !PAIR ? 2 : 3;
   static constexpr int OPA = 128 * 32 * 4;        // A operand chunk: 128 rows x 32 FP32 (128-byte rows)
-  static constexpr int BROWS = TN < 128 ? 128 : TN;   // B rows loaded (whole 128-row boxes; N = TN are used)
+  // B rows held by this CTA (whole 128-row boxes; N = TN are used; a CTA pair holds half of B in each CTA)
+  static constexpr int BROWS = PAIR ? TN / 2 : (TN < 128 ? 128 : TN);
   static constexpr int OPB = BROWS * 32 * 4;      // B operand chunk
   static constexpr int STAGE = 2 * OPA + 2 * OPB; // A_hi, A_lo, B_hi, B_lo
   static constexpr int SMEM = STAGES * STAGE + UW_EPI + UW_BAR + 1024;
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
                 int64_t ntiles, int kb, int mode, int group, DevPlan dp, const uint8_t* __restrict__ tmaps,
                 const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
                 float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err) {
-  using C = UW<TN>;
+  using C = UW<TN, PAIR>;
   constexpr int NS = C::STAGES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -583,16 +585,19 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; q++) {
       tcg::mbar_init(&full[q], 1);
-      tcg::mbar_init(&empty[q], PAIR ? 2 : 1);   // paired: both CTAs' MMAs must be done with the stage
+      tcg::mbar_init(&empty[q], 1);
     }
     for (int q = 0; q < 2; q++) {
       tcg::mbar_init(&tfull[q], 1);
-      tcg::mbar_init(&tempty[q], 8);
+      tcg::mbar_init(&tempty[q], PAIR ? 16 : 8);   // paired: both CTAs' epilogue warps drain the even CTA's MMAs
     }
-    *abort_flag = 0;
+    *abort_flag = *(volatile int32_t*)err != 0;   // an earlier launch of this factorization failed: skip the tiles
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 1) tcg::tmem_alloc(tslot, C::TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR) tcg::tmem_alloc2(tslot, C::TMEM_COLS);
+    else tcg::tmem_alloc(tslot, C::TMEM_COLS);
+  }
   tcg::tc_fence_before();
   if (PAIR) tcg::cluster_sync();   // the peer's barriers are initialised before anything reaches them
   else __syncthreads();
@@ -605,8 +610,9 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     *abort_flag = 1;
     atomicExch(err, 1);
   };
-  // which 128-row block of B holds the A rows (-1: none, A is loaded)
-  auto a_in_b = [](const UTile& u) -> int {
+  // which 128-row block of this CTA's B holds the A rows (-1: none, A is loaded)
+  auto a_in_b = [rank](const UTile& u) -> int {
+    if (PAIR) return u.i0 == u.j0 + 128 * rank ? 0 : -1;   // a diagonal pair: each CTA's A half is its B half
     if (u.i0 == u.j0) return 0;
     if (TN == 256 && u.i0 == u.j0 + 128) return 1;
     return -1;
@@ -629,17 +635,22 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             break;
           }
           const uint32_t sa = sbase + st * C::STAGE, sb = sa + 2 * C::OPA;
-          tcg::mbar_arrive_expect_tx(&full[st], (shared_a ? 0 : 2 * C::OPA) + 2 * C::OPB);
           const int x = u.kc + c * 32;
-          if (!shared_a) {
-            tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
-            tcg::tma_load_3d(sa + C::OPA, ml, x, (int)u.i0, u.b, &full[st]);
-          }
-          if (PAIR) {   // this CTA's half of B, into both CTAs
-            const int hb = rank;
-            tcg::tma_load_3d_mc(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st], 3);
-            tcg::tma_load_3d_mc(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st], 3);
+          if (PAIR) {   // this CTA's A rows and half of B, counted on the even CTA's barrier
+            const uint32_t fb = tcg::mapa_shared(tcg::smem_u32(&full[st]), 0);
+            if (rank == 0) tcg::mbar_arrive_expect_tx(&full[st], 2 * ((shared_a ? 0 : 2 * C::OPA) + 2 * C::OPB));
+            if (!shared_a) {
+              tcg::tma_load_3d_2sm(sa, mh, x, (int)u.i0, u.b, fb);
+              tcg::tma_load_3d_2sm(sa + C::OPA, ml, x, (int)u.i0, u.b, fb);
+            }
+            tcg::tma_load_3d_2sm(sb, mh, x, (int)u.j0 + 128 * rank, u.b, fb);
+            tcg::tma_load_3d_2sm(sb + C::OPB, ml, x, (int)u.j0 + 128 * rank, u.b, fb);
           } else {
+            tcg::mbar_arrive_expect_tx(&full[st], (shared_a ? 0 : 2 * C::OPA) + 2 * C::OPB);
+            if (!shared_a) {
+              tcg::tma_load_3d(sa, mh, x, (int)u.i0, u.b, &full[st]);
+              tcg::tma_load_3d(sa + C::OPA, ml, x, (int)u.i0, u.b, &full[st]);
+            }
 #pragma unroll
             for (int hb = 0; hb < C::BROWS / 128; hb++) {
               tcg::tma_load_3d(sb + hb * C::OPA, mh, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
@@ -654,8 +665,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {   // MMA issuer
-      const uint32_t idesc = tcg::idesc_tf32(128, TN);
+    if (lane == 0 && rank == 0) {   // MMA issuer (paired: the even CTA, for both)
+      const uint32_t idesc = tcg::idesc_tf32(PAIR ? 256 : 128, TN);
       uint32_t st = 0, ph = 0, acc = 0, aph = 0;
       for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
         const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
@@ -682,11 +693,17 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             const uint32_t o = kk * 32;
             const uint64_t ah = tcg::smem_desc_sw128(aH + o), al = tcg::smem_desc_sw128(aL + o);
             const uint64_t bh = tcg::smem_desc_sw128(bH + o), bl = tcg::smem_desc_sw128(bL + o);
-            tcg::mma_tf32(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-            tcg::mma_tf32(d, ah, bl, idesc, 1u);
-            tcg::mma_tf32(d, ah, bh, idesc, 1u);
+            if (PAIR) {
+              tcg::mma_tf32_2sm(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              tcg::mma_tf32_2sm(d, ah, bl, idesc, 1u);
+              tcg::mma_tf32_2sm(d, ah, bh, idesc, 1u);
+            } else {
+              tcg::mma_tf32(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              tcg::mma_tf32(d, ah, bl, idesc, 1u);
+              tcg::mma_tf32(d, ah, bh, idesc, 1u);
+            }
           }
-          if (PAIR) tcg::mma_commit_mc(&empty[st], 3);
+          if (PAIR) tcg::mma_commit2_mc(&empty[st], 3);
           else tcg::mma_commit(&empty[st]);
           if (++st == NS) {
             st = 0;
@@ -697,7 +714,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           fail();
           break;
         }
-        tcg::mma_commit(&tfull[acc]);
+        if (PAIR) tcg::mma_commit2_mc(&tfull[acc], 3);
+        else tcg::mma_commit(&tfull[acc]);
         if (++acc == 2) {
           acc = 0;
           aph ^= 1;
@@ -743,7 +761,10 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           if (sl == NSL - 1) {   // this warp's part of the accumulator has been read
             tcg::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tcg::mbar_arrive(&tempty[acc]);
+            if (lane == 0) {
+              if (PAIR) tcg::mbar_arrive_cluster(tcg::mapa_shared(tcg::smem_u32(&tempty[acc]), 0));
+              else tcg::mbar_arrive(&tempty[acc]);
+            }
           }
           __syncwarp();
 #pragma unroll
@@ -801,7 +822,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   else __syncthreads();
   if (warp == 1) {
     tcg::tc_fence_after();
-    tcg::tmem_dealloc(tmem, C::TMEM_COLS);
+    if (PAIR) tcg::tmem_dealloc2(tmem, C::TMEM_COLS);
+    else tcg::tmem_dealloc(tmem, C::TMEM_COLS);
   }
 }
 
@@ -815,7 +837,7 @@ void set_attrs() {   // once per process (contexts may run on several host threa
     GP_CUDA(cudaFuncSetAttribute(k_update_ws<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  UW<128>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 UW<256>::SMEM));
+                                 UW<256, true>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   });
 }
@@ -890,7 +912,7 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
     cfg.blockDim = dim3(UW_THREADS);
-    cfg.dynamicSmemBytes = UW<256>::SMEM;
+    cfg.dynamicSmemBytes = UW<256, true>::SMEM;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

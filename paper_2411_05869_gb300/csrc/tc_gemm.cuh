@@ -31,10 +31,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; returns false (and leaves the barrier as is) when the limit runs out.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait; returns false (and leaves the barrier as is) when the poll limit or WAIT_NS of wall-clock time
+// runs out (no legitimate wait in these kernels comes near a millisecond).
+constexpr uint64_t WAIT_NS = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; it++)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < WAIT_LIMIT; it++) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
+  }
   return false;
 }
 
@@ -152,6 +163,58 @@ __device__ __forceinline__ uint32_t cluster_count_x() {
 // All threads of every CTA of the cluster (release/acquire: earlier shared-memory and mbarrier writes are seen).
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// ------------------------------------------------------------------------------------------------
+// CTA-pair (cta_group::2) forms: one MMA issued by the even CTA of a two-CTA cluster computes a 256-row tile
+// whose A rows 0-127 and B columns 0-N/2-1 sit in the even CTA's shared memory and A rows 128-255 and B columns
+// N/2-N-1 in the odd CTA's, at the same offsets; accumulator rows 0-127 land in the even CTA's TMEM and rows
+// 128-255 in the odd CTA's. TMEM is allocated and freed by one warp of each CTA together.
+
+// Shared-memory address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void tmem_alloc2(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_tf32_2sm(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on the mbarrier at this offset in every CTA of ctamask once the pair's earlier MMAs have completed.
+__device__ __forceinline__ void mma_commit2_mc(uint64_t* bar, uint16_t ctamask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
+          smem_u32(bar)),
+      "h"(ctamask)
+      : "memory");
+}
+// Tile load into this CTA's shared memory whose transaction bytes complete on an mbarrier of either CTA of the
+// pair (`bar_cluster`: a shared::cluster address, e.g. from mapa_shared).
+__device__ __forceinline__ void tma_load_3d_2sm(uint32_t dst, const void* tmap, int x, int y, int z,
+                                                uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4}], [%5];\n" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
+      : "memory");
+}
+// Arrive (release, cluster scope) on an mbarrier of another CTA of the cluster.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(bar_cluster) : "memory");
 }
 
 }  // namespace tcg
