@@ -476,7 +476,7 @@ def main():
     per = np.array(res["per"])
     info = res["info"]
     prof = res["prof"]
-    a7 = ["extend_add", "front_small", "potrf", "trsm", "update"]
+    a7 = ["extend_add", "front_small", "potrf", "trsm", "update", "update_left"]
     t_a7 = sum(prof[k][0] for k in a7)
     flops = info["flops"]
     if args.precision == "mixed":
@@ -503,7 +503,7 @@ def main():
                                    "supernodes": info["nsuper"], "levels": info["nlevels"],
                                    "max_front": info["max_front"], "assemble_s": round(res["t_assemble"], 3)}),
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
-        "roofline": {"kernel": {"update": "k_update_ws (tensor-core trailing updates)"}.get(dom, dom),
+        "roofline": {"kernel": (KERNEL_OF_CLASS_MIXED if args.precision == "mixed" else KERNEL_OF_CLASS_FP64).get(dom, dom),
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get((args.workload, dom)),
                      "launches_per_step": d_n, "avg_launch_ms": d_ms / max(d_n, 1),
@@ -536,8 +536,15 @@ def main():
     print(json.dumps(line))
 
 
+# the kernel behind each timed class
+KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 256 x 256 CTA-pair tcgen05 MMAs)",
+                         "update_left": "k_update_ws<64> (left-looking block-column updates, 128 x 64 tiles)",
+                         "potrf": "k_potrf32", "trsm": "k_trsm32", "extend_add": "k_extend_add32"}
+KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
+                        "extend_add": "k_extend_add"}
+
 # DRAM bytes per launch of the dominant kernel, from ncu (profiles/), or None when the kernel changed since
-_TRAFFIC = {("station_1.2M", "update"): 6.1e8}
+_TRAFFIC = {}
 
 
 def _full_flops_hint(name):

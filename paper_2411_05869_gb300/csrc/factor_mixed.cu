@@ -180,54 +180,42 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// FP64 POTRF of diagonal tile kb, right-looking in shared memory (row stride T + 1, so walks down a column are
-// free of bank conflicts), with a one-column lookahead. The pivots d_k = L_kk^2 stay unscaled during the
-// elimination and column k enters the update through its scaled copy s_j = a_jk / d_k: a_ij -= a_ik s_j.
-// In step k warp 0 updates column k + 1, forms 1 / d_{k+1} and the scaled copy of column k + 1 (the division is
-// the longest dependency of a step: FP64 latencies on GB300 are some 64 cycles per DFMA and 440 per divide),
-// while warps 1-7 update the entries (i, j), k + 2 <= j <= i; one barrier per step. Those entries are numbered
-// column by column from the last column, so each step's work is a prefix of one fixed list, spread evenly,
-// four loads in flight per thread. Square roots and the column scaling L_ik = a_ik / sqrt(d_k) follow in one
-// parallel pass, then the FP32 inverse of L for the TRSM and the solves.
+// POTRF of diagonal tile kb. The tile accumulates its assembled values and every update in FP64; the
+// factorization itself runs in FP32 on the tile rounded once to FP32, the precision of every other entry of L
+// in this path (on GB300 an FP64 elimination of a 64 x 64 tile is bound by the FP64 pipe: some 44k dependent-
+// ordered DFMAs at under two per clock per SM, against 128 FP32 FMAs per clock). Right-looking in shared memory
+// (row stride T + 1, so walks down a column are free of bank conflicts), with a one-column lookahead: the pivots
+// d_k = L_kk^2 stay unscaled during the elimination and column k enters the update through its scaled copy
+// s_j = a_jk / d_k: a_ij -= a_ik s_j. In step k warp 0 updates column k + 1, forms 1 / d_{k+1} and the scaled
+// copy of column k + 1, while warps 1-7 update the entries (i, j), k + 2 <= j <= i; one barrier per step. Those
+// entries are numbered column by column from the last column, so each step's work is a prefix of one fixed
+// list, spread evenly, four in flight per thread. Square roots and the column scaling L_ik = a_ik / sqrt(d_k)
+// follow in one parallel pass, then the FP32 inverse of L for the TRSM and the solves; L goes back to the FP64
+// tile (the log-determinant reads its diagonal).
 constexpr int PT = T + 1;
 constexpr int POTRF_THREADS = 256;
-constexpr size_t POTRF_SMEM = (size_t)T * PT * sizeof(double) + (size_t)T * PT * sizeof(float) +
-                              (size_t)T * T * sizeof(float) + (size_t)T * T / 2 * sizeof(float) +
-                              (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
+constexpr size_t POTRF_SMEM = (size_t)T * PT * sizeof(float) + (size_t)T * T * sizeof(float) +
+                              (size_t)T * T / 2 * sizeof(float) + (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
 
-// 1 / d by Newton's iteration r <- r + r (1 - d r) from the hardware's approximate FP64 reciprocal; two steps
-// take its ~23 correct bits past 53 (error within an ulp or two; the pivot only needs FP64 accuracy, not
-// correct rounding). Shorter than an IEEE divide, and this sits on the critical path of every step.
-__device__ __forceinline__ double recip_nr(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
-__device__ __forceinline__ double pivot_recip(double d, double* a, int32_t* notpd, int32_t col) {
-  if (!(d > 0.0)) {
+__device__ __forceinline__ float pivot_recip(float d, float* a, int32_t* notpd, int32_t col) {
+  if (!(d > 0.f)) {
     atomicMin(notpd, col);
-    d = 1.0;
+    d = 1.f;
     *a = d;
   }
-  return recip_nr(d);
+  return __frcp_rn(d);
 }
 
-__global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
                                                            double* __restrict__ dg, int64_t DE,
                                                            int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
-  extern __shared__ double sm64[];
-  double* A = sm64;                                      // T x PT
-  float* Lf = reinterpret_cast<float*>(A + T * PT);     // T x PT, FP32 copy of L
-  float* Inv = Lf + T * PT;                              // T x T, row-major
-  float* Mt = Inv + T * T;                               // T x T / 2 scratch of the block inversion
+  extern __shared__ float smf[];
+  float* A = smf;                 // T x PT: the tile, then L (identity past bw) for the inversion
+  float* Inv = A + T * PT;        // T x T, row-major
+  float* Mt = Inv + T * T;        // T x T / 2 scratch of the block inversion
   uint16_t* tab = reinterpret_cast<uint16_t*>(Mt + T * T / 2);
-  __shared__ double rd[T];      // 1 / d_k
-  __shared__ double sc[2][T];   // scaled copy of the current column (double-buffered); later 1 / L_kk
-  __shared__ float rf[T];       // 1 / L_kk in FP32
+  __shared__ float rd[T];         // 1 / d_k
+  __shared__ float sc[2][T];      // scaled copy of the current column (double-buffered); later 1 / L_kk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
@@ -238,7 +226,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
 #pragma unroll
   for (int u = 0; u < T * T / POTRF_THREADS; u++) {
     const int t = tid + u * POTRF_THREADS;
-    A[(t >> 6) * PT + (t & 63)] = D[t];
+    A[(t >> 6) * PT + (t & 63)] = (float)D[t];
   }
   // entry list for this bw: column j = bw - 1 - c holds rows j .. bw - 1 at offsets c (c + 1) / 2 ..
   const int ne = bw * (bw - 1) / 2;
@@ -251,7 +239,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   }
   __syncthreads();
   if (warp == 0) {   // column 0: reciprocal and scaled copy
-    double r = 0.0;
+    float r = 0.f;
     if (lane == 0) r = rd[0] = pivot_recip(A[0], A, flag, first);
     r = __shfl_sync(0xffffffffu, r, 0);
     for (int i = 1 + lane; i < bw; i += 32) sc[0][i] = A[i * PT] * r;
@@ -259,18 +247,18 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   __syncthreads();
   constexpr int NB = POTRF_THREADS - 32;
   for (int k = 0; k + 1 < bw; k++) {
-    const double* scur = sc[k & 1];
+    const float* scur = sc[k & 1];
     const int k1 = k + 1;
     if (warp == 0) {
-      double* snxt = sc[(k & 1) ^ 1];
-      const double s1 = scur[k1];
+      float* snxt = sc[(k & 1) ^ 1];
+      const float s1 = scur[k1];
       const int i0 = k1 + lane, i1 = k1 + 32 + lane;
-      double v0 = 0.0, v1 = 0.0;
-      if (i0 < bw) v0 = A[i0 * PT + k1] - A[i0 * PT + k] * s1;
-      if (i1 < bw) v1 = A[i1 * PT + k1] - A[i1 * PT + k] * s1;
+      float v0 = 0.f, v1 = 0.f;
+      if (i0 < bw) v0 = fmaf(-A[i0 * PT + k], s1, A[i0 * PT + k1]);
+      if (i1 < bw) v1 = fmaf(-A[i1 * PT + k], s1, A[i1 * PT + k1]);
       if (i0 < bw) A[i0 * PT + k1] = v0;
       if (i1 < bw) A[i1 * PT + k1] = v1;
-      double r = 0.0;
+      float r = 0.f;
       if (lane == 0) r = rd[k1] = pivot_recip(v0, A + k1 * PT + k1, flag, first + k1);
       r = __shfl_sync(0xffffffffu, r, 0);
       if (i0 > k1 && i0 < bw) snxt[i0] = v0 * r;
@@ -279,7 +267,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
       const int cnt = (bw - 2 - k) * (bw - 1 - k) / 2;   // entries (i, j), k + 2 <= j <= i
       for (int e0 = tid - 32; e0 < cnt; e0 += 4 * NB) {
         int ij[4];
-        double v[4];
+        float v[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           const int e = e0 + q * NB;
@@ -288,7 +276,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           const int i = ij[q] >> 8, j = ij[q] & 255;
-          v[q] = A[i * PT + j] - A[i * PT + k] * scur[j];
+          v[q] = fmaf(-A[i * PT + k], scur[j], A[i * PT + j]);
         }
 #pragma unroll
         for (int q = 0; q < 4; q++)
@@ -299,30 +287,25 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   }
   if (tid < T) {
     if (tid < bw) {
-      const double l = sqrt(A[tid * PT + tid]);
+      const float l = sqrtf(A[tid * PT + tid]);
       A[tid * PT + tid] = l;
-      const double il = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
-      sc[0][tid] = il;
-      rf[tid] = (float)il;
+      sc[0][tid] = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
     } else {
-      rf[tid] = 1.f;   // rows past bw: identity, so the block inversion below stays finite
+      sc[0][tid] = 1.f;           // rows past bw: identity, so the block inversion below stays finite
     }
   }
   __syncthreads();
   for (int t = tid; t < T * T; t += POTRF_THREADS) {
     const int i = t >> 6, j = t & 63;
-    float lf = 0.f;
+    float v = 0.f;
     if (i < bw && j <= i) {
-      double v = A[i * PT + j];
-      if (j < i) {
-        v *= sc[0][j];
-        A[i * PT + j] = v;
-      }
-      lf = (float)v;
+      v = A[i * PT + j];
+      if (j < i) v *= sc[0][j];
+      D[t] = (double)v;
     } else if (i == j) {
-      lf = 1.f;
+      v = 1.f;
     }
-    Lf[i * PT + j] = lf;
+    A[i * PT + j] = v;
     Inv[t] = 0.f;
   }
   __syncthreads();
@@ -337,8 +320,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
       float acc = r == c ? 1.f : 0.f;
 #pragma unroll
       for (int l = 0; l < r; l++)
-        if (l >= c) acc = fmaf(-Lf[(o + r) * PT + o + l], x[l], acc);
-      x[r] = r < c ? 0.f : acc * rf[o + r];
+        if (l >= c) acc = fmaf(-A[(o + r) * PT + o + l], x[l], acc);
+      x[r] = r < c ? 0.f : acc * sc[0][o + r];
     }
 #pragma unroll
     for (int r = 0; r < 4; r++) Inv[(o + r) * T + o + c] = x[r];
@@ -349,7 +332,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
     for (int q = tid; q < nq; q += POTRF_THREADS) {   // M[r][c] = sum_{l >= c} B[r][l] inv(A)[l][c]
       const int p = q / (h * h), rem = q - p * h * h, r = rem / h, c = rem - r * h, o = p * 2 * h;
       float acc = 0.f;
-      for (int l = c; l < h; l++) acc = fmaf(Lf[(o + h + r) * PT + o + l], Inv[(o + l) * T + o + c], acc);
+      for (int l = c; l < h; l++) acc = fmaf(A[(o + h + r) * PT + o + l], Inv[(o + l) * T + o + c], acc);
       Mt[q] = acc;
     }
     __syncthreads();
@@ -367,7 +350,6 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf64(const int32_t* __rest
   for (int u = 0; u < T * T / POTRF_THREADS; u++) {
     const int t = tid + u * POTRF_THREADS;
     const int i = t >> 6, j = t & 63;
-    D[t] = A[i * PT + j];
     DI[t] = (i < bw && j < bw) ? Inv[t] : 0.f;
   }
 }
@@ -838,7 +820,7 @@ void set_attrs() {   // once per process (contexts may run on several host threa
                                  UW<128>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  UW<256, true>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
+    GP_CUDA(cudaFuncSetAttribute(k_potrf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   });
 }
 
@@ -1035,13 +1017,13 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
       if (stp.left_total > 0) {   // this block column from the earlier blocks of its group
-        ProfScope ps_(ctx, KC_UPDATE, B * stp.left_flops);
+        ProfScope ps_(ctx, KC_UPDATE_LEFT, B * stp.left_flops);
         launch_update(ctx, f, stp.left_total, dp.upd_fronts + stp.left_off, dp.upd_pre + stp.left_pre_off,
                       stp.n_left, stp.kb, 3);
       }
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf64<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
+        k_potrf32<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
                                                                                f->notpd, f->dinv32);
         GP_CHECK_LAUNCH(ctx);
       }

@@ -57,7 +57,7 @@ struct GpError {
 // ------------------------------------------------------------------------------------------ context
 // Kernel classes timed by the optional launch profiler (gp_profile / gp_profile_read).
 enum KClass { KC_VALUES = 0, KC_EXTEND_ADD, KC_FRONT_SMALL, KC_POTRF, KC_TRSM, KC_UPDATE, KC_SOLVE, KC_PREDICT,
-              KC_ASSEMBLE, KC_COUNT };
+              KC_ASSEMBLE, KC_UPDATE_LEFT, KC_COUNT };
 
 struct gp_ctx {
   int device = 0;

@@ -73,7 +73,7 @@ SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_points
            "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
            "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
-          "predict": 7}
+          "predict": 7, "update_left": 9}
 
 _lib = None
 _LIVE = {"server": weakref.WeakSet(), "factor": weakref.WeakSet(), "pointset": weakref.WeakSet(),
