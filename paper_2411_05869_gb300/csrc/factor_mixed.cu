@@ -180,178 +180,177 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// POTRF of diagonal tile kb. The tile accumulates its assembled values and every update in FP64; the
-// factorization itself runs in FP32 on the tile rounded once to FP32, the precision of every other entry of L
-// in this path (on GB300 an FP64 elimination of a 64 x 64 tile is bound by the FP64 pipe: some 44k dependent-
-// ordered DFMAs at under two per clock per SM, against 128 FP32 FMAs per clock). Right-looking in shared memory
-// (row stride T + 1, so walks down a column are free of bank conflicts), with a one-column lookahead: the pivots
-// d_k = L_kk^2 stay unscaled during the elimination and column k enters the update through its scaled copy
-// s_j = a_jk / d_k: a_ij -= a_ik s_j. In step k warp 0 updates column k + 1, forms 1 / d_{k+1} and the scaled
-// copy of column k + 1, while warps 1-7 update the entries (i, j), k + 2 <= j <= i; one barrier per step. Those
-// entries are numbered column by column from the last column, so each step's work is a prefix of one fixed
-// list, spread evenly, four in flight per thread. Square roots and the column scaling L_ik = a_ik / sqrt(d_k)
-// follow in one parallel pass, then the FP32 inverse of L for the TRSM and the solves; L goes back to the FP64
-// tile (the log-determinant reads its diagonal).
-constexpr int PT = T + 1;
+// POTRF of diagonal tile kb, with the inverse of its factor. The tile accumulates its assembled values and
+// every update in FP64; the factorization itself runs in FP32 on the tile rounded once to FP32, the precision of
+// every other entry of L in this path (on GB300 an FP64 elimination of a 64 x 64 tile is bound by the FP64 pipe
+// and its 64-cycle latencies). Right-looking, with the tile in registers: thread (tr, tc) of a 16 x 16 grid
+// holds the entries (tr + 16 p, tc + 16 q), p, q < 4, of the tile and of X = inv(U), U the unit lower factor
+// (A = U diag(d) U^T, U_ik = a_ik / d_k with a_ik column k as updated through column k - 1). The pivots
+// d_k = L_kk^2 stay unscaled: column k enters through s_j = a_jk / d_k as a_ij -= a_ik s_j (j > k), and the
+// same step eliminates below X's row k: X_ij -= U_ik X_kj (i > k, j <= k), the forward elimination of the
+// identity. Two columns per step and one barrier per step (the step's fixed costs -- barrier, shared-memory
+// round trip, reciprocal -- are what a column costs here): every thread reads columns k and k + 1 and rows k,
+// k + 1 of X as published by their holders, forms column k + 1's and row k + 1's updates by column k itself, and
+// applies both. Then L_ik = a_ik / sqrt(d_k), inv(L)_ij = X_ij / sqrt(d_i); L goes back to the FP64 tile (the
+// log-determinant reads its diagonal) and inv(L) to the FP32 inverse tile (the TRSM and the solves).
 constexpr int POTRF_THREADS = 256;
-constexpr size_t POTRF_SMEM = (size_t)T * PT * sizeof(float) + (size_t)T * T * sizeof(float) +
-                              (size_t)T * T / 2 * sizeof(float) + (size_t)T * (T - 1) / 2 * sizeof(uint16_t);
 
-__device__ __forceinline__ float pivot_recip(float d, float* a, int32_t* notpd, int32_t col) {
-  if (!(d > 0.f)) {
-    atomicMin(notpd, col);
-    d = 1.f;
-    *a = d;
-  }
-  return __frcp_rn(d);
+// 1 / d from the hardware's approximate reciprocal and one Newton step r <- r + r (1 - d r) (within about an
+// ulp; the pivots are normal numbers well away from the range limits).
+__device__ __forceinline__ float recip_nr(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return fmaf(r, fmaf(-d, r, 1.f), r);
 }
 
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
                                                            double* __restrict__ dg, int64_t DE,
                                                            int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
-  extern __shared__ float smf[];
-  float* A = smf;                 // T x PT: the tile, then L (identity past bw) for the inversion
-  float* Inv = A + T * PT;        // T x T, row-major
-  float* Mt = Inv + T * T;        // T x T / 2 scratch of the block inversion
-  uint16_t* tab = reinterpret_cast<uint16_t*>(Mt + T * T / 2);
+  __shared__ float col[2][2][T];  // columns k, k + 1 after the updates of columns < k (double-buffered)
+  __shared__ float xrow[2][2][T]; // rows k, k + 1 of X after the eliminations of rows < k (double-buffered)
+  __shared__ float piv[T];        // pivots d_k
   __shared__ float rd[T];         // 1 / d_k
-  __shared__ float sc[2][T];      // scaled copy of the current column (double-buffered); later 1 / L_kk
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ float sc[T];         // 1 / L_kk
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
   int32_t s = fronts[blockIdx.x];
   int b = blockIdx.y;
   double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int w = dp.w[s], bw = min(T, w - kb * T);
   const int32_t first = dp.sn_first[s] + kb * T;
   int32_t* flag = notpd + b;
+  float a[4][4], x[4][4];
+  uint32_t own = 0;   // bit 4 p + q: entry (tr + 16 p, tc + 16 q) is in the lower triangle of the bw x bw tile
 #pragma unroll
-  for (int u = 0; u < T * T / POTRF_THREADS; u++) {
-    const int t = tid + u * POTRF_THREADS;
-    A[(t >> 6) * PT + (t & 63)] = (float)D[t];
-  }
-  // entry list for this bw: column j = bw - 1 - c holds rows j .. bw - 1 at offsets c (c + 1) / 2 ..
-  const int ne = bw * (bw - 1) / 2;
-  for (int e = tid; e < ne; e += POTRF_THREADS) {
-    int c = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-    while ((c + 1) * (c + 2) / 2 <= e) c++;
-    while (c * (c + 1) / 2 > e) c--;
-    const int j = bw - 1 - c, i = j + (e - c * (c + 1) / 2);
-    tab[e] = (uint16_t)((i << 8) | j);
-  }
-  __syncthreads();
-  if (warp == 0) {   // column 0: reciprocal and scaled copy
-    float r = 0.f;
-    if (lane == 0) r = rd[0] = pivot_recip(A[0], A, flag, first);
-    r = __shfl_sync(0xffffffffu, r, 0);
-    for (int i = 1 + lane; i < bw; i += 32) sc[0][i] = A[i * PT] * r;
-  }
-  __syncthreads();
-  constexpr int NB = POTRF_THREADS - 32;
-  for (int k = 0; k + 1 < bw; k++) {
-    const float* scur = sc[k & 1];
-    const int k1 = k + 1;
-    if (warp == 0) {
-      float* snxt = sc[(k & 1) ^ 1];
-      const float s1 = scur[k1];
-      const int i0 = k1 + lane, i1 = k1 + 32 + lane;
-      float v0 = 0.f, v1 = 0.f;
-      if (i0 < bw) v0 = fmaf(-A[i0 * PT + k], s1, A[i0 * PT + k1]);
-      if (i1 < bw) v1 = fmaf(-A[i1 * PT + k], s1, A[i1 * PT + k1]);
-      if (i0 < bw) A[i0 * PT + k1] = v0;
-      if (i1 < bw) A[i1 * PT + k1] = v1;
-      float r = 0.f;
-      if (lane == 0) r = rd[k1] = pivot_recip(v0, A + k1 * PT + k1, flag, first + k1);
-      r = __shfl_sync(0xffffffffu, r, 0);
-      if (i0 > k1 && i0 < bw) snxt[i0] = v0 * r;
-      if (i1 < bw) snxt[i1] = v1 * r;
-    } else {
-      const int cnt = (bw - 2 - k) * (bw - 1 - k) / 2;   // entries (i, j), k + 2 <= j <= i
-      for (int e0 = tid - 32; e0 < cnt; e0 += 4 * NB) {
-        int ij[4];
-        float v[4];
+  for (int p = 0; p < 4; p++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int e = e0 + q * NB;
-          ij[q] = e < cnt ? tab[e] : 0;
+    for (int q = 0; q < 4; q++) {
+      const int i = tr + 16 * p, j = tc + 16 * q;
+      const bool in = j <= i && i < bw;
+      a[p][q] = in ? (float)D[i * T + j] : 0.f;
+      x[p][q] = i == j ? 1.f : 0.f;
+      own |= (in ? 1u : 0u) << (4 * p + q);
+    }
+  if (tc < 2) {
+#pragma unroll
+    for (int p = 0; p < 4; p++) col[0][tc][tr + 16 * p] = a[p][0];
+  }
+  if (tr < 2) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) xrow[0][tr][tc + 16 * q] = x[0][q];
+  }
+  // Four phases of 16 columns: in phase m columns below 16 m are final, so only the tile's entries of column
+  // groups q >= m and row groups p >= q take part (entries above the diagonal inside a diagonal block, and rows
+  // past bw, are updated but never read), and only X's entries of row groups p >= m and column groups q <= m.
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    const int kend = min(16 * (m + 1), bw);
+    for (int k = 16 * m; k < kend; k += 2) {
+      __syncthreads();
+      const int buf = k & 2 ? 1 : 0;
+      const float* ca = col[buf][0];   // column k
+      const float* cb = col[buf][1];   // column k + 1 (not yet updated by column k)
+      const float* xa = xrow[buf][0];  // row k of X (final)
+      const float* xb = xrow[buf][1];  // row k + 1 of X (not yet eliminated by row k)
+      const bool two = k + 1 < bw;
+      float d0 = ca[k];
+      if (!(d0 > 0.f)) {
+        if (tid == 0) atomicMin(flag, first + k);
+        d0 = 1.f;
+      }
+      const float r0 = recip_nr(d0);
+      const float s01 = two ? ca[k + 1] * r0 : 0.f;   // U_{k+1, k}
+      float d1 = two ? fmaf(-ca[k + 1], s01, cb[k + 1]) : 1.f;
+      if (!(d1 > 0.f)) {
+        if (tid == 0) atomicMin(flag, first + k + 1);
+        d1 = 1.f;
+      }
+      const float r1 = recip_nr(d1);
+      if (tid == 0) {
+        piv[k] = d0;
+        rd[k] = r0;
+        if (two) {
+          piv[k + 1] = d1;
+          rd[k + 1] = r1;
+        }
+      }
+      float ci0[4], ci1[4], sj0[4], sj1[4], xa4[4], xb4[4];
+#pragma unroll
+      for (int p = m; p < 4; p++) {
+        ci0[p] = ca[tr + 16 * p];
+        ci1[p] = fmaf(-ci0[p], s01, cb[tr + 16 * p]);
+      }
+#pragma unroll
+      for (int q = m; q < 4; q++) {
+        const float v = ca[tc + 16 * q];
+        sj0[q] = v * r0;
+        sj1[q] = fmaf(-v, s01, cb[tc + 16 * q]) * r1;
+      }
+#pragma unroll
+      for (int q = 0; q <= m; q++) {
+        xa4[q] = xa[tc + 16 * q];
+        xb4[q] = fmaf(-s01, xa4[q], xb[tc + 16 * q]);   // row k + 1 of X, eliminated by row k
+      }
+      const int jm = tc + 16 * m;   // this thread's column of group m
+      const int im = tr + 16 * m;   // this thread's row of group m
+#pragma unroll
+      for (int q = m; q < 4; q++)
+#pragma unroll
+        for (int p = q; p < 4; p++) {
+          if (q > m || jm > k) a[p][q] = fmaf(-ci0[p], sj0[q], a[p][q]);
+          if (two && (q > m || jm > k + 1)) a[p][q] = fmaf(-ci1[p], sj1[q], a[p][q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int i = ij[q] >> 8, j = ij[q] & 255;
-          v[q] = fmaf(-A[i * PT + k], scur[j], A[i * PT + j]);
-        }
+      for (int p = m; p < 4; p++) {
+        const float u0 = ci0[p] * r0, u1 = ci1[p] * r1;   // U_ik, U_i,k+1
 #pragma unroll
-        for (int q = 0; q < 4; q++)
-          if (e0 + q * NB < cnt) A[(ij[q] >> 8) * PT + (ij[q] & 255)] = v[q];
+        for (int q = 0; q <= m; q++) {
+          if (p > m || im > k) x[p][q] = fmaf(-u0, xa4[q], x[p][q]);
+          if (two && (p > m || im > k + 1)) x[p][q] = fmaf(-u1, xb4[q], x[p][q]);
+        }
+      }
+      const int k2 = k + 2;
+      if (k2 < bw) {
+        const int qb = k2 >> 4;
+        if ((tc >> 1) == ((k2 & 15) >> 1)) {   // publish columns k + 2 and k + 3
+          const int h = tc & 1;
+          float* cn = col[buf ^ 1][h];
+#pragma unroll
+          for (int p = m; p < 4; p++) {
+            const int i = tr + 16 * p;
+            float v = a[p][m];
+            if (m < 3 && qb == m + 1) v = a[p][m < 3 ? m + 1 : m];
+            if (i >= k2 + h && i < bw) cn[i] = v;
+          }
+        }
+        if ((tr >> 1) == ((k2 & 15) >> 1)) {   // publish rows k + 2 and k + 3 of X
+          const int h = tr & 1;
+          float* xn = xrow[buf ^ 1][h];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            float v = x[m][q];
+            if (m < 3 && qb == m + 1) v = x[m < 3 ? m + 1 : m][q];
+            xn[tc + 16 * q] = v;
+          }
+        }
       }
     }
-    __syncthreads();
-  }
-  if (tid < T) {
-    if (tid < bw) {
-      const float l = sqrtf(A[tid * PT + tid]);
-      A[tid * PT + tid] = l;
-      sc[0][tid] = l * rd[tid];   // sqrt(d) / d = 1 / L_kk
-    } else {
-      sc[0][tid] = 1.f;           // rows past bw: identity, so the block inversion below stays finite
-    }
   }
   __syncthreads();
-  for (int t = tid; t < T * T; t += POTRF_THREADS) {
-    const int i = t >> 6, j = t & 63;
-    float v = 0.f;
-    if (i < bw && j <= i) {
-      v = A[i * PT + j];
-      if (j < i) v *= sc[0][j];
-      D[t] = (double)v;
-    } else if (i == j) {
-      v = 1.f;
-    }
-    A[i * PT + j] = v;
-    Inv[t] = 0.f;
-  }
+  if (tid < T) sc[tid] = tid < bw ? sqrtf(piv[tid]) * rd[tid] : 1.f;   // sqrt(d) / d = 1 / L_kk
   __syncthreads();
-  // FP32 inverse of L by recursive 2 x 2 block inversion: inv([A 0; B C]) = [inv(A) 0; -inv(C) B inv(A) inv(C)].
-  // 4 x 4 diagonal blocks by substitution (thread per block column), then four doublings, each two parallel
-  // products (M = B inv(A), then -inv(C) M) over all pairs of blocks.
-  if (tid < T) {
-    const int o = tid & ~3, c = tid & 3;
-    float x[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      float acc = r == c ? 1.f : 0.f;
-#pragma unroll
-      for (int l = 0; l < r; l++)
-        if (l >= c) acc = fmaf(-A[(o + r) * PT + o + l], x[l], acc);
-      x[r] = r < c ? 0.f : acc * sc[0][o + r];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; r++) Inv[(o + r) * T + o + c] = x[r];
-  }
-  __syncthreads();
-  for (int h = 4; h < T; h *= 2) {
-    const int nq = (T / 2) * h;   // outputs per product over all pairs
-    for (int q = tid; q < nq; q += POTRF_THREADS) {   // M[r][c] = sum_{l >= c} B[r][l] inv(A)[l][c]
-      const int p = q / (h * h), rem = q - p * h * h, r = rem / h, c = rem - r * h, o = p * 2 * h;
-      float acc = 0.f;
-      for (int l = c; l < h; l++) acc = fmaf(A[(o + h + r) * PT + o + l], Inv[(o + l) * T + o + c], acc);
-      Mt[q] = acc;
-    }
-    __syncthreads();
-    for (int q = tid; q < nq; q += POTRF_THREADS) {   // X21[r][c] = -sum_{l <= r} inv(C)[r][l] M[l][c]
-      const int p = q / (h * h), rem = q - p * h * h, r = rem / h, c = rem - r * h, o = p * 2 * h;
-      const float* Mp = Mt + p * h * h;
-      float acc = 0.f;
-      for (int l = 0; l <= r; l++) acc = fmaf(Inv[(o + h + r) * T + o + h + l], Mp[l * h + c], acc);
-      Inv[(o + h + r) * T + o + c] = -acc;
-    }
-    __syncthreads();
-  }
   float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
 #pragma unroll
-  for (int u = 0; u < T * T / POTRF_THREADS; u++) {
-    const int t = tid + u * POTRF_THREADS;
-    const int i = t >> 6, j = t & 63;
-    DI[t] = (i < bw && j < bw) ? Inv[t] : 0.f;
-  }
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = tr + 16 * p, j = tc + 16 * q;
+      float li = 0.f;
+      if (own >> (4 * p + q) & 1) {
+        D[i * T + j] = i == j ? (double)sqrtf(piv[i]) : (double)(a[p][q] * sc[j]);
+        li = x[p][q] * sc[i];
+      }
+      DI[i * T + j] = li;
+    }
 }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -820,7 +819,6 @@ void set_attrs() {   // once per process (contexts may run on several host threa
                                  UW<128>::SMEM));
     GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  UW<256, true>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_potrf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
   });
 }
 
@@ -1023,7 +1021,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       }
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf32<<<dim3(stp.nfront, B), POTRF_THREADS, POTRF_SMEM, st>>>(fronts, stp.kb, dp, f->diag, DE,
+        k_potrf32<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, stp.kb, dp, f->diag, DE,
                                                                                f->notpd, f->dinv32);
         GP_CHECK_LAUNCH(ctx);
       }
