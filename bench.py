@@ -197,7 +197,11 @@ def run_gpu(args, rank, world, local_rank):
     nchunk = (B + Bc - 1) // Bc
     thetas = [synth.perturb(rng, hp, 0.05 if B == 1 else 0.1) for _ in range(B * (args.steps + args.warmup + 2))]
     tune = None
-    if prec == gp.GP_MIXED and args.autotune:   # update blocking chosen by timing factorizations of Bc settings
+    if prec == gp.GP_MIXED and args.blocking:   # a fixed update blocking (group blocks, group tile width)
+        g, tn = (int(v) for v in args.blocking.split(","))
+        ps.set_blocking(g, tn)
+        tune = {"chosen": {"group_blocks": g, "group_tile_n": tn}, "fixed": True}
+    elif prec == gp.GP_MIXED and args.autotune:   # update blocking chosen by timing factorizations of Bc settings
         t0 = time.perf_counter()
         tried = ps.autotune(thetas[:Bc], reps=1)
         best = min(tried, key=lambda t: t["ms"])
@@ -407,6 +411,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="proposals per step (default: 64 for batched_200k, else 1)")
     ap.add_argument("--autotune", type=int, default=-1, help="1/0: tune the update blocking first (default: "
                                                               "on in mixed precision)")
+    ap.add_argument("--blocking", default="", help="G,TN: fixed update blocking of mixed runs (no autotuner)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-sets", type=int, default=20)
@@ -505,11 +510,14 @@ def main():
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "roofline": {"kernel": (KERNEL_OF_CLASS_MIXED if args.precision == "mixed" else KERNEL_OF_CLASS_FP64).get(dom, dom),
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get((args.workload, dom)),
+                     "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get((args.workload, dom) + _blocking_of(res)),
                      "launches_per_step": d_n, "avg_launch_ms": d_ms / max(d_n, 1),
                      "algorithmic": f"useful flops of the class per step = {d_fl:.4g} (per launch "
                                     f"{d_fl / max(d_n, 1):.4g}); A7 total sum_j eta_j^2 = {flops:.4g}",
                      "peak_source": peak_note,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over the class's "
+                                        "launches of one factorization at this blocking (L2 cold at each launch under "
+                                        "ncu)") if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
                      "a7_total": {"ms": t_a7, "achieved": flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
         "kernels": kernels,
         "e2e": {"value": res["e2e_steps"] * res["B"] / res["e2e_s"], "unit": "evals/s", "h2d_bytes_per_step": res["h2d"],
@@ -543,8 +551,14 @@ KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 2
 KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
                         "extend_add": "k_extend_add"}
 
-# DRAM bytes per launch of the dominant kernel, from ncu (profiles/), or None when the kernel changed since
-_TRAFFIC = {}
+# DRAM bytes per launch of the dominant kernel, from ncu (profiles/), by (workload, class, update blocking);
+# None where no capture of the current kernel at that blocking exists
+_TRAFFIC = {("station_1.2M", "update", 16, 256): 2.711e9}
+
+
+def _blocking_of(res):
+    ch = (res.get("autotune") or {}).get("chosen") or {}
+    return (ch.get("group_blocks"), ch.get("group_tile_n"))
 
 
 def _full_flops_hint(name):

@@ -83,12 +83,17 @@ __device__ __forceinline__ double checked_sqrt(double d, int32_t* notpd, int32_t
   return sqrt(d);
 }
 
+// Zeroes the lower triangle (row a, columns b <= a) of the update matrices of a list of fronts, a warp per row:
+// nothing writes or reads their upper triangles.
 __global__ void k_zero_updates32(const int32_t* __restrict__ list, DevPlan dp, float* __restrict__ upd, int64_t UE) {
   int32_t s = list[blockIdx.x];
   float* U = upd + (int64_t)blockIdx.z * UE + dp.uoff[s];
-  int64_t cnt = (int64_t)dp.r[s] * dp.r[s];
-  for (int64_t t = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.y * blockDim.x)
-    U[t] = 0.f;
+  const int64_t r = dp.r[s];
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t a = (int64_t)blockIdx.y * warps + (threadIdx.x >> 5); a < r; a += (int64_t)gridDim.y * warps) {
+    float* row = U + a * r;
+    for (int64_t b = lane; b <= a; b += 32) row[b] = 0.f;
+  }
 }
 
 // One CTA per (child, 8 rows of its update matrix): row a of U_child, columns b <= a, into the parent front.
