@@ -1,6 +1,6 @@
 // factor_mixed.cu -- step A7 in mixed precision (GP_MIXED): the multifrontal supernodal Cholesky of
 // P C_z P^T with the off-diagonal supernode updates on TF32 tensor cores (tcgen05, FP32 accumulation in
-// tensor memory) and every diagonal 64 x 64 block kept, updated and factored in FP64.
+// tensor memory) and every diagonal 64 x 64 block kept and updated in FP64 (and factored in FP32 from it).
 //
 // Storage per proposal: FP32 panels row-major (row i of supernode s at loff32 + i * ldw, K = column index
 // contiguous, as the tensor-core operands want), FP64 diagonal tiles (tile t of s at doff + t * 4096, row-major
@@ -8,8 +8,9 @@
 // live in the FP64 tile, every other panel entry in FP32.
 // Per level: zero the update matrices, extend-add the children (FP32 sums into the parent's FP32 entries and
 // FP64 tiles), factor fronts of order <= 96 wholly in FP64 shared memory, and step the large fronts 64 columns
-// at a time: POTRF of the FP64 diagonal tile, TRSM of the rows below in FP32, then the trailing update
-// F[i, j] -= sum_l L[i, l] L[j, l] over 128 x 128 tiles on the tensor cores, each FP32 operand split into two
+// at a time: POTRF of the diagonal tile (FP32 from its FP64 sums, with the inverse of its factor), TRSM of the
+// rows below in FP32, then the updates F[i, j] -= sum_l L[i, l] L[j, l] on the tensor cores (left-looking
+// 128 x 64 strips per block, 256 x 256 CTA-pair tiles at a group's end), each FP32 operand split into two
 // round-to-nearest TF32 parts (three products per step, about 21 bits kept), with the tile results added in
 // FP64 to the diagonal tiles and in FP32 elsewhere.
 #include <cuda.h>

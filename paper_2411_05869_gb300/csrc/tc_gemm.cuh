@@ -127,24 +127,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
-// Multicast forms for a pair of CTAs in a cluster: the TMA load lands at the same shared-memory offset in every
-// CTA of ctamask and completes transaction bytes on the mbarrier at the same offset in each; the commit arrives
-// on the mbarrier at this offset in every CTA of ctamask.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const void* tmap, int x, int y, int z, uint64_t* bar,
-                                               uint16_t ctamask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3, %4}], [%5], %6;\n" ::"r"(dst),
-      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(ctamask)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t ctamask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
-          smem_u32(bar)),
-      "h"(ctamask)
-      : "memory");
-}
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));

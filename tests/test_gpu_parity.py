@@ -158,7 +158,7 @@ MIXED_RTOL = 1e-6
 
 
 def test_loglik_mixed_matches_oracle(case, ctx):
-    """GP_MIXED: TF32 tensor-core updates, FP64 diagonal tiles, FP64 refinement; loglik within 1e-6."""
+    """GP_MIXED: TF32 tensor-core updates, FP64-accumulated diagonal tiles, FP64 refinement; loglik within 1e-6."""
     from paper_2411_05869_gb300 import gp
     w, ps = case["w"], case["ps"]
     ref = oracle.sparse_loglik(w.hyper, w.X, case["rp"], case["col"], case["perm"], w.resid, want_alpha=True)
