@@ -237,6 +237,7 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     dp.small_list = upload(ctx, ps->bufs, sp.small_list);
     dp.large_fronts = upload(ctx, ps->bufs, sp.large_fronts);
     dp.step_pre = upload(ctx, ps->bufs, sp.step_pre);
+    dp.pair_pre = upload(ctx, ps->bufs, sp.pair_pre);
     dp.lev_sn = upload(ctx, ps->bufs, sp.lev_sn);
     dp.sn_parent = upload(ctx, ps->bufs, sp.sn_parent);
     dp.ldw = upload(ctx, ps->bufs, sp.sn_ldw);

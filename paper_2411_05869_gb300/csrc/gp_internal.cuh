@@ -164,6 +164,9 @@ struct SymPlan {
   // schedule for the numeric factorization, per level
   struct EaLaunch { int64_t tab_off; int64_t ncta; };            // extend-add: CTAs of one child slot
   struct StepLaunch { int64_t fr_off; int32_t nfront; int32_t kb; int64_t trsm_total; int64_t upd_total; int64_t pre_off;
+                      // forward solve, steps taken in pairs (set on the first step of a pair): the tile prefix
+                      // over this step's fronts, its total, and how many of them also have block kb + 1
+                      int64_t pair_pre_off, pair_total; int32_t pair_n2;
                       // mixed path, (64 GP_GROUP)-column groups: left-looking update of this block column
                       // (rows >= c0 x its 64 columns, K = the group's earlier blocks) and, at a group's last block,
                       // the deferred group update (rows/columns after the group, K = the group's width); fronts
@@ -185,6 +188,7 @@ struct SymPlan {
   struct LevelLarge { int64_t off = 0; int64_t count = 0; };    // all steps' entries of a level, contiguous
   std::vector<LevelLarge> level_large;
   std::vector<int64_t> step_pre;     // per step: prefix of TRSM tasks then of UPDATE tasks (2*(nfront+1))
+  std::vector<int64_t> pair_pre;     // per step pair: prefix of the paired forward-solve row tiles
 };
 
 // Device mirror of the plan (pointers into one allocation set owned by the point set).
@@ -208,6 +212,7 @@ struct DevPlan {
   int32_t* large_kb;
   int32_t* upd_fronts;
   int64_t* upd_pre;
+  int64_t* pair_pre;
 };
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);

@@ -144,12 +144,69 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
+// The pieces of a forward step, shared by the single and the paired launches.
+// x = inv(L_JJ) f_J for a block of width bw: inv is the block's 64 x 64 inverse, fb (shared) holds f_J; the
+// product is split four ways over l and combined in a fixed order.
+template <class V>
+__device__ __forceinline__ void fwd_block_solve(const V* __restrict__ inv, const V* fb, V* x, V* LiT, V (*part)[T],
+                                                int bw) {
+#pragma unroll
+  for (int u = 0; u < T * T / 256; u++) {
+    const int q = threadIdx.x + u * 256;
+    LiT[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
+  }
+  __syncthreads();
+  {   // the inverse is lower triangular with zeros above (and past bw), so every l enters
+    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+    V acc = 0;
+#pragma unroll
+    for (int l = g * 16; l < g * 16 + 16; l++) acc += LiT[l * (T + 1) + q] * fb[l];
+    part[g][q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const int q = threadIdx.x;
+    x[q] = q < bw ? (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]) : V(0);
+  }
+  __syncthreads();
+}
+
+// acc_i = L[i, c0 .. c0 + bw) x for the rows [r0, rend) (at most 64), handed to sink(i, acc) by one thread per
+// row. Row-major panels: a half-warp reads one row's 64 entries as 16 float4, four rows per half-warp with all
+// loads in flight, a fixed shuffle tree per row; column-major: thread per row.
+template <class St, class Sink>
+__device__ __forceinline__ void fwd_rows(const typename St::Acc& A, int64_t r0, int64_t rend, int c0, int bw,
+                                         const typename St::V* x, Sink&& sink) {
+  using V = typename St::V;
+  if constexpr (St::kRowMajor) {
+    // columns past bw are zero in x and the row is padded to ldw (a multiple of 4): whole float4 reads are safe
+    const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int64_t i = r0 + hw + 16 * u;
+      v[u] = (i < rend && l < bw) ? *reinterpret_cast<const float4*>(A.P + i * A.ldw + c0 + l)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      V acc = (V)v[u].x * x[l] + (V)v[u].y * x[l + 1] + (V)v[u].z * x[l + 2] + (V)v[u].w * x[l + 3];
+      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const int64_t i = r0 + hw + 16 * u;
+      if (i < rend && (threadIdx.x & 15) == 0) sink(i, acc);
+    }
+  } else {
+    for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
+      V acc = 0;
+      for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
+      sink(i, acc);
+    }
+  }
+}
+
 // Forward, block column kb of every large front of a step, one launch: every CTA forms x_J = inv(L_JJ) f_J
 // (a 64 x 64 product with the inverted diagonal block); tasks [0, nfront) write x_J to x (the front vector's
 // block stays untouched, others read it), the rest (64-row tile prefix) apply f_i -= L[i, J] x_J to one tile.
-// 256 threads: the inverse arrives transposed through unrolled coalesced loads, the product is split four
-// ways over l and combined in a fixed order; row-major panels: a half-warp reads one row's 64 entries as 16
-// float4, four rows per half-warp with all loads in flight; column-major: thread per row.
 template <class St>
 __global__ void __launch_bounds__(256) k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                                   int nfront, int kb, DevPlan dp, St store,
@@ -167,56 +224,65 @@ __global__ void __launch_bounds__(256) k_fwd_step(const int32_t* __restrict__ fr
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
   const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
-  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
-#pragma unroll
-  for (int u = 0; u < T * T / 256; u++) {
-    const int q = threadIdx.x + u * 256;
-    LiT[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
-  }
   if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
-  __syncthreads();
-  {   // the inverse is lower triangular with zeros above (and past bw), so every l enters
-    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
-    V acc = 0;
-#pragma unroll
-    for (int l = g * 16; l < g * 16 + 16; l++) acc += LiT[l * (T + 1) + q] * fb[l];
-    part[g][q] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x < T) {
-    const int q = threadIdx.x;
-    x[q] = q < bw ? (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]) : V(0);
-  }
-  __syncthreads();
+  fwd_block_solve(store.inv(dp, s, b) + (int64_t)kb * T * T, fb, x, LiT, part, bw);
   if (writer) {
     V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
     if (threadIdx.x < bw) xv[c0 + threadIdx.x] = x[threadIdx.x];
     return;
   }
   const int64_t r0 = c1 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
-  if constexpr (St::kRowMajor) {
-    // columns past bw are zero in x and the row is padded to ldw (a multiple of 4): whole float4 reads are safe
-    const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int64_t i = r0 + hw + 16 * u;
-      v[u] = (i < rend && l < bw) ? *reinterpret_cast<const float4*>(A.P + i * A.ldw + c0 + l)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      V acc = (V)v[u].x * x[l] + (V)v[u].y * x[l + 1] + (V)v[u].z * x[l + 2] + (V)v[u].w * x[l + 3];
-      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      const int64_t i = r0 + hw + 16 * u;
-      if (i < rend && (threadIdx.x & 15) == 0) fv[i] -= acc;
-    }
-  } else {
-    for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
-      V acc = 0;
-      for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
-      fv[i] -= acc;
-    }
+  fwd_rows<St>(A, r0, rend, c0, bw, x, [&](int64_t i, V acc) { fv[i] -= acc; });
+}
+
+// Forward, block columns kb and kb + 1 in one launch (the chain of forward steps is the sweep's latency). The
+// fronts [0, n2) of the list have block kb + 1: every CTA forms x1 = inv(L_11) f_1, f_2' = f_2 - L_21 x1 and
+// x2 = inv(L_22) f_2' itself (the same operations, in the same order, as two single steps), then a writer
+// stores x1, x2 and a tile task applies f_i -= L_i1 x1, then f_i -= L_i2 x2 to 64 rows after block kb + 1.
+// Fronts past n2 take block kb alone, as a single step.
+template <class St>
+__global__ void __launch_bounds__(256) k_fwd_pair(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                  int nfront, int n2, int kb, DevPlan dp, St store,
+                                                  typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
+  using V = typename St::V;
+  __shared__ V LiT[T * (T + 1)];   // LiT[l][q] = inv[q][l]
+  __shared__ V fb[T], x1[T], x2[T], part[4][T], a1[T], a2[T];
+  const int64_t t = blockIdx.x;
+  const bool writer = t < nfront;
+  const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  V* fv = work + (int64_t)b * ws + dp.frow_off[s];
+  const int w = dp.w[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const bool two = fi < n2;
+  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
+  const int bw2 = two ? min(T, w - c1) : 0, c2 = c1 + bw2;
+  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
+  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw1 ? fv[c0 + threadIdx.x] : V(0);
+  fwd_block_solve(inv, fb, x1, LiT, part, bw1);
+  if (two) {
+    fwd_rows<St>(A, c1, c2, c0, bw1, x1, [&](int64_t i, V acc) { a1[i - c1] = acc; });
+    __syncthreads();
+    if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw2 ? fv[c1 + threadIdx.x] - a1[threadIdx.x] : V(0);
+    fwd_block_solve(inv + T * T, fb, x2, LiT, part, bw2);
+  }
+  if (writer) {
+    V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
+    if (threadIdx.x < bw1) xv[c0 + threadIdx.x] = x1[threadIdx.x];
+    if (threadIdx.x < bw2) xv[c1 + threadIdx.x] = x2[threadIdx.x];
+    return;
+  }
+  const int64_t r0 = c2 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
+  fwd_rows<St>(A, r0, rend, c0, bw1, x1, [&](int64_t i, V acc) { a1[i - r0] = acc; });
+  if (two) fwd_rows<St>(A, r0, rend, c1, bw2, x2, [&](int64_t i, V acc) { a2[i - r0] = acc; });
+  __syncthreads();
+  if (threadIdx.x < T && r0 + threadIdx.x < rend) {
+    V v = fv[r0 + threadIdx.x];
+    v -= a1[threadIdx.x];
+    if (two) v -= a2[threadIdx.x];
+    fv[r0 + threadIdx.x] = v;
   }
 }
 
@@ -604,10 +670,19 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
                                                           xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
-    for (const auto& stp : lv.steps) {
-      k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 256, 0, st>>>(
-          dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, work, ws,
-          xv_off);
+    for (size_t q = 0; q < lv.steps.size();) {
+      const auto& stp = lv.steps[q];
+      if (q + 1 < lv.steps.size()) {   // block columns kb and kb + 1 together
+        k_fwd_pair<St><<<dim3((unsigned)(stp.nfront + stp.pair_total), B), 256, 0, st>>>(
+            dp.large_fronts + stp.fr_off, dp.pair_pre + stp.pair_pre_off, stp.nfront, stp.pair_n2, stp.kb, dp, store,
+            work, ws, xv_off);
+        q += 2;
+      } else {
+        k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 256, 0, st>>>(
+            dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, work, ws,
+            xv_off);
+        q += 1;
+      }
       GP_CHECK_LAUNCH(ctx);
     }
   }

@@ -479,6 +479,25 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
         }
         lv.steps.push_back(stp);
       }
+      // The forward solve takes the steps two at a time (kb even, kb + 1): step kb + 1's fronts are the first
+      // ones of step kb's (widths descending), and they apply both blocks to the rows after block kb + 1.
+      for (size_t q = 0; q + 1 < lv.steps.size(); q += 2) {
+        SymPlan::StepLaunch& s0 = lv.steps[q];
+        const SymPlan::StepLaunch& s1 = lv.steps[q + 1];
+        s0.pair_pre_off = (int64_t)sp.pair_pre.size();
+        s0.pair_n2 = s1.nfront;
+        int64_t acc = 0;
+        sp.pair_pre.push_back(0);
+        for (int32_t t = 0; t < s0.nfront; t++) {
+          const int32_t s = sp.large_fronts[s0.fr_off + t];
+          const int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
+          const int64_t c1 = std::min<int64_t>((int64_t)(s0.kb + 1) * GP_TILE, w);
+          const int64_t cs = t < s1.nfront ? std::min<int64_t>((int64_t)(s0.kb + 2) * GP_TILE, w) : c1;
+          acc += (m - cs + GP_TILE - 1) / GP_TILE;
+          sp.pair_pre.push_back(acc);
+        }
+        s0.pair_total = acc;
+      }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
   }
