@@ -400,37 +400,21 @@ __global__ void k_bwd_prep_sum(const int32_t* __restrict__ fronts, const int32_t
   W[dp.frow_off[s] + j0 + c] = W[xv_off + dp.sn_first[s] + j0 + c] - acc;
 }
 
-// Backward, block column kb of every large front of a step, one launch: every CTA forms
-// z_J = inv(L_JJ)^T t_J; task 0 of a front writes z_J to alpha', tasks 1..kb apply t_k -= L[J, k]^T z_J to
-// one 64-column tile of the earlier columns k < c0. 256 threads; the product and the tile update are split
-// four ways over l (16 independent loads per thread in flight) and combined in a fixed order.
-template <class St>
-__global__ void __launch_bounds__(256) k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp,
-                                                  St store, typename St::V* __restrict__ work, int64_t ws,
-                                                  int64_t apv_off) {
-  using V = typename St::V;
-  __shared__ V Li[T * (T + 1)];   // the inverse block (row-major), then (column-major path) the block's rows
-  __shared__ V tb[T], z[T], part[4][T];
-  const int64_t t = blockIdx.x;
-  const int fi = (int)(t / (kb + 1));
-  const int task = (int)(t % (kb + 1));
-  const int32_t s = fronts[fi];
-  const int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  V* W = work + (int64_t)b * ws;
-  V* fv = W + dp.frow_off[s];
-  const int w = dp.w[s];
-  const int c0 = kb * T, bw = min(T, w - c0);
-  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
+// The pieces of a backward step, shared by the single and the paired launches.
+// z = inv(L_JJ)^T t_J for a block of width bw: inv is the block's 64 x 64 inverse (row-major into Li), tb
+// (shared) holds t_J; z_q = sum_{l >= q} inv[l][q] t_l (zeros above the diagonal and past bw), split four ways
+// over l and combined in a fixed order.
+template <class V>
+__device__ __forceinline__ void bwd_block_solve(const V* __restrict__ inv, const V* tb, V* z, V* Li, V (*part)[T],
+                                                int bw) {
 #pragma unroll
   for (int u = 0; u < T * T / 256; u++) {
     const int q = threadIdx.x + u * 256;
     Li[(q >> 6) * (T + 1) + (q & 63)] = inv[q];
   }
-  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
   __syncthreads();
   const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
-  {   // z_q = sum_{l >= q} inv[l][q] t_l (zeros above the diagonal and past bw)
+  {
     V acc = 0;
 #pragma unroll
     for (int l = g * 16; l < g * 16 + 16; l++) acc += Li[l * (T + 1) + q] * tb[l];
@@ -442,36 +426,126 @@ __global__ void __launch_bounds__(256) k_bwd_step(const int32_t* __restrict__ fr
     z[k] = k < bw ? (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]) : V(0);
   }
   __syncthreads();
-  if (task == 0) {
-    V* apv = W + apv_off;
-    const int32_t first = dp.sn_first[s];
-    if (threadIdx.x < bw) apv[first + c0 + threadIdx.x] = z[threadIdx.x];
-    return;
-  }
-  const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
+}
+
+// sum_k = sum_l L[r0 + l, k0 + k] z_l over the bw rows of a block (k < 64; returned to threads k < 64), split
+// four ways over l (16 independent loads per thread in flight) and combined in a fixed order.
+template <class St>
+__device__ __forceinline__ typename St::V bwd_tile_sum(const typename St::Acc& A, int r0, int bw, int k0,
+                                                       const typename St::V* z, typename St::V (*part)[T]) {
+  using V = typename St::V;
+  const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
   V acc = 0;
-  if constexpr (St::kRowMajor) {   // row c0 + l is contiguous over the tile's columns
+  if constexpr (St::kRowMajor) {   // row r0 + l is contiguous over the tile's columns
     V v[16];
 #pragma unroll
     for (int e = 0; e < 16; e++) {
       const int l = g * 16 + e;
-      v[e] = l < bw ? (V)A.P[(int64_t)(c0 + l) * A.ldw + k0 + q] : V(0);
+      v[e] = l < bw ? (V)A.P[(int64_t)(r0 + l) * A.ldw + k0 + q] : V(0);
     }
 #pragma unroll
     for (int e = 0; e < 16; e++) acc += v[e] * z[g * 16 + e];
   } else {
     for (int e = 0; e < 16; e++) {
       const int l = g * 16 + e;
-      if (l < bw) acc += A.L(c0 + l, k0 + q) * z[l];
+      if (l < bw) acc += A.L(r0 + l, k0 + q) * z[l];
     }
   }
   __syncthreads();   // part is reused
   part[g][q] = acc;
   __syncthreads();
+  V sum = 0;
   if (threadIdx.x < T) {
     const int k = threadIdx.x;
-    fv[k0 + k] -= (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]);
+    sum = (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]);
   }
+  return sum;
+}
+
+// Backward, block column kb of every large front of a step, one launch: every CTA forms
+// z_J = inv(L_JJ)^T t_J; task 0 of a front writes z_J to alpha', tasks 1..kb apply t_k -= L[J, k]^T z_J to
+// one 64-column tile of the earlier columns k < c0.
+template <class St>
+__global__ void __launch_bounds__(256) k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp,
+                                                  St store, typename St::V* __restrict__ work, int64_t ws,
+                                                  int64_t apv_off) {
+  using V = typename St::V;
+  __shared__ V Li[T * (T + 1)];   // the inverse block (row-major)
+  __shared__ V tb[T], z[T], part[4][T];
+  const int64_t t = blockIdx.x;
+  const int fi = (int)(t / (kb + 1));
+  const int task = (int)(t % (kb + 1));
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
+  const int w = dp.w[s];
+  const int c0 = kb * T, bw = min(T, w - c0);
+  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
+  bwd_block_solve(store.inv(dp, s, b) + (int64_t)kb * T * T, tb, z, Li, part, bw);
+  if (task == 0) {
+    V* apv = W + apv_off;
+    if (threadIdx.x < bw) apv[dp.sn_first[s] + c0 + threadIdx.x] = z[threadIdx.x];
+    return;
+  }
+  const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
+  const V sum = bwd_tile_sum<St>(A, c0, bw, k0, z, part);
+  if (threadIdx.x < T) fv[k0 + threadIdx.x] -= sum;
+}
+
+// Backward, block columns kb + 1 and kb in one launch (the chain of backward steps is the sweep's latency). The
+// fronts [0, n2) of step kb's list have block kb + 1: every CTA forms z2 = inv(L_22)^T t_2,
+// t_1' = t_1 - L_21^T z2 and z1 = inv(L_11)^T t_1' itself (the same operations, in the same order, as two
+// single steps); task 0 writes z1, z2 to alpha', tasks 1..kb apply t_k -= L[2, k]^T z2, then t_k -= L[1, k]^T z1
+// to one 64-column tile k < c0. Fronts past n2 take block kb alone, as a single step.
+template <class St>
+__global__ void __launch_bounds__(256) k_bwd_pair(const int32_t* __restrict__ fronts, int nfront, int n2, int kb,
+                                                  DevPlan dp, St store, typename St::V* __restrict__ work,
+                                                  int64_t ws, int64_t apv_off) {
+  using V = typename St::V;
+  __shared__ V Li[T * (T + 1)];
+  __shared__ V tb[T], z1[T], z2[T], part[4][T];
+  const int64_t t = blockIdx.x;
+  const int fi = (int)(t / (kb + 1));
+  const int task = (int)(t % (kb + 1));
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
+  auto A = store.acc(dp, s, b);
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
+  const int w = dp.w[s];
+  const bool two = fi < n2;
+  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
+  const int bw2 = two ? min(T, w - c1) : 0;
+  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
+  V t1 = 0;
+  if (two) {
+    if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw2 ? fv[c1 + threadIdx.x] : V(0);
+    bwd_block_solve(inv + T * T, tb, z2, Li, part, bw2);
+    const V sum = bwd_tile_sum<St>(A, c1, bw2, c0, z2, part);   // block kb's columns
+    if (threadIdx.x < T) t1 = fv[c0 + threadIdx.x] - sum;
+  } else if (threadIdx.x < T) {
+    t1 = fv[c0 + threadIdx.x];
+  }
+  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw1 ? t1 : V(0);
+  bwd_block_solve(inv, tb, z1, Li, part, bw1);
+  if (task == 0) {
+    V* apv = W + apv_off + dp.sn_first[s];
+    if (threadIdx.x < bw1) apv[c0 + threadIdx.x] = z1[threadIdx.x];
+    if (threadIdx.x < bw2) apv[c1 + threadIdx.x] = z2[threadIdx.x];
+    return;
+  }
+  const int k0 = (task - 1) * T;
+  V v = 0;
+  if (threadIdx.x < T) v = fv[k0 + threadIdx.x];
+  if (two) {
+    const V sum2 = bwd_tile_sum<St>(A, c1, bw2, k0, z2, part);
+    v -= sum2;
+  }
+  const V sum1 = bwd_tile_sum<St>(A, c0, bw1, k0, z1, part);
+  v -= sum1;
+  if (threadIdx.x < T) fv[k0 + threadIdx.x] = v;
 }
 
 // Per-block partial sums: log L_jj and x_j^2 (x = forward solution on own columns).
@@ -708,10 +782,18 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       k_bwd_prep_sum<V><<<dim3((unsigned)ll.count, B), T, 0, st>>>(dp.large_fronts + ll.off, dp.large_kb + ll.off,
                                                                    (int)ll.count, nch, dp, work, ws, xv_off, part);
       GP_CHECK_LAUNCH(ctx);
-      for (int q = (int)lv.steps.size() - 1; q >= 0; q--) {
-        const auto& stp = lv.steps[q];
-        k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
-            dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, work, ws, apv_off);
+      for (int q = (int)lv.steps.size() - 1; q >= 0;) {
+        if (q >= 1) {   // block columns kb + 1 = q and kb = q - 1 together
+          const auto& stp = lv.steps[q - 1];
+          k_bwd_pair<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
+              dp.large_fronts + stp.fr_off, stp.nfront, lv.steps[q].nfront, stp.kb, dp, store, work, ws, apv_off);
+          q -= 2;
+        } else {
+          const auto& stp = lv.steps[q];
+          k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
+              dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, work, ws, apv_off);
+          q -= 1;
+        }
         GP_CHECK_LAUNCH(ctx);
       }
     }
