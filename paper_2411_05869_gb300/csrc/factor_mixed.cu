@@ -209,21 +209,18 @@ __device__ __forceinline__ float recip_nr(float d) {
   return fmaf(r, fmaf(-d, r, 1.f), r);
 }
 
-__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
-                                                           double* __restrict__ dg, int64_t DE,
-                                                           int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
+// The factorization of one tile by the CTA's 256 threads: D the FP64 tile (in: the accumulated entries, out: L),
+// DI its FP32 inverse tile (out), bw its width, first the global column of its first column (a failed pivot
+// records the smallest such column in *flag).
+__device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __restrict__ DI, int bw, int32_t first,
+                                           int32_t* __restrict__ flag) {
   __shared__ float col[2][2][T];  // columns k, k + 1 after the updates of columns < k (double-buffered)
   __shared__ float xrow[2][2][T]; // rows k, k + 1 of X after the eliminations of rows < k (double-buffered)
   __shared__ float piv[T];        // pivots d_k
   __shared__ float rd[T];         // 1 / d_k
   __shared__ float sc[T];         // 1 / L_kk
   const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
-  int32_t s = fronts[blockIdx.x];
-  int b = blockIdx.y;
-  double* D = dg + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  const int w = dp.w[s], bw = min(T, w - kb * T);
-  const int32_t first = dp.sn_first[s] + kb * T;
-  int32_t* flag = notpd + b;
+  __syncthreads();   // an earlier call's readers of the shared arrays are done
   float a[4][4], x[4][4];
   uint32_t own = 0;   // bit 4 p + q: entry (tr + 16 p, tc + 16 q) is in the lower triangle of the bw x bw tile
 #pragma unroll
@@ -344,7 +341,6 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __rest
   __syncthreads();
   if (tid < T) sc[tid] = tid < bw ? sqrtf(piv[tid]) * rd[tid] : 1.f;   // sqrt(d) / d = 1 / L_kk
   __syncthreads();
-  float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
 #pragma unroll
   for (int p = 0; p < 4; p++)
 #pragma unroll
@@ -359,6 +355,15 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __rest
     }
 }
 
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
+                                                           double* __restrict__ dg, int64_t DE,
+                                                           int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
+  const int32_t s = fronts[blockIdx.x];
+  const int b = blockIdx.y;
+  const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  potrf_tile(dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T, notpd + b);
+}
+
 __device__ __forceinline__ float tf32_rn(float x) {
   uint32_t u;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
@@ -369,65 +374,61 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // X = B L^{-T}, X[r][j] = sum_{l <= j} B[r][l] Inv[j][l], one CTA of 256 threads per 64-row tile, each thread a
 // 4 x 4 block of X (no dependency chains, unlike a column-by-column substitution). The L entries are written
 // with their TF32 pair (hi = rn(x), lo = rn(x - hi)), the tensor-core operands of the updates.
-__global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                                int nfront, int kb, DevPlan dp, float* __restrict__ p32,
-                                                float* __restrict__ oph, float* __restrict__ opl,
-                                                const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
-  constexpr int S = T + 4;            // transposed tiles, rows 16-byte aligned for vector reads
-  __shared__ __align__(16) float BsT[T * S];   // BsT[l][r] = B[r][l]
-  __shared__ __align__(16) float IsT[T * S];   // IsT[l][j] = Inv[j][l]
-  int64_t t = blockIdx.x;
-  int fi = find_front(pre, nfront, t);
-  int32_t s = fronts[fi];
-  int b = blockIdx.y;
-  float* P = p32 + (int64_t)b * P32E + dp.loff32[s];
-  const float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  const int w = dp.w[s], ldw = dp.ldw[s];
-  const int64_t m = (int64_t)w + dp.r[s];
-  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
-  const int64_t r0 = c1 + (t - pre[fi]) * T;
-  const int nr = (int)imin64(T, m - r0);
-  // all 32 loads of a thread in flight at once (the rows of B are 64 contiguous FP32 at stride ldw)
-  float bv[16], iv[16];
+constexpr int TS = T + 4;   // transposed shared tiles, rows 16-byte aligned for vector reads
+
+// dst[l][r] = src[r][l] for a 64 x 64 block at src (row stride lds), rows >= nr and columns >= nc read as zero;
+// all 16 loads of a thread in flight at once.
+__device__ __forceinline__ void load_tile_t(float* dst, const float* __restrict__ src, int64_t lds, int nr, int nc) {
+  float v[16];
 #pragma unroll
   for (int u = 0; u < 16; u++) {
     const int q = threadIdx.x + u * 256, i = q >> 6, j = q & 63;
-    iv[u] = DI[q];   // zero outside the lower bw x bw triangle
-    bv[u] = (i < nr && j < bw) ? P[(r0 + i) * ldw + c0 + j] : 0.f;
+    v[u] = (i < nr && j < nc) ? src[i * lds + j] : 0.f;
   }
 #pragma unroll
   for (int u = 0; u < 16; u++) {
     const int q = threadIdx.x + u * 256, i = q >> 6, j = q & 63;
-    IsT[j * S + i] = iv[u];
-    BsT[j * S + i] = bv[u];
+    dst[j * TS + i] = v[u];
   }
-  __syncthreads();
-  // thread: rows tr..tr+3 x columns tc..tc+3 of X, one 16-byte read of each operand per l
+}
+
+// acc[e][f] = sum_{l < kl} BT[l][tr + e] CT[l][tc + f] (thread: rows tr..tr+3 x columns tc..tc+3, one 16-byte
+// read of each operand per l).
+__device__ __forceinline__ void prod_tile(const float* BT, const float* CT, int kl, float (&acc)[4][4]) {
   const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
-  float acc[4][4] = {};
-  for (int l = 0; l < bw; l++) {
-    const float4 bq = *reinterpret_cast<const float4*>(BsT + l * S + tr);
-    const float4 iq = *reinterpret_cast<const float4*>(IsT + l * S + tc);
-    const float bv4[4] = {bq.x, bq.y, bq.z, bq.w}, iv4[4] = {iq.x, iq.y, iq.z, iq.w};
+#pragma unroll
+  for (int e = 0; e < 4; e++)
+#pragma unroll
+    for (int f = 0; f < 4; f++) acc[e][f] = 0.f;
+  for (int l = 0; l < kl; l++) {
+    const float4 bq = *reinterpret_cast<const float4*>(BT + l * TS + tr);
+    const float4 cq = *reinterpret_cast<const float4*>(CT + l * TS + tc);
+    const float bv4[4] = {bq.x, bq.y, bq.z, bq.w}, cv4[4] = {cq.x, cq.y, cq.z, cq.w};
 #pragma unroll
     for (int e = 0; e < 4; e++)
 #pragma unroll
-      for (int f = 0; f < 4; f++) acc[e][f] = fmaf(bv4[e], iv4[f], acc[e][f]);
+      for (int f = 0; f < 4; f++) acc[e][f] = fmaf(bv4[e], cv4[f], acc[e][f]);
   }
-  const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
+}
+
+// Rows tr..tr+3 x columns tc..tc+3 of X into the panel at P + o (row stride ldw) and into its TF32 pair (the
+// same offsets in oph, opl), for rows < nr and columns < bw.
+__device__ __forceinline__ void store_x(const float (&acc)[4][4], float* __restrict__ P, float* __restrict__ oph,
+                                        float* __restrict__ opl, int64_t o0, int ldw, int nr, int bw) {
+  const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int i = tr + e;
     if (i >= nr) continue;
-    const int64_t o = (r0 + i) * ldw + c0 + tc;   // 16-byte aligned: ldw, c0, tc and the panel offset are x4
+    const int64_t o = o0 + (int64_t)i * ldw + tc;   // 16-byte aligned: ldw, the columns, tc and the panel offset are x4
     if (tc + 4 <= bw) {
       float4 x, hi, lo;
       x = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
       hi = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
       lo = make_float4(tf32_rn(x.x - hi.x), tf32_rn(x.y - hi.y), tf32_rn(x.z - hi.z), tf32_rn(x.w - hi.w));
       *reinterpret_cast<float4*>(P + o) = x;
-      *reinterpret_cast<float4*>(oph + ob + o) = hi;
-      *reinterpret_cast<float4*>(opl + ob + o) = lo;
+      *reinterpret_cast<float4*>(oph + o) = hi;
+      *reinterpret_cast<float4*>(opl + o) = lo;
     } else {
 #pragma unroll
       for (int f = 0; f < 4; f++) {
@@ -435,18 +436,150 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
         const float x = acc[e][f];
         P[o + f] = x;
         const float hi = tf32_rn(x);
-        oph[ob + o + f] = hi;
-        opl[ob + o + f] = tf32_rn(x - hi);
+        oph[o + f] = hi;
+        opl[o + f] = tf32_rn(x - hi);
       }
     }
   }
+}
+
+// acc -> BT[l][r] (the transposed form prod_tile reads).
+__device__ __forceinline__ void stash_t(const float (&acc)[4][4], float* BT) {
+  const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+  for (int e = 0; e < 4; e++)
+#pragma unroll
+    for (int f = 0; f < 4; f++) BT[(tc + f) * TS + tr + e] = acc[e][f];
+}
+
+__global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                int nfront, int kb, DevPlan dp, float* __restrict__ p32,
+                                                float* __restrict__ oph, float* __restrict__ opl,
+                                                const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
+  __shared__ __align__(16) float BsT[T * TS];   // BsT[l][r] = B[r][l]
+  __shared__ __align__(16) float IsT[T * TS];   // IsT[l][j] = Inv[j][l]
+  int64_t t = blockIdx.x;
+  int fi = find_front(pre, nfront, t);
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
+  const float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const int w = dp.w[s], ldw = dp.ldw[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
+  const int64_t r0 = c1 + (t - pre[fi]) * T;
+  const int nr = (int)imin64(T, m - r0);
+  load_tile_t(IsT, DI, T, T, T);   // zero outside the lower bw x bw triangle
+  load_tile_t(BsT, p32 + ob + r0 * ldw + c0, ldw, nr, bw);
+  __syncthreads();
+  float acc[4][4];
+  prod_tile(BsT, IsT, bw, acc);
+  store_x(acc, p32 + ob, oph + ob, opl + ob, r0 * ldw + c0, ldw, nr, bw);
+}
+
+// Block columns kb and kb + 1 at once (the mixed path's block steps in pairs, for an even group width): fronts
+// [0, n2) of the list have block kb + 1. POTRF of tile kb; then, for those fronts, L_21 = A_21 inv(L_11)^T (the
+// 64 rows of block kb + 1 in block column kb, with their TF32 pair), A_22 -= L_21 L_21^T into the FP64 tile of
+// block kb + 1 (FP32 products, as the tensor-core updates give it), and the POTRF of that tile. One CTA per front.
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32_pair(const int32_t* __restrict__ fronts, int n2, int kb,
+                                                                DevPlan dp, float* __restrict__ p32,
+                                                                float* __restrict__ oph, float* __restrict__ opl,
+                                                                double* __restrict__ dg, float* __restrict__ dinv32,
+                                                                int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
+  __shared__ __align__(16) float BsT[T * TS];
+  __shared__ __align__(16) float IsT[T * TS];
+  const int fi = blockIdx.x;
+  const int32_t s = fronts[fi];
+  const int b = blockIdx.y;
+  const int w = dp.w[s], ldw = dp.ldw[s];
+  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
+  const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const int32_t first = dp.sn_first[s] + c0;
+  potrf_tile(dg + off, dinv32 + off, bw1, first, notpd + b);
+  if (fi >= n2) return;
+  const int bw2 = min(T, w - c1);
+  const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
+  __syncthreads();   // the inverse tile is in global memory, written by this CTA
+  load_tile_t(IsT, dinv32 + off, T, T, T);
+  load_tile_t(BsT, p32 + ob + (int64_t)c1 * ldw + c0, ldw, bw2, bw1);
+  __syncthreads();
+  float acc[4][4];
+  prod_tile(BsT, IsT, bw1, acc);   // L_21
+  store_x(acc, p32 + ob, oph + ob, opl + ob, (int64_t)c1 * ldw + c0, ldw, bw2, bw1);
+  __syncthreads();
+  stash_t(acc, BsT);   // BsT[l][r] = L_21[r][l]; rows past bw2 hold zeros
+  __syncthreads();
+  float g[4][4];
+  prod_tile(BsT, BsT, bw1, g);   // g = L_21 L_21^T
+  double* D2 = dg + off + T * T;
+  const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+  for (int e = 0; e < 4; e++)
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      const int i = tr + e, j = tc + f;
+      if (j <= i && i < bw2) D2[i * T + j] -= (double)g[e][f];
+    }
+  potrf_tile(D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
+}
+
+// The TRSM of a pair of block columns kb, kb + 1: for each 64-row tile below the pair (below block kb alone for
+// fronts past n2), X_1 = B_1 inv(L_11)^T, B_2' = B_2 - X_1 L_21^T, X_2 = B_2' inv(L_22)^T.
+__global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
+                                                     int nfront, int n2, int kb, DevPlan dp, float* __restrict__ p32,
+                                                     float* __restrict__ oph, float* __restrict__ opl,
+                                                     const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
+  __shared__ __align__(16) float BsT[T * TS];
+  __shared__ __align__(16) float IsT[T * TS];
+  int64_t t = blockIdx.x;
+  int fi = find_front(pre, nfront, t);
+  int32_t s = fronts[fi];
+  int b = blockIdx.y;
+  const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
+  const float* DI = dinv32 + (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  const int w = dp.w[s], ldw = dp.ldw[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const bool two = fi < n2;
+  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
+  const int bw2 = two ? min(T, w - c1) : 0, c2 = c1 + bw2;
+  const int64_t r0 = c2 + (t - pre[fi]) * T;
+  const int nr = (int)imin64(T, m - r0);
+  float* P = p32 + ob;
+  load_tile_t(IsT, DI, T, T, T);
+  load_tile_t(BsT, P + r0 * ldw + c0, ldw, nr, bw1);
+  __syncthreads();
+  float acc[4][4];
+  prod_tile(BsT, IsT, bw1, acc);   // X_1
+  store_x(acc, P, oph + ob, opl + ob, r0 * ldw + c0, ldw, nr, bw1);
+  if (!two) return;
+  __syncthreads();
+  stash_t(acc, BsT);                                            // BsT[l][r] = X_1[r][l]
+  load_tile_t(IsT, P + (int64_t)c1 * ldw + c0, ldw, bw2, bw1);  // IsT[l][j] = L_21[j][l]
+  __syncthreads();
+  prod_tile(BsT, IsT, bw1, acc);   // X_1 L_21^T
+  __syncthreads();
+  load_tile_t(BsT, P + r0 * ldw + c1, ldw, nr, bw2);   // B_2
+  load_tile_t(IsT, DI + T * T, T, T, T);              // inv(L_22)
+  __syncthreads();
+  {
+    const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; e++)
+#pragma unroll
+      for (int f = 0; f < 4; f++) acc[e][f] = BsT[(tc + f) * TS + tr + e] - acc[e][f];   // B_2' (zero past nr, bw2)
+    __syncthreads();
+    stash_t(acc, BsT);
+  }
+  __syncthreads();
+  prod_tile(BsT, IsT, bw2, acc);   // X_2
+  store_x(acc, P, oph + ob, opl + ob, r0 * ldw + c1, ldw, nr, bw2);
 }
 
 // ---------------------------------------------------------------------------------------------------------
 // Trailing updates on the tensor cores: F[i, j] -= sum_{l in K} L[i, l] L[j, l] over 128 x TN tiles, j <= i.
 // Modes (block column kb = columns [c0, c1), in the (64 G)-column group [g0, gend), G = the plan's group):
 //   3: left-looking, before the block's POTRF: rows >= c0 x the block's columns, 128 x 64 tiles, K = [g0, c0)
-//      (the group's earlier blocks);
+//      (the group's earlier blocks); 4: the same for block columns kb and kb + 1 at once, 128 x 128 tiles;
 //   2: group end: rows/columns >= gend, 128 x 256 tiles on and below the diagonal, K = the whole group [g0, gend).
 // The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
 // tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
@@ -512,11 +645,11 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   (void)bw;
   const int64_t loc = t - pre[fi];
   int64_t I, J, base;
-  if (mode == 3) {
+  if (mode >= 3) {   // 4: the strip of block columns kb and kb + 1 (the block steps in pairs)
     I = loc;
     J = 0;
     base = c0;
-    u.jlim = c1;
+    u.jlim = mode == 4 ? min(c0 + 2 * T, u.w) : c1;
     u.K = c0 - g0;
     u.kc = g0;
   } else {
@@ -894,7 +1027,7 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
     k_update_ws<GP_TN_LEFT, false><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
         f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
-  } else if (sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
+  } else if (mode == 2 && sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
     cfg.blockDim = dim3(UW_THREADS);
@@ -1017,8 +1150,40 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
           dp.small_list + lv.small_off, dp, f->panels32, f->diag, f->upd32, P32E, DE, UE, f->notpd);
       GP_CHECK_LAUNCH(ctx);
     }
-    for (const auto& stp : lv.steps) {
+    for (size_t q = 0; q < lv.steps.size();) {
+      const auto& stp = lv.steps[q];
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
+      if (sp.group % 2 == 0 && q + 1 < lv.steps.size()) {   // block columns kb and kb + 1 (never across a group)
+        const auto& st2 = lv.steps[q + 1];
+        if (stp.left_total > 0) {
+          ProfScope ps_(ctx, KC_UPDATE_LEFT, B * stp.left2_flops);
+          launch_update(ctx, f, stp.left_total, dp.upd_fronts + stp.left_off, dp.upd_pre + stp.left_pre_off,
+                        stp.n_left, stp.kb, 4);
+        }
+        {
+          ProfScope ps_(ctx, KC_POTRF, B * (stp.potrf_flops + st2.potrf_flops));
+          k_potrf32_pair<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp,
+                                                                        f->panels32, f->op_hi, f->op_lo, f->diag,
+                                                                        f->dinv32, P32E, DE, f->notpd);
+          GP_CHECK_LAUNCH(ctx);
+        }
+        if (stp.pair_total > 0) {
+          ProfScope ps_(ctx, KC_TRSM, B * (stp.trsm_flops + st2.trsm_flops));
+          k_trsm32_pair<<<dim3((unsigned)stp.pair_total, B), 256, 0, st>>>(
+              fronts, dp.pair_pre + stp.pair_pre_off, stp.nfront, st2.nfront, stp.kb, dp, f->panels32, f->op_hi,
+              f->op_lo, f->dinv32, P32E, DE);
+          GP_CHECK_LAUNCH(ctx);
+        }
+        for (const auto* sg : {&stp, &st2})
+          if (sg->group_total > 0) {   // fronts whose group ends at kb (their last block) or at kb + 1
+            ProfScope ps_(ctx, KC_UPDATE, B * sg->group_flops);
+            launch_update(ctx, f, sg->group_total, dp.upd_fronts + sg->group_off, dp.upd_pre + sg->group_pre_off,
+                          sg->n_group, sg->kb, 2);
+          }
+        q += 2;
+        continue;
+      }
+      q += 1;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
       if (stp.left_total > 0) {   // this block column from the earlier blocks of its group
         ProfScope ps_(ctx, KC_UPDATE_LEFT, B * stp.left_flops);

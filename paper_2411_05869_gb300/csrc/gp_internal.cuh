@@ -174,6 +174,7 @@ struct SymPlan {
                       int64_t left_off, left_pre_off, left_total; int32_t n_left;
                       int64_t group_off, group_pre_off, group_total; int32_t n_group;
                       double left_flops, group_flops;
+                      double left2_flops;   // the left update of block columns kb and kb + 1 together
                       double potrf_flops, trsm_flops, upd_flops; };   // useful flops of the step's launches
   struct Level {
     std::vector<EaLaunch> ea;        // one per child slot

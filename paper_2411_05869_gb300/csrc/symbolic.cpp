@@ -519,6 +519,7 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
       stp.left_pre_off = (int64_t)sp.upd_pre.size();
       stp.n_left = 0;
       stp.left_flops = 0.0;
+      stp.left2_flops = 0.0;
       int64_t acc = 0;
       sp.upd_pre.push_back(0);
       for (int32_t t = 0; t < cnt; t++) {   // block column kb from the earlier blocks of its group
@@ -533,6 +534,9 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
         stp.n_left++;
         double bw = (double)(c1 - c0);
         stp.left_flops += 2.0 * (double)(c0 - g0) * (bw * (bw + 1.0) / 2.0 + (double)(m - c1) * bw);
+        const int64_t c2 = std::min<int64_t>(c0 + 2 * GP_TILE, w);
+        double cw = (double)(c2 - c0);
+        stp.left2_flops += 2.0 * (double)(c0 - g0) * (cw * (cw + 1.0) / 2.0 + (double)(m - c2) * cw);
       }
       stp.left_total = acc;
       stp.group_off = (int64_t)sp.upd_fronts.size();
