@@ -670,34 +670,35 @@ __global__ void k_residual(const int64_t* __restrict__ rowptr, const int32_t* __
   }
 }
 
-// Fixed-order reduction of the residual partials: err[b] = |res| / |r|, rdot[b] = r . alpha.
-__global__ void k_relres(const double* __restrict__ red, int64_t rs, int nblk, double* __restrict__ err,
-                         double* __restrict__ rdot) {
-  __shared__ double sa[256], sb[256], sc[256];
-  int b = blockIdx.x;
+// Fixed-order reduction of the residual partials: err[b] = |res| / |r|, rdot[b] = r . alpha. Thread t sums
+// partials t, t + 1024, ... in order (three independent chains), then one tree over the 1024 threads.
+constexpr int RELRES_THREADS = 1024;
+__global__ void __launch_bounds__(RELRES_THREADS) k_relres(const double* __restrict__ red, int64_t rs, int nblk,
+                                                           double* __restrict__ err, double* __restrict__ rdot) {
+  __shared__ double sa[RELRES_THREADS], sb[RELRES_THREADS], sc[RELRES_THREADS];
+  const int b = blockIdx.x, t = threadIdx.x;
+  const double* ra = red + (int64_t)b * rs;
   double ta = 0.0, tb = 0.0, tc = 0.0;
-  for (int base = 0; base < nblk; base += 256) {
-    int i = base + threadIdx.x;
-    sa[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + i] : 0.0;
-    sb[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + nblk + i] : 0.0;
-    sc[threadIdx.x] = i < nblk ? red[(int64_t)b * rs + 2 * nblk + i] : 0.0;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        sa[threadIdx.x] += sa[threadIdx.x + o];
-        sb[threadIdx.x] += sb[threadIdx.x + o];
-        sc[threadIdx.x] += sc[threadIdx.x + o];
-      }
-      __syncthreads();
+  for (int i = t; i < nblk; i += RELRES_THREADS) {
+    ta += ra[i];
+    tb += ra[nblk + i];
+    tc += ra[2 * (int64_t)nblk + i];
+  }
+  sa[t] = ta;
+  sb[t] = tb;
+  sc[t] = tc;
+  __syncthreads();
+  for (int o = RELRES_THREADS / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      sa[t] += sa[t + o];
+      sb[t] += sb[t + o];
+      sc[t] += sc[t + o];
     }
-    ta += sa[0];
-    tb += sb[0];
-    tc += sc[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (err) err[b] = tb > 0.0 ? sqrt(ta / tb) : sqrt(ta);
-    if (rdot) rdot[2 * b + 1] = tc;
+  if (t == 0) {
+    if (err) err[b] = sb[0] > 0.0 ? sqrt(sa[0] / sb[0]) : sqrt(sa[0]);
+    if (rdot) rdot[2 * b + 1] = sc[0];
   }
 }
 
@@ -813,7 +814,7 @@ void residual_impl(gp_ctx* ctx, gp_factor_t* f, const double* rhs, const double*
   k_residual<<<dim3(nblk, f->B), 256, 0, ctx->stream>>>(ps->rowptr, ps->col, n, ps->nnz, f->val, alpha, rhs, res,
                                                         f->work, f->work_stride, nblk);
   GP_CHECK_LAUNCH(ctx);
-  k_relres<<<f->B, 256, 0, ctx->stream>>>(f->work, f->work_stride, nblk, err, rdot);
+  k_relres<<<f->B, RELRES_THREADS, 0, ctx->stream>>>(f->work, f->work_stride, nblk, err, rdot);
   GP_CHECK_LAUNCH(ctx);
 }
 
