@@ -60,6 +60,7 @@ typedef enum {
 typedef struct gp_ctx gp_ctx;
 typedef struct gp_pointset gp_pointset;
 typedef struct gp_factor_s gp_factor_t;   /* a numeric factorization (B proposals) */
+typedef struct gp_symbolic gp_symbolic;   /* a host-side symbolic analysis (step A6 alone) */
 
 /* One hyperparameter setting (host memory, FP64). Sec. 2.1 lists theta_sparse = (s0, r0, {h, a, b, r});
  * core_var / core_radius parameterise the compact core, noise_var is tau^2 of Eq. Zcov (constant).
@@ -127,6 +128,26 @@ GP_API gp_status gp_pointset_info(const gp_pointset* ps, gp_pointset_info_t* inf
  *   8 sn_parent[nsuper] int32, 9 sn_level[nsuper] int32, 10 cell_perm[n] int32 (points by (cell, index)).
  * `bytes` must equal the array size. Synchronous. Errors: GP_ERR_ARG. */
 GP_API gp_status gp_pointset_export(const gp_pointset* ps, int what, void* host_dst, size_t bytes);
+
+/* Step A6 alone, on the host: the symbolic analysis gp_assemble runs on the device pattern (postorder
+ * relabelling of the elimination tree, etree by Liu's algorithm, exact column counts, fundamental and relaxed
+ * supernodes, supernodal row structures and levels, and the frontal plan), here from a caller's host pattern
+ * and nested-dissection order, with no device call. The analysis of the paper's exact sparse Cholesky, named in
+ * its Discussion; the structure rules are those of gp_assemble.
+ *   rowptr[n+1] int64 (rowptr[0] = 0, non-decreasing), col[rowptr[n]] int32: the symmetric pattern of C_z, both
+ *   triangles and the diagonal, columns strictly ascending in each row, all in 0..n-1;
+ *   nd_perm[n] int32: a permutation (new -> old), the order before the postorder relabelling.
+ * The caller keeps ownership of its arrays (read during the call only); *out is freed with gp_symbolic_free.
+ * Synchronous. Errors: GP_ERR_ARG (n outside 1..2^31-2, a malformed pattern or permutation, null pointers),
+ * GP_ERR_NOMEM, GP_ERR_STATE (inconsistent analysis, e.g. an unsymmetric pattern). */
+GP_API gp_status gp_symbolic_host(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* nd_perm,
+                                  gp_symbolic** out);
+/* The analysis' sizes in a gp_pointset_info_t (d = 0, ncells = 0; nnz = rowptr[n]). Errors: GP_ERR_ARG. */
+GP_API gp_status gp_symbolic_info(const gp_symbolic* sym, gp_pointset_info_t* info);
+/* Export one of its arrays to host memory; `what` as for gp_pointset_export, the analysis' arrays only (0, 1, 2,
+ * 5, 6, 7, 8, 9); `bytes` must equal the array size. Errors: GP_ERR_ARG. */
+GP_API gp_status gp_symbolic_export(const gp_symbolic* sym, int what, void* host_dst, size_t bytes);
+GP_API void gp_symbolic_free(gp_symbolic* sym);
 
 /* Steps A3, A4, A7 for B proposals sharing the point set: bump features, kernel values of the pattern
  * (fused with the scatter into supernodal panels) and the supernodal numeric Cholesky of P C_z P^T.

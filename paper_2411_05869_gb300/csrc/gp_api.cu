@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include "gp_internal.cuh"
 
@@ -320,6 +321,88 @@ extern "C" gp_status gp_pointset_export(const gp_pointset* ps, int what, void* d
     default: return fail(ctx, GpError{GP_ERR_ARG, "unknown export"});
   }
 }
+
+// ------------------------------------------------------------------------------------------ host symbolic
+struct gp_symbolic {
+  int64_t n = 0, nnz = 0;
+  SymPlan sp;
+};
+
+extern "C" gp_status gp_symbolic_host(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* nd_perm,
+                                      gp_symbolic** out) {
+  if (!out) return GP_ERR_ARG;
+  *out = nullptr;
+  if (!rowptr || !col || !nd_perm || n < 1 || n >= ((int64_t)1 << 31) - 1 || rowptr[0] != 0) return GP_ERR_ARG;
+  for (int64_t i = 0; i < n; i++) {   // the pattern: ascending in-range columns, the diagonal present
+    if (rowptr[i + 1] < rowptr[i]) return GP_ERR_ARG;
+    bool diag = false;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+      if (col[e] < 0 || col[e] >= n || (e > rowptr[i] && col[e] <= col[e - 1])) return GP_ERR_ARG;
+      diag = diag || col[e] == i;
+    }
+    if (!diag) return GP_ERR_ARG;
+  }
+  try {
+    std::vector<char> seen((size_t)n, 0);
+    for (int64_t k = 0; k < n; k++) {
+      const int32_t v = nd_perm[k];
+      if (v < 0 || v >= n || seen[v]) return GP_ERR_ARG;
+      seen[v] = 1;
+    }
+    std::unique_ptr<gp_symbolic> s(new gp_symbolic);
+    s->n = n;
+    s->nnz = rowptr[n];
+    build_symbolic(n, rowptr, col, nd_perm, s->sp);
+    *out = s.release();
+    return GP_OK;
+  } catch (const GpError& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    return GP_ERR_NOMEM;
+  } catch (const std::exception&) {
+    return GP_ERR_STATE;
+  }
+}
+
+extern "C" gp_status gp_symbolic_info(const gp_symbolic* sym, gp_pointset_info_t* info) {
+  if (!sym || !info) return GP_ERR_ARG;
+  const SymPlan& sp = sym->sp;
+  *info = gp_pointset_info_t{};
+  info->n = sym->n;
+  info->nnz = sym->nnz;
+  info->nnzL = sp.nnzL;
+  info->nsuper = sp.ns;
+  info->panel_entries = sp.panel_entries;
+  info->update_entries = sp.update_entries;
+  info->nlevels = sp.nlevels;
+  info->max_front = sp.max_front;
+  info->flops = sp.flops;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_symbolic_export(const gp_symbolic* sym, int what, void* dst, size_t bytes) {
+  if (!sym || !dst) return GP_ERR_ARG;
+  const SymPlan& sp = sym->sp;
+  auto host = [&](const void* src, size_t b) -> gp_status {
+    if (b != bytes) return GP_ERR_ARG;
+    if (b) memcpy(dst, src, b);
+    return GP_OK;
+  };
+  const size_t n = (size_t)sym->n;
+  switch (what) {
+    case 0: return host(sp.perm.data(), n * 4);
+    case 1: return host(sp.parent.data(), n * 4);
+    case 2: return host(sp.eta.data(), n * 4);
+    case 5: return host(sp.sn_first.data(), sp.sn_first.size() * 4);
+    case 6: return host(sp.sn_rowptr.data(), sp.sn_rowptr.size() * 8);
+    case 7: return host(sp.sn_rows.data(), sp.sn_rows.size() * 4);
+    case 8: return host(sp.sn_parent.data(), sp.sn_parent.size() * 4);
+    case 9: return host(sp.sn_level.data(), sp.sn_level.size() * 4);
+    default: return GP_ERR_ARG;
+  }
+}
+
+extern "C" void gp_symbolic_free(gp_symbolic* sym) { delete sym; }
 
 // The mixed-path update schedule on the device (replaced when it is re-planned).
 void upload_schedule(gp_ctx* ctx, gp_pointset* ps) {

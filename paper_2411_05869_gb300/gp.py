@@ -70,7 +70,8 @@ GP_REQ_LOGLIK, GP_REQ_PREDICT = 0, 1
 SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_pointset_free", "gp_pointset_info",
            "gp_pointset_export", "gp_factor", "gp_factor_update", "gp_factor_free", "gp_factor_info", "gp_loglik",
            "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read", "gp_factor_bytes",
-           "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
+           "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_symbolic_host", "gp_symbolic_info",
+           "gp_symbolic_export", "gp_symbolic_free", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
            "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7, "update_left": 9}
@@ -151,6 +152,14 @@ def load(build_if_missing: bool = True):
                               ctypes.POINTER(c_int)]
     L.gp_pointset_set_blocking.restype = c_int
     L.gp_pointset_set_blocking.argtypes = [P, P, c_int, c_int]
+    L.gp_symbolic_host.restype = c_int
+    L.gp_symbolic_host.argtypes = [c_i64, P, P, P, ctypes.POINTER(P)]
+    L.gp_symbolic_info.restype = c_int
+    L.gp_symbolic_info.argtypes = [P, ctypes.POINTER(PointsetInfo)]
+    L.gp_symbolic_export.restype = c_int
+    L.gp_symbolic_export.argtypes = [P, c_int, P, ctypes.c_size_t]
+    L.gp_symbolic_free.argtypes = [P]
+    L.gp_symbolic_free.restype = None
     L.gp_pointset_prepare.restype = c_int
     L.gp_pointset_prepare.argtypes = [P, P, c_int]
     L.gp_server_create.restype = c_int
@@ -270,6 +279,39 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def symbolic_host(rowptr, col, nd_perm) -> dict:
+    """gp_symbolic_host: step A6 alone on the host (no device) for a host CSR pattern and a nested-dissection
+    order; returns the sizes and the structural arrays (the names of PointSet.export)."""
+    lib = load()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    pm = np.ascontiguousarray(nd_perm, dtype=np.int32)
+    h = P()
+    st = lib.gp_symbolic_host(pm.shape[0], rp.ctypes.data_as(P), cl.ctypes.data_as(P), pm.ctypes.data_as(P),
+                              ctypes.byref(h))
+    if st != 0:
+        raise GpError(st, "gp_symbolic_host failed")
+    try:
+        inf = PointsetInfo()
+        if lib.gp_symbolic_info(h, ctypes.byref(inf)) != 0:
+            raise GpError(1, "gp_symbolic_info failed")
+        out = {k: getattr(inf, k) for k, _ in PointsetInfo._fields_}
+        n, ns = out["n"], out["nsuper"]
+        sizes = {"perm": n, "parent": n, "eta": n, "sn_first": ns + 1, "sn_rowptr": ns + 1, "sn_parent": ns,
+                 "sn_level": ns}
+        for name in ["perm", "parent", "eta", "sn_first", "sn_rowptr", "sn_parent", "sn_level", "sn_rows"]:
+            what, dt = EXPORTS[name]
+            size = int(out["sn_rowptr"][-1]) if name == "sn_rows" else sizes[name]
+            arr = np.empty(size, dtype=dt)
+            st = lib.gp_symbolic_export(h, what, arr.ctypes.data_as(P), arr.nbytes)
+            if st != 0:
+                raise GpError(st, f"gp_symbolic_export({name}) failed")
+            out[name] = arr
+        return out
+    finally:
+        lib.gp_symbolic_free(h)
 
 
 class PointSet:
