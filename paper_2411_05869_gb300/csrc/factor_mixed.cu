@@ -580,7 +580,8 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
 // Modes (block column kb = columns [c0, c1), in the (64 G)-column group [g0, gend), G = the plan's group):
 //   3: left-looking, before the block's POTRF: rows >= c0 x the block's columns, 128 x 64 tiles, K = [g0, c0)
 //      (the group's earlier blocks); 4: the same for block columns kb and kb + 1 at once, 128 x 128 tiles;
-//   2: group end: rows/columns >= gend, 128 x 256 tiles on and below the diagonal, K = the whole group [g0, gend).
+//   2: group end: rows/columns >= gend, tiles on and below the diagonal (the plan's tile width: 256 x 256 per
+//      CTA pair, or 128 x 128), K = the whole group [g0, gend).
 // The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
 // tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
 // significant bits survive the products instead of the 11 of one TF32 pass). The wide tiles of mode 2 halve
@@ -1018,6 +1019,8 @@ void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps) {
 }
 
 namespace {
+// One update launch over `total` tiles per proposal of the fronts of a list: mode 3 on 128 x 64 tiles, mode 2
+// with 256-column tiles on clusters of two CTAs, mode 2 with 128-column tiles and mode 4 on 128 x 128 tiles.
 void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
                    int32_t nfront, int32_t kb, int mode) {
   const SymPlan& sp = f->ps->sp;
