@@ -323,6 +323,57 @@ def run_gpu(args, rank, world, local_rank):
     return res
 
 
+# ------------------------------------------------------------------------------------------------ MCMC leg
+
+def run_mcmc(args):
+    """The App. C sampler on the 200k-point batched workload: `--batch` lockstep chains (default 16), every block
+    update one batched factorization and solve of all chains (the mean block solves only). Times --steps full
+    iterations after --warmup, with the mixed path and the autotuner's blocking."""
+    import torch
+    from paper_2411_05869_gb300 import gp, mcmc
+    w = make_workload("batched_200k")
+    hp = w.hyper
+    B = args.batch
+    ctx = gp.Context(0)
+    ps = ctx.assemble(torch.as_tensor(w.X, dtype=torch.float64, device="cuda"), hp.core_radius)
+    rng = np.random.default_rng(7)
+    tried = ps.autotune([synth_perturb(rng, hp) for _ in range(B)], reps=1)
+    best = min(tried, key=lambda t: t["ms"])
+    ps.set_blocking(best["group_blocks"], best["group_tile_n"])
+    ev = mcmc.GpEvaluator(ctx, ps, B, gp.GP_MIXED)
+    bounds = mcmc.Bounds(r0=(1e-3, 2.0 * float(hp.core_radius.max())), r=(0.02, 0.6), h=(-0.1, 1.1))
+    s = mcmc.BlockMCMC(ev, w.resid, hp, B, seed=11, bounds=bounds)
+    s.run(args.warmup)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    calls0, fac0 = ev.calls, ev.factorizations
+    t0 = time.perf_counter()
+    s.run(args.steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clocks = clk.stop()
+    evals = (ev.calls - calls0) * B
+    acc = {k: v / float(B * s.iterations) for k, v in s.accept_counts.items()}
+    line = {"metric": "MCMC iterations/s (App. C blocks, lockstep chains)", "value": args.steps / dt,
+            "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "dtype": "tf32+f64",
+            "data": "synthetic (seeded; the 200k-point batched workload)",
+            "config": {"workload": "mcmc_200k", "n": int(w.X.shape[0]), "chains": B,
+                       "blocking": {"group_blocks": best["group_blocks"], "group_tile_n": best["group_tile_n"]}},
+            "loglik_evals_per_s": evals / dt,
+            "factorizations_per_iteration": (ev.factorizations - fac0) / args.steps,
+            "acceptance": acc, "clocks": clocks}
+    print(json.dumps(line))
+    ev.free()
+    ps.free()
+
+
+def synth_perturb(rng, hp):
+    from paper_2411_05869_gb300 import synth
+    return synth.perturb(rng, hp, 0.1)
+
+
 # ------------------------------------------------------------------------------------------------ serving leg
 
 def run_serving(args):
@@ -408,7 +459,8 @@ def main():
     ap.add_argument("--precision", default=os.environ.get("GP_BENCH_PRECISION", "mixed"), choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fp64-proposals", type=int, default=8, help="batched runs: proposals compared with FP64")
-    ap.add_argument("--batch", type=int, default=0, help="proposals per step (default: 64 for batched_200k, else 1)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="proposals per step (default: 64 for batched_200k, 16 chains for mcmc_200k, else 1)")
     ap.add_argument("--autotune", type=int, default=-1, help="1/0: tune the update blocking first (default: "
                                                               "on in mixed precision)")
     ap.add_argument("--blocking", default="", help="G,TN: fixed update blocking of mixed runs (no autotuner)")
@@ -422,7 +474,7 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 1.0, 1.5])
     args = ap.parse_args()
     if args.batch <= 0:
-        args.batch = 64 if args.workload == "batched_200k" else 1
+        args.batch = {"batched_200k": 64, "mcmc_200k": 16}.get(args.workload, 1)
     if args.autotune < 0:   # the library's autotuner picks the update blocking of mixed runs
         args.autotune = 1 if args.precision == "mixed" else 0
 
@@ -462,6 +514,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             run_serving(args)
+        return
+    if args.workload == "mcmc_200k":
+        if rank == 0:
+            run_mcmc(args)
         return
 
     import torch
