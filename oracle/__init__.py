@@ -306,6 +306,24 @@ def sparse_factor_dense(hp, X, rowptr, col, perm) -> np.ndarray:
     return Ld
 
 
+def predictive_variance(hp, X, Xtest) -> np.ndarray:
+    """diag(C_{y|z}) at the test inputs: C_y(x*, x*) - c^T C_z^{-1} c with c = C_y(X, x*) (Sec. 3.2, the
+    conditional covariance C_{y|z} = C_y - C_{y,z} C_z^{-1} C_{z,y}; no noise at the test inputs). Dense: C_y over
+    the stacked training and test inputs gives the cross block and the test diagonal, and the Cholesky factor L of
+    C_z turns each term into |L^{-1} c|^2. Small n only (n <= 8000)."""
+    X = _f64(X); Xt = _f64(Xtest)
+    n, m = X.shape[0], Xt.shape[0]
+    if n > 8000:
+        raise ValueError("predictive_variance is dense: n <= 8000")
+    Cz = dense_cov(hp, X, noise=True)
+    Ly = dense_cov(hp, np.vstack([X, Xt]), noise=False)
+    cross = Ly[:n, n:]                 # n x m
+    prior = np.diag(Ly[n:, n:]).copy()
+    L = dense_chol(Cz)
+    W = np.linalg.solve(np.tril(L), cross)   # L^{-1} C_{z,y}
+    return prior - np.einsum("ij,ij->j", W, W)
+
+
 def predict(hp, X, alpha, Xtest, mu_test=None) -> np.ndarray:
     """m* = mu* + C_y(X*, X) alpha with alpha = C_z^{-1} r (Sec. 3.2), brute force over training points."""
     X = _f64(X); Xt = _f64(Xtest); a = _f64(alpha)
