@@ -133,7 +133,7 @@ class BlockMCMC:
     """B lockstep chains of the App. C sampler for data z with mean W beta (W: n x p, default a constant)."""
 
     def __init__(self, evaluator: Callable, z: np.ndarray, theta0, nchains: int, seed: int,
-                 W: Optional[np.ndarray] = None, beta0: Optional[np.ndarray] = None, bounds: Bounds = Bounds(),
+                 W: Optional[np.ndarray] = None, beta0: Optional[np.ndarray] = None, bounds: Optional[Bounds] = None,
                  init_sd: float = 0.1, every: int = 20, update_pi: bool = True,
                  blocks: Sequence[str] = ("mean", "core", "bumps", "amplitudes")):
         self.eval = evaluator
@@ -143,6 +143,7 @@ class BlockMCMC:
         p = self.W.shape[1]
         self.rng = np.random.default_rng(seed)
         self.B = nchains
+        bounds = Bounds() if bounds is None else bounds
         self.bounds = bounds
         self.update_pi = update_pi
         self.blocks_on = set(blocks)
