@@ -179,3 +179,68 @@ def test_hyperparameter_counts():
         assert synth.pack_sparse(hp).shape[0] == cnt
     for d, n1, n2, cnt in GOLD["hyperparameter_count_anisotropic"]["cases"]:
         assert synth.sparse_param_count(d, n1, n2, anisotropic_r0=True) == cnt
+
+
+# ------------------------------------------------------------------ features f_i = sum_j g_ij (Sec. 2.1)
+
+def _two_family_hyper():
+    """n1 = 2 families of n2 = 3 bumps in 2-D, placed around x = (0.4, 0.5) at distances with closed forms.
+
+    Family 1: bump 0 at distance r/2 (g = a e^{-b/3}), bump 1 at distance r/sqrt(2) (t = 1/2, so
+    1 - (1 - t)^{-1} = -1 and g = a e^{-b}), bump 2 beyond its radius (g = 0).
+    Family 2: bump 0 centred on x (g = a), bumps 1 and 2 beyond their radii."""
+    x = np.array([0.4, 0.5])
+    h = np.array([[0.46, 0.58],    # |x - h| = 0.1, r = 0.2: t = 1/4
+                  [0.3, 0.4],      # |x - h|^2 = 0.02, r = 0.2: t = 1/2
+                  [0.9, 0.9],      # far outside r = 0.2
+                  [0.4, 0.5],      # on x
+                  [0.0, 0.0],
+                  [0.8, 0.1]])
+    a = np.array([1.3, 0.7, 1.9, 1.6, 1.1, 0.9])
+    b = np.array([0.5, 2.0, 1.0, 1.0, 1.0, 1.0])
+    r = np.array([0.2, 0.2, 0.2, 0.25, 0.3, 0.3])
+    hp = synth.Hyper(d=2, n1=2, n2=3, bump_dims=2, core_var=1.7, core_radius=np.array([0.3, 0.3]), s0=0.8,
+                     r0=np.array([0.25, 0.25]), h=h.ravel(), a=a, b=b, r=r, noise_var=1e-2)
+    return hp, x
+
+
+def test_features_sum_of_bumps_closed_form():
+    """f_1(x) = a_11 e^{-b_11/3} + a_12 e^{-b_12} + 0 and f_2(x) = a_21, written out by hand: a maximum over j,
+    a sum of squares, a dropped bump or a family mix-up all give other numbers."""
+    hp, x = _two_family_hyper()
+    F = oracle.features(hp, x[None, :])[0]
+    f1 = 1.3 * math.exp(-0.5 / 3.0) + 0.7 * math.exp(-2.0)
+    f2 = 1.6
+    assert F[0] == pytest.approx(f1, rel=1e-13)
+    assert F[1] == pytest.approx(f2, rel=1e-15)
+    assert F[0] != pytest.approx(max(1.3 * math.exp(-0.5 / 3.0), 0.7 * math.exp(-2.0)), rel=1e-6)
+
+
+def test_csparse_and_cy_of_a_pair_by_hand():
+    """C_sparse(x, y) = s0 f0(|x - y| / r0) + f_1(x) f_1(y) + f_2(x) f_2(y) (Eq. C_sparse) and
+    C_y = core_var f0(|x - y| / rho) C_sparse, at a pair whose features are closed forms: y = x + (0.06, 0.08)
+    sits on bump 11 (g = a), at |y - h_12| = sqrt(0.0436) from bump 12, on nothing of family 2 but bump 21 (at
+    |y - h_21| = 0.1 of r = 0.25: t = 0.16). f0 comes from the expanded polynomial (numpy), not from the oracle."""
+    hp, x = _two_family_hyper()
+    y = x + np.array([0.06, 0.08])
+    c3 = float(GOLD["wendland_cubic_coefficient"]["c3"])
+    poly = np.polynomial.polynomial.polymul(np.polynomial.polynomial.polypow([1.0, -1.0], 8), [1.0, 8.0, 25.0, c3])
+
+    def f0(q):
+        return float(np.polynomial.polynomial.polyval(q, poly)) if q < 1 else 0.0
+
+    def g(dist2, a, b, r):
+        t = dist2 / (r * r)
+        return a * math.exp(b * (1.0 - 1.0 / (1.0 - t))) if t < 1 else 0.0
+
+    fx = [1.3 * math.exp(-0.5 / 3.0) + 0.7 * math.exp(-2.0), 1.6]
+    d12 = (0.46 - 0.3) ** 2 + (0.58 - 0.4) ** 2
+    fy = [1.3 + g(d12, 0.7, 2.0, 0.2), g(0.01, 1.6, 1.0, 0.25)]
+    assert oracle.features(hp, y[None, :])[0] == pytest.approx(fy, rel=1e-13)
+    q0 = 0.1 / 0.25
+    cs = 0.8 * f0(q0) + fx[0] * fy[0] + fx[1] * fy[1]
+    assert oracle.csparse(hp, x, y) == pytest.approx(cs, rel=1e-12)
+    qc = 0.1 / 0.3
+    assert oracle.cy(hp, x, y) == pytest.approx(1.7 * f0(qc) * cs, rel=1e-12)
+    # the diagonal: C_y(x, x) = core_var (s0 + f_1^2 + f_2^2) with the hand-computed features
+    assert oracle.cy(hp, x, x) == pytest.approx(1.7 * (0.8 + fx[0] ** 2 + fx[1] ** 2), rel=1e-13)

@@ -165,3 +165,160 @@ def test_symbolic_levels_and_parents_consistent():
         if sp[k] >= 0:
             assert sp[k] > k and lev[sp[k]] > lev[k]
     assert (np.diff(s["sn_rowptr"]) == s["eta"][s["sn_first"][1:] - 1] - 1).all()
+
+
+# ------------------------------------------------------------------ etree postorder relabelling (fill_order)
+
+def _elimination_tree(rp, col, perm):
+    """Boolean dense elimination of P C P^T (tiny n): the lower pattern of L, its etree and its column counts."""
+    n = perm.shape[0]
+    pinv = np.empty(n, int)
+    pinv[perm] = np.arange(n)
+    M = np.zeros((n, n), bool)
+    for i in range(n):
+        M[pinv[i], pinv[col[rp[i]:rp[i + 1]]]] = True
+    Lb = _boolean_elimination(M)
+    parent = np.array([(np.nonzero(Lb[j + 1:, j])[0][0] + j + 1) if Lb[j + 1:, j].any() else -1 for j in range(n)])
+    return Lb, parent, Lb.sum(0)
+
+
+@pytest.mark.parametrize("d,n,seed", [(2, 220, 8), (3, 240, 9)])
+def test_etree_postorder_keeps_fill_and_makes_subtrees_contiguous(d, n, seed):
+    """The relabelling of the nested-dissection order by a postorder of its elimination tree (the build's rule;
+    the paper is silent) must (i) be a permutation, (ii) keep the fill: the same nnz(L) and the same multiset of
+    column counts as the order it relabels, (iii) make every subtree a contiguous range of columns ending at its
+    root, and (iv) visit children in increasing index order and roots in increasing order. Each property is
+    checked on the etree of a brute-force boolean elimination, not on the oracle's own analysis."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (n, d))
+    rho = np.array([0.2, 0.2, 0.25][:d])
+    rp, col = oracle.pattern(X, rho)
+    nd = oracle.nd_order(X, rho, rp, col)
+    po = oracle.fill_order(X, rho, rp, col)
+    assert np.array_equal(np.sort(po), np.arange(n))
+    Lnd, par_nd, eta_nd = _elimination_tree(rp, col, nd)
+    Lpo, par_po, eta_po = _elimination_tree(rp, col, po)
+    assert Lpo.sum() == Lnd.sum()
+    assert np.array_equal(np.sort(eta_po), np.sort(eta_nd))
+    # subtree sizes from the relabelled etree: children precede parents
+    size = np.ones(n, int)
+    for j in range(n):
+        if par_po[j] >= 0:
+            assert par_po[j] > j
+            size[par_po[j]] += size[j]
+    for j in range(n):   # descendants of j are exactly the columns j - size_j + 1 .. j
+        k, anc = j - size[j] + 1, True
+        for c in range(k, j):
+            p = c
+            while p >= 0 and p != j:
+                p = par_po[p]
+            anc = anc and p == j
+        assert anc, j
+    # the same tree: relabelled node new = old position post[new] in the nd order, with the edges preserved
+    pos_nd = np.empty(n, int)
+    pos_nd[nd] = np.arange(n)
+    post = pos_nd[po]               # new label -> nd label
+    for j in range(n):
+        pj = par_po[j]
+        assert (par_nd[post[j]] == -1) if pj < 0 else (par_nd[post[j]] == post[pj])
+    # the traversal rule, restated as a recursive walk over the nd etree (tiny n)
+    kids = [[] for _ in range(n)]
+    for v in range(n):
+        if par_nd[v] >= 0:
+            kids[par_nd[v]].append(v)
+    walk = []
+
+    def visit(v):
+        for c in sorted(kids[v]):
+            visit(c)
+        walk.append(v)
+
+    import sys
+    old = sys.getrecursionlimit()
+    sys.setrecursionlimit(max(old, 4 * n))
+    try:
+        for v in range(n):
+            if par_nd[v] < 0:
+                visit(v)
+    finally:
+        sys.setrecursionlimit(old)
+    assert post.tolist() == walk
+
+
+@pytest.mark.parametrize("d,n,seed", [(2, 190, 10), (3, 210, 11)])
+def test_symbolic_on_fill_order_against_boolean_elimination(d, n, seed):
+    """The symbolic analysis of the relabelled (factorization) order against a boolean dense elimination."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (n, d))
+    rho = np.array([0.2, 0.2, 0.25][:d])
+    rp, col = oracle.pattern(X, rho)
+    perm = oracle.fill_order(X, rho, rp, col)
+    Lb, parent, eta = _elimination_tree(rp, col, perm)
+    s = oracle.symbolic(rp, col, perm)
+    assert np.array_equal(s["eta"], eta)
+    assert np.array_equal(s["parent"], parent)
+    assert s["nnzL"] == Lb.sum()
+    snf = s["sn_first"]
+    for k in range(len(snf) - 1):
+        f, l = snf[k], snf[k + 1] - 1
+        rows = s["sn_rows"][s["sn_rowptr"][k]:s["sn_rowptr"][k + 1]]
+        assert rows.tolist() == (np.nonzero(Lb[l + 1:, l])[0] + l + 1).tolist()
+        # a (relaxed) supernode is a contiguous piece of the tree rooted at its last column
+        assert np.all((parent[f:l] > np.arange(f, l)) & (parent[f:l] <= l)), "supernode columns must hang off its last"
+
+
+# ------------------------------------------------------------------ relaxed amalgamation: the explicit-zeros branch
+
+def _two_chain_etree(a, b, k, r):
+    """Columns 0..a-1 (child chain c) then a..a+b-1 (parent chain p), one path, p's last column with r rows below.
+    Within each chain eta drops by one per column (fundamental supernodes); between them column a-1 has k fewer
+    rows than a fundamental merge would need, so merging c into p stores a * k explicit zeros."""
+    n = a + b
+    parent = np.arange(1, n + 1, dtype=np.int32)
+    parent[-1] = -1
+    eta = np.empty(n, np.int32)
+    for j in range(a, n):
+        eta[j] = r + 1 + (n - 1 - j)
+    for j in range(a):
+        eta[j] = eta[a] + 1 - k + (a - 1 - j)
+    return parent, eta
+
+
+def _merged_panel(a, b, r):
+    w = a + b
+    return w * (w + 1) // 2 + w * r
+
+
+def test_relaxation_explicit_zeros_branch_at_exactly_ten_percent():
+    """A merge wider than 16 columns is taken iff the merged panel holds at most 10 % explicit zeros: the
+    boundary case (zeros = 10 % of the panel's entries exactly) merges, one more zero row per column does not."""
+    found = None
+    for a in range(2, 30):
+        for b in range(2, 30):
+            if a + b <= 16:
+                continue
+            for r in range(0, 60):
+                ent = _merged_panel(a, b, r)
+                if ent % (10 * a) == 0:
+                    k = ent // (10 * a)
+                    if 1 <= k <= r + b - 1:
+                        found = (a, b, k, r)
+                        break
+            if found:
+                break
+        if found:
+            break
+    assert found is not None
+    a, b, k, r = found
+    parent, eta = _two_chain_etree(a, b, k, r)
+    # the panel bookkeeping: explicit zeros = entries - sum of the exact column counts = a * k
+    assert _merged_panel(a, b, r) - int(eta.sum()) == a * k
+    assert 10 * a * k == _merged_panel(a, b, r)
+    # without relaxation these are two fundamental supernodes
+    assert oracle.supernodes(parent, eta).tolist() == [0, a + b]
+    parent2, eta2 = _two_chain_etree(a, b, k + 1, r)
+    assert oracle.supernodes(parent2, eta2).tolist() == [0, a, a + b]
+    # and width alone decides at or below 16 columns, whatever the zeros
+    a3, b3 = 8, 8
+    parent3, eta3 = _two_chain_etree(a3, b3, b3 + 5, 5)
+    assert oracle.supernodes(parent3, eta3).tolist() == [0, a3 + b3]
