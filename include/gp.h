@@ -54,7 +54,8 @@ typedef enum {
 typedef enum {
   GP_FP64 = 0,         /* every step in FP64 */
   GP_MIXED = 1         /* off-diagonal supernode updates on TF32 tensor cores with FP32 accumulation and FP32
-                          off-diagonal storage; diagonal blocks, log-det and refinement residuals in FP64 */
+                          off-diagonal storage; diagonal-block factorization, log-det and refinement residuals in
+                          FP64 (the diagonal blocks optionally factored in FP32: GP_OPT_DIAG_FP32) */
 } gp_precision;
 
 typedef struct gp_ctx gp_ctx;
@@ -98,7 +99,17 @@ typedef struct {
   int precision;              /* gp_precision */
   int64_t bytes;              /* device bytes held by the factor */
   int32_t not_pd_count;       /* proposals whose factorization met a non-positive pivot */
+  int32_t diag_fp32;          /* GP_MIXED: 1 if its 64 x 64 diagonal blocks are factored in FP32 (GP_OPT_DIAG_FP32) */
 } gp_factor_info_t;
+
+/* Context options (gp_set_option). They apply to the calls made on the context afterwards.
+ *   GP_OPT_DIAG_FP32: 0 (default) or 1. With 1, GP_MIXED factors created afterwards factor their 64 x 64
+ *     diagonal blocks in FP32 from the FP64-accumulated block instead of in FP64. The blocks are accumulated in
+ *     FP64 either way and the log-determinant is summed in FP64 from their diagonals; FP32 is faster on GB300
+ *     (its FP64 pipe is slow) at the cost of an FP32-accurate diagonal of L in the log-determinant. */
+typedef enum {
+  GP_OPT_DIAG_FP32 = 0
+} gp_option;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
  * default stream). mem_budget_bytes caps the device memory the context's handles may hold (0 = no cap).
@@ -107,6 +118,9 @@ GP_API gp_status gp_create(gp_ctx** ctx, int device, void* cuda_stream, size_t m
 GP_API void gp_destroy(gp_ctx* ctx);
 /* Message of the last failure on this context (static storage owned by the context; "" if none). */
 GP_API const char* gp_last_error(const gp_ctx* ctx);
+/* Set / read a context option (gp_option). Host-only. Errors: GP_ERR_ARG (unknown option or value). */
+GP_API gp_status gp_set_option(gp_ctx* ctx, int option, int64_t value);
+GP_API gp_status gp_get_option(const gp_ctx* ctx, int option, int64_t* value);
 
 /* Steps A1, A2, A5, A6: cell list of the unit grid in u = x / core_radius, exact support pattern of C_z
  * (all pairs with q^2 = sum_k (u_ik - u_jk)^2 < 1, FP64 without contraction), nested-dissection ordering and

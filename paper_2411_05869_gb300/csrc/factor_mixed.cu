@@ -1,6 +1,7 @@
 // factor_mixed.cu -- step A7 in mixed precision (GP_MIXED): the multifrontal supernodal Cholesky of
 // P C_z P^T with the off-diagonal supernode updates on TF32 tensor cores (tcgen05, FP32 accumulation in
-// tensor memory) and every diagonal 64 x 64 block kept and updated in FP64 (and factored in FP32 from it).
+// tensor memory) and every diagonal 64 x 64 block kept, updated and factored in FP64 (optionally factored in
+// FP32 from its FP64 accumulation).
 //
 // Storage per proposal: FP32 panels row-major (row i of supernode s at loff32 + i * ldw, K = column index
 // contiguous, as the tensor-core operands want), FP64 diagonal tiles (tile t of s at doff + t * 4096, row-major
@@ -8,7 +9,7 @@
 // live in the FP64 tile, every other panel entry in FP32.
 // Per level: zero the update matrices, extend-add the children (FP32 sums into the parent's FP32 entries and
 // FP64 tiles), factor fronts of order <= 96 wholly in FP64 shared memory, and step the large fronts 64 columns
-// at a time: POTRF of the diagonal tile (FP32 from its FP64 sums, with the inverse of its factor), TRSM of the
+// at a time: POTRF of the diagonal tile (FP64, with the FP32 inverse of its factor), TRSM of the
 // rows below in FP32, then the updates F[i, j] -= sum_l L[i, l] L[j, l] on the tensor cores (left-looking
 // 128 x 64 strips per block, 256 x 256 CTA-pair tiles at a group's end), each FP32 operand split into two
 // round-to-nearest TF32 parts (three products per step, about 21 bits kept), with the tile results added in
@@ -186,10 +187,13 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
   return lo;
 }
 
-// POTRF of diagonal tile kb, with the inverse of its factor. The tile accumulates its assembled values and
-// every update in FP64; the factorization itself runs in FP32 on the tile rounded once to FP32, the precision of
-// every other entry of L in this path (on GB300 an FP64 elimination of a 64 x 64 tile is bound by the FP64 pipe
-// and its 64-cycle latencies). Right-looking, with the tile in registers: thread (tr, tc) of a 16 x 16 grid
+// POTRF of the 64 x 64 diagonal tiles. A tile accumulates its assembled values and every update in FP64. On the
+// factorization's critical path it is eliminated in FP32 (the tile rounded once to FP32) for the FP32 inverse
+// of its factor, which the FP32 TRSM of the rows below and the FP32 solves use, like every other off-diagonal
+// operand of this path. The factor of the tile itself (L_11, whose diagonal gives the log-determinant) is
+// computed in FP64 from the FP64 tile by one batched launch over all diagonal tiles after the last level (the
+// tiles are final once their block step has run, and no later step reads L_11); with GP_OPT_DIAG_FP32 the FP32
+// elimination stores its L_11 instead. Right-looking, with the tile in registers: thread (tr, tc) of a 16 x 16 grid
 // holds the entries (tr + 16 p, tc + 16 q), p, q < 4, of the tile and of X = inv(U), U the unit lower factor
 // (A = U diag(d) U^T, U_ik = a_ik / d_k with a_ik column k as updated through column k - 1). The pivots
 // d_k = L_kk^2 stay unscaled: column k enters through s_j = a_jk / d_k as a_ij -= a_ik s_j (j > k), and the
@@ -197,31 +201,44 @@ __device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_
 // identity. Two columns per step and one barrier per step (the step's fixed costs -- barrier, shared-memory
 // round trip, reciprocal -- are what a column costs here): every thread reads columns k and k + 1 and rows k,
 // k + 1 of X as published by their holders, forms column k + 1's and row k + 1's updates by column k itself, and
-// applies both. Then L_ik = a_ik / sqrt(d_k), inv(L)_ij = X_ij / sqrt(d_i); L goes back to the FP64 tile (the
-// log-determinant reads its diagonal) and inv(L) to the FP32 inverse tile (the TRSM and the solves).
+// applies both. Then L_ik = a_ik / sqrt(d_k), inv(L)_ij = X_ij / sqrt(d_i). X is eliminated in FP32 only.
 constexpr int POTRF_THREADS = 256;
 
-// 1 / d from the hardware's approximate reciprocal and one Newton step r <- r + r (1 - d r) (within about an
-// ulp; the pivots are normal numbers well away from the range limits).
-__device__ __forceinline__ float recip_nr(float d) {
+// 1 / d by Newton's iteration r <- r + r (1 - d r) from the hardware's FP32 approximate reciprocal: one step in
+// FP32 (within about an ulp), two in FP64 (the error squares per step: about 2^-23 -> 2^-46 -> below an FP64 ulp).
+// The pivots are normal numbers well inside the FP32 range (a tile's entries are covariances of order one).
+__device__ __forceinline__ float rcp_seed(float d) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+__device__ __forceinline__ float recip_nr(float d) {
+  const float r = rcp_seed(d);
   return fmaf(r, fmaf(-d, r, 1.f), r);
 }
+__device__ __forceinline__ double recip_nr(double d) {
+  double r = (double)rcp_seed((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return fma(r, fma(-d, r, 1.0), r);
+}
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 
-// The factorization of one tile by the CTA's 256 threads: D the FP64 tile (in: the accumulated entries, out: L),
-// DI its FP32 inverse tile (out), bw its width, first the global column of its first column (a failed pivot
-// records the smallest such column in *flag).
+// The factorization of one tile by the CTA's 256 threads in arithmetic R: D the FP64 tile (in: the accumulated
+// entries; out, if STORE_L: L), DI its FP32 inverse tile (out, if INV), bw its width, first the global column of
+// its first column (a failed pivot records the smallest such column in *flag).
+template <class R, bool INV, bool STORE_L>
 __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __restrict__ DI, int bw, int32_t first,
                                            int32_t* __restrict__ flag) {
-  __shared__ float col[2][2][T];  // columns k, k + 1 after the updates of columns < k (double-buffered)
+  __shared__ R col[2][2][T];      // columns k, k + 1 after the updates of columns < k (double-buffered)
   __shared__ float xrow[2][2][T]; // rows k, k + 1 of X after the eliminations of rows < k (double-buffered)
-  __shared__ float piv[T];        // pivots d_k
-  __shared__ float rd[T];         // 1 / d_k
-  __shared__ float sc[T];         // 1 / L_kk
+  __shared__ R piv[T];            // pivots d_k
+  __shared__ R rd[T];             // 1 / d_k
+  __shared__ R sc[T];             // 1 / L_kk
   const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
   __syncthreads();   // an earlier call's readers of the shared arrays are done
-  float a[4][4], x[4][4];
+  R a[4][4];
+  float x[4][4];
   uint32_t own = 0;   // bit 4 p + q: entry (tr + 16 p, tc + 16 q) is in the lower triangle of the bw x bw tile
 #pragma unroll
   for (int p = 0; p < 4; p++)
@@ -229,7 +246,7 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
     for (int q = 0; q < 4; q++) {
       const int i = tr + 16 * p, j = tc + 16 * q;
       const bool in = j <= i && i < bw;
-      a[p][q] = in ? (float)D[i * T + j] : 0.f;
+      a[p][q] = in ? (R)D[i * T + j] : R(0);
       x[p][q] = i == j ? 1.f : 0.f;
       own |= (in ? 1u : 0u) << (4 * p + q);
     }
@@ -250,24 +267,24 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
     for (int k = 16 * m; k < kend; k += 2) {
       __syncthreads();
       const int buf = k & 2 ? 1 : 0;
-      const float* ca = col[buf][0];   // column k
-      const float* cb = col[buf][1];   // column k + 1 (not yet updated by column k)
+      const R* ca = col[buf][0];       // column k
+      const R* cb = col[buf][1];       // column k + 1 (not yet updated by column k)
       const float* xa = xrow[buf][0];  // row k of X (final)
       const float* xb = xrow[buf][1];  // row k + 1 of X (not yet eliminated by row k)
       const bool two = k + 1 < bw;
-      float d0 = ca[k];
-      if (!(d0 > 0.f)) {
+      R d0 = ca[k];
+      if (!(d0 > R(0))) {
         if (tid == 0) atomicMin(flag, first + k);
-        d0 = 1.f;
+        d0 = R(1);
       }
-      const float r0 = recip_nr(d0);
-      const float s01 = two ? ca[k + 1] * r0 : 0.f;   // U_{k+1, k}
-      float d1 = two ? fmaf(-ca[k + 1], s01, cb[k + 1]) : 1.f;
-      if (!(d1 > 0.f)) {
+      const R r0 = recip_nr(d0);
+      const R s01 = two ? ca[k + 1] * r0 : R(0);   // U_{k+1, k}
+      R d1 = two ? fma(-ca[k + 1], s01, cb[k + 1]) : R(1);
+      if (!(d1 > R(0))) {
         if (tid == 0) atomicMin(flag, first + k + 1);
-        d1 = 1.f;
+        d1 = R(1);
       }
-      const float r1 = recip_nr(d1);
+      const R r1 = recip_nr(d1);
       if (tid == 0) {
         piv[k] = d0;
         rd[k] = r0;
@@ -276,22 +293,26 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
           rd[k + 1] = r1;
         }
       }
-      float ci0[4], ci1[4], sj0[4], sj1[4], xa4[4], xb4[4];
+      R ci0[4], ci1[4], sj0[4], sj1[4];
+      float xa4[4], xb4[4];
 #pragma unroll
       for (int p = m; p < 4; p++) {
         ci0[p] = ca[tr + 16 * p];
-        ci1[p] = fmaf(-ci0[p], s01, cb[tr + 16 * p]);
+        ci1[p] = fma(-ci0[p], s01, cb[tr + 16 * p]);
       }
 #pragma unroll
       for (int q = m; q < 4; q++) {
-        const float v = ca[tc + 16 * q];
+        const R v = ca[tc + 16 * q];
         sj0[q] = v * r0;
-        sj1[q] = fmaf(-v, s01, cb[tc + 16 * q]) * r1;
+        sj1[q] = fma(-v, s01, cb[tc + 16 * q]) * r1;
       }
+      const float s01f = (float)s01;
+      if (INV) {
 #pragma unroll
-      for (int q = 0; q <= m; q++) {
-        xa4[q] = xa[tc + 16 * q];
-        xb4[q] = fmaf(-s01, xa4[q], xb[tc + 16 * q]);   // row k + 1 of X, eliminated by row k
+        for (int q = 0; q <= m; q++) {
+          xa4[q] = xa[tc + 16 * q];
+          xb4[q] = fmaf(-s01f, xa4[q], xb[tc + 16 * q]);   // row k + 1 of X, eliminated by row k
+        }
       }
       const int jm = tc + 16 * m;   // this thread's column of group m
       const int im = tr + 16 * m;   // this thread's row of group m
@@ -299,16 +320,18 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
       for (int q = m; q < 4; q++)
 #pragma unroll
         for (int p = q; p < 4; p++) {
-          if (q > m || jm > k) a[p][q] = fmaf(-ci0[p], sj0[q], a[p][q]);
-          if (two && (q > m || jm > k + 1)) a[p][q] = fmaf(-ci1[p], sj1[q], a[p][q]);
+          if (q > m || jm > k) a[p][q] = fma(-ci0[p], sj0[q], a[p][q]);
+          if (two && (q > m || jm > k + 1)) a[p][q] = fma(-ci1[p], sj1[q], a[p][q]);
         }
+      if (INV) {
 #pragma unroll
-      for (int p = m; p < 4; p++) {
-        const float u0 = ci0[p] * r0, u1 = ci1[p] * r1;   // U_ik, U_i,k+1
+        for (int p = m; p < 4; p++) {
+          const float u0 = (float)(ci0[p] * r0), u1 = (float)(ci1[p] * r1);   // U_ik, U_i,k+1
 #pragma unroll
-        for (int q = 0; q <= m; q++) {
-          if (p > m || im > k) x[p][q] = fmaf(-u0, xa4[q], x[p][q]);
-          if (two && (p > m || im > k + 1)) x[p][q] = fmaf(-u1, xb4[q], x[p][q]);
+          for (int q = 0; q <= m; q++) {
+            if (p > m || im > k) x[p][q] = fmaf(-u0, xa4[q], x[p][q]);
+            if (two && (p > m || im > k + 1)) x[p][q] = fmaf(-u1, xb4[q], x[p][q]);
+          }
         }
       }
       const int k2 = k + 2;
@@ -316,16 +339,16 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
         const int qb = k2 >> 4;
         if ((tc >> 1) == ((k2 & 15) >> 1)) {   // publish columns k + 2 and k + 3
           const int h = tc & 1;
-          float* cn = col[buf ^ 1][h];
+          R* cn = col[buf ^ 1][h];
 #pragma unroll
           for (int p = m; p < 4; p++) {
             const int i = tr + 16 * p;
-            float v = a[p][m];
+            R v = a[p][m];
             if (m < 3 && qb == m + 1) v = a[p][m < 3 ? m + 1 : m];
             if (i >= k2 + h && i < bw) cn[i] = v;
           }
         }
-        if ((tr >> 1) == ((k2 & 15) >> 1)) {   // publish rows k + 2 and k + 3 of X
+        if (INV && (tr >> 1) == ((k2 & 15) >> 1)) {   // publish rows k + 2 and k + 3 of X
           const int h = tr & 1;
           float* xn = xrow[buf ^ 1][h];
 #pragma unroll
@@ -339,7 +362,7 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
     }
   }
   __syncthreads();
-  if (tid < T) sc[tid] = tid < bw ? sqrtf(piv[tid]) * rd[tid] : 1.f;   // sqrt(d) / d = 1 / L_kk
+  if (tid < T) sc[tid] = tid < bw ? sqrt_r(piv[tid]) * rd[tid] : R(1);   // sqrt(d) / d = 1 / L_kk
   __syncthreads();
 #pragma unroll
   for (int p = 0; p < 4; p++)
@@ -348,20 +371,35 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
       const int i = tr + 16 * p, j = tc + 16 * q;
       float li = 0.f;
       if (own >> (4 * p + q) & 1) {
-        D[i * T + j] = i == j ? (double)sqrtf(piv[i]) : (double)(a[p][q] * sc[j]);
-        li = x[p][q] * sc[i];
+        if (STORE_L) D[i * T + j] = i == j ? (double)sqrt_r(piv[i]) : (double)(a[p][q] * sc[j]);
+        li = x[p][q] * (float)sc[i];
       }
-      DI[i * T + j] = li;
+      if (INV) DI[i * T + j] = li;
     }
 }
 
-__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
-                                                           double* __restrict__ dg, int64_t DE,
-                                                           int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
+// The FP32 elimination of diagonal tile kb of each front of a step (its inverse; L_11 too if STORE_L).
+template <bool STORE_L>
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
+                                                              double* __restrict__ dg, int64_t DE,
+                                                              int32_t* __restrict__ notpd, float* __restrict__ dinv32) {
   const int32_t s = fronts[blockIdx.x];
   const int b = blockIdx.y;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  potrf_tile(dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T, notpd + b);
+  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T,
+                                   notpd + b);
+}
+
+// L_11 of every diagonal tile of the large fronts in FP64 (tile t of the launch: front fronts[t], block kb[t];
+// proposal blockIdx.y), from the FP64 tile as the factorization left it.
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_tiles64(const int32_t* __restrict__ fronts,
+                                                                 const int32_t* __restrict__ kbs, DevPlan dp,
+                                                                 double* __restrict__ dg, int64_t DE,
+                                                                 int32_t* __restrict__ notpd) {
+  const int32_t s = fronts[blockIdx.x], kb = kbs[blockIdx.x];
+  const int b = blockIdx.y;
+  const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
+  potrf_tile<double, false, true>(dg + off, nullptr, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T, notpd + b);
 }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -481,11 +519,12 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 // [0, n2) of the list have block kb + 1. POTRF of tile kb; then, for those fronts, L_21 = A_21 inv(L_11)^T (the
 // 64 rows of block kb + 1 in block column kb, with their TF32 pair), A_22 -= L_21 L_21^T into the FP64 tile of
 // block kb + 1 (FP32 products, as the tensor-core updates give it), and the POTRF of that tile. One CTA per front.
-__global__ void __launch_bounds__(POTRF_THREADS) k_potrf32_pair(const int32_t* __restrict__ fronts, int n2, int kb,
-                                                                DevPlan dp, float* __restrict__ p32,
-                                                                float* __restrict__ oph, float* __restrict__ opl,
-                                                                double* __restrict__ dg, float* __restrict__ dinv32,
-                                                                int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
+template <bool STORE_L>
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __restrict__ fronts, int n2, int kb,
+                                                              DevPlan dp, float* __restrict__ p32,
+                                                              float* __restrict__ oph, float* __restrict__ opl,
+                                                              double* __restrict__ dg, float* __restrict__ dinv32,
+                                                              int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
   __shared__ __align__(16) float BsT[T * TS];
   __shared__ __align__(16) float IsT[T * TS];
   const int fi = blockIdx.x;
@@ -495,7 +534,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf32_pair(const int32_t* _
   const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int32_t first = dp.sn_first[s] + c0;
-  potrf_tile(dg + off, dinv32 + off, bw1, first, notpd + b);
+  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, bw1, first, notpd + b);
   if (fi >= n2) return;
   const int bw2 = min(T, w - c1);
   const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
@@ -520,7 +559,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf32_pair(const int32_t* _
       const int i = tr + e, j = tc + f;
       if (j <= i && i < bw2) D2[i * T + j] -= (double)g[e][f];
     }
-  potrf_tile(D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
+  potrf_tile<float, true, STORE_L>(D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
 }
 
 // The TRSM of a pair of block columns kb, kb + 1: for each 64-row tile below the pair (below block kb alone for
@@ -1165,9 +1204,9 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
         }
         {
           ProfScope ps_(ctx, KC_POTRF, B * (stp.potrf_flops + st2.potrf_flops));
-          k_potrf32_pair<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp,
-                                                                        f->panels32, f->op_hi, f->op_lo, f->diag,
-                                                                        f->dinv32, P32E, DE, f->notpd);
+          auto kp = f->diag_fp32 ? k_potrf_pair<true> : k_potrf_pair<false>;
+          kp<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp, f->panels32, f->op_hi,
+                                                            f->op_lo, f->diag, f->dinv32, P32E, DE, f->notpd);
           GP_CHECK_LAUNCH(ctx);
         }
         if (stp.pair_total > 0) {
@@ -1195,8 +1234,8 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       }
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
-        k_potrf32<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, stp.kb, dp, f->diag, DE,
-                                                                               f->notpd, f->dinv32);
+        auto kd = f->diag_fp32 ? k_potrf_diag<true> : k_potrf_diag<false>;
+        kd<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, stp.kb, dp, f->diag, DE, f->notpd, f->dinv32);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.trsm_total > 0) {
@@ -1212,5 +1251,11 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                       stp.n_group, stp.kb, 2);
       }
     }
+  }
+  if (!f->diag_fp32 && !sp.large_fronts.empty()) {   // L_11 of every diagonal tile in FP64
+    ProfScope ps_(ctx, KC_POTRF);
+    k_potrf_tiles64<<<dim3((unsigned)sp.large_fronts.size(), B), POTRF_THREADS, 0, st>>>(
+        dp.large_fronts, dp.large_kb, dp, f->diag, DE, f->notpd);
+    GP_CHECK_LAUNCH(ctx);
   }
 }

@@ -156,6 +156,26 @@ extern "C" const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.
 
 extern "C" int64_t gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+extern "C" gp_status gp_set_option(gp_ctx* ctx, int option, int64_t value) {
+  if (!ctx) return GP_ERR_ARG;
+  switch (option) {
+    case GP_OPT_DIAG_FP32:
+      if (value != 0 && value != 1) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_DIAG_FP32 takes 0 or 1"});
+      ctx->opt_diag_fp32 = (int)value;
+      return GP_OK;
+    default:
+      return fail(ctx, GpError{GP_ERR_ARG, "unknown option " + std::to_string(option)});
+  }
+}
+
+extern "C" gp_status gp_get_option(const gp_ctx* ctx, int option, int64_t* value) {
+  if (!ctx || !value) return GP_ERR_ARG;
+  switch (option) {
+    case GP_OPT_DIAG_FP32: *value = ctx->opt_diag_fp32; return GP_OK;
+    default: return GP_ERR_ARG;
+  }
+}
+
 namespace {
 void prof_collect(gp_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
@@ -428,6 +448,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->ps = ps;
     f->B = B;
     f->prec = prec;
+    f->diag_fp32 = prec == GP_MIXED && ctx->opt_diag_fp32 != 0;
     ThetaDims td{thetas[0].d, thetas[0].n1, thetas[0].n2, thetas[0].bump_dims};
     GP_REQUIRE(td.d == ps->d, "theta.d differs from the point set dimension");
     GP_REQUIRE(td.n1 >= 0 && td.n1 <= GP_MAX_N1, "n1 must be in 0..32");
@@ -636,6 +657,7 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
   for (auto& b : f->bufs) bytes += (int64_t)b.bytes;
   info->bytes = bytes;
   info->not_pd_count = 0;
+  info->diag_fp32 = f->diag_fp32 ? 1 : 0;
   for (int b = 0; b < f->B; b++) {   // flags hold the smallest failing permuted column, INT_MAX if none
     bool bad = flags[b] != 0x7fffffff;
     if (bad) info->not_pd_count++;

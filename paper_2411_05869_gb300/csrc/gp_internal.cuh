@@ -76,6 +76,8 @@ struct gp_ctx {
   int64_t prof_n[KC_COUNT] = {};
   double prof_flops[KC_COUNT] = {};
   cudaEvent_t prof_open = nullptr;
+  // options (gp_set_option)
+  int opt_diag_fp32 = 0;     // GP_MIXED factors created afterwards factor their diagonal blocks in FP32
 };
 
 // RAII timer of one launch (no-op unless profiling); `flops` is the useful work the launch performs.
@@ -252,6 +254,7 @@ struct gp_factor_s {
   std::vector<DevBuf> bufs;
   int B = 0;
   gp_precision prec = GP_FP64;
+  bool diag_fp32 = false;       // GP_MIXED: diagonal blocks factored in FP32 (default FP64)
   double* theta_dev = nullptr;  // B packed settings
   int64_t theta_stride = 0;
   double* F = nullptr;          // B x n x n1 bump features

@@ -42,7 +42,12 @@ class PointsetInfo(ctypes.Structure):
 
 
 class FactorInfo(ctypes.Structure):
-    _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32)]
+    _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32),
+                ("diag_fp32", ctypes.c_int32)]
+
+
+GP_OPT_DIAG_FP32 = 0
+OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32}
 
 
 class GpRequest(ctypes.Structure):
@@ -72,7 +77,8 @@ SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_points
            "gp_predict", "gp_launch_count", "gp_profile", "gp_profile_read", "gp_factor_bytes",
            "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_symbolic_host", "gp_symbolic_info",
            "gp_symbolic_export", "gp_symbolic_free", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
-           "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy"]
+           "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy",
+           "gp_set_option", "gp_get_option"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7, "update_left": 9}
 
@@ -141,6 +147,10 @@ def load(build_if_missing: bool = True):
     L.gp_predict.argtypes = [P, P, c_int, P, c_i64, P, P]
     L.gp_launch_count.restype = c_i64
     L.gp_launch_count.argtypes = [P]
+    L.gp_set_option.restype = c_int
+    L.gp_set_option.argtypes = [P, c_int, c_i64]
+    L.gp_get_option.restype = c_int
+    L.gp_get_option.argtypes = [P, c_int, ctypes.POINTER(c_i64)]
     L.gp_profile.restype = c_int
     L.gp_profile.argtypes = [P, c_int]
     L.gp_profile_read.restype = c_int
@@ -238,6 +248,15 @@ class Context:
 
     def launches(self) -> int:
         return int(self.lib.gp_launch_count(self.h))
+
+    def set_option(self, name: str, value: int):
+        """gp_set_option by name (OPTIONS): applies to the context's later calls."""
+        self.check(self.lib.gp_set_option(self.h, OPTIONS[name], int(value)))
+
+    def get_option(self, name: str) -> int:
+        v = c_i64()
+        self.check(self.lib.gp_get_option(self.h, OPTIONS[name], ctypes.byref(v)))
+        return int(v.value)
 
     def profile(self, enable: bool):
         """Start (clearing counters) or stop the per-kernel-class launch profiler."""

@@ -157,12 +157,19 @@ def test_edge_sizes(ctx, n, d):
 MIXED_RTOL = 1e-6
 
 
-def test_loglik_mixed_matches_oracle(case, ctx):
-    """GP_MIXED: TF32 tensor-core updates, FP64-accumulated diagonal tiles, FP64 refinement; loglik within 1e-6."""
+@pytest.mark.parametrize("diag_fp32", [0, 1])
+def test_loglik_mixed_matches_oracle(case, ctx, diag_fp32):
+    """GP_MIXED: TF32 tensor-core updates, FP64-accumulated diagonal tiles factored in FP64 (default) or in FP32
+    (GP_OPT_DIAG_FP32), FP64 refinement; loglik within 1e-6."""
     from paper_2411_05869_gb300 import gp
     w, ps = case["w"], case["ps"]
     ref = oracle.sparse_loglik(w.hyper, w.X, case["rp"], case["col"], case["perm"], w.resid, want_alpha=True)
-    f = ctx.factor(ps, [w.hyper], gp.GP_MIXED)
+    ctx.set_option("diag_fp32", diag_fp32)
+    try:
+        f = ctx.factor(ps, [w.hyper], gp.GP_MIXED)
+    finally:
+        ctx.set_option("diag_fp32", 0)
+    assert f.info()["diag_fp32"] == diag_fp32
     err = torch.empty(1, dtype=torch.float64, device="cuda")
     ll = float(f.loglik(_dev(w.resid), err=err).cpu()[0])
     assert abs(ll - ref["loglik"]) <= MIXED_RTOL * abs(ref["loglik"]), (ll, ref["loglik"])
