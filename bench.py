@@ -29,7 +29,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MEASURED_FP64_TFLOPS = 1.011   # FP64 FMA throughput measured on this GB300 pool
+# FP64 FMA throughput of a GB300 of this machine, measured with a dependent-free FP64 FMA loop over all SMs (the FP64
+# path's A7 kernels are bound by it; FP64 tensor-core DMMA measured no faster on this part)
+MEASURED_FP64_TFLOPS = 1.011
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
 
@@ -158,12 +160,73 @@ class OracleLeg:
 
     def step(self, theta) -> float:
         t0 = time.perf_counter()
-        self.oracle.sparse_loglik(theta, self.X, self.rp, self.col, self.perm, self.r)
+        self.last = self.oracle.sparse_loglik(theta, self.X, self.rp, self.col, self.perm, self.r)["loglik"]
+        return time.perf_counter() - t0
+
+    def step_threads(self, thetas, threads: int) -> float:
+        """One evaluation per setting, `threads` at a time on host threads (the oracle's C call releases the
+        interpreter lock, so the evaluations run in parallel); returns the wall time of all of them."""
+        import concurrent.futures as cf
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda th: self.oracle.sparse_loglik(th, self.X, self.rp, self.col, self.perm, self.r),
+                        thetas))
         return time.perf_counter() - t0
 
     def describe(self, t_eval: float) -> str:
         return (f"{self.desc}; oracle sparse loglik {t_eval:.2f} s per evaluation ({self.sample_flops:.3g} flops), "
                 f"projected to the full workload by the flop ratio x{self.scale:.4g}")
+
+
+def host_cpu():
+    """The host's cores and CPU model (the oracle baseline runs there)."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            key = ln.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or "unknown"}
+
+
+def subwindow_parity(ctx, leg, theta, prec_list):
+    """The GPU path on the oracle leg's sub-window, against the oracle's log-likelihood for the same setting."""
+    import torch
+    from paper_2411_05869_gb300 import gp
+    dev = torch.device("cuda", ctx.device)
+    st = ctx.stream
+    with torch.cuda.stream(st):
+        X = torch.as_tensor(leg.X, dtype=torch.float64, device=dev)
+        r = torch.as_tensor(leg.r, dtype=torch.float64, device=dev)
+    st.synchronize()
+    ps = ctx.assemble(X, theta.core_radius)
+    ref = leg.oracle.sparse_loglik(theta, leg.X, leg.rp, leg.col, leg.perm, leg.r)["loglik"]
+    out = {"points": int(leg.X.shape[0]), "oracle_loglik": float(ref),
+           "structure_bit_exact": bool(np.array_equal(ps.export("col"), leg.col) and
+                                       np.array_equal(ps.export("perm"), leg.perm))}
+    for name, prec in prec_list:
+        f = ctx.factor(ps, [theta], prec)
+        with torch.cuda.stream(st):
+            o = f.loglik(r)
+        st.synchronize()   # the log-likelihood is written on the library's stream
+        ll = float(o.cpu()[0])
+        f.free()
+        out[f"{name}_loglik"] = ll
+        out[f"{name}_rel_err"] = abs(ll - ref) / abs(ref)
+    ps.free()
+    return out
 
 
 # ------------------------------------------------------------------------------------------------ GPU leg
@@ -179,6 +242,7 @@ def run_gpu(args, rank, world, local_rank):
     prec = gp.GP_MIXED if args.precision == "mixed" else gp.GP_FP64
     stream = torch.cuda.Stream(device=dev)
     ctx = gp.Context(local_rank, stream=stream)
+    ctx.set_option("diag_fp32", int(args.diag_fp32))
     with torch.cuda.stream(stream):
         X = torch.as_tensor(w.X, dtype=torch.float64, device=dev)
         resid = torch.as_tensor(w.resid, dtype=torch.float64, device=dev)
@@ -289,8 +353,9 @@ def run_gpu(args, rank, world, local_rank):
                autotune=tune, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
                h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
-    # FP64 comparison (mixed runs only): one evaluation of the same setting through the FP64 path, timed from
-    # the call that creates (allocates and factors) the FP64 factor to its log-likelihood
+    # FP64 comparison (mixed runs only): the same settings through the FP64 path. The factor is created (allocated
+    # and factored once) outside the timing; then --fp64-steps steady-state steps of update + loglik are timed
+    # with CUDA events, like the mixed steps, for p50/p99.
     if prec == gp.GP_MIXED and args.fp64_steps > 0:
         nb = min(Bc, args.fp64_proposals)
         ths = thetas[:Bc]
@@ -299,27 +364,36 @@ def run_gpu(args, rank, world, local_rank):
         stream.synchronize()   # out is written on the library's stream
         ll_mixed = out.cpu().numpy()[:nb].copy()
         f.free()   # room for the FP64 factor
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r64 = resid_b[:nb] if nb > 1 else resid
         stream.synchronize()
         with torch.cuda.stream(stream):
-            e0.record(stream)
             f64 = ctx.factor(ps, ths[:nb], gp.GP_FP64)
-            out64 = f64.loglik(resid_b[:nb] if nb > 1 else resid)
-            e1.record(stream)
+            out64 = f64.loglik(r64)
+            stream.synchronize()
+            ll64 = out64.cpu().numpy()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps + 1)]
+            evs[0].record(stream)
+            for k in range(args.fp64_steps):
+                f64.update(ths[:nb])
+                f64.loglik(r64, out=out64)
+                evs[k + 1].record(stream)
         stream.synchronize()
-        ll64 = out64.cpu().numpy()
+        per64 = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.fp64_steps)]
         rel = np.abs(ll_mixed - ll64) / np.abs(ll64)
-        res["fp64"] = {"ms_per_step": e0.elapsed_time(e1) / nb, "evals_per_s": nb * 1e3 / e0.elapsed_time(e1),
+        res["fp64"] = {"ms_per_step": float(np.mean(per64)) / nb, "evals_per_s": nb * 1e3 / float(np.mean(per64)),
+                       "latency_ms": {"p50": float(np.percentile(per64, 50)), "p99": float(np.percentile(per64, 99)),
+                                      "steps": len(per64)},
                        "loglik": float(ll64[0]), "mixed_loglik": float(ll_mixed[0]),
                        "mixed_rel_diff": float(rel.max()), "proposals_compared": int(nb),
                        "mixed_rel_diff_per_proposal": [float(x) for x in rel] if nb > 1 else None,
-                       "note": f"FP64 path on {nb} of the settings (one factor creation, first factorization "
-                               "and loglik), per-evaluation time; mixed_rel_diff is the largest over them"}
+                       "note": f"FP64 path on {nb} of the settings: steady-state update + loglik steps (factor "
+                               "created before timing); mixed_rel_diff is the largest over the settings"}
         f64.free()
         f = None
     if f is not None:
         f.free()
     ps.free()
+    res["ctx"] = ctx
     return res
 
 
@@ -457,19 +531,25 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=os.environ.get("GP_BENCH_WORKLOAD", "station_1.2M"))
     ap.add_argument("--precision", default=os.environ.get("GP_BENCH_PRECISION", "mixed"), choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3, help="mixed runs: timed FP64 comparison steps (0: none)")
     ap.add_argument("--fp64-proposals", type=int, default=8, help="batched runs: proposals compared with FP64")
     ap.add_argument("--batch", type=int, default=0,
                     help="proposals per step (default: 64 for batched_200k, 16 chains for mcmc_200k, else 1)")
     ap.add_argument("--autotune", type=int, default=-1, help="1/0: tune the update blocking first (default: "
                                                               "on in mixed precision)")
     ap.add_argument("--blocking", default="", help="G,TN: fixed update blocking of mixed runs (no autotuner)")
+    ap.add_argument("--diag-fp32", action="store_true",
+                    help="mixed runs: factor the 64 x 64 diagonal blocks in FP32 (default FP64)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=0, help="host threads of the threaded oracle leg "
+                                                                   "(0: all cores)")
+    ap.add_argument("--subwindow-parity", type=int, default=1, help="1: the GPU path on the oracle's sub-window "
+                                                                    "against the oracle (FP64 and mixed)")
     ap.add_argument("--serve-sets", type=int, default=20)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-fp64-requests", type=int, default=12)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 1.0, 1.5])
     args = ap.parse_args()
@@ -492,21 +572,25 @@ def main():
         leg = OracleLeg(w, args.oracle_points, full_flops)
         from paper_2411_05869_gb300 import synth
         rng = np.random.default_rng(1234)
-        ts = []
+        cpu = host_cpu()
+        thr = max(1, args.oracle_threads or cpu["nproc"] or 1)
+        ts = []   # per step: `thr` evaluations of the sample, one per host thread
         for k in range(max(args.warmup, 0) + args.steps):
-            dt = leg.step(synth.perturb(rng, w.hyper, 0.05))
+            dt = leg.step_threads([synth.perturb(rng, w.hyper, 0.05) for _ in range(thr)], thr)
             if k >= args.warmup:
                 ts.append(dt)
-        t_eval = float(np.mean(ts)) * leg.scale
-        value = 1.0 / t_eval
+        t_step = float(np.mean(ts)) * leg.scale          # projected wall time of thr full evaluations
+        value = thr / t_step
         line = {"impl": "reference", "metric": metric, "value": value, "unit": "evals/s", "n_gpus": 0,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_eval * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(w, args.workload, "fp64"),
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / thr,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(w, args.workload, "fp64"),
                 "latency_ms": {"p50": float(np.percentile(ts, 50)) * leg.scale * 1e3,
                                "p99": float(np.percentile(ts, 99)) * leg.scale * 1e3},
-                "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                                 "sample": leg.describe(float(np.mean(ts)))},
+                "cpu_baseline": {"value": value, "unit": "evals/s", "cores": thr, "kind": "oracle",
+                                 "cpu": cpu,
+                                 "sample": leg.describe(float(np.mean(ts))) +
+                                           f"; {thr} settings per step, one per host thread"},
                 "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -540,14 +624,19 @@ def main():
     a7 = ["extend_add", "front_small", "potrf", "trsm", "update", "update_left"]
     t_a7 = sum(prof[k][0] for k in a7)
     flops = info["flops"]
-    if args.precision == "mixed":
-        peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
-        bound, peak_note = "tensor", f"TF32 = {peak_src} bf16 burst x nominal 1.1/2.25 (of {peak_src})"
+    if args.precision == "mixed":   # the kernel runs inside a seconds-long step: the sustained figure applies
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_TF32_OVER_BF16
+        bound, peak_note = "tensor", f"TF32 = {peak_src} bf16 sustained x nominal 1.1/2.25 (of {peak_src})"
     else:
         peak = MEASURED_FP64_TFLOPS
         bound, peak_note = "alu", "FP64 FMA throughput measured on this pool"
     dom = max(a7, key=lambda k: prof[k][0])
-    d_ms, d_n, d_fl = prof[dom]
+    d_ms, d_n, d_fl_front = prof[dom]
+    # The classes count the flops of the relaxed fronts (explicit zeros included); the algorithmic work is
+    # sum_j eta_j^2 over the exact column counts, so each class's count is scaled by the ratio of the two totals.
+    front_total = sum(prof[k][2] for k in ("potrf", "trsm", "update", "update_left"))
+    alg_ratio = (res["B"] * flops / front_total) if front_total > 0 else 1.0
+    d_fl = d_fl_front * alg_ratio
     achieved = d_fl / (d_ms * 1e-3) / 1e12 if d_ms > 0 else 0.0
     kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "useful_tflops": (round(v[2] / (v[0] * 1e-3) / 1e12, 3)
                                                                             if v[0] > 0 and v[2] > 0 else None)}
@@ -568,13 +657,16 @@ def main():
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get((args.workload, dom) + _blocking_of(res)),
                      "launches_per_step": d_n, "avg_launch_ms": d_ms / max(d_n, 1),
-                     "algorithmic": f"useful flops of the class per step = {d_fl:.4g} (per launch "
-                                    f"{d_fl / max(d_n, 1):.4g}); A7 total sum_j eta_j^2 = {flops:.4g}",
+                     "algorithmic": f"algorithmic flops of the class per step = {d_fl:.4g} (per launch "
+                                    f"{d_fl / max(d_n, 1):.4g}): its relaxed-front flops {d_fl_front:.4g} x "
+                                    f"{alg_ratio:.4f} (sum_j eta_j^2 = {flops:.4g} per proposal over the relaxed-front "
+                                    f"flops of all A7 classes)",
                      "peak_source": peak_note,
                      "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over the class's "
                                         "launches of one factorization at this blocking (L2 cold at each launch under "
                                         "ncu)") if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
-                     "a7_total": {"ms": t_a7, "achieved": flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
+                     "a7_total": {"ms": t_a7, "proposals": res["B"],
+                                  "achieved": res["B"] * flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
         "kernels": kernels,
         "e2e": {"value": res["e2e_steps"] * res["B"] / res["e2e_s"], "unit": "evals/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"]},
@@ -589,14 +681,32 @@ def main():
     if res.get("autotune"):
         line["autotune"] = res["autotune"]
     if world == 1 and not args.no_cpu_baseline:
+        cpu = host_cpu()
         try:
             leg = OracleLeg(res["w"], args.oracle_points, flops)
             dt = leg.step(res["w"].hyper)
             line["cpu_baseline"] = {"value": 1.0 / (dt * leg.scale), "unit": "evals/s", "cores": 1,
-                                    "kind": "oracle", "sample": leg.describe(dt)}
+                                    "kind": "oracle", "cpu": cpu, "sample": leg.describe(dt)}
+            thr = max(1, args.oracle_threads or cpu["nproc"] or 1)
+            if thr > 1:
+                from paper_2411_05869_gb300 import synth
+                rng = np.random.default_rng(99)
+                dtt = leg.step_threads([synth.perturb(rng, res["w"].hyper, 0.05) for _ in range(thr)], thr)
+                line["cpu_baseline_threads"] = {"value": thr / (dtt * leg.scale), "unit": "evals/s", "cores": thr,
+                                                "kind": "oracle", "sample": f"{thr} settings at once, one per host "
+                                                f"thread, on the same sample ({dtt:.2f} s wall)"}
         except Exception as e:  # the baseline is reported, never required
-            line["cpu_baseline"] = {"value": None, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": "evals/s", "cores": 1, "kind": "oracle", "cpu": cpu,
                                     "sample": f"failed: {e}"}
+            leg = None
+        if leg is not None and args.subwindow_parity:
+            from paper_2411_05869_gb300 import gp
+            ctx = res["ctx"]
+            try:
+                line["subwindow_parity"] = subwindow_parity(ctx, leg, res["w"].hyper,
+                                                            [("fp64", gp.GP_FP64), ("mixed", gp.GP_MIXED)])
+            except Exception as e:
+                line["subwindow_parity"] = {"failed": str(e)}
     print(json.dumps(line))
 
 
@@ -607,7 +717,8 @@ KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 2
 KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
                         "extend_add": "k_extend_add"}
 
-# DRAM bytes per launch of the dominant kernel, from ncu (profiles/), by (workload, class, update blocking);
+# DRAM bytes per launch of the dominant kernel, from an ncu capture of this kernel's launches, by (workload, class,
+# update blocking);
 # None where no capture of the current kernel at that blocking exists
 _TRAFFIC = {("station_1.2M", "update", 16, 256): 2.712e9}
 

@@ -27,12 +27,16 @@ P = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, no vectorisation assumptions, no FMA contraction)."""
+    """Compile the oracle with gcc (plain C, no vectorisation assumptions, no FMA contraction). The brute-force
+    pattern's independent rows run on OpenMP threads when gcc has OpenMP (same results); otherwise serially."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -76,6 +80,7 @@ def lib():
         L.or_sparse_factor.restype = c_i64
         L.or_sparse_factor.argtypes = [c_i64, P, P, P, P, P, P, P, P, P, c_i64]
         L.or_predict.argtypes = [c_i64, c_i64, P, P, P, P, P, P, P]
+        L.or_csr_values.argtypes = [c_i64, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -333,3 +338,14 @@ def predict(hp, X, alpha, Xtest, mu_test=None) -> np.ndarray:
     mu = None if mu_test is None else _f64(mu_test)
     lib().or_predict(X.shape[0], m, _p(dims), _p(th), _p(X), _p(a), _p(Xt), _p(mu), _p(mean))
     return mean
+
+
+def csr_values(hp, X, rowptr, col) -> np.ndarray:
+    """C_z (Eq. Zcov) at the entries of a CSR pattern, rows in index order."""
+    X = _f64(X)
+    dims, th = theta_block(hp)
+    rp = np.ascontiguousarray(rowptr, np.int64)
+    cc = np.ascontiguousarray(col, np.int32)
+    val = np.empty(cc.shape[0])
+    lib().or_csr_values(X.shape[0], _p(dims), _p(th), _p(X), _p(rp), _p(cc), _p(val))
+    return val

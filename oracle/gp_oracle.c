@@ -19,6 +19,7 @@
  *   or_dense_chol, or_dense_loglik, or_sample_dense   dense Cholesky, log-likelihood of Sec. 3.3
  *   or_sparse_chol, or_sparse_loglik                  left-looking sparse Cholesky, same log-likelihood
  *   or_predict           predictive mean m = mu* + C_{y,z} C_z^{-1} r (Sec. 3.2)
+ *   or_csr_values        C_z on a given pattern (the matrix of the iterative path of Sec. 3.3)
  *
  * Hyperparameter block (theta, doubles), used by every kernel function:
  *   [0] core_var, [1..d] core_radius, [1+d] s0, [2+d..1+2d] r0, [2+2d] noise_var,
@@ -165,9 +166,11 @@ static int in_support(const double* xi, const double* xj, const double* rho, int
   return s < 1.0;
 }
 
-/* Row counts (rowcnt[n]) of the full symmetric pattern; returns total. */
+/* Row counts (rowcnt[n]) of the full symmetric pattern; returns total. Rows are independent, so they may be
+ * spread over threads (OpenMP, when the oracle is built with it) without changing any result. */
 int64_t or_pattern_count(int64_t n, int d, const double* X, const double* rho, int64_t* rowcnt) {
   int64_t tot = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : tot)
   for (int64_t i = 0; i < n; i++) {
     int64_t c = 0;
     for (int64_t j = 0; j < n; j++) c += in_support(X + i * d, X + j * d, rho, d);
@@ -179,6 +182,7 @@ int64_t or_pattern_count(int64_t n, int d, const double* X, const double* rho, i
 
 /* CSR fill: rowptr[n+1] must hold the prefix sums of or_pattern_count; columns ascending. */
 void or_pattern_fill(int64_t n, int d, const double* X, const double* rho, const int64_t* rowptr, int32_t* col) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t i = 0; i < n; i++) {
     int64_t o = rowptr[i];
     for (int64_t j = 0; j < n; j++)
@@ -820,5 +824,23 @@ void or_predict(int64_t n, int64_t m, const int* dims, const double* th, const d
     }
     mean[k] = (mu_t ? mu_t[k] : 0.0) + acc;
   }
+  free(F);
+}
+
+/* ---------------------------------------------------------------- C_z on a given pattern (Sec. 3.1, Eq. Zcov) */
+/* val[e] = C_y(x_i, x_col[e]) + tau^2 [i = col[e]] for every entry e of row i of a CSR pattern: the matrix the
+ * iterative path (stochastic Lanczos log-determinant, MINRES) multiplies by. */
+void or_csr_values(int64_t n, const int* dims, const double* th, const double* X, const int64_t* rowptr,
+                   const int32_t* col, double* val) {
+  hyp_t p = unpack(dims, th);
+  double* F = (double*)malloc(sizeof(double) * (size_t)(n * (p.n1 > 0 ? p.n1 : 1)));
+  or_features(n, dims, th, X, F);
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+      int64_t j = col[e];
+      double v = cy_f(&p, X + i * p.d, X + j * p.d, F + i * p.n1, F + j * p.n1);
+      if (i == j) v = v + p.noise_var;
+      val[e] = v;
+    }
   free(F);
 }
