@@ -81,6 +81,9 @@ def lib():
         L.or_sparse_factor.argtypes = [c_i64, P, P, P, P, P, P, P, P, P, c_i64]
         L.or_predict.argtypes = [c_i64, c_i64, P, P, P, P, P, P, P]
         L.or_csr_values.argtypes = [c_i64, P, P, P, P, P, P]
+        L.or_pattern_count_sparse.restype = c_i64
+        L.or_pattern_count_sparse.argtypes = [c_i64, P, P, P, P]
+        L.or_pattern_fill_sparse.argtypes = [c_i64, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -94,10 +97,13 @@ def _f64(a):
 
 
 def theta_block(hp):
-    """(dims int32[4], theta float64[]) in the oracle's layout from a synth.Hyper."""
-    dims = np.array([hp.d, hp.n1, hp.n2, hp.bump_dims], dtype=np.int32)
-    th = np.concatenate([[hp.core_var], hp.core_radius, [hp.s0], hp.r0, [hp.noise_var],
-                         hp.h, hp.a, hp.b, hp.r]).astype(np.float64)
+    """(dims int32[5], theta float64[]) in the oracle's layout from a synth.Hyper."""
+    kind = int(getattr(hp, "core_kind", 0))
+    dims = np.array([hp.d, hp.n1, hp.n2, hp.bump_dims, kind], dtype=np.int32)
+    parts = [[hp.core_var], hp.core_radius, [hp.s0], hp.r0, [hp.noise_var], hp.h, hp.a, hp.b, hp.r]
+    if kind == 1:
+        parts += [[hp.sigma0, hp.Sigma0], hp.phi_sigma, hp.phi_Sigma]
+    th = np.concatenate(parts).astype(np.float64)
     return dims, th
 
 
@@ -155,6 +161,21 @@ def pattern(X, rho):
     np.cumsum(cnt, out=rowptr[1:])
     col = np.empty(int(rowptr[-1]), dtype=np.int32)
     lib().or_pattern_fill(n, d, _p(X), _p(rho), _p(rowptr), _p(col))
+    return rowptr, col
+
+
+def pattern_sparse(hp, X):
+    """The support of C_sparse by brute force (the pattern with the non-compact core of App. B): pairs with q0 < 1
+    for the radii r0, or both inside one bump family's support. (rowptr int64[n+1], col int32[nnz])."""
+    X = _f64(X)
+    n = X.shape[0]
+    dims, th = theta_block(hp)
+    cnt = np.zeros(n, dtype=np.int64)
+    lib().or_pattern_count_sparse(n, _p(dims), _p(th), _p(X), _p(cnt))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt, out=rowptr[1:])
+    col = np.empty(int(rowptr[-1]), dtype=np.int32)
+    lib().or_pattern_fill_sparse(n, _p(dims), _p(th), _p(X), _p(rowptr), _p(col))
     return rowptr, col
 
 

@@ -20,11 +20,14 @@
  *   or_sparse_chol, or_sparse_loglik                  left-looking sparse Cholesky, same log-likelihood
  *   or_predict           predictive mean m = mu* + C_{y,z} C_z^{-1} r (Sec. 3.2)
  *   or_csr_values        C_z on a given pattern (the matrix of the iterative path of Sec. 3.3)
+ *   core_paciorek        the parametric nonstationary Matern core of App. B (Eq. PScov), a non-compact core
+ *   or_pattern_*_sparse  brute-force support of C_sparse (the pattern with a non-compact core)
  *
  * Hyperparameter block (theta, doubles), used by every kernel function:
  *   [0] core_var, [1..d] core_radius, [1+d] s0, [2+d..1+2d] r0, [2+2d] noise_var,
  *   then h (n1*n2*bump_dims), a (n1*n2), b (n1*n2), r (n1*n2).
- * Integer block (dims): d, n1, n2, bump_dims.
+ *   With the non-compact core (kind 1) the block continues with sigma0, Sigma0, phi_sigma (d), phi_Sigma (d).
+ * Integer block (dims): d, n1, n2, bump_dims, core kind (0 compact Wendland, 1 parametric nonstationary Matern).
  */
 #include <math.h>
 #include <stdint.h>
@@ -37,6 +40,9 @@ typedef struct {
   int d, n1, n2, bd;
   double core_var, s0, noise_var;
   const double *core_radius, *r0, *h, *a, *b, *r;
+  int kind;                       /* 0: compact Wendland core; 1: parametric nonstationary Matern core (App. B) */
+  double sigma0, Sigma0;
+  const double *phi_sigma, *phi_Sigma;
 } hyp_t;
 
 static hyp_t unpack(const int* dims, const double* th) {
@@ -52,6 +58,16 @@ static hyp_t unpack(const int* dims, const double* th) {
   p.a = p.h + nb * p.bd;
   p.b = p.a + nb;
   p.r = p.b + nb;
+  p.kind = dims[4];
+  p.sigma0 = p.Sigma0 = 1.0;
+  p.phi_sigma = p.phi_Sigma = NULL;
+  if (p.kind == 1) {
+    const double* c = p.r + nb;
+    p.sigma0 = c[0];
+    p.Sigma0 = c[1];
+    p.phi_sigma = c + 2;
+    p.phi_Sigma = c + 2 + d;
+  }
   return p;
 }
 
@@ -113,7 +129,42 @@ static double csparse_f(const hyp_t* p, const double* xi, const double* xj, cons
   return acc;
 }
 
+/* Matern correlation of smoothness 3/2: M(t) = (1 + sqrt(3) t) exp(-sqrt(3) t). */
+static double matern32(double t) {
+  double st = sqrt(3.0) * t;
+  return (1.0 + st) * exp(-st);
+}
+
+/* The parametric nonstationary core of App. B (Eq. PScov), locally isotropic, smoothness 3/2:
+ *   C(x, x') = sigma(x) sigma(x') (Sigma(x) Sigma(x'))^(d/4) / ((Sigma(x) + Sigma(x')) / 2)^(d/2) M(sqrt(Q)),
+ *   Q = |x - x'|^2 / ((Sigma(x) + Sigma(x')) / 2),
+ * with log sigma(x) = log sigma0 + sum_k phi_sigma_k x_k and log Sigma(x) = log Sigma0 + sum_k phi_Sigma_k x_k.
+ * (The printed denominator repeats Sigma(x'); the average of Sigma(x) and Sigma(x') is the Paciorek form it cites.) */
+static double core_paciorek(const hyp_t* p, const double* x, const double* y) {
+  double lsx = log(p->sigma0), lsy = log(p->sigma0), lSx = log(p->Sigma0), lSy = log(p->Sigma0);
+  for (int k = 0; k < p->d; k++) {
+    lsx = lsx + p->phi_sigma[k] * x[k];
+    lsy = lsy + p->phi_sigma[k] * y[k];
+    lSx = lSx + p->phi_Sigma[k] * x[k];
+    lSy = lSy + p->phi_Sigma[k] * y[k];
+  }
+  double sx = exp(lsx), sy = exp(lsy), Sx = exp(lSx), Sy = exp(lSy);
+  double avg = (Sx + Sy) / 2.0;
+  double pref = sx * sy * pow(Sx * Sy, p->d / 4.0) / pow(avg, p->d / 2.0);
+  double r2 = 0.0;
+  for (int k = 0; k < p->d; k++) {
+    double dk = x[k] - y[k];
+    r2 = r2 + dk * dk;
+  }
+  return pref * matern32(sqrt(r2 / avg));
+}
+
 static double cy_f(const hyp_t* p, const double* xi, const double* xj, const double* fi, const double* fj) {
+  if (p->kind == 1) {
+    double cs = csparse_f(p, xi, xj, fi, fj);
+    if (cs == 0.0) return 0.0;
+    return core_paciorek(p, xi, xj) * cs;
+  }
   double wc = or_wendland(sqrt(q2_scaled(xi, xj, p->core_radius, p->d)));
   if (wc == 0.0) return 0.0;
   return (p->core_var * wc) * csparse_f(p, xi, xj, fi, fj);
@@ -843,4 +894,55 @@ void or_csr_values(int64_t n, const int* dims, const double* th, const double* X
       val[e] = v;
     }
   free(F);
+}
+
+
+/* ---------------------------------------------------------------- support of C_sparse (non-compact core) */
+/* With a non-compact core (App. B) C_y(x, x') != 0 only where C_sparse(x, x') can be: q0 < 1 for the Wendland
+ * radii r0 (u = x / r0 per coordinate, q0^2 as in the compact pattern), or x and x' both inside the support of one
+ * bump family i (|x - h_ij|^2 < r_ij^2 for some j, and the same for x' and some j'; Eq. bumpFcn, Eq. C_sparse).
+ * Structural: bumps count by their radii whatever their amplitudes. */
+static int in_family(const hyp_t* p, const double* x, int i) {
+  for (int j = 0; j < p->n2; j++) {
+    const double* h = p->h + (size_t)(i * p->n2 + j) * p->bd;
+    double s = 0.0;
+    for (int k = 0; k < p->bd; k++) {
+      double dk = x[k] - h[k];
+      s = s + dk * dk;
+    }
+    double r = p->r[i * p->n2 + j];
+    if (s < r * r) return 1;
+  }
+  return 0;
+}
+
+static int in_sparse_support(const hyp_t* p, const double* xi, const double* xj) {
+  if (in_support(xi, xj, p->r0, p->d)) return 1;
+  for (int i = 0; i < p->n1; i++)
+    if (in_family(p, xi, i) && in_family(p, xj, i)) return 1;
+  return 0;
+}
+
+int64_t or_pattern_count_sparse(int64_t n, const int* dims, const double* th, const double* X, int64_t* rowcnt) {
+  hyp_t p = unpack(dims, th);
+  int64_t tot = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : tot)
+  for (int64_t i = 0; i < n; i++) {
+    int64_t c = 0;
+    for (int64_t j = 0; j < n; j++) c += in_sparse_support(&p, X + i * p.d, X + j * p.d);
+    rowcnt[i] = c;
+    tot += c;
+  }
+  return tot;
+}
+
+void or_pattern_fill_sparse(int64_t n, const int* dims, const double* th, const double* X, const int64_t* rowptr,
+                            int32_t* col) {
+  hyp_t p = unpack(dims, th);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; i++) {
+    int64_t o = rowptr[i];
+    for (int64_t j = 0; j < n; j++)
+      if (in_sparse_support(&p, X + i * p.d, X + j * p.d)) col[o++] = (int32_t)j;
+  }
 }

@@ -42,10 +42,21 @@ class Hyper:
     b: np.ndarray
     r: np.ndarray
     noise_var: float
+    # core kind: 0 the compact Wendland-type core core_var * f0(q; core_radius); 1 the parametric nonstationary
+    # Matern core of App. B (Eq. PScov, smoothness 3/2) with log sigma(x) = log sigma0 + phi_sigma . x and
+    # log Sigma(x) = log Sigma0 + phi_Sigma . x (the coordinates as basis functions); then core_var and core_radius
+    # are unused and the support is that of C_sparse
+    core_kind: int = 0
+    sigma0: float = 1.0
+    Sigma0: float = 1.0
+    phi_sigma: Optional[np.ndarray] = None
+    phi_Sigma: Optional[np.ndarray] = None
 
     def copy(self) -> "Hyper":
+        cp = lambda a: None if a is None else a.copy()
         return dataclasses.replace(self, core_radius=self.core_radius.copy(), r0=self.r0.copy(), h=self.h.copy(),
-                                   a=self.a.copy(), b=self.b.copy(), r=self.r.copy())
+                                   a=self.a.copy(), b=self.b.copy(), r=self.r.copy(), phi_sigma=cp(self.phi_sigma),
+                                   phi_Sigma=cp(self.phi_Sigma))
 
     def validate(self) -> None:
         nb = self.n1 * self.n2
