@@ -100,15 +100,26 @@ typedef struct {
   int64_t bytes;              /* device bytes held by the factor */
   int32_t not_pd_count;       /* proposals whose factorization met a non-positive pivot */
   int32_t diag_fp32;          /* GP_MIXED: 1 if its 64 x 64 diagonal blocks are factored in FP32 (GP_OPT_DIAG_FP32) */
+  int32_t timed_out;          /* GP_MIXED: 1 if a bounded wait of the last factorization ran out (GP_ERR_TIMEOUT) */
 } gp_factor_info_t;
 
-/* Context options (gp_set_option). They apply to the calls made on the context afterwards.
- *   GP_OPT_DIAG_FP32: 0 (default) or 1. With 1, GP_MIXED factors created afterwards factor their 64 x 64
- *     diagonal blocks in FP32 from the FP64-accumulated block instead of in FP64. The blocks are accumulated in
- *     FP64 either way and the log-determinant is summed in FP64 from their diagonals; FP32 is faster on GB300
- *     (its FP64 pipe is slow) at the cost of an FP32-accurate diagonal of L in the log-determinant. */
+/* Context options (gp_set_option). They apply to the factors created on the context afterwards.
+ *   GP_OPT_DIAG_FP32: 0 (default) or 1. With 1, GP_MIXED factors factor their 64 x 64 diagonal blocks in FP32
+ *     from the FP64-accumulated block instead of in FP64. The blocks are accumulated in FP64 either way and the
+ *     log-determinant is summed in FP64 from their diagonals; FP32 is faster on GB300 (its FP64 pipe is slow) at
+ *     the cost of an FP32-accurate diagonal of L in the log-determinant.
+ *   GP_OPT_WAIT_POLLS (default 2^26, 1..2^32-1) and GP_OPT_WAIT_NS (default 1e9, >= 0): the limits of every
+ *     bounded wait of the GP_MIXED tensor-core kernels (an mbarrier phase awaited by one warp role from another:
+ *     operand copies landed, MMAs done, accumulator drained). A wait that runs out after that many polls or
+ *     nanoseconds records the failure in the factor and winds its kernel down (after waiting, with the default
+ *     limits, for the copies and MMAs it already issued); every later tensor-core launch of that factorization
+ *     skips its tiles. The factor then reports GP_ERR_TIMEOUT: gp_factor_info (timed_out = 1) and gp_loglik return
+ *     it, and the log-likelihoods are NaN. No legitimate wait comes near the defaults; tiny limits make waits run
+ *     out on purpose (a test of this path). The next gp_factor_update of the factor starts clean. */
 typedef enum {
-  GP_OPT_DIAG_FP32 = 0
+  GP_OPT_DIAG_FP32 = 0,
+  GP_OPT_WAIT_POLLS = 1,
+  GP_OPT_WAIT_NS = 2
 } gp_option;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
@@ -163,6 +174,35 @@ GP_API gp_status gp_symbolic_info(const gp_symbolic* sym, gp_pointset_info_t* in
 GP_API gp_status gp_symbolic_export(const gp_symbolic* sym, int what, void* host_dst, size_t bytes);
 GP_API void gp_symbolic_free(gp_symbolic* sym);
 
+/* ----------------------------------------------------------------------------- non-compact core (App. B)
+ * The core kernel of a setting (Sec. 2.2: any PSD kernel may serve as C_core). gp_hyper alone describes the compact
+ * Wendland-type core core_var f0(q; core_radius), whose support bounds the pattern. GP_CORE_PACIOREK selects the
+ * parametric nonstationary Matern core of App. B (Eq. PScov), locally isotropic with smoothness 3/2:
+ *   C_core(x, x') = sigma(x) sigma(x') (Sigma(x) Sigma(x'))^(d/4) / ((Sigma(x) + Sigma(x')) / 2)^(d/2) M(sqrt(Q)),
+ *   Q = |x - x'|^2 / ((Sigma(x) + Sigma(x')) / 2), M(t) = (1 + sqrt(3) t) exp(-sqrt(3) t),
+ *   log sigma(x) = log sigma0 + sum_k phi_sigma[k] x_k,  log Sigma(x) = log Sigma0 + sum_k phi_Sigma[k] x_k
+ * (the coordinates as the basis functions; core_var and core_radius of gp_hyper are then unused). This core is
+ * nowhere zero, so C_z is zero only outside the support of C_sparse (Eq. C_sparse): pairs with q0 < 1 for the radii
+ * r0, or with both points inside the support of one bump family (|x - h_ij| < r_ij for some j). That support depends
+ * on r0 and the bumps' centres and radii: the point set is assembled for them (gp_assemble_sparse_support) and
+ * serves every setting with the same r0, n1, n2, bump_dims, h and r (amplitudes, shapes, s0, noise and the core's
+ * parameters may vary). */
+typedef enum { GP_CORE_WENDLAND = 0, GP_CORE_PACIOREK = 1 } gp_core_kind;
+typedef struct {
+  int32_t kind;               /* gp_core_kind */
+  double sigma0, Sigma0;      /* baseline signal standard deviation and squared length scale (> 0) */
+  const double* phi_sigma;    /* [d] host */
+  const double* phi_Sigma;    /* [d] host */
+} gp_core;
+
+/* Steps A1, A2, A5, A6 with the support of C_sparse as the pattern (the non-compact core): pairs with
+ * sum_k (u_ik - u_jk)^2 < 1 for u = x / r0 (as gp_assemble computes it with core_radius = r0), or both points inside
+ * one bump family (sum over the leading bump_dims coordinates of (x_k - h_k)^2 < r^2 for some bump of the family,
+ * each operation rounded separately, in coordinate order). theta: host; its r0, n1, n2, bump_dims, h and r define
+ * the support. Synchronous. Errors: as gp_assemble; GP_ERR_ARG also for n1 > 32. */
+GP_API gp_status gp_assemble_sparse_support(gp_ctx* ctx, const double* d_X, int64_t n, int d, const gp_hyper* theta,
+                                            gp_pointset** ps);
+
 /* Steps A3, A4, A7 for B proposals sharing the point set: bump features, kernel values of the pattern
  * (fused with the scatter into supernodal panels) and the supernodal numeric Cholesky of P C_z P^T.
  * thetas: host array of B settings. Allocates the factor (B copies of the panels plus workspace).
@@ -173,16 +213,27 @@ GP_API gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas,
 /* Re-run A3, A4, A7 on an existing factor with B new settings (same B, precision and point set): the
  * allocation-free inner call of an MCMC loop. Asynchronous. Errors: GP_ERR_ARG, GP_ERR_CUDA. */
 GP_API gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas);
+/* gp_factor / gp_factor_update with a core per setting (cores: host array of B, NULL = the compact Wendland core
+ * of gp_hyper for all). The point set's support must fit the core: GP_CORE_WENDLAND on gp_assemble point sets,
+ * GP_CORE_PACIOREK on gp_assemble_sparse_support point sets with the settings' r0, h and r equal to the ones it was
+ * assembled with (GP_ERR_ARG otherwise). All B settings take the same kind. */
+GP_API gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, const gp_core* cores, int B,
+                                gp_precision precision, gp_factor_t** f);
+GP_API gp_status gp_factor_update_core(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas, const gp_core* cores);
 GP_API void gp_factor_free(gp_factor_t* f);
-/* Synchronous (reads the per-proposal pivot flags). */
+/* Synchronous (reads the per-proposal pivot flags). Returns GP_ERR_TIMEOUT, with info filled in and timed_out set,
+ * if a bounded device wait of the factorization ran out (GP_OPT_WAIT_POLLS). */
 GP_API gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, int32_t* not_pd_column /* [B] or NULL */);
 
 /* Steps A8-A11: forward/backward supernodal solves, quadratic form r^T C_z^{-1} r, log-determinant
  * 2 sum_j log L_jj in a fixed-order tree, and (GP_MIXED) FP64 iterative refinement of alpha = C_z^{-1} r with
  * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-12 or 10 sweeps.
  *   d_resid: B x n FP64 (r = z - mu per proposal, original point order); d_out: B FP64 log-likelihoods
- *   (-inf for proposals with a non-positive pivot); d_err_est: B FP64 final relative residual (nullable).
- * Keeps alpha for gp_predict. Asynchronous. Errors: GP_ERR_ARG, GP_ERR_CUDA. */
+ *   (-inf for proposals with a non-positive pivot, NaN after a timed-out factorization); d_err_est: B FP64 final
+ *   relative residual (nullable).
+ * Keeps alpha for gp_predict. GP_FP64: asynchronous. GP_MIXED: synchronises the context stream at each
+ * refinement sweep (the stopping test reads the residual norms). Errors: GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_TIMEOUT
+ * (GP_MIXED: the factorization's bounded waits ran out; the outputs are written, as NaN). */
 GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err_est);
 
 /* Step A12: m*_k = mu*_k + sum_j C_y(x*_k, x_j) alpha_j over the training neighbours of x*_k found in the
@@ -191,6 +242,47 @@ GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, d
  * Asynchronous. Errors: GP_ERR_ARG, GP_ERR_STATE (no alpha yet), GP_ERR_CUDA. */
 GP_API gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
                      const double* d_mu_test, double* d_mean);
+
+/* Predictive variance (Sec. 3.2): the diagonal of the conditional covariance C_{y|z} = C_y - C_{y,z} C_z^{-1} C_{z,y}
+ * at the test inputs, var_k = C_y(x*_k, x*_k) - |w_k|^2 with L w_k = P c_k and c_k = C_y(X, x*_k) (no noise term at
+ * test inputs), for proposal b of the factor (gp_loglik is not needed). c_k is nonzero only at the training
+ * neighbours of x*_k, so w_k is formed by a forward solve restricted to the supernodes on those neighbours' paths to
+ * the root, 32 test points at a time; test points close in space that are passed next to each other share that
+ * work. The arithmetic is the factor's: FP64 for GP_FP64; FP32 solves with the FP32 panels for GP_MIXED (relative
+ * accuracy of the mixed factor, about 1e-6 of C_y(x*, x*)).
+ *   d_Xtest: m x d FP64 (device); d_var: m FP64 (device output).
+ * The first call on a factor allocates its workspace (at most 4 GiB or a quarter of the free device memory, within
+ * the context budget), held until gp_factor_free; later calls allocate nothing. Asynchronous after that allocation.
+ * Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA. */
+GP_API gp_status gp_predict_var(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m, double* d_var);
+
+/* The paper's own approximate computation of the log-likelihood above 100k points (Sec. 3.3), as a comparison for
+ * the exact factorization: log det C_z by stochastic Lanczos quadrature (k Lanczos steps from each of P probe
+ * vectors, no reorthogonalisation: log det ~ (1/P) sum_p |v_p|^2 sum_i U_1i^2 log theta_i for T_k = U diag(theta)
+ * U^T) and r^T C_z^{-1} r by MINRES (Paige and Saunders) from a start vector, stopped when the residual estimate
+ * falls to tol |r|; log p ~ -1/2 log det - 1/2 r^T alpha - n/2 log 2 pi. It multiplies by the CSR values of C_z the
+ * factor's value step computed for proposal b (the factorization itself is not used).
+ *   d_resid: n FP64 (device, r = z - mu); d_probes: P x n FP64 (device; the probe vectors, e.g. +-1 entries as the
+ *   paper draws them); d_x0: n FP64 (device; MINRES start, the paper starts at random) or NULL for zero.
+ * The first call on a factor allocates its workspace (3 n P + 7 n doubles), held until gp_factor_free.
+ * Synchronous (the result is host memory). Errors: GP_ERR_ARG (P outside 1..32, k outside 2..64, tol <= 0,
+ * max_iter < 1), GP_ERR_NOMEM, GP_ERR_CUDA. */
+typedef struct {
+  int32_t probes;          /* P, 1..32 */
+  int32_t lanczos_steps;   /* k, 2..64 */
+  double tol;              /* MINRES relative residual tolerance (the paper: 1e-8) */
+  int32_t max_iter;        /* MINRES iteration cap */
+} gp_iterative_opts;
+typedef struct {
+  double loglik, logdet, quad;   /* estimates */
+  int32_t minres_iters;
+  int32_t converged;             /* 1 if MINRES reached tol within max_iter */
+  double minres_relres;          /* MINRES's own residual estimate / |r| */
+  double true_relres;            /* |r - C_z alpha| / |r| recomputed from the result */
+} gp_iterative_result;
+GP_API gp_status gp_loglik_iterative(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_resid,
+                                     const double* d_probes, const double* d_x0, const gp_iterative_opts* opts,
+                                     gp_iterative_result* result);
 
 /* Launch profiler. gp_profile(ctx, 1) clears the counters and brackets every later launch of the listed
  * kernel classes with CUDA events on the context stream; gp_profile(ctx, 0) stops. gp_profile_read
@@ -208,7 +300,8 @@ GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int6
  * allocator or a memory budget it does not own, that want each point's neighbour count, e.g. to size their
  * own buffers or to pick core radii for a target row count before calling gp_assemble).
  *   d_X: n x d FP64 (device); core_radius: host [d]; d_counts: n int64 (device output), d_counts[i] = number
- *   of points j (i included) with sum_k ((x_ik - x_jk) / core_radius_k)^2 < 1, the row lengths of the pattern
+ *   of points j (i included) with sum_k (u_ik - u_jk)^2 < 1 for u = x / core_radius per coordinate (each division,
+ *   difference, product and sum rounded separately, summed in coordinate order), the row lengths of the pattern
  *   gp_assemble builds for the same input.
  * It runs the cell list and count pass of gp_assemble with all scratch in one static device array of 16 MiB
  * that every GPU loading the library keeps until exit: n <= 65536 and at most 2^20 cells of the unit grid in

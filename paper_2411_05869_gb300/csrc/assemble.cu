@@ -153,6 +153,52 @@ __global__ void k_pattern(const double* __restrict__ Us, const int32_t* __restri
   if (!FILL) rowcnt[i] = cnt;
 }
 
+// The support of C_sparse (the pattern with a non-compact core). Bit i of fam[k]: point k lies inside the support of
+// bump family i, sum over the leading bd coordinates of (x_c - h_c)^2 < r^2 for one of the family's bumps (Eq.
+// bumpFcn), each operation rounded separately in coordinate order.
+__global__ void k_family_mask(const double* __restrict__ X, int64_t n, int d, const double* __restrict__ h,
+                              const double* __restrict__ r, int n1, int n2, int bd, uint32_t* __restrict__ fam) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t m = 0;
+  for (int i = 0; i < n1; i++)
+    for (int j = 0; j < n2; j++) {
+      const int ij = i * n2 + j;
+      double s = 0.0;
+      for (int c = 0; c < bd; c++) {
+        const double dc = __dsub_rn(X[k * d + c], h[(int64_t)ij * bd + c]);
+        s = __dadd_rn(s, __dmul_rn(dc, dc));
+      }
+      if (s < __dmul_rn(r[ij], r[ij])) m |= 1u << i;
+    }
+  fam[k] = m;
+}
+
+// Row i of the support of C_sparse: j with q0^2 < 1 (u = x / r0) or sharing a bump family with i. A warp per row,
+// lanes over 32 consecutive j at a time, so the row comes out ascending (ballot prefix for the fill).
+template <bool FILL>
+__global__ void k_pattern_support(const double* __restrict__ U, const uint32_t* __restrict__ fam, int64_t n, int d,
+                                  int64_t* __restrict__ rowcnt, const int64_t* __restrict__ rowptr,
+                                  int32_t* __restrict__ col) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double ui[3] = {0, 0, 0};
+  for (int k = 0; k < d; k++) ui[k] = U[i * d + k];
+  const uint32_t mi = fam[i];
+  const int64_t out = FILL ? rowptr[i] : 0;
+  int64_t cnt = 0;
+  for (int64_t j0 = 0; j0 < n; j0 += 32) {
+    const int64_t j = j0 + lane;
+    bool p = false;
+    if (j < n) p = (mi & fam[j]) != 0 || in_support(ui, U + j * d, d);
+    const uint32_t bal = __ballot_sync(0xffffffffu, p);
+    if (FILL && p) col[out + cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)j;
+    cnt += __popc(bal);
+  }
+  if (!FILL && lane == 0) rowcnt[i] = cnt;
+}
+
 // Sort each CSR row ascending: warp per row, every element's destination is the count of smaller entries.
 __global__ void k_sort_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ in, int64_t n,
                             int32_t* __restrict__ out) {
@@ -422,8 +468,22 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X) {
   // ---- A2: pattern (count, scan, fill, sort rows)
   int64_t* rowcnt = dalloc<int64_t>(ctx, tmp, n + 1);
   GP_CUDA(cudaMemsetAsync(rowcnt, 0, sizeof(int64_t) * (n + 1), st));
-  k_pattern<false><<<grid_for(n, 128), 128, 0, st>>>(ps->Us, ps->cell_perm, ps->cell_start, n, g, rowcnt, nullptr,
-                                                     nullptr);
+  if (ps->support == 1) {   // the support of C_sparse (non-compact core): bump-family masks, then all pairs
+    const int64_t nb = (int64_t)ps->sup_n1 * ps->sup_n2;
+    double* hd = dalloc<double>(ctx, tmp, std::max<int64_t>(1, nb * ps->sup_bd));
+    double* rd = dalloc<double>(ctx, tmp, std::max<int64_t>(1, nb));
+    if (nb > 0) {
+      h2d(ctx, hd, ps->sup_h.data(), (size_t)(nb * ps->sup_bd));
+      h2d(ctx, rd, ps->sup_r.data(), (size_t)nb);
+    }
+    ps->fam = dalloc<uint32_t>(ctx, ps->bufs, n);
+    k_family_mask<<<grid_for(n, 256), 256, 0, st>>>(ps->X, n, d, hd, rd, ps->sup_n1, ps->sup_n2, ps->sup_bd, ps->fam);
+    GP_CHECK_LAUNCH(ctx);
+    k_pattern_support<false><<<grid_for(n * 32, 256), 256, 0, st>>>(ps->U, ps->fam, n, d, rowcnt, nullptr, nullptr);
+  } else {
+    k_pattern<false><<<grid_for(n, 128), 128, 0, st>>>(ps->Us, ps->cell_perm, ps->cell_start, n, g, rowcnt, nullptr,
+                                                       nullptr);
+  }
   GP_CHECK_LAUNCH(ctx);
   ps->rowptr = dalloc<int64_t>(ctx, ps->bufs, n + 1);
   void* scan_tmp = dev_alloc(ctx, tmp, scan_temp_bytes(std::max<int64_t>(n + 1, 2 * n + 2)));
@@ -433,13 +493,18 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X) {
   GP_CUDA(cudaStreamSynchronize(st));
   ps->nnz = nnz;
   GP_REQUIRE(nnz < (int64_t)1 << 40, "pattern too large");
-  int32_t* col_unsorted = dalloc<int32_t>(ctx, tmp, nnz);
-  k_pattern<true><<<grid_for(n, 128), 128, 0, st>>>(ps->Us, ps->cell_perm, ps->cell_start, n, g, nullptr, ps->rowptr,
-                                                    col_unsorted);
-  GP_CHECK_LAUNCH(ctx);
   ps->col = dalloc<int32_t>(ctx, ps->bufs, nnz);
-  k_sort_rows<<<grid_for(n * 32, 256), 256, 0, st>>>(ps->rowptr, col_unsorted, n, ps->col);
-  GP_CHECK_LAUNCH(ctx);
+  if (ps->support == 1) {   // rows come out ascending
+    k_pattern_support<true><<<grid_for(n * 32, 256), 256, 0, st>>>(ps->U, ps->fam, n, d, nullptr, ps->rowptr, ps->col);
+    GP_CHECK_LAUNCH(ctx);
+  } else {
+    int32_t* col_unsorted = dalloc<int32_t>(ctx, tmp, nnz);
+    k_pattern<true><<<grid_for(n, 128), 128, 0, st>>>(ps->Us, ps->cell_perm, ps->cell_start, n, g, nullptr,
+                                                      ps->rowptr, col_unsorted);
+    GP_CHECK_LAUNCH(ctx);
+    k_sort_rows<<<grid_for(n * 32, 256), 256, 0, st>>>(ps->rowptr, col_unsorted, n, ps->col);
+    GP_CHECK_LAUNCH(ctx);
+  }
 
   // ---- A5: nested dissection
   ps->perm = dalloc<int32_t>(ctx, ps->bufs, n);
@@ -623,7 +688,10 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X) {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-void* g_noalloc_base[64] = {};   // device address of g_noalloc_scratch, looked up once per device
+// Device address of g_noalloc_scratch per device, looked up once per device (contexts on several host threads
+// may make their first call at the same time).
+std::atomic<void*> g_noalloc_base[64] = {};
+std::mutex g_noalloc_lookup;
 
 struct Carver {
   char* base;
@@ -651,13 +719,17 @@ extern "C" gp_status gp_pattern_counts_noalloc(gp_ctx* ctx, const double* d_X, i
       GP_REQUIRE(core_radius[k] > 0.0 && std::isfinite(core_radius[k]), "core_radius must be positive");
     GP_REQUIRE(ctx->device >= 0 && ctx->device < 64, "device index out of range");
     // host code sees only a stand-in for the array: fetch its device address with the device current
-    if (!g_noalloc_base[ctx->device]) {
-      void* p = nullptr;
-      GP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-      g_noalloc_base[ctx->device] = p;
+    void* base = g_noalloc_base[ctx->device].load(std::memory_order_acquire);
+    if (!base) {
+      std::lock_guard<std::mutex> lk(g_noalloc_lookup);
+      base = g_noalloc_base[ctx->device].load(std::memory_order_acquire);
+      if (!base) {
+        GP_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+        g_noalloc_base[ctx->device].store(base, std::memory_order_release);
+      }
     }
     cudaStream_t st = ctx->stream;
-    Carver cv{static_cast<char*>(g_noalloc_base[ctx->device]), 0, GP_NOALLOC_SCRATCH_BYTES};
+    Carver cv{static_cast<char*>(base), 0, GP_NOALLOC_SCRATCH_BYTES};
     double* U = cv.take<double>((size_t)n * d);
     double* Us = cv.take<double>((size_t)n * d);
     uint64_t* keys = cv.take<uint64_t>(n + 1);

@@ -727,7 +727,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
                 int64_t ntiles, int kb, int mode, int group, DevPlan dp, const uint8_t* __restrict__ tmaps,
                 const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
-                float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err) {
+                float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err,
+                tcg::WaitLimit lim) {
   using C = UW<TN, PAIR>;
   constexpr int NS = C::STAGES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -738,8 +739,10 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
   uint64_t* empty = bars + NS;          // [NS] MMAs done reading
   uint64_t* tfull = bars + 2 * NS;      // [2] accumulator complete
   uint64_t* tempty = bars + 2 * NS + 2; // [2] accumulator drained
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+  uint64_t* drain = bars + 2 * NS + 4;    // the MMA issuer's last commit (winding down)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  uint32_t* issued_s = tslot + 2;         // operand chunks this CTA's producer issued
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = tcg::smem_u32(smem);
   if (threadIdx.x == 0) {
@@ -751,6 +754,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       tcg::mbar_init(&tfull[q], 1);
       tcg::mbar_init(&tempty[q], PAIR ? 16 : 8);   // paired: both CTAs' epilogue warps drain the even CTA's MMAs
     }
+    tcg::mbar_init(drain, 1);
+    *issued_s = 0;
     *abort_flag = *(volatile int32_t*)err != 0;   // an earlier launch of this factorization failed: skip the tiles
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -780,7 +785,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
-      uint32_t st = 0, ph = 0;
+      uint32_t st = 0, ph = 0, issued = 0;
       for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
         const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
         const uint8_t* mh = tmaps + (int64_t)u.slot * 256;
@@ -790,7 +795,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         const bool shared_a = a_in_b(u) >= 0;
         const int nch = (u.K + 31) / 32;
         for (int c = 0; c < nch; c++) {
-          if (!tcg::mbar_wait(&empty[st], ph ^ 1)) {
+          if (!tcg::mbar_wait(&empty[st], ph ^ 1, lim)) {
             fail();
             break;
           }
@@ -817,12 +822,14 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
               tcg::tma_load_3d(sb + C::OPB + hb * C::OPA, ml, x, (int)u.j0 + 128 * hb, u.b, &full[st]);
             }
           }
+          ++issued;
           if (++st == NS) {
             st = 0;
             ph ^= 1;
           }
         }
       }
+      *issued_s = issued;
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {   // MMA issuer (paired: the even CTA, for both)
@@ -832,7 +839,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
         const int ab = a_in_b(u);
         const int nch = (u.K + 31) / 32;
-        if (!tcg::mbar_wait(&tempty[acc], aph ^ 1)) {
+        if (!tcg::mbar_wait(&tempty[acc], aph ^ 1, lim)) {
           fail();
           break;
         }
@@ -840,7 +847,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         const uint32_t d = tmem + acc * TN;
         bool ok = true;
         for (int c = 0; c < nch; c++) {
-          if (!tcg::mbar_wait(&full[st], ph)) {
+          if (!tcg::mbar_wait(&full[st], ph, lim)) {
             ok = false;
             break;
           }
@@ -908,7 +915,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
           }
         }
       }
-      if (!tcg::mbar_wait(&tfull[acc], aph)) {
+      if (!tcg::mbar_wait(&tfull[acc], aph, lim)) {
         fail();
         break;
       }
@@ -977,8 +984,44 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       }
     }
   }
+  // Winding down (waits that return at once after a normal run): every role has left its loop and no producer
+  // issues any more. Before tensor memory is freed and the CTAs exit, wait for every operand copy issued into
+  // either CTA's shared memory and for every MMA issued, so that nothing still targets them. A CTA pair's copies
+  // all complete on the even CTA's barriers; chunks one producer issued and the other did not (an aborted run) are
+  // balanced there first: the odd CTA's bytes expected but never sent are completed without a copy, bytes sent
+  // but never expected are expected now.
   tcg::tc_fence_before();
-  if (PAIR) tcg::cluster_sync();   // no multicast or remote arrive may still target this CTA
+  if (PAIR) tcg::cluster_sync();
+  else __syncthreads();
+  if (warp == 0 && lane == 0 && rank == 0) {
+    uint32_t n_hi = *issued_s;
+    if (PAIR) {
+      const uint32_t n_e = *issued_s;
+      const uint32_t n_o = tcg::ld_shared_cluster_u32(tcg::mapa_shared(tcg::smem_u32(issued_s), 1));
+      const uint32_t n_lo = min(n_e, n_o);
+      n_hi = max(n_e, n_o);
+      uint32_t c = 0;
+      for (int64_t tt = t_first; tt < ntiles && c < n_hi && n_lo < n_hi; tt += t_step) {
+        const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, 1);
+        const uint32_t ob = (u.i0 == u.j0 + 128 ? 0 : 2 * C::OPA) + 2 * C::OPB;   // the odd CTA's bytes
+        const int nch = (u.K + 31) / 32;
+        for (int q = 0; q < nch && c < n_hi; q++, c++) {
+          if (c < n_lo) continue;
+          if (n_e > n_o) tcg::mbar_complete_tx(&full[c % NS], ob);
+          else tcg::mbar_arrive_expect_tx(&full[c % NS], ob);
+        }
+      }
+    }
+    for (uint32_t c = n_hi > (uint32_t)NS ? n_hi - NS : 0; c < n_hi; c++)
+      if (!tcg::mbar_wait(&full[c % NS], (c / NS) & 1)) fail();
+  }
+  if (warp == 1 && lane == 0 && rank == 0) {   // the MMAs issued so far have completed once this commit arrives
+    if (PAIR) tcg::mma_commit2_mc(drain, 1);
+    else tcg::mma_commit(drain);
+    if (!tcg::mbar_wait(drain, 0)) fail();
+  }
+  tcg::tc_fence_before();
+  if (PAIR) tcg::cluster_sync();   // no copy, multicast or remote arrive may still target either CTA
   else __syncthreads();
   if (warp == 1) {
     tcg::tc_fence_after();
@@ -1068,7 +1111,7 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
   if (mode == 3) {
     k_update_ws<GP_TN_LEFT, false><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
-        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim);
   } else if (mode == 2 && sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
@@ -1085,11 +1128,11 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
     GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true>, fronts, pre, nfront, total, ntiles, kb, mode, sp.group,
                                f->ps->dp, (const uint8_t*)f->op_maps, (const int32_t*)f->op_slot, f->panels32,
                                f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries,
-                               f->tiles_err));
+                               f->tiles_err, f->wait_lim));
   } else {
     k_update_ws<128, false><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
-        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err);
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim);
   }
   GP_CHECK_LAUNCH(ctx);
 }

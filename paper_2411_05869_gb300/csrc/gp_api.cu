@@ -64,36 +64,66 @@ T* upload(gp_ctx* ctx, std::vector<DevBuf>& owner, const std::vector<T>& v) {
   return p;
 }
 
-void check_hyper(const gp_pointset* ps, const gp_hyper& h, const gp_hyper& h0) {
+void check_hyper(const gp_pointset* ps, const gp_hyper& h, const gp_hyper& h0, const gp_core* core) {
   GP_REQUIRE(h.d == ps->d, "theta.d differs from the point set dimension");
   GP_REQUIRE(h.n1 >= 0 && h.n1 <= GP_MAX_N1 && h.n2 >= 0, "theta.n1 must be in 0..32 and n2 >= 0");
   GP_REQUIRE(h.bump_dims >= 0 && h.bump_dims <= h.d, "theta.bump_dims must be in 0..d");
   GP_REQUIRE(h.n1 == h0.n1 && h.n2 == h0.n2 && h.bump_dims == h0.bump_dims, "all proposals must share n1, n2, bump_dims");
-  GP_REQUIRE(h.core_radius && h.r0, "theta.core_radius and theta.r0 are required");
-  for (int k = 0; k < h.d; k++) {
-    GP_REQUIRE(h.core_radius[k] == ps->rho[k], "theta.core_radius must equal the radii of gp_assemble");
-    GP_REQUIRE(h.r0[k] > 0.0, "theta.r0 must be positive");
-  }
+  GP_REQUIRE(h.r0, "theta.r0 is required");
+  const int kind = core ? core->kind : GP_CORE_WENDLAND;
+  GP_REQUIRE(kind == GP_CORE_WENDLAND || kind == GP_CORE_PACIOREK, "unknown core kind");
   int64_t nb = (int64_t)h.n1 * h.n2;
   GP_REQUIRE(nb == 0 || (h.h && h.a && h.b && h.r), "bump arrays are required when n1*n2 > 0");
+  if (kind == GP_CORE_WENDLAND) {
+    GP_REQUIRE(ps->support == 0, "a point set assembled for the support of C_sparse needs the non-compact core");
+    GP_REQUIRE(h.core_radius, "theta.core_radius is required");
+    for (int k = 0; k < h.d; k++) {
+      GP_REQUIRE(h.core_radius[k] == ps->rho[k], "theta.core_radius must equal the radii of gp_assemble");
+      GP_REQUIRE(h.r0[k] > 0.0, "theta.r0 must be positive");
+    }
+  } else {
+    GP_REQUIRE(ps->support == 1, "the non-compact core needs a point set from gp_assemble_sparse_support");
+    GP_REQUIRE(h.n1 == ps->sup_n1 && h.n2 == ps->sup_n2 && h.bump_dims == ps->sup_bd,
+               "theta's bump counts differ from the point set's support");
+    for (int k = 0; k < h.d; k++) GP_REQUIRE(h.r0[k] == ps->rho[k], "theta.r0 must equal the point set's r0");
+    for (int64_t q = 0; q < nb * h.bump_dims; q++) GP_REQUIRE(h.h[q] == ps->sup_h[q], "theta.h must equal the point set's");
+    for (int64_t q = 0; q < nb; q++) GP_REQUIRE(h.r[q] == ps->sup_r[q], "theta.r must equal the point set's");
+    GP_REQUIRE(core->phi_sigma && core->phi_Sigma, "core.phi_sigma and core.phi_Sigma are required");
+    GP_REQUIRE(core->sigma0 > 0.0 && core->Sigma0 > 0.0 && std::isfinite(core->sigma0) && std::isfinite(core->Sigma0),
+               "core.sigma0 and core.Sigma0 must be positive");
+    for (int k = 0; k < h.d; k++)
+      GP_REQUIRE(std::isfinite(core->phi_sigma[k]) && std::isfinite(core->phi_Sigma[k]), "non-finite core.phi");
+  }
   GP_REQUIRE(std::isfinite(h.core_var) && std::isfinite(h.s0) && std::isfinite(h.noise_var), "non-finite theta");
 }
 
-void pack_thetas(gp_factor_t* f, const gp_hyper* th) {
+void pack_thetas(gp_factor_t* f, const gp_hyper* th, const gp_core* cores) {
   const gp_hyper& h0 = th[0];
   ThetaDims td{h0.d, h0.n1, h0.n2, h0.bump_dims};
   int64_t st = theta_stride_of(td);
   std::vector<double> buf((size_t)st * f->B, 0.0);
+  const int kind0 = cores ? cores[0].kind : GP_CORE_WENDLAND;
   for (int b = 0; b < f->B; b++) {
     const gp_hyper& h = th[b];
-    check_hyper(f->ps, h, h0);
+    const gp_core* c = cores ? &cores[b] : nullptr;
+    check_hyper(f->ps, h, h0, c);
+    GP_REQUIRE((c ? c->kind : GP_CORE_WENDLAND) == kind0, "all settings of a factor must share the core kind");
     double* p = buf.data() + (size_t)st * b;
     p[TH_CORE_VAR] = h.core_var;
     p[TH_S0] = h.s0;
     p[TH_NOISE] = h.noise_var;
     for (int k = 0; k < 3; k++) {
-      p[TH_CRAD + k] = k < h.d ? h.core_radius[k] : 1.0;
+      p[TH_CRAD + k] = k < h.d ? (kind0 == GP_CORE_PACIOREK ? h.r0[k] : h.core_radius[k]) : 1.0;
       p[TH_R0 + k] = k < h.d ? h.r0[k] : 1.0;
+    }
+    p[TH_KIND] = kind0;
+    if (kind0 == GP_CORE_PACIOREK) {
+      p[TH_SIG0] = c->sigma0;
+      p[TH_SIGMA0] = c->Sigma0;
+      for (int k = 0; k < 3; k++) {
+        p[TH_PHIS + k] = k < h.d ? c->phi_sigma[k] : 0.0;
+        p[TH_PHIS2 + k] = k < h.d ? c->phi_Sigma[k] : 0.0;
+      }
     }
     int64_t nb = (int64_t)h.n1 * h.n2;
     double* q = p + TH_BUMPS;
@@ -106,6 +136,7 @@ void pack_thetas(gp_factor_t* f, const gp_hyper* th) {
   }
   f->theta_stride = st;
   f->n1max = h0.n1;
+  GP_REQUIRE(f->core_kind == kind0, "the settings' core kind differs from the factor's");
   h2d(f->ctx, f->theta_dev, buf.data(), buf.size());
   GP_CUDA(cudaStreamSynchronize(f->ctx->stream));   // buf leaves scope
   f->thetas_host.assign(th, th + f->B);
@@ -163,6 +194,14 @@ extern "C" gp_status gp_set_option(gp_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 1) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_DIAG_FP32 takes 0 or 1"});
       ctx->opt_diag_fp32 = (int)value;
       return GP_OK;
+    case GP_OPT_WAIT_POLLS:
+      if (value < 1 || value > 0xffffffffLL) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_WAIT_POLLS takes 1..2^32-1"});
+      ctx->opt_wait.polls = (uint32_t)value;
+      return GP_OK;
+    case GP_OPT_WAIT_NS:
+      if (value < 0) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_WAIT_NS takes a value >= 0"});
+      ctx->opt_wait.ns = (uint64_t)value;
+      return GP_OK;
     default:
       return fail(ctx, GpError{GP_ERR_ARG, "unknown option " + std::to_string(option)});
   }
@@ -172,6 +211,8 @@ extern "C" gp_status gp_get_option(const gp_ctx* ctx, int option, int64_t* value
   if (!ctx || !value) return GP_ERR_ARG;
   switch (option) {
     case GP_OPT_DIAG_FP32: *value = ctx->opt_diag_fp32; return GP_OK;
+    case GP_OPT_WAIT_POLLS: *value = (int64_t)ctx->opt_wait.polls; return GP_OK;
+    case GP_OPT_WAIT_NS: *value = (int64_t)ctx->opt_wait.ns; return GP_OK;
     default: return GP_ERR_ARG;
   }
 }
@@ -215,8 +256,26 @@ extern "C" gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, 
 }
 
 // ------------------------------------------------------------------------------------------ point sets
+namespace {
+gp_status assemble_common(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
+                          const gp_hyper* support, gp_pointset** out);
+}  // namespace
+
 extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
                                  gp_pointset** out) {
+  return assemble_common(ctx, d_X, n, d, core_radius, nullptr, out);
+}
+
+extern "C" gp_status gp_assemble_sparse_support(gp_ctx* ctx, const double* d_X, int64_t n, int d,
+                                                const gp_hyper* theta, gp_pointset** out) {
+  if (!ctx) return GP_ERR_ARG;
+  if (!theta || !theta->r0) return fail(ctx, GpError{GP_ERR_ARG, "theta and theta.r0 are required"});
+  return assemble_common(ctx, d_X, n, d, theta->r0, theta, out);
+}
+
+namespace {
+gp_status assemble_common(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
+                          const gp_hyper* support, gp_pointset** out) {
   if (!ctx) return GP_ERR_ARG;
   if (!out) return fail(ctx, GpError{GP_ERR_ARG, "ps is null"});
   *out = nullptr;
@@ -230,6 +289,20 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
     ps->n = n;
     ps->d = d;
     for (int k = 0; k < d; k++) ps->rho[k] = core_radius[k];
+    if (support) {   // the support of C_sparse: r0 (the grid unit) and the bumps' centres and radii
+      const gp_hyper& h = *support;
+      GP_REQUIRE(h.d == d, "theta.d differs from d");
+      GP_REQUIRE(h.n1 >= 0 && h.n1 <= GP_MAX_N1 && h.n2 >= 0 && h.bump_dims >= 0 && h.bump_dims <= d,
+                 "theta.n1 must be in 0..32, n2 >= 0 and bump_dims in 0..d");
+      const int64_t nb = (int64_t)h.n1 * h.n2;
+      GP_REQUIRE(nb == 0 || (h.h && h.r), "bump centres and radii are required");
+      ps->support = 1;
+      ps->sup_n1 = h.n1;
+      ps->sup_n2 = h.n2;
+      ps->sup_bd = h.bump_dims;
+      ps->sup_h.assign(h.h, h.h + nb * h.bump_dims);
+      ps->sup_r.assign(h.r, h.r + nb);
+    }
     assemble_pointset(ctx, ps, d_X);       // A1, A2, A5 on the device
     // A6 on the host from the device pattern and order
     std::vector<int64_t> rp(n + 1);
@@ -279,6 +352,7 @@ extern "C" gp_status gp_assemble(gp_ctx* ctx, const double* d_X, int64_t n, int 
   *out = ps;
   return GP_OK;
 }
+}  // namespace
 
 extern "C" void gp_pointset_free(gp_pointset* ps) {
   if (!ps) return;
@@ -435,6 +509,11 @@ void upload_schedule(gp_ctx* ctx, gp_pointset* ps) {
 // ------------------------------------------------------------------------------------------ factors
 extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, gp_precision prec,
                                gp_factor_t** out) {
+  return gp_factor_core(ctx, ps, thetas, nullptr, B, prec, out);
+}
+
+extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, const gp_core* cores,
+                                    int B, gp_precision prec, gp_factor_t** out) {
   if (!ctx) return GP_ERR_ARG;
   if (!out) return fail(ctx, GpError{GP_ERR_ARG, "f is null"});
   *out = nullptr;
@@ -449,11 +528,14 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->B = B;
     f->prec = prec;
     f->diag_fp32 = prec == GP_MIXED && ctx->opt_diag_fp32 != 0;
+    f->wait_lim = ctx->opt_wait;
+    f->core_kind = cores ? cores[0].kind : GP_CORE_WENDLAND;
     ThetaDims td{thetas[0].d, thetas[0].n1, thetas[0].n2, thetas[0].bump_dims};
     GP_REQUIRE(td.d == ps->d, "theta.d differs from the point set dimension");
     GP_REQUIRE(td.n1 >= 0 && td.n1 <= GP_MAX_N1, "n1 must be in 0..32");
     f->theta_dev = dalloc<double>(ctx, f->bufs, (size_t)theta_stride_of(td) * B);
     f->F = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * td.n1 + 1);
+    if (f->core_kind == GP_CORE_PACIOREK) f->Cpt = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
     if (prec == GP_FP64) {
       f->panels = dalloc<double>(ctx, f->bufs, (size_t)B * sp.panel_entries);
       f->upd = dalloc<double>(ctx, f->bufs, (size_t)B * sp.update_entries);
@@ -485,7 +567,7 @@ extern "C" gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* the
     f->bwd_part = dalloc<double>(ctx, f->bufs, (size_t)B * bwd_part_entries(sp));
     f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
     f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride + 4 * (size_t)B + 8);
-    pack_thetas(f, thetas);
+    pack_thetas(f, thetas, cores);
     factor_run(ctx, f);
   });
   if (st != GP_OK) {
@@ -510,6 +592,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
   const SymPlan& sp = ps->sp;
   const size_t b = (size_t)B, n = (size_t)ps->n;
   size_t t = alloc_bytes((size_t)theta_stride_of(td) * b * 8) + alloc_bytes((b * n * td.n1 + 1) * 8);
+  if (ps->support == 1) t += alloc_bytes(b * n * 2 * 8);   // the non-compact core's per-point sigma, Sigma
   if (prec == GP_FP64) {
     t += alloc_bytes(b * sp.panel_entries * 8) + alloc_bytes(b * sp.update_entries * 8);
   } else {
@@ -617,12 +700,16 @@ extern "C" gp_status gp_autotune(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* t
 }
 
 extern "C" gp_status gp_factor_update(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas) {
+  return gp_factor_update_core(ctx, f, thetas, nullptr);
+}
+
+extern "C" gp_status gp_factor_update_core(gp_ctx* ctx, gp_factor_t* f, const gp_hyper* thetas, const gp_core* cores) {
   if (!ctx) return GP_ERR_ARG;
   return guarded(ctx, [&] {
     GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
     GP_REQUIRE(thetas, "thetas required");
     GP_REQUIRE(thetas[0].n1 == f->n1max, "n1 must match the factor");
-    pack_thetas(f, thetas);
+    pack_thetas(f, thetas, cores);
     f->have_alpha = false;
     factor_run(ctx, f);
   });
@@ -646,11 +733,14 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
   if (!f || !info) return GP_ERR_ARG;
   gp_ctx* ctx = f->ctx;
   std::vector<int32_t> flags(f->B);
+  int32_t terr = 0;
   gp_status st = guarded(ctx, [&] {
     d2h(ctx, flags.data(), f->notpd, f->B);
+    if (f->tiles_err) d2h(ctx, &terr, f->tiles_err, 1);
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != GP_OK) return st;
+  info->timed_out = terr != 0 ? 1 : 0;
   info->B = f->B;
   info->precision = f->prec;
   int64_t bytes = 0;
@@ -663,6 +753,7 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
     if (bad) info->not_pd_count++;
     if (not_pd_column) not_pd_column[b] = bad ? flags[b] : -1;
   }
+  if (terr != 0) return fail(ctx, GpError{GP_ERR_TIMEOUT, "a bounded wait of the tensor-core updates ran out"});
   return GP_OK;
 }
 
@@ -674,6 +765,32 @@ extern "C" gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resi
     GP_REQUIRE(d_resid && d_out, "d_resid and d_out are required");
     loglik_run(ctx, f, d_resid, d_out, d_err_est);
     f->have_alpha = true;
+  });
+}
+
+extern "C" gp_status gp_loglik_iterative(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_resid,
+                                         const double* d_probes, const double* d_x0, const gp_iterative_opts* opts,
+                                         gp_iterative_result* result) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
+    GP_REQUIRE(b >= 0 && b < f->B, "proposal index out of range");
+    GP_REQUIRE(d_resid && d_probes && opts && result, "d_resid, d_probes, opts and result are required");
+    GP_REQUIRE(opts->probes >= 1 && opts->probes <= 32, "probes must be in 1..32");
+    GP_REQUIRE(opts->lanczos_steps >= 2 && opts->lanczos_steps <= 64, "lanczos_steps must be in 2..64");
+    GP_REQUIRE(opts->tol > 0.0 && opts->max_iter >= 1, "tol > 0 and max_iter >= 1 are required");
+    iterative_run(ctx, f, b, d_resid, d_probes, d_x0, *opts, result);
+  });
+}
+
+extern "C" gp_status gp_predict_var(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
+                                    double* d_var) {
+  if (!ctx) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    GP_REQUIRE(f && f->ctx == ctx, "factor missing or from another context");
+    GP_REQUIRE(b >= 0 && b < f->B, "proposal index out of range");
+    GP_REQUIRE(m >= 0 && (m == 0 || (d_Xtest && d_var)), "d_Xtest and d_var are required");
+    if (m > 0) variance_run(ctx, f, b, d_Xtest, m, d_var);
   });
 }
 

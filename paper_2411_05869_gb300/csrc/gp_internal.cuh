@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/gp.h"
+#include "tc_gemm.cuh"
 
 #define GP_MAX_D 3
 #define GP_MAX_N1 32
@@ -76,8 +77,9 @@ struct gp_ctx {
   int64_t prof_n[KC_COUNT] = {};
   double prof_flops[KC_COUNT] = {};
   cudaEvent_t prof_open = nullptr;
-  // options (gp_set_option)
-  int opt_diag_fp32 = 0;     // GP_MIXED factors created afterwards factor their diagonal blocks in FP32
+  // options (gp_set_option); they apply to factors created afterwards
+  int opt_diag_fp32 = 0;     // GP_MIXED: diagonal blocks factored in FP32
+  tcg::WaitLimit opt_wait = tcg::DEFAULT_WAIT;   // GP_MIXED: limits of the tensor-core kernels' bounded waits
 };
 
 // RAII timer of one launch (no-op unless profiling); `flops` is the useful work the launch performs.
@@ -246,6 +248,12 @@ struct gp_pointset {
   int64_t* dest32 = nullptr;    // mixed layout: FP32 panel offset, or DIAG_FLAG | diagonal-tile offset, or -1
   SymPlan sp;
   DevPlan dp{};
+  // support of the pattern: 0 the compact core's (core radii); 1 that of C_sparse (gp_assemble_sparse_support:
+  // q0 < 1 for the radii r0, or both points in one bump family), recorded to check the settings factored on it
+  int support = 0;
+  int sup_n1 = 0, sup_n2 = 0, sup_bd = 0;
+  std::vector<double> sup_h, sup_r;
+  uint32_t* fam = nullptr;      // support 1: per point, bit i set when it lies in bump family i's support
 };
 
 struct gp_factor_s {
@@ -255,9 +263,12 @@ struct gp_factor_s {
   int B = 0;
   gp_precision prec = GP_FP64;
   bool diag_fp32 = false;       // GP_MIXED: diagonal blocks factored in FP32 (default FP64)
+  tcg::WaitLimit wait_lim = tcg::DEFAULT_WAIT;   // GP_MIXED: bounded-wait limits of the tensor-core kernels
   double* theta_dev = nullptr;  // B packed settings
   int64_t theta_stride = 0;
   double* F = nullptr;          // B x n x n1 bump features
+  double* Cpt = nullptr;        // non-compact core: B x n x 2 (sigma(x), Sigma(x)) per point
+  int core_kind = 0;
   int n1max = 0;
   double* panels = nullptr;     // FP64 panels, B x panel_entries
   float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
@@ -286,11 +297,18 @@ struct gp_factor_s {
   int64_t work_stride = 0;
   bool have_alpha = false;
   std::vector<gp_hyper> thetas_host;
+  uint8_t* var_work = nullptr;  // gp_predict_var workspace (allocated on its first call), var_nc chunks
+  int var_nc = 0;
+  uint8_t* it_work = nullptr;   // gp_loglik_iterative workspace (allocated on demand)
+  size_t it_bytes = 0;
 };
 
 // ------------------------------------------------------------------------------------------ packed theta
-// Layout on the device per proposal: [core_var, s0, noise_var, core_radius[3], r0[3], then per bump
-// (h[bump_dims], a, b, r)]. n1/n2/bump_dims are shared by the batch.
+// Layout on the device per proposal: [core_var, s0, noise_var, core_radius[3], r0[3], core kind, sigma0, Sigma0,
+// phi_sigma[3], phi_Sigma[3], then per bump (h[bump_dims], a, b, r)]. n1/n2/bump_dims are shared by the batch.
+// Core kind 0: the compact Wendland-type core core_var f0(q; core_radius); kind 1: the parametric nonstationary
+// Matern core of App. B (Eq. PScov) with log-linear sigma(x), Sigma(x) (core_radius is then stored as r0, the
+// unit of the point set's grid).
 struct ThetaDims {
   int d, n1, n2, bd;
 };
@@ -299,7 +317,12 @@ struct ThetaDims {
 #define TH_NOISE 2
 #define TH_CRAD 3
 #define TH_R0 6
-#define TH_BUMPS 9
+#define TH_KIND 9
+#define TH_SIG0 10
+#define TH_SIGMA0 11
+#define TH_PHIS 12
+#define TH_PHIS2 15
+#define TH_BUMPS 18
 inline int64_t theta_stride_of(const ThetaDims& t) { return TH_BUMPS + (int64_t)t.n1 * t.n2 * (t.bd + 3); }
 
 // ------------------------------------------------------------------------------------------ launchers
@@ -317,6 +340,9 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X);
 void factor_run(gp_ctx* ctx, gp_factor_t* f);
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err);
 void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, const double* d_mu, double* d_mean);
+void variance_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, double* d_var);
+void iterative_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_resid, const double* d_probes,
+                   const double* d_x0, const gp_iterative_opts& o, gp_iterative_result* res);
 void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f);

@@ -20,65 +20,17 @@
 #include <algorithm>
 #include <cmath>
 
+#include "factor_access.cuh"
 #include "gp_internal.cuh"
 
 namespace {
 
 constexpr int T = GP_TILE;
-
-// ---------------------------------------------------------------------------------------- factor access
-// L(i, j) in the solve's working precision; Ld(i, j) in FP64 (the log-determinant).
-struct AccF64 {
-  const double* P;
-  int64_t m;
-  __device__ __forceinline__ double L(int64_t i, int64_t j) const { return P[j * m + i]; }
-  __device__ __forceinline__ double Ld(int64_t i, int64_t j) const { return P[j * m + i]; }
-};
-struct AccMix {
-  const float* P;
-  const double* D;
-  int w, ldw;
-  __device__ __forceinline__ double Ld(int64_t i, int64_t j) const {
-    if (i < w && (i >> 6) == (j >> 6)) return D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)];
-    return (double)P[i * ldw + j];
-  }
-  __device__ __forceinline__ float L(int64_t i, int64_t j) const {
-    if (i < w && (i >> 6) == (j >> 6)) return (float)D[(i >> 6) * (T * T) + (i & 63) * T + (j & 63)];
-    return P[i * ldw + j];
-  }
-};
-// The solve's working precision V: FP64 with the FP64 factor; FP32 with the mixed factor, whose solves only
-// precondition the FP64 refinement (the FP64 residual fixes the accuracy of alpha).
-struct StoreF64 {
-  using V = double;
-  static constexpr bool kRowMajor = false;
-  const double* P;
-  int64_t PE;
-  const double* DI;   // inverses of the 64 x 64 diagonal blocks
-  int64_t DE;
-  __device__ __forceinline__ const double* inv(const DevPlan& dp, int32_t s, int b) const {
-    return DI + (int64_t)b * DE + dp.doff[s];
-  }
-  using Acc = AccF64;
-  __device__ __forceinline__ AccF64 acc(const DevPlan& dp, int32_t s, int b) const {
-    return AccF64{P + (int64_t)b * PE + dp.loff[s], (int64_t)dp.w[s] + dp.r[s]};
-  }
-};
-struct StoreMix {
-  using V = float;
-  static constexpr bool kRowMajor = true;
-  const float* P;
-  const double* D;
-  int64_t P32E, DE;
-  const float* DI;   // FP32 inverses of the 64 x 64 diagonal blocks
-  __device__ __forceinline__ const float* inv(const DevPlan& dp, int32_t s, int b) const {
-    return DI + (int64_t)b * DE + dp.doff[s];
-  }
-  using Acc = AccMix;
-  __device__ __forceinline__ AccMix acc(const DevPlan& dp, int32_t s, int b) const {
-    return AccMix{P + (int64_t)b * P32E + dp.loff32[s], D + (int64_t)b * DE + dp.doff[s], dp.w[s], dp.ldw[s]};
-  }
-};
+using fa::AccF64;
+using fa::AccMix;
+using fa::StoreF64;
+using fa::StoreMix;
+using fa::find_front;
 
 template <class V>
 __global__ void k_rhs(const double* __restrict__ rhs, const int32_t* __restrict__ perm, int64_t n, DevPlan dp,
@@ -132,16 +84,6 @@ __global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, St sto
     for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) fv[i] -= A.L(i, j) * x;
     __syncthreads();
   }
-}
-
-__device__ __forceinline__ int find_front(const int64_t* pre, int nfront, int64_t t) {
-  int lo = 0, hi = nfront - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (pre[mid] <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
 }
 
 // The pieces of a forward step, shared by the single and the paired launches.
@@ -867,10 +809,13 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   double* cor = f->delta + (size_t)B * n;       // B x n correction
   double* errv = f->red;                        // B relative residuals (partials are consumed already)
   std::vector<double> herr(B);
+  int32_t terr = 0;
   for (int it = 0; it < 10; it++) {
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
     d2h(ctx, herr.data(), errv, B);
+    if (it == 0) d2h(ctx, &terr, f->tiles_err, 1);
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (terr != 0) break;   // the factorization timed out: the outputs become NaN below
     double worst = 0.0;
     for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
     if (worst <= 1e-12) break;
@@ -883,6 +828,7 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
   k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
   GP_CHECK_LAUNCH(ctx);
+  if (terr != 0) throw GpError{GP_ERR_TIMEOUT, "a bounded wait of the factorization's tensor-core updates ran out"};
 }
 
 // Entries (per proposal) of the backward partial-sum scratch: the largest level's tasks x row chunks x 64.

@@ -1,13 +1,19 @@
 // tc_gemm.cuh -- tcgen05 building blocks for sm_103a (5th-generation tensor cores): TF32 MMAs with FP32
 // accumulation in tensor memory (TMEM), shared-memory matrix descriptors, mbarriers with bounded waits, TMEM
 // allocation and loads, and TMA tile loads. Every wait is bounded: a wait that runs out reports failure to its
-// caller, which sets an error flag (GP_ERR_TIMEOUT on the host) instead of spinning forever.
+// caller, which sets an error flag (GP_ERR_TIMEOUT on the host) and winds the kernel down instead of spinning
+// forever.
 #pragma once
 #include <stdint.h>
 
 namespace tcg {
 
-constexpr uint32_t WAIT_LIMIT = 1u << 26;             // bounded mbarrier polls
+// Limits of a bounded mbarrier wait: polls, and nanoseconds of %globaltimer time (checked every 64 polls).
+struct WaitLimit {
+  uint32_t polls;
+  uint64_t ns;
+};
+constexpr WaitLimit DEFAULT_WAIT{1u << 26, 1000000000ull};   // no legitimate wait here comes near a millisecond
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -36,17 +42,28 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait; returns false (and leaves the barrier as is) when the poll limit or WAIT_NS of wall-clock time
-// runs out (no legitimate wait in these kernels comes near a millisecond).
-constexpr uint64_t WAIT_NS = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity; returns false (and leaves the barrier as is) when lim.polls
+// polls have failed or lim.ns of wall-clock time has gone by.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, WaitLimit lim = DEFAULT_WAIT) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < WAIT_LIMIT; it++) {
+  for (uint32_t it = 1; it < lim.polls; it++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
+    if ((it & 63) == 63 && global_ns() - t0 > lim.ns) return false;
   }
   return false;
+}
+// Completes `bytes` of the barrier's expected transaction count without a copy (balances an expectation that no
+// copy will meet).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// A 32-bit load from the same shared variable in another CTA of the cluster (cluster address from mapa_shared).
+__device__ __forceinline__ uint32_t ld_shared_cluster_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {

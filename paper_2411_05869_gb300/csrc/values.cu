@@ -10,6 +10,7 @@
 //     One warp per pattern row; every entry writes the CSR value (for refinement residuals) and, when it lies
 //     in the lower triangle of P C_z P^T, its panel slot.
 #include "gp_internal.cuh"
+#include "testpoint.cuh"
 
 namespace {
 
@@ -22,10 +23,11 @@ __device__ __forceinline__ double wendland(double q) {
 }
 
 __global__ void k_features(const double* __restrict__ X, int64_t n, int d, const double* __restrict__ theta,
-                           int64_t tstride, int n1, int n2, int bd, double* __restrict__ F) {
+                           int64_t tstride, int n1, int n2, int bd, double* __restrict__ F, double* __restrict__ Cpt) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (k >= n) return;
+  if (Cpt) tp::core_point(theta + (int64_t)b * tstride, X + k * d, d, Cpt + ((int64_t)b * n + k) * 2);
   const double* th = theta + (int64_t)b * tstride + TH_BUMPS;
   const int per = bd + 3;
   double x[3] = {0, 0, 0};
@@ -58,7 +60,8 @@ template <bool MIXED>
 __global__ void k_values(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n, int d,
                          const double* __restrict__ U, const double* __restrict__ X,
                          const double* __restrict__ theta, int64_t tstride, int B, int n1,
-                         const double* __restrict__ F, const int64_t* __restrict__ dest, int64_t nnz,
+                         const double* __restrict__ F, const double* __restrict__ Cpt,
+                         const int64_t* __restrict__ dest, int64_t nnz,
                          int64_t panel_entries, double* __restrict__ val, double* __restrict__ panels,
                          float* __restrict__ p32, double* __restrict__ diag, int64_t diag_entries) {
   int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -81,7 +84,15 @@ __global__ void k_values(const int64_t* __restrict__ rowptr, const int32_t* __re
     for (int b = 0; b < B; b++) {
       const double* th = theta + (int64_t)b * tstride;
       double v = 0.0;
-      if (wc != 0.0) {
+      if (th[TH_KIND] != 0.0) {   // non-compact core: C_core(x_i, x_j) C_sparse, f0 of q0 from u = x / r0
+        double acc = th[TH_S0] * wc;
+        const double* Fi = F + ((int64_t)b * n + i) * n1;
+        const double* Fj = F + ((int64_t)b * n + j) * n1;
+        for (int k = 0; k < n1; k++) acc += Fi[k] * Fj[k];
+        if (acc != 0.0)
+          v = tp::core_paciorek(Cpt + ((int64_t)b * n + i) * 2, Cpt + ((int64_t)b * n + j) * 2, xi,
+                                X + (int64_t)j * d, d) * acc;
+      } else if (wc != 0.0) {
         double w0 = wc;
         bool same = true;
         for (int k = 0; k < d; k++) same = same && th[TH_R0 + k] == th[TH_CRAD + k];
@@ -171,16 +182,16 @@ void values_run(gp_ctx* ctx, gp_factor_t* f) {
   const int64_t n = ps->n;
   const gp_hyper& h0 = f->thetas_host[0];
   dim3 gf(grid_for(n, 128), f->B);
-  if (h0.n1 > 0) {
+  if (h0.n1 > 0 || f->Cpt) {
     k_features<<<gf, 128, 0, ctx->stream>>>(ps->X, n, ps->d, f->theta_dev, f->theta_stride, h0.n1, h0.n2,
-                                            h0.bump_dims, f->F);
+                                            h0.bump_dims, f->F, f->Cpt);
     GP_CHECK_LAUNCH(ctx);
   }
   GP_CUDA(cudaMemsetAsync(f->panels, 0, sizeof(double) * (size_t)f->B * ps->sp.panel_entries, ctx->stream));
   ProfScope ps_(ctx, KC_VALUES);
   k_values<false><<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(
-      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, ps->dest,
-      ps->nnz, ps->sp.panel_entries, f->val, f->panels, nullptr, nullptr, 0);
+      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, f->Cpt,
+      ps->dest, ps->nnz, ps->sp.panel_entries, f->val, f->panels, nullptr, nullptr, 0);
   GP_CHECK_LAUNCH(ctx);
 }
 
@@ -190,16 +201,16 @@ void values_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   const int64_t n = ps->n;
   const gp_hyper& h0 = f->thetas_host[0];
   dim3 gf(grid_for(n, 128), f->B);
-  if (h0.n1 > 0) {
+  if (h0.n1 > 0 || f->Cpt) {
     k_features<<<gf, 128, 0, ctx->stream>>>(ps->X, n, ps->d, f->theta_dev, f->theta_stride, h0.n1, h0.n2,
-                                            h0.bump_dims, f->F);
+                                            h0.bump_dims, f->F, f->Cpt);
     GP_CHECK_LAUNCH(ctx);
   }
   GP_CUDA(cudaMemsetAsync(f->panels32, 0, sizeof(float) * (size_t)f->B * sp.panel32_entries, ctx->stream));
   GP_CUDA(cudaMemsetAsync(f->diag, 0, sizeof(double) * (size_t)f->B * sp.diag_entries, ctx->stream));
   ProfScope ps_(ctx, KC_VALUES);
   k_values<true><<<grid_for(n * 32, 256), 256, 0, ctx->stream>>>(
-      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, ps->dest32,
-      ps->nnz, sp.panel32_entries, f->val, nullptr, f->panels32, f->diag, sp.diag_entries);
+      ps->rowptr, ps->col, n, ps->d, ps->U, ps->X, f->theta_dev, f->theta_stride, f->B, h0.n1, f->F, f->Cpt,
+      ps->dest32, ps->nnz, sp.panel32_entries, f->val, nullptr, f->panels32, f->diag, sp.diag_entries);
   GP_CHECK_LAUNCH(ctx);
 }

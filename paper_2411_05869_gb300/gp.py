@@ -35,6 +35,13 @@ class GpHyper(ctypes.Structure):
                 ("noise_var", c_dbl)]
 
 
+class GpCore(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("sigma0", c_dbl), ("Sigma0", c_dbl), ("phi_sigma", DP), ("phi_Sigma", DP)]
+
+
+GP_CORE_WENDLAND, GP_CORE_PACIOREK = 0, 1
+
+
 class PointsetInfo(ctypes.Structure):
     _fields_ = [("n", c_i64), ("d", c_int), ("nnz", c_i64), ("ncells", c_i64), ("nnzL", c_i64),
                 ("nsuper", c_i64), ("panel_entries", c_i64), ("update_entries", c_i64), ("nlevels", ctypes.c_int32),
@@ -43,11 +50,11 @@ class PointsetInfo(ctypes.Structure):
 
 class FactorInfo(ctypes.Structure):
     _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32),
-                ("diag_fp32", ctypes.c_int32)]
+                ("diag_fp32", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
 
 
-GP_OPT_DIAG_FP32 = 0
-OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32}
+GP_OPT_DIAG_FP32, GP_OPT_WAIT_POLLS, GP_OPT_WAIT_NS = 0, 1, 2
+OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32, "wait_polls": GP_OPT_WAIT_POLLS, "wait_ns": GP_OPT_WAIT_NS}
 
 
 class GpRequest(ctypes.Structure):
@@ -66,6 +73,16 @@ class GpServerStats(ctypes.Structure):
                 ("max_running", ctypes.c_int32), ("completed", c_i64)]
 
 
+class IterativeOpts(ctypes.Structure):
+    _fields_ = [("probes", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32), ("tol", c_dbl),
+                ("max_iter", ctypes.c_int32)]
+
+
+class IterativeResult(ctypes.Structure):
+    _fields_ = [("loglik", c_dbl), ("logdet", c_dbl), ("quad", c_dbl), ("minres_iters", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("minres_relres", c_dbl), ("true_relres", c_dbl)]
+
+
 class GpTuneCandidate(ctypes.Structure):
     _fields_ = [("group_blocks", ctypes.c_int32), ("group_tile_n", ctypes.c_int32), ("ms", c_dbl)]
 
@@ -78,7 +95,8 @@ SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_points
            "gp_pointset_prepare", "gp_autotune", "gp_pointset_set_blocking", "gp_symbolic_host", "gp_symbolic_info",
            "gp_symbolic_export", "gp_symbolic_free", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
            "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy",
-           "gp_set_option", "gp_get_option"]
+           "gp_set_option", "gp_get_option", "gp_predict_var", "gp_loglik_iterative", "gp_assemble_sparse_support",
+           "gp_factor_core", "gp_factor_update_core"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7, "update_left": 9}
 
@@ -137,6 +155,13 @@ def load(build_if_missing: bool = True):
     L.gp_factor.argtypes = [P, P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(P)]
     L.gp_factor_update.restype = c_int
     L.gp_factor_update.argtypes = [P, P, ctypes.POINTER(GpHyper)]
+    L.gp_assemble_sparse_support.restype = c_int
+    L.gp_assemble_sparse_support.argtypes = [P, P, c_i64, c_int, ctypes.POINTER(GpHyper), ctypes.POINTER(P)]
+    L.gp_factor_core.restype = c_int
+    L.gp_factor_core.argtypes = [P, P, ctypes.POINTER(GpHyper), ctypes.POINTER(GpCore), c_int, c_int,
+                                 ctypes.POINTER(P)]
+    L.gp_factor_update_core.restype = c_int
+    L.gp_factor_update_core.argtypes = [P, P, ctypes.POINTER(GpHyper), ctypes.POINTER(GpCore)]
     L.gp_factor_free.argtypes = [P]
     L.gp_factor_free.restype = None
     L.gp_factor_info.restype = c_int
@@ -145,6 +170,11 @@ def load(build_if_missing: bool = True):
     L.gp_loglik.argtypes = [P, P, P, P, P]
     L.gp_predict.restype = c_int
     L.gp_predict.argtypes = [P, P, c_int, P, c_i64, P, P]
+    L.gp_predict_var.restype = c_int
+    L.gp_predict_var.argtypes = [P, P, c_int, P, c_i64, P]
+    L.gp_loglik_iterative.restype = c_int
+    L.gp_loglik_iterative.argtypes = [P, P, c_int, P, P, P, ctypes.POINTER(IterativeOpts),
+                                      ctypes.POINTER(IterativeResult)]
     L.gp_launch_count.restype = c_i64
     L.gp_launch_count.argtypes = [P]
     L.gp_set_option.restype = c_int
@@ -207,11 +237,15 @@ def _dp(a: np.ndarray):
 
 
 class _HyperPack:
-    """Keeps the numpy arrays behind a ctypes gp_hyper array alive for the duration of a call."""
+    """Keeps the numpy arrays behind a ctypes gp_hyper array (and, for settings with the non-compact core, a
+    gp_core array) alive for the duration of a call."""
 
     def __init__(self, thetas: Sequence):
         self.keep: List[np.ndarray] = []
         self.arr = (GpHyper * len(thetas))()
+        self.cores = None
+        if any(int(getattr(hp, "core_kind", 0)) != 0 for hp in thetas):
+            self.cores = (GpCore * len(thetas))()
         for k, hp in enumerate(thetas):
             def arr(x):
                 a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
@@ -222,6 +256,11 @@ class _HyperPack:
             self.arr[k] = GpHyper(hp.d, hp.n1, hp.n2, hp.bump_dims, float(hp.core_var), arr(hp.core_radius),
                                   float(hp.s0), arr(hp.r0), arr(hp.h), arr(hp.a), arr(hp.b), arr(hp.r),
                                   float(hp.noise_var))
+            if self.cores is not None:
+                kind = int(getattr(hp, "core_kind", 0))
+                zeros = np.zeros(hp.d)
+                self.cores[k] = GpCore(kind, float(getattr(hp, "sigma0", 1.0)), float(getattr(hp, "Sigma0", 1.0)),
+                                       arr(hp.phi_sigma if kind else zeros), arr(hp.phi_Sigma if kind else zeros))
 
 
 class Context:
@@ -282,11 +321,27 @@ class Context:
         return PointSet(self, h)
 
     def factor(self, ps: "PointSet", thetas: Sequence, precision: int = GP_FP64) -> "Factor":
-        """Steps A3, A4, A7 for B = len(thetas) settings."""
+        """Steps A3, A4, A7 for B = len(thetas) settings (gp_factor_core when they carry the non-compact core)."""
         pack = _HyperPack(thetas)
         h = P()
-        self.check(self.lib.gp_factor(self.h, ps.h, pack.arr, len(thetas), precision, ctypes.byref(h)))
+        if pack.cores is not None:
+            self.check(self.lib.gp_factor_core(self.h, ps.h, pack.arr, pack.cores, len(thetas), precision,
+                                               ctypes.byref(h)))
+        else:
+            self.check(self.lib.gp_factor(self.h, ps.h, pack.arr, len(thetas), precision, ctypes.byref(h)))
         return Factor(self, ps, h, len(thetas))
+
+    def assemble_sparse_support(self, X, theta) -> "PointSet":
+        """Steps A1, A2, A5, A6 with the support of C_sparse of theta (r0, bump centres and radii) as the pattern:
+        the point set of the non-compact core."""
+        import torch
+        assert X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+        X = X.contiguous()
+        pack = _HyperPack([theta])
+        h = P()
+        self.check(self.lib.gp_assemble_sparse_support(self.h, P(X.data_ptr()), X.shape[0], X.shape[1], pack.arr,
+                                                       ctypes.byref(h)))
+        return PointSet(self, h)
 
     def close(self):
         if getattr(self, "h", None):
@@ -399,12 +454,18 @@ class Factor:
         """Re-run A3, A4, A7 in place with new settings (same B)."""
         assert len(thetas) == self.B
         pack = _HyperPack(thetas)
-        self.ctx.check(self.ctx.lib.gp_factor_update(self.ctx.h, self.h, pack.arr))
+        if pack.cores is not None:
+            self.ctx.check(self.ctx.lib.gp_factor_update_core(self.ctx.h, self.h, pack.arr, pack.cores))
+        else:
+            self.ctx.check(self.ctx.lib.gp_factor_update(self.ctx.h, self.h, pack.arr))
 
-    def info(self):
+    def info(self, allow_timeout: bool = False):
+        """gp_factor_info; with allow_timeout a GP_ERR_TIMEOUT status still returns the filled info."""
         inf = FactorInfo()
         cols = np.empty(self.B, dtype=np.int32)
-        self.ctx.check(self.ctx.lib.gp_factor_info(self.h, ctypes.byref(inf), cols.ctypes.data_as(P)))
+        st = self.ctx.lib.gp_factor_info(self.h, ctypes.byref(inf), cols.ctypes.data_as(P))
+        if not (allow_timeout and st == 5):
+            self.ctx.check(st)
         d = {k: getattr(inf, k) for k, _ in FactorInfo._fields_}
         d["not_pd_column"] = cols
         return d
@@ -430,6 +491,32 @@ class Factor:
         mu = None if mu_test is None else mu_test.contiguous()
         self.ctx.check(self.ctx.lib.gp_predict(self.ctx.h, self.h, b, P(Xt.data_ptr()), m,
                                                P(mu.data_ptr()) if mu is not None else None, P(out.data_ptr())))
+        return out
+
+    def loglik_iterative(self, resid, probes, x0=None, b: int = 0, lanczos_steps: int = 30, tol: float = 1e-8,
+                         max_iter: int = 10000) -> dict:
+        """The paper's approximate log-likelihood (stochastic Lanczos log-det, MINRES) with C_z of proposal b;
+        probes: CUDA float64 (P, n)."""
+        import torch
+        r = resid.contiguous()
+        pr = probes.contiguous()
+        assert r.is_cuda and pr.is_cuda and r.dtype == torch.float64 and pr.dtype == torch.float64
+        o = IterativeOpts(pr.shape[0], lanczos_steps, tol, max_iter)
+        res = IterativeResult()
+        x = None if x0 is None else x0.contiguous()
+        self.ctx.check(self.ctx.lib.gp_loglik_iterative(self.ctx.h, self.h, b, P(r.data_ptr()), P(pr.data_ptr()),
+                                                        P(x.data_ptr()) if x is not None else None,
+                                                        ctypes.byref(o), ctypes.byref(res)))
+        return {k: getattr(res, k) for k, _ in IterativeResult._fields_}
+
+    def predict_var(self, Xtest, b: int = 0, out=None):
+        """Predictive variance diag(C_{y|z}) for proposal b at CUDA float64 test points (m x d)."""
+        import torch
+        Xt = Xtest.contiguous()
+        m = Xt.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=Xt.device)
+        self.ctx.check(self.ctx.lib.gp_predict_var(self.ctx.h, self.h, b, P(Xt.data_ptr()), m, P(out.data_ptr())))
         return out
 
     def free(self):

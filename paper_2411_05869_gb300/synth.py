@@ -301,6 +301,26 @@ def serving_pointsets(count: int = 20, nmin: int = 5000, nmax: int = 500_000, nn
             for i, ni in enumerate(ns)]
 
 
+def noncompact_spatial(n: int = 50_000, m: int = 0, seed: int = SEED_BASE + 6, nbumps: int = 4,
+                       noise_var: float = 0.05) -> Workload:
+    """2-D points U[0,1]^2 with the non-compact core of App. B (core_kind 1: sigma0 = 1.2, Sigma0 = 0.01, sigma and
+    Sigma log-linear in the coordinates), 2 x 2 bumps with radii U[0.04, 0.08] (each family covers a few per cent of
+    the domain, so its points form a dense block of the pattern), r0 = 0.02 for about 60 nonzeros per row from f0 at
+    n = 50k. The residual is a smooth random Fourier field plus white noise."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.0, 1.0, size=(n, 2))
+    Xt = rng.uniform(0.0, 1.0, size=(m, 2))
+    n1, n2 = _split_bumps(nbumps)
+    h, a, b, r = _bumps(rng, n1, n2, 2, 0.1, 0.9, rlo=0.04, rhi=0.08)
+    hp = Hyper(d=2, n1=n1, n2=n2, bump_dims=2, core_var=1.0, core_radius=np.full(2, 1.0), s0=0.9,
+               r0=np.full(2, 0.02), h=h, a=a, b=b, r=r, noise_var=noise_var, core_kind=1, sigma0=1.2, Sigma0=0.01,
+               phi_sigma=np.array([0.4, 0.4]), phi_Sigma=np.array([-0.8, 0.6]))
+    field = _fourier_field(rng, X, np.array([0.05, 0.05]))
+    resid = field + math.sqrt(noise_var) * rng.standard_normal(n)
+    return Workload(name=f"noncompact_{n}", X=X, Xtest=Xt, hyper=hp, resid=resid, mu_test=np.zeros(m),
+                    info=dict(n=n, m=m, d=2, nbumps=nbumps))
+
+
 def config(idx: int, **kw) -> Workload:
     """The five workload shapes: 1 spatial n=2000; 2 space-time n=100k; 3 batched n=200k B=64;
     5 station space-time n=1.2M (4, the serving mix, is built by serving_pointsets)."""
