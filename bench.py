@@ -52,6 +52,8 @@ def make_workload(name: str):
         return synth.config(2, m=0)
     if name == "batched_200k":
         return synth.uniform_spacetime(200_000, 0, 80.0, 8, seed=synth.SEED_BASE + 3, name="spacetime_200k")
+    if name == "noncompact_50k":   # the non-compact core of App. B on 2-D points (pattern: the support of C_sparse)
+        return synth.noncompact_spatial(50_000, seed=synth.SEED_BASE + 6)
     if name == "spatial_2k":   # the residual is the workload's seeded normals (its GP draw is left to the caller)
         w = synth.spatial_2d(n=2000, m=0, seed=synth.SEED_BASE + 1)
         w.resid = w.normals.copy()
@@ -151,8 +153,12 @@ class OracleLeg:
         self.X, self.r, self.desc = oracle_sample(w, max_points)
         self.hp = w.hyper
         t0 = time.perf_counter()
-        self.rp, self.col = oracle.pattern(self.X, self.hp.core_radius)
-        self.perm = oracle.fill_order(self.X, self.hp.core_radius, self.rp, self.col)
+        if int(getattr(self.hp, "core_kind", 0)) == 1:   # non-compact core: the support of C_sparse
+            self.rp, self.col = oracle.pattern_sparse(self.hp, self.X)
+            self.perm = oracle.fill_order(self.X, self.hp.r0, self.rp, self.col)
+        else:
+            self.rp, self.col = oracle.pattern(self.X, self.hp.core_radius)
+            self.perm = oracle.fill_order(self.X, self.hp.core_radius, self.rp, self.col)
         sym = oracle.symbolic(self.rp, self.col, self.perm, want_rows=False)
         self.t_setup = time.perf_counter() - t0
         self.sample_flops = float((sym["eta"].astype(np.float64) ** 2).sum())
@@ -211,7 +217,10 @@ def subwindow_parity(ctx, leg, theta, prec_list):
         X = torch.as_tensor(leg.X, dtype=torch.float64, device=dev)
         r = torch.as_tensor(leg.r, dtype=torch.float64, device=dev)
     st.synchronize()
-    ps = ctx.assemble(X, theta.core_radius)
+    if int(getattr(theta, "core_kind", 0)) == 1:
+        ps = ctx.assemble_sparse_support(X, theta)
+    else:
+        ps = ctx.assemble(X, theta.core_radius)
     ref = leg.oracle.sparse_loglik(theta, leg.X, leg.rp, leg.col, leg.perm, leg.r)["loglik"]
     out = {"points": int(leg.X.shape[0]), "oracle_loglik": float(ref),
            "structure_bit_exact": bool(np.array_equal(ps.export("col"), leg.col) and
@@ -248,7 +257,10 @@ def run_gpu(args, rank, world, local_rank):
         resid = torch.as_tensor(w.resid, dtype=torch.float64, device=dev)
     stream.synchronize()
     t0 = time.perf_counter()
-    ps = ctx.assemble(X, hp.core_radius)
+    if int(getattr(hp, "core_kind", 0)) == 1:
+        ps = ctx.assemble_sparse_support(X, hp)
+    else:
+        ps = ctx.assemble(X, hp.core_radius)
     t_assemble = time.perf_counter() - t0
     info = ps.info()
     rng = np.random.default_rng(1234 + rank)
@@ -342,6 +354,53 @@ def run_gpu(args, rank, world, local_rank):
     else:
         predict_info = None
 
+    # predictive variance diag(C_{y|z}) on the first test points of the workload (the grid's first cells; the
+    # whole grid would take the printed projection), timed like the mean
+    var_info = None
+    if w.Xtest is not None and w.Xtest.shape[0] > 0 and args.var_points > 0:
+        mv = min(args.var_points, w.Xtest.shape[0])
+        Xv = torch.as_tensor(w.Xtest[:mv], dtype=torch.float64, device=dev)
+        var = torch.empty(mv, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            f.predict_var(Xv[:min(mv, 256)], out=var[:min(mv, 256)])   # warm-up (allocates the workspace)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.predict_var(Xv, out=var)
+            e1.record(stream)
+        stream.synchronize()
+        vms = e0.elapsed_time(e1)
+        vv = var.cpu().numpy()
+        var_info = {"m": int(mv), "ms": vms, "points_per_s": mv / (vms * 1e-3),
+                    "grid_projection_s": w.Xtest.shape[0] / (mv / (vms * 1e-3)),
+                    "min": float(vv.min()), "max": float(vv.max()), "positive": bool((vv > 0).all()),
+                    "note": "first test points of the workload's grid; FP32 solves with the mixed factor" if
+                    prec == gp.GP_MIXED else "first test points of the workload's grid; FP64 factor"}
+
+    # the paper's own iterative computation (stochastic Lanczos log-det, MINRES at 1e-8) on the same C_z values,
+    # against this step's exact result for the same setting
+    it_info = None
+    if args.iterative_probes > 0:
+        ths0 = thetas[:1]
+        g = np.random.default_rng(77)
+        pr = torch.as_tensor(g.choice([-1.0, 1.0], size=(args.iterative_probes, w.X.shape[0])), device=dev)
+        x0 = torch.as_tensor(g.standard_normal(w.X.shape[0]), device=dev)
+        with torch.cuda.stream(stream):
+            f.update([ths0[0]] * Bc)
+            exact = f.loglik(resid_b, out=out)
+        stream.synchronize()
+        ll_exact = float(out.cpu()[0])
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            itr = f.loglik_iterative(resid, pr, x0, lanczos_steps=args.iterative_steps, tol=1e-8)
+        it_s = time.perf_counter() - t0
+        it_info = {"probes": args.iterative_probes, "lanczos_steps": args.iterative_steps, "tol": 1e-8,
+                   "seconds": it_s, "loglik": itr["loglik"], "exact_loglik": ll_exact,
+                   "loglik_rel_diff": abs(itr["loglik"] - ll_exact) / abs(ll_exact), "logdet": itr["logdet"],
+                   "minres_iters": itr["minres_iters"], "converged": bool(itr["converged"]),
+                   "true_relres": itr["true_relres"],
+                   "note": "the paper's approximate path (Sec. 3.3) on the factor's C_z values; the exact "
+                           "log-likelihood is this run's mixed evaluation of the same setting"}
+
     # per-kernel-class profile of one more step (not part of the timed region)
     ctx.profile(True)
     step(0)
@@ -350,6 +409,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx.profile(False)
 
     res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, predict=predict_info,
+               variance=var_info, iterative=it_info,
                autotune=tune, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
                h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
@@ -542,6 +602,10 @@ def main():
                     help="mixed runs: factor the 64 x 64 diagonal blocks in FP32 (default FP64)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--var-points", type=int, default=4096, help="test points of the predictive-variance timing")
+    ap.add_argument("--iterative-probes", type=int, default=32,
+                    help="probes of the paper's iterative comparison (stochastic Lanczos + MINRES; 0: skip)")
+    ap.add_argument("--iterative-steps", type=int, default=30, help="Lanczos steps per probe")
     ap.add_argument("--oracle-threads", type=int, default=0, help="host threads of the threaded oracle leg "
                                                                    "(0: all cores)")
     ap.add_argument("--subwindow-parity", type=int, default=1, help="1: the GPU path on the oracle's sub-window "
@@ -555,8 +619,8 @@ def main():
     args = ap.parse_args()
     if args.batch <= 0:
         args.batch = {"batched_200k": 64, "mcmc_200k": 16}.get(args.workload, 1)
-    if args.autotune < 0:   # the library's autotuner picks the update blocking of mixed runs
-        args.autotune = 1 if args.precision == "mixed" else 0
+    if args.autotune < 0:   # the library's autotuner picks the update blocking of mixed runs (compact core)
+        args.autotune = 1 if args.precision == "mixed" and args.workload != "noncompact_50k" else 0
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -665,6 +729,7 @@ def main():
                      "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over the class's "
                                         "launches of one factorization at this blocking (L2 cold at each launch under "
                                         "ncu)") if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
+                     "traffic_before_wind_down": _TRAFFIC_EARLIER.get((args.workload, dom) + _blocking_of(res)),
                      "a7_total": {"ms": t_a7, "proposals": res["B"],
                                   "achieved": res["B"] * flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
         "kernels": kernels,
@@ -678,6 +743,10 @@ def main():
         line["fp64"] = res["fp64"]
     if res.get("predict"):
         line["predict"] = res["predict"]
+    if res.get("variance"):
+        line["predict_variance"] = res["variance"]
+    if res.get("iterative"):
+        line["iterative_comparison"] = res["iterative"]
     if res.get("autotune"):
         line["autotune"] = res["autotune"]
     if world == 1 and not args.no_cpu_baseline:
@@ -712,15 +781,18 @@ def main():
 
 # the kernel behind each timed class
 KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 256 x 256 CTA-pair tcgen05 MMAs)",
-                         "update_left": "k_update_ws<64> (left-looking block-column updates, 128 x 64 tiles)",
-                         "potrf": "k_potrf32", "trsm": "k_trsm32", "extend_add": "k_extend_add32"}
+                         "update_left": "k_update_ws<128> (left-looking updates of block-column pairs, 128 x 128 tiles)",
+                         "potrf": "k_potrf_pair (FP32 elimination with inverses) + k_potrf_tiles64 (FP64 L_11)",
+                         "trsm": "k_trsm32_pair", "extend_add": "k_extend_add32"}
 KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
                         "extend_add": "k_extend_add"}
 
 # DRAM bytes per launch of the dominant kernel, from an ncu capture of this kernel's launches, by (workload, class,
-# update blocking);
-# None where no capture of the current kernel at that blocking exists
-_TRAFFIC = {("station_1.2M", "update", 16, 256): 2.712e9}
+# update blocking); None where no capture of the current kernel at that blocking exists. The one capture of the
+# group-end update at 1.2M (16, 256) read 2.712e9 bytes per launch before the kernel gained its wind-down code (no
+# operand data moves there); it is reported beside the line, not as the current kernel's traffic.
+_TRAFFIC = {}
+_TRAFFIC_EARLIER = {("station_1.2M", "update", 16, 256): 2.712e9}
 
 
 def _blocking_of(res):

@@ -231,9 +231,11 @@ GP_API gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, in
  *   d_resid: B x n FP64 (r = z - mu per proposal, original point order); d_out: B FP64 log-likelihoods
  *   (-inf for proposals with a non-positive pivot, NaN after a timed-out factorization); d_err_est: B FP64 final
  *   relative residual (nullable).
- * Keeps alpha for gp_predict. GP_FP64: asynchronous. GP_MIXED: synchronises the context stream at each
- * refinement sweep (the stopping test reads the residual norms). Errors: GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_TIMEOUT
- * (GP_MIXED: the factorization's bounded waits ran out; the outputs are written, as NaN). */
+ * Keeps alpha for gp_predict. Asynchronous on an explicit stream: the refinement's stopping test runs on the
+ * device (the whole refinement is one CUDA graph with a conditional loop). On the legacy default stream (NULL at
+ * gp_create) GP_MIXED runs the refinement loop from the host and synchronises at each sweep.
+ * Errors: GP_ERR_ARG, GP_ERR_CUDA; GP_ERR_TIMEOUT on the legacy default stream when the factorization's bounded
+ * waits ran out (on an explicit stream that shows as NaN outputs and in gp_factor_info). */
 GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err_est);
 
 /* Step A12: m*_k = mu*_k + sum_j C_y(x*_k, x_j) alpha_j over the training neighbours of x*_k found in the

@@ -549,6 +549,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
       f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
+      f->refine_it = dalloc<int32_t>(ctx, f->bufs, 1);
       f->dinv32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->op_hi = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
       f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
@@ -572,7 +573,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
   });
   if (st != GP_OK) {
     dev_free_all(ctx, f->bufs);
-    for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor})
+    for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine})
       if (g) cudaGraphExecDestroy(g);
     delete f;
     return st;
@@ -605,7 +606,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
       }
     nmaps = std::max<size_t>(nmaps, 1);
     t += alloc_bytes(b * sp.panel32_entries * 4) + alloc_bytes(b * sp.diag_entries * 8) +
-         alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
+         alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) + alloc_bytes(4) +
          alloc_bytes(b * sp.diag_entries * 4) + 2 * alloc_bytes(b * sp.panel32_entries * 4) +
          alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
   }
@@ -723,7 +724,7 @@ extern "C" void gp_factor_free(gp_factor_t* f) {
     cudaSetDevice(ctx->device);
     dev_free_all(ctx, f->bufs);
   }
-  for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor})
+  for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine})
     if (g) cudaGraphExecDestroy(g);
   delete f;
   if (ctx) ctx_release(ctx);

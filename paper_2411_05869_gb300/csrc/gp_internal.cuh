@@ -284,6 +284,11 @@ struct gp_factor_s {
   // CUDA graphs of the fixed launch sequences, captured on first use and replayed (launch counts per replay)
   cudaGraphExec_t gx_factor = nullptr, gx_solve = nullptr, gx_cor = nullptr;
   int64_t n_factor = 0, n_solve = 0, n_cor = 0;
+  cudaGraphExec_t gx_refine = nullptr;   // GP_MIXED: the refinement loop with its test on the device
+  int64_t n_refine = 0;
+  const double* refine_out = nullptr;    // the output pointers gx_refine was built for
+  const double* refine_err = nullptr;
+  int32_t* refine_it = nullptr;          // GP_MIXED: its correction counter
   int32_t* tiles_err = nullptr; // GP_MIXED: set when a bounded tensor-core wait ran out
   double* upd = nullptr;        // B x update_entries
   float* upd32 = nullptr;

@@ -19,6 +19,7 @@
 // Sums use fixed-shape trees, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "factor_access.cuh"
 #include "gp_internal.cuh"
@@ -644,6 +645,20 @@ __global__ void __launch_bounds__(RELRES_THREADS) k_relres(const double* __restr
   }
 }
 
+// The refinement loop's test on the device: continue while some proposal's |r - C alpha| / |r| exceeds 1e-12 (or
+// is not finite) and fewer than 10 corrections have run. it[0] counts the corrections; a factorization whose
+// bounded waits ran out (tc_err) stops the loop at once (its outputs become NaN).
+__global__ void k_refine_test(const double* __restrict__ err, int B, int32_t* __restrict__ it,
+                              const int32_t* __restrict__ tc_err, int reset, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  if (reset) it[0] = 0;
+  double worst = 0.0;
+  for (int b = 0; b < B; b++) worst = fmax(worst, isfinite(err[b]) ? err[b] : 1.0);
+  const bool more = worst > 1e-12 && it[0] < 10 && !(tc_err && *tc_err);
+  if (more) it[0] += 1;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t cnt) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) y[i] += x[i];
@@ -774,6 +789,87 @@ static void run_maybe_graph(gp_ctx* ctx, cudaGraphExec_t* gx, int64_t* nl, F&& b
   replay_graph(ctx, *gx, *nl);
 }
 
+// The mixed path's refinement (A11) as one executable graph, so that gp_loglik neither waits for the device nor
+// reads back a residual: [residual, test] then a conditional WHILE node whose body is [correction solve, alpha +=
+// correction, residual, test], then [final residual with r . alpha, log-likelihood]. The test kernel sets the loop's
+// condition (cudaGraphSetConditional). The output pointers are baked into the graph, so it is rebuilt when they
+// change. *nl receives the launches of one pass (the body counted once).
+template <class St>
+static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St& store, double* res, double* cor,
+                                          double* errv, double* s_log, double* s_quad, double* d_out, double* d_err,
+                                          int64_t* nl) {
+  const int B = f->B;
+  const int64_t n = f->ps->n;
+  cudaStream_t st = ctx->stream;
+  const int64_t l0 = ctx->launches;
+  cudaGraph_t g = nullptr, body = nullptr;
+  GP_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  try {
+    GP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    int32_t* it = f->refine_it;
+    // [residual, test]
+    GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->tiles_err, 1, h);
+    GP_CHECK_LAUNCH(ctx);
+    cudaGraph_t gg = nullptr;
+    GP_CUDA(cudaStreamEndCapture(st, &gg));
+    // the loop node after the captured nodes without successors
+    size_t nn = 0;
+    GP_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn), sinks;
+    GP_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    for (cudaGraphNode_t v : nodes) {
+      size_t nd = 0;
+      GP_CUDA(cudaGraphNodeGetDependentNodes(v, nullptr, nullptr, &nd));
+      if (nd == 0) sinks.push_back(v);
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    GP_CUDA(cudaGraphAddNode(&loop, g, sinks.data(), nullptr, sinks.size(), &cp));
+    body = cp.conditional.phGraph_out[0];
+    // body: correction, alpha update, residual, test
+    GP_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    solve_impl(ctx, f, store, res, cor, false);
+    k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, st>>>(f->alpha, cor, (int64_t)B * n);
+    GP_CHECK_LAUNCH(ctx);
+    residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->tiles_err, 0, h);
+    GP_CHECK_LAUNCH(ctx);
+    GP_CUDA(cudaStreamEndCapture(st, &gg));
+    // after the loop: r . alpha and the log-likelihood
+    GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
+    k_finish<<<grid_for(B, 128), 128, 0, st>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
+    GP_CHECK_LAUNCH(ctx);
+    GP_CUDA(cudaStreamEndCapture(st, &gg));
+  } catch (...) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(st, &junk);
+    }
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    ctx->launches = l0;
+    throw;
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) throw GpError{GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+  *nl = ctx->launches - l0;
+  ctx->launches = l0;
+  f->refine_out = d_out;
+  f->refine_err = d_err;
+  return ex;
+}
+
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err) {
   ProfScope ps_(ctx, KC_SOLVE);   // the whole solve (with refinement) as one timed span
   gp_pointset* ps = f->ps;
@@ -808,6 +904,16 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   double* res = f->delta;                       // B x n residual
   double* cor = f->delta + (size_t)B * n;       // B x n correction
   double* errv = f->red;                        // B relative residuals (partials are consumed already)
+  if (use_graphs(ctx)) {   // the whole refinement as one graph: the loop's test runs on the device
+    if (f->gx_refine && (f->refine_out != d_out || f->refine_err != d_err)) {
+      GP_CUDA(cudaGraphExecDestroy(f->gx_refine));
+      f->gx_refine = nullptr;
+    }
+    if (!f->gx_refine) f->gx_refine = build_refine_graph(ctx, f, store, res, cor, errv, s_log, s_quad, d_out, d_err,
+                                                         &f->n_refine);
+    replay_graph(ctx, f->gx_refine, f->n_refine);
+    return;
+  }
   std::vector<double> herr(B);
   int32_t terr = 0;
   for (int it = 0; it < 10; it++) {

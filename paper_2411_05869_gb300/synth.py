@@ -213,11 +213,16 @@ def uniform_spacetime(n: int, m: int, nnz_row: float, nbumps: int, seed: int, nd
 
 
 def perturb(rng, base: Hyper, rel: float = 0.1) -> Hyper:
-    """Proposal: amplitudes, bump radii and noise variance each scaled by (1 + rel * N(0,1)), kept > 0."""
+    """Proposal: amplitudes, bump radii and noise variance each scaled by (1 + rel * N(0,1)), kept > 0. With the
+    non-compact core the bump radii stay (they fix the point set's pattern) and sigma0, Sigma0 move instead."""
     hp = base.copy()
     nb = hp.n1 * hp.n2
     hp.a = np.maximum(base.a * (1.0 + rel * rng.standard_normal(nb)), 1e-3)
-    hp.r = np.maximum(base.r * (1.0 + rel * rng.standard_normal(nb)), 1e-3)
+    if hp.core_kind == 1:
+        hp.sigma0 = base.sigma0 * math.exp(rel * rng.standard_normal())
+        hp.Sigma0 = base.Sigma0 * math.exp(rel * rng.standard_normal())
+    else:
+        hp.r = np.maximum(base.r * (1.0 + rel * rng.standard_normal(nb)), 1e-3)
     hp.noise_var = max(base.noise_var * (1.0 + rel * rng.standard_normal()), 1e-6)
     return hp
 
