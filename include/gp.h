@@ -314,7 +314,8 @@ GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int6
 GP_API gp_status gp_pattern_counts_noalloc(gp_ctx* ctx, const double* d_X, int64_t n, int d, const double* core_radius,
                                            int64_t* d_counts);
 
-/* Number of kernel launches this context has issued (a counter for launch accounting). */
+/* Number of kernel launches this context has issued (a counter for launch accounting). The passes of the mixed
+ * refinement loop, decided on the device, are added when gp_factor_info next reads the factor. */
 GP_API int64_t gp_launch_count(const gp_ctx* ctx);
 
 /* Device bytes gp_factor allocates for B settings of `theta`'s shape on point set ps in precision prec (the

@@ -550,6 +550,8 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
       f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
       f->refine_it = dalloc<int32_t>(ctx, f->bufs, 1);
+      f->refine_runs = dalloc<unsigned long long>(ctx, f->bufs, 1);
+      GP_CUDA(cudaMemsetAsync(f->refine_runs, 0, sizeof(unsigned long long), ctx->stream));
       f->dinv32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->op_hi = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
       f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
@@ -607,6 +609,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
     nmaps = std::max<size_t>(nmaps, 1);
     t += alloc_bytes(b * sp.panel32_entries * 4) + alloc_bytes(b * sp.diag_entries * 8) +
          alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) + alloc_bytes(4) +
+         alloc_bytes(8) +
          alloc_bytes(b * sp.diag_entries * 4) + 2 * alloc_bytes(b * sp.panel32_entries * 4) +
          alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
   }
@@ -735,12 +738,18 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
   gp_ctx* ctx = f->ctx;
   std::vector<int32_t> flags(f->B);
   int32_t terr = 0;
+  unsigned long long runs = 0;
   gp_status st = guarded(ctx, [&] {
     d2h(ctx, flags.data(), f->notpd, f->B);
     if (f->tiles_err) d2h(ctx, &terr, f->tiles_err, 1);
+    if (f->refine_runs) d2h(ctx, &runs, f->refine_runs, 1);
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != GP_OK) return st;
+  if (runs > f->refine_runs_seen) {   // the refinement loop's passes, counted once they are known
+    ctx->launches += (int64_t)(runs - f->refine_runs_seen) * f->n_refine_body;
+    const_cast<gp_factor_t*>(f)->refine_runs_seen = runs;
+  }
   info->timed_out = terr != 0 ? 1 : 0;
   info->B = f->B;
   info->precision = f->prec;

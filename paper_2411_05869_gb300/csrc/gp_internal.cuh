@@ -289,6 +289,9 @@ struct gp_factor_s {
   const double* refine_out = nullptr;    // the output pointers gx_refine was built for
   const double* refine_err = nullptr;
   int32_t* refine_it = nullptr;          // GP_MIXED: its correction counter
+  unsigned long long* refine_runs = nullptr;   // corrections the loop has run (device, for launch accounting)
+  int64_t n_refine_body = 0;             // launches of one pass of the loop body
+  unsigned long long refine_runs_seen = 0;     // corrections already added to the context's launch count
   int32_t* tiles_err = nullptr; // GP_MIXED: set when a bounded tensor-core wait ran out
   double* upd = nullptr;        // B x update_entries
   float* upd32 = nullptr;

@@ -649,13 +649,17 @@ __global__ void __launch_bounds__(RELRES_THREADS) k_relres(const double* __restr
 // is not finite) and fewer than 10 corrections have run. it[0] counts the corrections; a factorization whose
 // bounded waits ran out (tc_err) stops the loop at once (its outputs become NaN).
 __global__ void k_refine_test(const double* __restrict__ err, int B, int32_t* __restrict__ it,
-                              const int32_t* __restrict__ tc_err, int reset, cudaGraphConditionalHandle h) {
+                              unsigned long long* __restrict__ runs, const int32_t* __restrict__ tc_err, int reset,
+                              cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0) return;
   if (reset) it[0] = 0;
   double worst = 0.0;
   for (int b = 0; b < B; b++) worst = fmax(worst, isfinite(err[b]) ? err[b] : 1.0);
   const bool more = worst > 1e-12 && it[0] < 10 && !(tc_err && *tc_err);
-  if (more) it[0] += 1;
+  if (more) {
+    it[0] += 1;
+    runs[0] += 1;   // corrections run by the loop over the factor's life (launch accounting)
+  }
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
@@ -811,7 +815,7 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     // [residual, test]
     GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->tiles_err, 1, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->refine_runs, f->tiles_err, 1, h);
     GP_CHECK_LAUNCH(ctx);
     cudaGraph_t gg = nullptr;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
@@ -835,12 +839,14 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     body = cp.conditional.phGraph_out[0];
     // body: correction, alpha update, residual, test
     GP_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int64_t lb = ctx->launches;
     solve_impl(ctx, f, store, res, cor, false);
     k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, st>>>(f->alpha, cor, (int64_t)B * n);
     GP_CHECK_LAUNCH(ctx);
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->tiles_err, 0, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->refine_runs, f->tiles_err, 0, h);
     GP_CHECK_LAUNCH(ctx);
+    f->n_refine_body = ctx->launches - lb;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
     // after the loop: r . alpha and the log-likelihood
     GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal));
@@ -863,7 +869,7 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
   cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) throw GpError{GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
-  *nl = ctx->launches - l0;
+  *nl = ctx->launches - l0 - f->n_refine_body;   // a replay counts the loop body only as it runs (below)
   ctx->launches = l0;
   f->refine_out = d_out;
   f->refine_err = d_err;
