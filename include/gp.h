@@ -100,7 +100,8 @@ typedef struct {
   int64_t bytes;              /* device bytes held by the factor */
   int32_t not_pd_count;       /* proposals whose factorization met a non-positive pivot */
   int32_t diag_fp32;          /* GP_MIXED: 1 if its 64 x 64 diagonal blocks are factored in FP32 (GP_OPT_DIAG_FP32) */
-  int32_t timed_out;          /* GP_MIXED: 1 if a bounded wait of the last factorization ran out (GP_ERR_TIMEOUT) */
+  int32_t timed_out;          /* 1 if a bounded wait of the last factorization or of a later solve ran out
+                                 (GP_ERR_TIMEOUT) */
 } gp_factor_info_t;
 
 /* Context options (gp_set_option). They apply to the factors created on the context afterwards.
@@ -110,12 +111,14 @@ typedef struct {
  *     the cost of an FP32-accurate diagonal of L in the log-determinant.
  *   GP_OPT_WAIT_POLLS (default 2^26, 1..2^32-1) and GP_OPT_WAIT_NS (default 1e9, >= 0): the limits of every
  *     bounded wait of the GP_MIXED tensor-core kernels (an mbarrier phase awaited by one warp role from another:
- *     operand copies landed, MMAs done, accumulator drained). A wait that runs out after that many polls or
- *     nanoseconds records the failure in the factor and winds its kernel down (after waiting, with the default
- *     limits, for the copies and MMAs it already issued); every later tensor-core launch of that factorization
- *     skips its tiles. The factor then reports GP_ERR_TIMEOUT: gp_factor_info (timed_out = 1) and gp_loglik return
- *     it, and the log-likelihoods are NaN. No legitimate wait comes near the defaults; tiny limits make waits run
- *     out on purpose (a test of this path). The next gp_factor_update of the factor starts clean. */
+ *     operand copies landed, MMAs done, accumulator drained) and of the solves' tasks in both precisions (a task
+ *     awaiting a block another task of the same launch publishes). A wait that runs out after that many polls or
+ *     nanoseconds records the failure in the factor and ends its wait: a tensor-core kernel winds down (after
+ *     waiting, with the default limits, for the copies and MMAs it already issued) and every later tensor-core
+ *     launch of that factorization skips its tiles; a solve task goes on with what it has. The factor then
+ *     reports GP_ERR_TIMEOUT: gp_factor_info (timed_out = 1) and gp_loglik return it, and the log-likelihoods are
+ *     NaN. No legitimate wait comes near the defaults; tiny limits make waits run out on purpose (a test of this
+ *     path). The next gp_factor_update of the factor starts clean. */
 typedef enum {
   GP_OPT_DIAG_FP32 = 0,
   GP_OPT_WAIT_POLLS = 1,
@@ -296,6 +299,10 @@ GP_API gp_status gp_loglik_iterative(gp_ctx* ctx, gp_factor_t* f, int b, const d
  * Errors: GP_ERR_ARG (class out of range), GP_ERR_CUDA. */
 GP_API gp_status gp_profile(gp_ctx* ctx, int enable);
 GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops);
+/* The same, restricted to the launches a factorization issued for elimination-tree level `level` (0 = the
+ * leaves' level, as gp_pointset_export's sn_level numbers them; 0 <= level < 64). Classes 1-5 and 9 are issued per
+ * level; the others read 0. Errors: GP_ERR_ARG (class or level out of range), GP_ERR_CUDA. */
+GP_API gp_status gp_profile_read_level(gp_ctx* ctx, int kclass, int level, double* total_ms, int64_t* launches);
 
 /* Support-pattern row counts without any device allocation (the paper has no counterpart: this serves
  * callers that must not allocate device memory, such as code running under another framework's memory

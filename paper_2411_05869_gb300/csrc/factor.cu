@@ -330,9 +330,12 @@ static void factor_body(gp_ctx* ctx, gp_factor_t* f) {
   values_run(ctx, f);   // A3, A4 (zeroes and fills the panels)
   k_fill_i32<<<grid_for(B, 128), 128, 0, st>>>(f->notpd, B, INT_MAX);
   GP_CHECK_LAUNCH(ctx);
+  GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), st));
   const int32_t* d_sn_parent = dp.sn_parent;
+  ProfLevelScope pls_(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
+    ctx->prof_level = L;
     int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
     k_zero_updates<<<dim3(nl, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd, UE);
     GP_CHECK_LAUNCH(ctx);

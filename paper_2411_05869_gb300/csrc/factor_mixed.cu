@@ -98,41 +98,53 @@ __global__ void k_zero_updates32(const int32_t* __restrict__ list, DevPlan dp, f
   }
 }
 
-// One CTA per (child, 8 rows of its update matrix): row a of U_child, columns b <= a, into the parent front.
-__global__ void k_extend_add32(const int2* __restrict__ tab, DevPlan dp, float* __restrict__ p32,
-                               double* __restrict__ dg, float* __restrict__ u32, int64_t P32E, int64_t DE,
-                               int64_t UE) {
-  int2 task = tab[blockIdx.x];
-  int32_t c = task.x, a0 = task.y;
-  int b = blockIdx.y;
+// One CTA per (child, 8 rows of its update matrix): row a of U_child, columns b <= a, into the parent front
+// (row rel[a], columns rel[b]). A thread takes EA_U entries of a row per round with all their loads in flight
+// before any store; the targets of a row are distinct (rel is increasing), as are those of different rows, and a
+// launch takes one child of each parent, so no two threads of a launch touch one target.
+constexpr int EA_THREADS = 256, EA_U = 4;
+__global__ void __launch_bounds__(EA_THREADS) k_extend_add32(const int2* __restrict__ tab, DevPlan dp,
+                                                             float* __restrict__ p32, double* __restrict__ dg,
+                                                             float* __restrict__ u32, int64_t P32E, int64_t DE,
+                                                             int64_t UE) {
+  const int2 task = tab[blockIdx.x];
+  const int32_t c = task.x, a0 = task.y;
+  const int b = blockIdx.y;
   float* pp = p32 + (int64_t)b * P32E;
   double* pd = dg + (int64_t)b * DE;
   float* pu = u32 + (int64_t)b * UE;
-  int32_t p = dp.sn_parent[c];
-  int32_t rc = dp.r[c];
+  const int32_t p = dp.sn_parent[c];
+  const int32_t rc = dp.r[c];
   const float* Uc = pu + dp.uoff[c];
   const int32_t* rel = dp.relidx + dp.relidx_off[c];
-  MixFront fp = mix_front(dp, p, pp, pd, pu);
-  int32_t a1 = min(a0 + 8, rc);
-  // two entries per thread per round, both loads of the targets in flight before either store (the targets of
-  // one row are distinct: rel is increasing)
+  const MixFront fp = mix_front(dp, p, pp, pd, pu);
+  const int32_t a1 = min(a0 + 8, rc);
   for (int32_t a = a0; a < a1; a++) {
     const int32_t tr = rel[a];
     const float* ur = Uc + (int64_t)a * rc;
-    for (int32_t b0 = threadIdx.x; b0 <= a; b0 += 2 * blockDim.x) {
-      const int32_t b1 = b0 + blockDim.x;
-      const bool two = b1 <= a;
-      const int32_t c0 = rel[b0], c1 = two ? rel[b1] : 0;
-      const float v0 = ur[b0], v1 = two ? ur[b1] : 0.f;
-      if (two && c1 >= fp.w && c0 >= fp.w) {   // both in the update matrix (the common case below the front)
-        float* t0 = fp.Uu + (int64_t)(tr - fp.w) * fp.r + (c0 - fp.w);
-        float* t1 = fp.Uu + (int64_t)(tr - fp.w) * fp.r + (c1 - fp.w);
-        const float o0 = *t0, o1 = *t1;
-        *t0 = o0 + v0;
-        *t1 = o1 + v1;
-      } else {
-        mix_add(fp, tr, c0, v0);
-        if (two) mix_add(fp, tr, c1, v1);
+    for (int32_t base = 0; base <= a; base += EA_U * EA_THREADS) {
+      int32_t cc[EA_U];
+      float vv[EA_U];
+#pragma unroll
+      for (int k = 0; k < EA_U; k++) {
+        const int32_t bb = base + k * EA_THREADS + (int32_t)threadIdx.x;
+        cc[k] = bb <= a ? rel[bb] : -1;
+        vv[k] = bb <= a ? ur[bb] : 0.f;
+      }
+      if (tr >= fp.w) {   // a row below the parent's columns: its update-matrix row or its FP32 panel row
+        float* urow = fp.Uu + (int64_t)(tr - fp.w) * fp.r - fp.w;   // indexed by the parent column
+        float* prow = fp.P + (int64_t)tr * fp.ldw;
+        float old[EA_U];
+#pragma unroll
+        for (int k = 0; k < EA_U; k++)
+          if (cc[k] >= 0) old[k] = cc[k] >= fp.w ? urow[cc[k]] : prow[cc[k]];
+#pragma unroll
+        for (int k = 0; k < EA_U; k++)
+          if (cc[k] >= 0) (cc[k] >= fp.w ? urow[cc[k]] : prow[cc[k]]) = old[k] + vv[k];
+      } else {   // a row of the parent's columns: panel or FP64 diagonal tile
+#pragma unroll
+        for (int k = 0; k < EA_U; k++)
+          if (cc[k] >= 0) mix_add(fp, tr, cc[k], vv[k]);
       }
     }
   }
@@ -1207,8 +1219,10 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   k_fill_i32<<<grid_for(B, 128), 128, 0, st>>>(f->notpd, B, INT_MAX);
   GP_CHECK_LAUNCH(ctx);
   GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), st));
+  ProfLevelScope pls_(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
+    ctx->prof_level = L;
     int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
     int64_t r2max = 1;   // CTAs per front sized by the level's largest update matrix
     for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
@@ -1220,8 +1234,8 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
     GP_CHECK_LAUNCH(ctx);
     for (const auto& ea : lv.ea) {
       ProfScope ps_(ctx, KC_EXTEND_ADD);
-      k_extend_add32<<<dim3((unsigned)ea.ncta, B), 128, 0, st>>>(dp.ea_tab + ea.tab_off, dp, f->panels32, f->diag,
-                                                                 f->upd32, P32E, DE, UE);
+      k_extend_add32<<<dim3((unsigned)ea.ncta, B), EA_THREADS, 0, st>>>(dp.ea_tab + ea.tab_off, dp, f->panels32,
+                                                                        f->diag, f->upd32, P32E, DE, UE);
       GP_CHECK_LAUNCH(ctx);
     }
     if (lv.nsmall > 0) {
@@ -1295,6 +1309,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       }
     }
   }
+  ctx->prof_level = -1;   // one launch over all levels
   if (!f->diag_fp32 && !sp.large_fronts.empty()) {   // L_11 of every diagonal tile in FP64
     ProfScope ps_(ctx, KC_POTRF);
     k_potrf_tiles64<<<dim3((unsigned)sp.large_fronts.size(), B), POTRF_THREADS, 0, st>>>(

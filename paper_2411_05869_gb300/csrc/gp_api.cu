@@ -221,13 +221,20 @@ namespace {
 void prof_collect(gp_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (int k = 0; k < KC_COUNT; k++) {
-    for (auto& ev : ctx->prof_ev[k]) {
+    for (size_t e = 0; e < ctx->prof_ev[k].size(); e++) {
+      const auto& ev = ctx->prof_ev[k][e];
+      const int lv = e < ctx->prof_lv[k].size() ? ctx->prof_lv[k][e] : -1;
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) ctx->prof_ms[k] += ms;
+      if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+        ctx->prof_ms[k] += ms;
+        if (lv >= 0 && lv < GP_PROF_LEVELS) ctx->prof_ms_lv[k][lv] += ms;
+      }
+      if (lv >= 0 && lv < GP_PROF_LEVELS) ctx->prof_n_lv[k][lv]++;
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);
     }
     ctx->prof_ev[k].clear();
+    ctx->prof_lv[k].clear();
   }
 }
 }  // namespace
@@ -240,6 +247,10 @@ extern "C" gp_status gp_profile(gp_ctx* ctx, int enable) {
       ctx->prof_ms[k] = 0.0;
       ctx->prof_n[k] = 0;
       ctx->prof_flops[k] = 0.0;
+      for (int l = 0; l < GP_PROF_LEVELS; l++) {
+        ctx->prof_ms_lv[k][l] = 0.0;
+        ctx->prof_n_lv[k][l] = 0;
+      }
     }
     ctx->prof = enable != 0;
   });
@@ -252,6 +263,16 @@ extern "C" gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, 
     if (total_ms) *total_ms = ctx->prof_ms[kclass];
     if (launches) *launches = ctx->prof_n[kclass];
     if (flops) *flops = ctx->prof_flops[kclass];
+  });
+}
+
+extern "C" gp_status gp_profile_read_level(gp_ctx* ctx, int kclass, int level, double* total_ms,
+                                           int64_t* launches) {
+  if (!ctx || kclass < 0 || kclass >= KC_COUNT || level < 0 || level >= GP_PROF_LEVELS) return GP_ERR_ARG;
+  return guarded(ctx, [&] {
+    prof_collect(ctx);
+    if (total_ms) *total_ms = ctx->prof_ms_lv[kclass][level];
+    if (launches) *launches = ctx->prof_n_lv[kclass][level];
   });
 }
 
@@ -338,6 +359,9 @@ gp_status assemble_common(gp_ctx* ctx, const double* d_X, int64_t n, int d, cons
     dp.loff32 = upload(ctx, ps->bufs, sp.sn_loff32);
     dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
     dp.large_kb = upload(ctx, ps->bufs, sp.large_kb);
+    dp.sn_fl = upload(ctx, ps->bufs, sp.sn_fl);
+    dp.flow_fwd = upload(ctx, ps->bufs, sp.flow_fwd);
+    dp.flow_bwd = upload(ctx, ps->bufs, sp.flow_bwd);
     upload_schedule(ctx, ps);
     compute_dest_map(ctx, ps);             // pinv and the CSR -> panel scatter map
     GP_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -548,7 +572,6 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->diag = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
-      f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
       f->refine_it = dalloc<int32_t>(ctx, f->bufs, 1);
       f->refine_runs = dalloc<unsigned long long>(ctx, f->bufs, 1);
       GP_CUDA(cudaMemsetAsync(f->refine_runs, 0, sizeof(unsigned long long), ctx->stream));
@@ -568,6 +591,9 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
     f->work_stride = 3 * ps->n + sp.vec_update_entries + 64;
     f->work = dalloc<double>(ctx, f->bufs, (size_t)B * f->work_stride);
     f->bwd_part = dalloc<double>(ctx, f->bufs, (size_t)B * bwd_part_entries(sp));
+    f->tiles_err = dalloc<int32_t>(ctx, f->bufs, 1);
+    GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), ctx->stream));
+    f->flow_sync = dalloc<int32_t>(ctx, f->bufs, flow_sync_entries(sp, B));
     f->red_stride = 2 * ((ps->n + 1023) / 1024) + 8;
     f->red = dalloc<double>(ctx, f->bufs, (size_t)B * f->red_stride + 4 * (size_t)B + 8);
     pack_thetas(f, thetas, cores);
@@ -608,7 +634,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
       }
     nmaps = std::max<size_t>(nmaps, 1);
     t += alloc_bytes(b * sp.panel32_entries * 4) + alloc_bytes(b * sp.diag_entries * 8) +
-         alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) + alloc_bytes(4) +
+         alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
          alloc_bytes(8) +
          alloc_bytes(b * sp.diag_entries * 4) + 2 * alloc_bytes(b * sp.panel32_entries * 4) +
          alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
@@ -617,6 +643,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
   if (prec == GP_FP64) t += alloc_bytes(b * sp.diag_entries * 8);
   t += alloc_bytes(b * n * 8) + alloc_bytes(b * (3 * n + sp.vec_update_entries + 64) * 8) +
        alloc_bytes(b * (size_t)bwd_part_entries(sp) * 8) +
+       alloc_bytes(4) + alloc_bytes((size_t)flow_sync_entries(sp, (int)b) * 4) +
        alloc_bytes((b * (2 * ((n + 1023) / 1024) + 8) + 4 * b + 8) * 8);
   return t;
 }
@@ -763,7 +790,8 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
     if (bad) info->not_pd_count++;
     if (not_pd_column) not_pd_column[b] = bad ? flags[b] : -1;
   }
-  if (terr != 0) return fail(ctx, GpError{GP_ERR_TIMEOUT, "a bounded wait of the tensor-core updates ran out"});
+  if (terr != 0)
+    return fail(ctx, GpError{GP_ERR_TIMEOUT, "a bounded wait of the tensor-core updates or of a solve ran out"});
   return GP_OK;
 }
 

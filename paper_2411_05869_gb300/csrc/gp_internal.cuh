@@ -57,6 +57,7 @@ struct GpError {
 
 // ------------------------------------------------------------------------------------------ context
 // Kernel classes timed by the optional launch profiler (gp_profile / gp_profile_read).
+constexpr int GP_PROF_LEVELS = 64;   // levels the profiler resolves (deeper levels are counted in the totals only)
 enum KClass { KC_VALUES = 0, KC_EXTEND_ADD, KC_FRONT_SMALL, KC_POTRF, KC_TRSM, KC_UPDATE, KC_SOLVE, KC_PREDICT,
               KC_ASSEMBLE, KC_UPDATE_LEFT, KC_COUNT };
 
@@ -77,6 +78,12 @@ struct gp_ctx {
   int64_t prof_n[KC_COUNT] = {};
   double prof_flops[KC_COUNT] = {};
   cudaEvent_t prof_open = nullptr;
+  // the same by elimination-tree level for the factorization's classes (prof_level: the level whose launches
+  // are being issued, -1 outside the level loop)
+  int prof_level = -1;
+  std::vector<int> prof_lv[KC_COUNT];
+  double prof_ms_lv[KC_COUNT][GP_PROF_LEVELS] = {};
+  int64_t prof_n_lv[KC_COUNT][GP_PROF_LEVELS] = {};
   // options (gp_set_option); they apply to factors created afterwards
   int opt_diag_fp32 = 0;     // GP_MIXED: diagonal blocks factored in FP32
   tcg::WaitLimit opt_wait = tcg::DEFAULT_WAIT;   // GP_MIXED: limits of the tensor-core kernels' bounded waits
@@ -100,8 +107,16 @@ struct ProfScope {
     cudaEventCreate(&b);
     cudaEventRecord(b, c->stream);
     c->prof_ev[cls].push_back({c->prof_open, b});
+    c->prof_lv[cls].push_back(c->prof_level);
     c->prof_n[cls]++;
   }
+};
+
+// Clears the profiler's current level when a factorization's level loop ends (normally or by an exception).
+struct ProfLevelScope {
+  gp_ctx* c;
+  explicit ProfLevelScope(gp_ctx* ctx) : c(ctx) {}
+  ~ProfLevelScope() { c->prof_level = -1; }
 };
 
 // Device buffer owned by a handle; charged against the context budget.
@@ -194,6 +209,16 @@ struct SymPlan {
   std::vector<LevelLarge> level_large;
   std::vector<int64_t> step_pre;     // per step: prefix of TRSM tasks then of UPDATE tasks (2*(nfront+1))
   std::vector<int64_t> pair_pre;     // per step pair: prefix of the paired forward-solve row tiles
+  // Solves of the large fronts as one launch per level (tasks that wait for the blocks they need):
+  //   flow_fwd: per level, the forward tasks (front, i): i < nb the front's block row i, i >= nb the 64-row tile
+  //     i - nb of the rows below its columns; ordered by i, then by the level's large-front order;
+  //   flow_bwd: per level, the backward tasks (front, block column J), ordered by nb - 1 - J, then front order.
+  //   sn_fl: first readiness flag of each large front (one per 64-column block; -1 for small fronts).
+  // Every task waits only for tasks earlier in its list.
+  std::vector<int2> flow_fwd, flow_bwd;
+  std::vector<int32_t> sn_fl;
+  int64_t n_fl = 0;
+  std::vector<int64_t> flow_fwd_ptr, flow_bwd_ptr;   // nlevels + 1
 };
 
 // Device mirror of the plan (pointers into one allocation set owned by the point set).
@@ -218,6 +243,8 @@ struct DevPlan {
   int32_t* upd_fronts;
   int64_t* upd_pre;
   int64_t* pair_pre;
+  int32_t* sn_fl;
+  int2 *flow_fwd, *flow_bwd;
 };
 
 void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, SymPlan& sp);
@@ -263,7 +290,7 @@ struct gp_factor_s {
   int B = 0;
   gp_precision prec = GP_FP64;
   bool diag_fp32 = false;       // GP_MIXED: diagonal blocks factored in FP32 (default FP64)
-  tcg::WaitLimit wait_lim = tcg::DEFAULT_WAIT;   // GP_MIXED: bounded-wait limits of the tensor-core kernels
+  tcg::WaitLimit wait_lim = tcg::DEFAULT_WAIT;   // bounded-wait limits (tensor-core kernels, solve tasks)
   double* theta_dev = nullptr;  // B packed settings
   int64_t theta_stride = 0;
   double* F = nullptr;          // B x n x n1 bump features
@@ -292,7 +319,8 @@ struct gp_factor_s {
   unsigned long long* refine_runs = nullptr;   // corrections the loop has run (device, for launch accounting)
   int64_t n_refine_body = 0;             // launches of one pass of the loop body
   unsigned long long refine_runs_seen = 0;     // corrections already added to the context's launch count
-  int32_t* tiles_err = nullptr; // GP_MIXED: set when a bounded tensor-core wait ran out
+  int32_t* tiles_err = nullptr; // set when a bounded wait (tensor-core updates, solve tasks) ran out
+  int32_t* flow_sync = nullptr; // the solve tasks' tickets and readiness flags (flow_sync_entries)
   double* upd = nullptr;        // B x update_entries
   float* upd32 = nullptr;
   double* val = nullptr;        // B x nnz CSR values of C_z (refinement SpMV)
@@ -355,6 +383,11 @@ void compute_dest_map(gp_ctx* ctx, gp_pointset* ps);
 void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps);
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f);
 int64_t bwd_part_entries(const SymPlan& sp);
+// The solve tasks' tickets (forward and backward, one each per level) and readiness flags (forward and
+// backward, B x n_fl each).
+inline int64_t flow_sync_entries(const SymPlan& sp, int B) {
+  return 2 * (int64_t)sp.nlevels + 2 * (int64_t)B * sp.n_fl;
+}
 void plan_mixed_updates(SymPlan& sp, int group, int tn);
 void upload_schedule(gp_ctx* ctx, gp_pointset* ps);
 size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const ThetaDims& td);

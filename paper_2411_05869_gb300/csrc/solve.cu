@@ -7,9 +7,9 @@
 // starts as the permuted right-hand side on its columns, receives every child's update vector through the
 // child's relative indices (children in order), then x = L11^{-1} f_1 and f_2 -= L21 x; f_2 is the update
 // vector handed to the parent. Backward (levels descending): t = x - L21^T alpha'(rows below), then
-// L11^T z = t. Fronts of order <= 96 use one CTA; larger ones advance 64 columns per launch, every CTA
-// multiplying by the inverted 64 x 64 diagonal block (formed by the factorization) and applying the result
-// to its own 64-row (or 64-column) tile.
+// L11^T z = t. Fronts of order <= 96 use one CTA; the larger fronts of a level take one launch per sweep, in
+// tasks of 64 rows (forward) or 64 columns (backward) that wait for the blocks they need (k_fwd_flow,
+// k_bwd_flow), each block solved with the inverted 64 x 64 diagonal block the factorization formed.
 // The kernels read the factor through an accessor: FP64 column-major panels (GP_FP64) or FP32 row-major
 // panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the solves run in FP64 and the quadratic form is
 // |L^{-1} P r|^2. In GP_MIXED the solves run in FP32 (FP32 inverses, FP32 vectors): they only precondition
@@ -84,148 +84,6 @@ __global__ void k_fwd_small(const int32_t* __restrict__ list, DevPlan dp, St sto
     V x = xs;
     for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) fv[i] -= A.L(i, j) * x;
     __syncthreads();
-  }
-}
-
-// The pieces of a forward step, shared by the single and the paired launches.
-// x = inv(L_JJ) f_J for a block of width bw: inv is the block's 64 x 64 inverse, fb (shared) holds f_J; the
-// product is split four ways over l and combined in a fixed order.
-template <class V>
-__device__ __forceinline__ void fwd_block_solve(const V* __restrict__ inv, const V* fb, V* x, V* LiT, V (*part)[T],
-                                                int bw) {
-#pragma unroll
-  for (int u = 0; u < T * T / 256; u++) {
-    const int q = threadIdx.x + u * 256;
-    LiT[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
-  }
-  __syncthreads();
-  {   // the inverse is lower triangular with zeros above (and past bw), so every l enters
-    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
-    V acc = 0;
-#pragma unroll
-    for (int l = g * 16; l < g * 16 + 16; l++) acc += LiT[l * (T + 1) + q] * fb[l];
-    part[g][q] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x < T) {
-    const int q = threadIdx.x;
-    x[q] = q < bw ? (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]) : V(0);
-  }
-  __syncthreads();
-}
-
-// acc_i = L[i, c0 .. c0 + bw) x for the rows [r0, rend) (at most 64), handed to sink(i, acc) by one thread per
-// row. Row-major panels: a half-warp reads one row's 64 entries as 16 float4, four rows per half-warp with all
-// loads in flight, a fixed shuffle tree per row; column-major: thread per row.
-template <class St, class Sink>
-__device__ __forceinline__ void fwd_rows(const typename St::Acc& A, int64_t r0, int64_t rend, int c0, int bw,
-                                         const typename St::V* x, Sink&& sink) {
-  using V = typename St::V;
-  if constexpr (St::kRowMajor) {
-    // columns past bw are zero in x and the row is padded to ldw (a multiple of 4): whole float4 reads are safe
-    const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int64_t i = r0 + hw + 16 * u;
-      v[u] = (i < rend && l < bw) ? *reinterpret_cast<const float4*>(A.P + i * A.ldw + c0 + l)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      V acc = (V)v[u].x * x[l] + (V)v[u].y * x[l + 1] + (V)v[u].z * x[l + 2] + (V)v[u].w * x[l + 3];
-      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      const int64_t i = r0 + hw + 16 * u;
-      if (i < rend && (threadIdx.x & 15) == 0) sink(i, acc);
-    }
-  } else {
-    for (int64_t i = r0 + threadIdx.x; i < rend; i += blockDim.x) {
-      V acc = 0;
-      for (int l = 0; l < bw; l++) acc += A.L(i, c0 + l) * x[l];
-      sink(i, acc);
-    }
-  }
-}
-
-// Forward, block column kb of every large front of a step, one launch: every CTA forms x_J = inv(L_JJ) f_J
-// (a 64 x 64 product with the inverted diagonal block); tasks [0, nfront) write x_J to x (the front vector's
-// block stays untouched, others read it), the rest (64-row tile prefix) apply f_i -= L[i, J] x_J to one tile.
-template <class St>
-__global__ void __launch_bounds__(256) k_fwd_step(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                                  int nfront, int kb, DevPlan dp, St store,
-                                                  typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
-  using V = typename St::V;
-  __shared__ V LiT[T * (T + 1)];   // LiT[l][q] = inv[q][l]
-  __shared__ V fb[T], x[T], part[4][T];
-  const int64_t t = blockIdx.x;
-  const bool writer = t < nfront;
-  const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
-  const int32_t s = fronts[fi];
-  const int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  V* fv = work + (int64_t)b * ws + dp.frow_off[s];
-  const int w = dp.w[s];
-  const int64_t m = (int64_t)w + dp.r[s];
-  const int c0 = kb * T, bw = min(T, w - c0), c1 = c0 + bw;
-  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
-  fwd_block_solve(store.inv(dp, s, b) + (int64_t)kb * T * T, fb, x, LiT, part, bw);
-  if (writer) {
-    V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
-    if (threadIdx.x < bw) xv[c0 + threadIdx.x] = x[threadIdx.x];
-    return;
-  }
-  const int64_t r0 = c1 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
-  fwd_rows<St>(A, r0, rend, c0, bw, x, [&](int64_t i, V acc) { fv[i] -= acc; });
-}
-
-// Forward, block columns kb and kb + 1 in one launch (the chain of forward steps is the sweep's latency). The
-// fronts [0, n2) of the list have block kb + 1: every CTA forms x1 = inv(L_11) f_1, f_2' = f_2 - L_21 x1 and
-// x2 = inv(L_22) f_2' itself (the same operations, in the same order, as two single steps), then a writer
-// stores x1, x2 and a tile task applies f_i -= L_i1 x1, then f_i -= L_i2 x2 to 64 rows after block kb + 1.
-// Fronts past n2 take block kb alone, as a single step.
-template <class St>
-__global__ void __launch_bounds__(256) k_fwd_pair(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                                  int nfront, int n2, int kb, DevPlan dp, St store,
-                                                  typename St::V* __restrict__ work, int64_t ws, int64_t xv_off) {
-  using V = typename St::V;
-  __shared__ V LiT[T * (T + 1)];   // LiT[l][q] = inv[q][l]
-  __shared__ V fb[T], x1[T], x2[T], part[4][T], a1[T], a2[T];
-  const int64_t t = blockIdx.x;
-  const bool writer = t < nfront;
-  const int fi = writer ? (int)t : find_front(pre, nfront, t - nfront);
-  const int32_t s = fronts[fi];
-  const int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  V* fv = work + (int64_t)b * ws + dp.frow_off[s];
-  const int w = dp.w[s];
-  const int64_t m = (int64_t)w + dp.r[s];
-  const bool two = fi < n2;
-  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
-  const int bw2 = two ? min(T, w - c1) : 0, c2 = c1 + bw2;
-  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
-  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw1 ? fv[c0 + threadIdx.x] : V(0);
-  fwd_block_solve(inv, fb, x1, LiT, part, bw1);
-  if (two) {
-    fwd_rows<St>(A, c1, c2, c0, bw1, x1, [&](int64_t i, V acc) { a1[i - c1] = acc; });
-    __syncthreads();
-    if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < bw2 ? fv[c1 + threadIdx.x] - a1[threadIdx.x] : V(0);
-    fwd_block_solve(inv + T * T, fb, x2, LiT, part, bw2);
-  }
-  if (writer) {
-    V* xv = work + (int64_t)b * ws + xv_off + dp.sn_first[s];
-    if (threadIdx.x < bw1) xv[c0 + threadIdx.x] = x1[threadIdx.x];
-    if (threadIdx.x < bw2) xv[c1 + threadIdx.x] = x2[threadIdx.x];
-    return;
-  }
-  const int64_t r0 = c2 + (t - nfront - pre[fi]) * T, rend = imin64(r0 + T, m);
-  fwd_rows<St>(A, r0, rend, c0, bw1, x1, [&](int64_t i, V acc) { a1[i - r0] = acc; });
-  if (two) fwd_rows<St>(A, r0, rend, c1, bw2, x2, [&](int64_t i, V acc) { a2[i - r0] = acc; });
-  __syncthreads();
-  if (threadIdx.x < T && r0 + threadIdx.x < rend) {
-    V v = fv[r0 + threadIdx.x];
-    v -= a1[threadIdx.x];
-    if (two) v -= a2[threadIdx.x];
-    fv[r0 + threadIdx.x] = v;
   }
 }
 
@@ -343,152 +201,263 @@ __global__ void k_bwd_prep_sum(const int32_t* __restrict__ fronts, const int32_t
   W[dp.frow_off[s] + j0 + c] = W[xv_off + dp.sn_first[s] + j0 + c] - acc;
 }
 
-// The pieces of a backward step, shared by the single and the paired launches.
-// z = inv(L_JJ)^T t_J for a block of width bw: inv is the block's 64 x 64 inverse (row-major into Li), tb
-// (shared) holds t_J; z_q = sum_{l >= q} inv[l][q] t_l (zeros above the diagonal and past bw), split four ways
-// over l and combined in a fixed order.
-template <class V>
-__device__ __forceinline__ void bwd_block_solve(const V* __restrict__ inv, const V* tb, V* z, V* Li, V (*part)[T],
-                                                int bw) {
-#pragma unroll
-  for (int u = 0; u < T * T / 256; u++) {
-    const int q = threadIdx.x + u * 256;
-    Li[(q >> 6) * (T + 1) + (q & 63)] = inv[q];
-  }
-  __syncthreads();
-  const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
-  {
-    V acc = 0;
-#pragma unroll
-    for (int l = g * 16; l < g * 16 + 16; l++) acc += Li[l * (T + 1) + q] * tb[l];
-    part[g][q] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x < T) {
-    const int k = threadIdx.x;
-    z[k] = k < bw ? (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]) : V(0);
-  }
-  __syncthreads();
+// ---------------------------------------------------------------------------------------------------------
+// The large fronts of a level, one launch per sweep. Every CTA draws a ticket, the index of its task in the
+// level's task list (tasks x proposals, proposals inner), and waits (bounded) only for blocks that tasks with
+// lower tickets publish. A task that drew a ticket is running, so the lowest unfinished ticket never waits for
+// an unfinished task and every wait ends.
+//   forward task (s, i < nb): x_i = inv(L_ii) (f_i - sum_{J < i} L_iJ x_J), written to x and published (flag i);
+//   forward task (s, i >= nb): f_R -= sum_{J < nb} L_RJ x_J for the 64 rows R = w + 64 (i - nb) + [0, 64)
+//     below the front's columns (the update vector handed to the parent);
+//   backward task (s, J): z_J = inv(L_JJ)^T (t_J - sum_{I > J} L_IJ^T z_I), with t_J = x_J - L_{R,J}^T alpha'(R)
+//     as the level's partial-sum launches left it in the front vector, written to alpha' and published (flag J).
+// A task publishes only after it has read every block it needs, so a published flag implies all flags before it
+// (after it, backward): one acquire of the last block a task needs covers the rest once the chain has passed.
+// A task reads the L tile of its next block while it waits for the current one. Every task sums its blocks in
+// a fixed order (J ascending, I descending) with fixed-shape trees, so results do not depend on timing.
+
+__device__ __forceinline__ int32_t ld_acquire_gpu(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int32_t* p, int32_t v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// sum_k = sum_l L[r0 + l, k0 + k] z_l over the bw rows of a block (k < 64; returned to threads k < 64), split
-// four ways over l (16 independent loads per thread in flight) and combined in a fixed order.
-template <class St>
-__device__ __forceinline__ typename St::V bwd_tile_sum(const typename St::Acc& A, int r0, int bw, int k0,
-                                                       const typename St::V* z, typename St::V (*part)[T]) {
-  using V = typename St::V;
+// Waits (every calling thread polls; a converged warp makes one request per poll) until *flag != 0. A wait that
+// runs out of polls or time sets *err and returns: the task goes on with what it has and the factor reports
+// the timeout (its log-likelihoods become NaN). Once *err is set no wait of the factor waits any longer, so a
+// launch ends soon after its first wait ran out.
+__device__ __forceinline__ void wait_flag(const int32_t* flag, tcg::WaitLimit lim, int32_t* err) {
+  if (ld_acquire_gpu(flag) != 0) return;
+  const uint64_t t0 = tcg::global_ns();
+  for (uint32_t it = 1; it < lim.polls; it++) {
+    __nanosleep(20);
+    if (ld_acquire_gpu(flag) != 0) return;
+    if ((it & 15) == 15 && (tcg::global_ns() - t0 > lim.ns || ld_acquire_gpu(err) != 0)) break;
+  }
+  atomicExch(err, 1);
+}
+
+// The CTA's ticket (thread 0 draws it; all threads get it).
+__device__ __forceinline__ int draw_ticket(int32_t* ticket, int* slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(ticket, 1);
+  __syncthreads();
+  return *slot;
+}
+
+// y = M f for a 64 x 64 matrix staged in shared memory as Ms[l * (T + 1) + q] = M[q][l] (the forward solve's
+// inverse, transposed) or = M[l][q] (the backward solve's inverse^T), f in shared memory; the product is split
+// four ways over l and combined in a fixed order; y[q] = 0 for q >= bw.
+template <class V>
+__device__ __forceinline__ void block_apply(const V* Ms, const V* fvec, V* y, V (*part)[T], int bw) {
   const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
   V acc = 0;
-  if constexpr (St::kRowMajor) {   // row r0 + l is contiguous over the tile's columns
-    V v[16];
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
-      const int l = g * 16 + e;
-      v[e] = l < bw ? (V)A.P[(int64_t)(r0 + l) * A.ldw + k0 + q] : V(0);
-    }
-#pragma unroll
-    for (int e = 0; e < 16; e++) acc += v[e] * z[g * 16 + e];
-  } else {
-    for (int e = 0; e < 16; e++) {
-      const int l = g * 16 + e;
-      if (l < bw) acc += A.L(r0 + l, k0 + q) * z[l];
-    }
-  }
-  __syncthreads();   // part is reused
+  for (int l = g * 16; l < g * 16 + 16; l++) acc += Ms[l * (T + 1) + q] * fvec[l];
   part[g][q] = acc;
   __syncthreads();
-  V sum = 0;
-  if (threadIdx.x < T) {
-    const int k = threadIdx.x;
-    sum = (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]);
-  }
-  return sum;
+  if (threadIdx.x < T) y[threadIdx.x] = threadIdx.x < bw ? (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]) : V(0);
+  __syncthreads();
 }
 
-// Backward, block column kb of every large front of a step, one launch: every CTA forms
-// z_J = inv(L_JJ)^T t_J; task 0 of a front writes z_J to alpha', tasks 1..kb apply t_k -= L[J, k]^T z_J to
-// one 64-column tile of the earlier columns k < c0.
 template <class St>
-__global__ void __launch_bounds__(256) k_bwd_step(const int32_t* __restrict__ fronts, int nfront, int kb, DevPlan dp,
-                                                  St store, typename St::V* __restrict__ work, int64_t ws,
-                                                  int64_t apv_off) {
+__global__ void __launch_bounds__(256, sizeof(typename St::V) == 4 ? 4 : 1)
+    k_fwd_flow(const int2* __restrict__ tasks, int B, DevPlan dp, St store, typename St::V* __restrict__ work,
+               int64_t ws, int64_t xv_off, int32_t* __restrict__ ticket, int32_t* __restrict__ flags, int64_t nfl,
+               int32_t* __restrict__ err, tcg::WaitLimit lim) {
   using V = typename St::V;
-  __shared__ V Li[T * (T + 1)];   // the inverse block (row-major)
+  __shared__ V Ms[T * (T + 1)];   // Ms[l][q] = inv(L_ii)[q][l]
+  __shared__ V fb[T], x[T], part[4][T];
+  __shared__ int tk_s;
+  const int tk = draw_ticket(ticket, &tk_s);
+  const int2 task = tasks[tk / B];
+  const int b = tk % B;
+  const int32_t s = task.x;
+  const int i = task.y;
+  auto A = store.acc(dp, s, b);
+  V* W = work + (int64_t)b * ws;
+  V* fv = W + dp.frow_off[s];
+  V* xs = W + xv_off + dp.sn_first[s];   // x on the front's columns
+  const int w = dp.w[s];
+  const int64_t m = (int64_t)w + dp.r[s];
+  const int nb = (w + T - 1) / T;
+  const int32_t* fl = flags + (int64_t)b * nfl + dp.sn_fl[s];
+  const bool own = i < nb;
+  const int64_t r0 = own ? (int64_t)i * T : (int64_t)w + (int64_t)(i - nb) * T;
+  const int nr = (int)imin64(T, (own ? (int64_t)w : m) - r0);
+  const int nJ = own ? i : nb;
+  V fpre = 0;
+  if (own) {   // the block's inverse and f_i, staged while the earlier blocks arrive
+    const V* inv = store.inv(dp, s, b) + (int64_t)i * T * T;
+#pragma unroll
+    for (int u = 0; u < T * T / 256; u++) {
+      const int q = threadIdx.x + u * 256;
+      Ms[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
+    }
+    if (threadIdx.x < nr) fpre = fv[r0 + threadIdx.x];
+  }
+  int ready = -1;   // blocks [0, ready] are known published
+  auto need = [&](int J) {
+    if (J <= ready) return;
+    if (ld_acquire_gpu(fl + nJ - 1) != 0) {
+      ready = nJ - 1;
+      return;
+    }
+    wait_flag(fl + J, lim, err);
+    ready = J;
+  };
+  V tot = 0;   // row r0 + threadIdx.x (threads < 64): sum over J of L[row, J] x_J
+  if constexpr (St::kRowMajor) {
+    // a half-warp reads one row's 64 entries of a tile as 16 float4, rows hw + 16 u of the tile
+    const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
+    auto load = [&](int J, float4 (&v)[4]) {
+      const int c0 = J * T, bw = min(T, w - c0);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int rr = hw + 16 * u;
+        v[u] = (rr < nr && l < bw) ? *reinterpret_cast<const float4*>(A.P + (r0 + rr) * A.ldw + c0 + l)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 v[4], vn[4];
+    if (nJ > 0) load(0, v);
+    for (int J = 0; J < nJ; J++) {
+      if (J + 1 < nJ) load(J + 1, vn);
+      need(J);
+      const int c0 = J * T, bw = min(T, w - c0);
+      float xq[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) xq[e] = l + e < bw ? __ldcg(xs + c0 + l + e) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        float a = v[u].x * xq[0] + v[u].y * xq[1] + v[u].z * xq[2] + v[u].w * xq[3];
+        for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        acc[u] += a;
+      }
+      if (J + 1 < nJ) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = vn[u];
+      }
+    }
+    if ((threadIdx.x & 15) == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) part[0][hw + 16 * u] = acc[u];
+    }
+    __syncthreads();
+    if (threadIdx.x < T) tot = part[0][threadIdx.x];
+  } else {
+    // thread (g, q): row r0 + q, the 16 columns 16 g + [0, 16) of each tile
+    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+    V acc = 0;
+    for (int J = 0; J < nJ; J++) {
+      need(J);
+      const int c0 = J * T, bw = min(T, w - c0);
+      if (q < nr)
+        for (int e = 0; e < 16; e++) {
+          const int l = g * 16 + e;
+          if (l < bw) acc += A.L(r0 + q, c0 + l) * __ldcg(xs + c0 + l);
+        }
+    }
+    part[g][q] = acc;
+    __syncthreads();
+    if (threadIdx.x < T) tot = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
+  }
+  if (!own) {
+    if (threadIdx.x < nr) fv[r0 + threadIdx.x] -= tot;
+    return;
+  }
+  __syncthreads();   // part is reused
+  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < nr ? fpre - tot : V(0);
+  __syncthreads();
+  block_apply(Ms, fb, x, part, nr);
+  if (threadIdx.x < nr) xs[r0 + threadIdx.x] = x[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_gpu(const_cast<int32_t*>(fl) + i, 1);
+}
+
+template <class St>
+__global__ void __launch_bounds__(256, sizeof(typename St::V) == 4 ? 3 : 1)
+    k_bwd_flow(const int2* __restrict__ tasks, int B, DevPlan dp, St store, typename St::V* __restrict__ work,
+               int64_t ws, int64_t apv_off, int32_t* __restrict__ ticket, int32_t* __restrict__ flags, int64_t nfl,
+               int32_t* __restrict__ err, tcg::WaitLimit lim) {
+  using V = typename St::V;
+  __shared__ V Ms[T * (T + 1)];   // Ms[l][q] = inv(L_JJ)[l][q]: z_q = sum_l inv[l][q] t_l
   __shared__ V tb[T], z[T], part[4][T];
-  const int64_t t = blockIdx.x;
-  const int fi = (int)(t / (kb + 1));
-  const int task = (int)(t % (kb + 1));
-  const int32_t s = fronts[fi];
-  const int b = blockIdx.y;
+  __shared__ int tk_s;
+  const int tk = draw_ticket(ticket, &tk_s);
+  const int2 task = tasks[tk / B];
+  const int b = tk % B;
+  const int32_t s = task.x;
+  const int J = task.y;
   auto A = store.acc(dp, s, b);
   V* W = work + (int64_t)b * ws;
   V* fv = W + dp.frow_off[s];
+  V* zs = W + apv_off + dp.sn_first[s];   // alpha' on the front's columns
   const int w = dp.w[s];
-  const int c0 = kb * T, bw = min(T, w - c0);
-  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw ? fv[c0 + threadIdx.x] : V(0);
-  bwd_block_solve(store.inv(dp, s, b) + (int64_t)kb * T * T, tb, z, Li, part, bw);
-  if (task == 0) {
-    V* apv = W + apv_off;
-    if (threadIdx.x < bw) apv[dp.sn_first[s] + c0 + threadIdx.x] = z[threadIdx.x];
-    return;
+  const int nb = (w + T - 1) / T;
+  const int c0 = J * T, bw = min(T, w - c0);
+  int32_t* fl = flags + (int64_t)b * nfl + dp.sn_fl[s];
+  {
+    const V* inv = store.inv(dp, s, b) + (int64_t)J * T * T;
+#pragma unroll
+    for (int u = 0; u < T * T / 256; u++) {
+      const int q = threadIdx.x + u * 256;
+      Ms[(q >> 6) * (T + 1) + (q & 63)] = inv[q];
+    }
   }
-  const int k0 = (task - 1) * T;   // columns [k0, k0 + 64) < c0
-  const V sum = bwd_tile_sum<St>(A, c0, bw, k0, z, part);
-  if (threadIdx.x < T) fv[k0 + threadIdx.x] -= sum;
-}
-
-// Backward, block columns kb + 1 and kb in one launch (the chain of backward steps is the sweep's latency). The
-// fronts [0, n2) of step kb's list have block kb + 1: every CTA forms z2 = inv(L_22)^T t_2,
-// t_1' = t_1 - L_21^T z2 and z1 = inv(L_11)^T t_1' itself (the same operations, in the same order, as two
-// single steps); task 0 writes z1, z2 to alpha', tasks 1..kb apply t_k -= L[2, k]^T z2, then t_k -= L[1, k]^T z1
-// to one 64-column tile k < c0. Fronts past n2 take block kb alone, as a single step.
-template <class St>
-__global__ void __launch_bounds__(256) k_bwd_pair(const int32_t* __restrict__ fronts, int nfront, int n2, int kb,
-                                                  DevPlan dp, St store, typename St::V* __restrict__ work,
-                                                  int64_t ws, int64_t apv_off) {
-  using V = typename St::V;
-  __shared__ V Li[T * (T + 1)];
-  __shared__ V tb[T], z1[T], z2[T], part[4][T];
-  const int64_t t = blockIdx.x;
-  const int fi = (int)(t / (kb + 1));
-  const int task = (int)(t % (kb + 1));
-  const int32_t s = fronts[fi];
-  const int b = blockIdx.y;
-  auto A = store.acc(dp, s, b);
-  V* W = work + (int64_t)b * ws;
-  V* fv = W + dp.frow_off[s];
-  const int w = dp.w[s];
-  const bool two = fi < n2;
-  const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
-  const int bw2 = two ? min(T, w - c1) : 0;
-  const V* inv = store.inv(dp, s, b) + (int64_t)kb * T * T;
-  V t1 = 0;
-  if (two) {
-    if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw2 ? fv[c1 + threadIdx.x] : V(0);
-    bwd_block_solve(inv + T * T, tb, z2, Li, part, bw2);
-    const V sum = bwd_tile_sum<St>(A, c1, bw2, c0, z2, part);   // block kb's columns
-    if (threadIdx.x < T) t1 = fv[c0 + threadIdx.x] - sum;
-  } else if (threadIdx.x < T) {
-    t1 = fv[c0 + threadIdx.x];
+  V tpre = 0;
+  if (threadIdx.x < bw) tpre = fv[c0 + threadIdx.x];
+  int ready = nb;   // blocks [ready, nb) are known published
+  auto need = [&](int I) {
+    if (I >= ready) return;
+    if (ld_acquire_gpu(fl + J + 1) != 0) {
+      ready = J + 1;
+      return;
+    }
+    wait_flag(fl + I, lim, err);
+    ready = I;
+  };
+  // thread (g, q): column c0 + q, rows 16 g + [0, 16) of tile (I, J)
+  const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+  auto load = [&](int I, V (&v)[16]) {
+    const int bwI = min(T, w - I * T);
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      const int l = g * 16 + e;
+      v[e] = (l < bwI && q < bw) ? (V)A.L((int64_t)I * T + l, c0 + q) : V(0);
+    }
+  };
+  V acc = 0;
+  {
+    V v[16], vn[16];
+    if (J + 1 < nb) load(nb - 1, v);
+    for (int I = nb - 1; I > J; I--) {
+      if (I - 1 > J) load(I - 1, vn);
+      need(I);
+      const int bwI = min(T, w - I * T);
+#pragma unroll
+      for (int e = 0; e < 16; e++) {
+        const int l = g * 16 + e;
+        acc += v[e] * (l < bwI ? __ldcg(zs + I * T + l) : V(0));
+      }
+      if (I - 1 > J) {
+#pragma unroll
+        for (int e = 0; e < 16; e++) v[e] = vn[e];
+      }
+    }
   }
-  if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw1 ? t1 : V(0);
-  bwd_block_solve(inv, tb, z1, Li, part, bw1);
-  if (task == 0) {
-    V* apv = W + apv_off + dp.sn_first[s];
-    if (threadIdx.x < bw1) apv[c0 + threadIdx.x] = z1[threadIdx.x];
-    if (threadIdx.x < bw2) apv[c1 + threadIdx.x] = z2[threadIdx.x];
-    return;
-  }
-  const int k0 = (task - 1) * T;
-  V v = 0;
-  if (threadIdx.x < T) v = fv[k0 + threadIdx.x];
-  if (two) {
-    const V sum2 = bwd_tile_sum<St>(A, c1, bw2, k0, z2, part);
-    v -= sum2;
-  }
-  const V sum1 = bwd_tile_sum<St>(A, c0, bw1, k0, z1, part);
-  v -= sum1;
-  if (threadIdx.x < T) fv[k0 + threadIdx.x] = v;
+  part[g][q] = acc;
+  __syncthreads();
+  if (threadIdx.x < T)
+    tb[threadIdx.x] = threadIdx.x < bw ? tpre - ((part[0][q] + part[1][q]) + (part[2][q] + part[3][q])) : V(0);
+  __syncthreads();
+  block_apply(Ms, tb, z, part, bw);
+  if (threadIdx.x < bw) zs[c0 + threadIdx.x] = z[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_gpu(fl + J, 1);
 }
 
 // Per-block partial sums: log L_jj and x_j^2 (x = forward solution on own columns).
@@ -692,6 +661,10 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
   using V = typename St::V;
   V* work = reinterpret_cast<V*>(f->work);   // ws entries of V per proposal
   GP_CUDA(cudaMemsetAsync(f->work, 0, sizeof(V) * (size_t)B * ws, st));
+  // tickets and readiness flags of the large fronts' tasks
+  GP_CUDA(cudaMemsetAsync(f->flow_sync, 0, sizeof(int32_t) * (size_t)flow_sync_entries(sp, B), st));
+  int32_t* fwd_flags = f->flow_sync + 2 * sp.nlevels;
+  int32_t* bwd_flags = fwd_flags + (int64_t)B * sp.n_fl;
   k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(rhs, ps->perm, n, dp, work, ws);
   GP_CHECK_LAUNCH(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
@@ -706,19 +679,11 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
                                                           xv_off);
       GP_CHECK_LAUNCH(ctx);
     }
-    for (size_t q = 0; q < lv.steps.size();) {
-      const auto& stp = lv.steps[q];
-      if (q + 1 < lv.steps.size()) {   // block columns kb and kb + 1 together
-        k_fwd_pair<St><<<dim3((unsigned)(stp.nfront + stp.pair_total), B), 256, 0, st>>>(
-            dp.large_fronts + stp.fr_off, dp.pair_pre + stp.pair_pre_off, stp.nfront, stp.pair_n2, stp.kb, dp, store,
-            work, ws, xv_off);
-        q += 2;
-      } else {
-        k_fwd_step<St><<<dim3((unsigned)(stp.nfront + stp.trsm_total), B), 256, 0, st>>>(
-            dp.large_fronts + stp.fr_off, dp.step_pre + stp.pre_off, stp.nfront, stp.kb, dp, store, work, ws,
-            xv_off);
-        q += 1;
-      }
+    const int64_t nt = sp.flow_fwd_ptr[L + 1] - sp.flow_fwd_ptr[L];
+    if (nt > 0) {
+      k_fwd_flow<St><<<(unsigned)(nt * B), 256, 0, st>>>(dp.flow_fwd + sp.flow_fwd_ptr[L], B, dp, store, work, ws,
+                                                          xv_off, f->flow_sync + 2 * L, fwd_flags, sp.n_fl,
+                                                          f->tiles_err, f->wait_lim);
       GP_CHECK_LAUNCH(ctx);
     }
   }
@@ -744,20 +709,11 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
       k_bwd_prep_sum<V><<<dim3((unsigned)ll.count, B), T, 0, st>>>(dp.large_fronts + ll.off, dp.large_kb + ll.off,
                                                                    (int)ll.count, nch, dp, work, ws, xv_off, part);
       GP_CHECK_LAUNCH(ctx);
-      for (int q = (int)lv.steps.size() - 1; q >= 0;) {
-        if (q >= 1) {   // block columns kb + 1 = q and kb = q - 1 together
-          const auto& stp = lv.steps[q - 1];
-          k_bwd_pair<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
-              dp.large_fronts + stp.fr_off, stp.nfront, lv.steps[q].nfront, stp.kb, dp, store, work, ws, apv_off);
-          q -= 2;
-        } else {
-          const auto& stp = lv.steps[q];
-          k_bwd_step<St><<<dim3((unsigned)((int64_t)stp.nfront * (stp.kb + 1)), B), 256, 0, st>>>(
-              dp.large_fronts + stp.fr_off, stp.nfront, stp.kb, dp, store, work, ws, apv_off);
-          q -= 1;
-        }
-        GP_CHECK_LAUNCH(ctx);
-      }
+      const int64_t nt = sp.flow_bwd_ptr[L + 1] - sp.flow_bwd_ptr[L];
+      k_bwd_flow<St><<<(unsigned)(nt * B), 256, 0, st>>>(dp.flow_bwd + sp.flow_bwd_ptr[L], B, dp, store, work, ws,
+                                                          apv_off, f->flow_sync + 2 * L + 1, bwd_flags, sp.n_fl,
+                                                          f->tiles_err, f->wait_lim);
+      GP_CHECK_LAUNCH(ctx);
     }
   }
   k_alpha<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(work, ws, apv_off, ps->perm, n, alpha_out);

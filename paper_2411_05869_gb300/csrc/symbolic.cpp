@@ -399,6 +399,12 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   // ---- launch schedule
   sp.levels.assign(sp.nlevels, SymPlan::Level());
   sp.level_large.assign(sp.nlevels, SymPlan::LevelLarge());
+  sp.sn_fl.assign(sp.ns, -1);
+  sp.n_fl = 0;
+  sp.flow_fwd.clear();
+  sp.flow_bwd.clear();
+  sp.flow_fwd_ptr.assign(1, 0);
+  sp.flow_bwd_ptr.assign(1, 0);
   for (int32_t L = 0; L < sp.nlevels; L++) {
     SymPlan::Level& lv = sp.levels[L];
     // extend-add: k-th child of every supernode of this level, 8 update columns per CTA
@@ -500,7 +506,29 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
+    // dataflow solve tasks of this level's large fronts
+    int64_t imax = 0, nbmax = 0;
+    for (int32_t s : large) {
+      const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
+      sp.sn_fl[s] = (int32_t)sp.n_fl;
+      sp.n_fl += nb;
+      imax = std::max<int64_t>(imax, nb + ((int64_t)sp.sn_r[s] + GP_TILE - 1) / GP_TILE);
+      nbmax = std::max<int64_t>(nbmax, nb);
+    }
+    for (int64_t i = 0; i < imax; i++)
+      for (int32_t s : large) {
+        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
+        if (i < nb + ((int64_t)sp.sn_r[s] + GP_TILE - 1) / GP_TILE) sp.flow_fwd.push_back(make_int2(s, (int)i));
+      }
+    for (int64_t d = 0; d < nbmax; d++)
+      for (int32_t s : large) {
+        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
+        if (d < nb) sp.flow_bwd.push_back(make_int2(s, (int)(nb - 1 - d)));
+      }
+    sp.flow_fwd_ptr.push_back((int64_t)sp.flow_fwd.size());
+    sp.flow_bwd_ptr.push_back((int64_t)sp.flow_bwd.size());
   }
+  GP_REQUIRE(sp.n_fl < INT32_MAX, "too many solve blocks");
   plan_mixed_updates(sp, GP_GROUP, GP_TN_GROUP);
 }
 

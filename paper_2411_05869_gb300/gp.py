@@ -96,7 +96,7 @@ SYMBOLS = ["gp_create", "gp_destroy", "gp_last_error", "gp_assemble", "gp_points
            "gp_symbolic_export", "gp_symbolic_free", "gp_server_create", "gp_server_add_pointset", "gp_server_submit",
            "gp_server_poll", "gp_server_wait", "gp_server_stats", "gp_server_last_error", "gp_server_destroy",
            "gp_set_option", "gp_get_option", "gp_predict_var", "gp_loglik_iterative", "gp_assemble_sparse_support",
-           "gp_factor_core", "gp_factor_update_core"]
+           "gp_factor_core", "gp_factor_update_core", "gp_profile_read_level"]
 KCLASS = {"values": 0, "extend_add": 1, "front_small": 2, "potrf": 3, "trsm": 4, "update": 5, "solve": 6,
           "predict": 7, "update_left": 9}
 
@@ -185,6 +185,8 @@ def load(build_if_missing: bool = True):
     L.gp_profile.argtypes = [P, c_int]
     L.gp_profile_read.restype = c_int
     L.gp_profile_read.argtypes = [P, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]
+    L.gp_profile_read_level.restype = c_int
+    L.gp_profile_read_level.argtypes = [P, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64)]
     L.gp_factor_bytes.restype = c_int
     L.gp_factor_bytes.argtypes = [P, ctypes.POINTER(GpHyper), c_int, c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gp_autotune.restype = c_int
@@ -308,6 +310,19 @@ class Context:
             ms, n, fl = c_dbl(), c_i64(), c_dbl()
             self.check(self.lib.gp_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
             out[name] = (ms.value, n.value, fl.value)
+        return out
+
+    def profile_read_levels(self, nlevels: int) -> dict:
+        """{class: [(ms, launches) per elimination-tree level]} for the classes a factorization issues per level."""
+        out = {}
+        for name in ("extend_add", "front_small", "potrf", "trsm", "update", "update_left"):
+            rows = []
+            for lev in range(min(nlevels, 64)):
+                ms, n = c_dbl(), c_i64()
+                self.check(self.lib.gp_profile_read_level(self.h, KCLASS[name], lev, ctypes.byref(ms),
+                                                          ctypes.byref(n)))
+                rows.append((ms.value, n.value))
+            out[name] = rows
         return out
 
     def assemble(self, X, core_radius) -> "PointSet":
