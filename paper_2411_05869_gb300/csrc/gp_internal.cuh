@@ -28,6 +28,7 @@
 #define GP_RELAX_WIDTH 16      // relaxed amalgamation: merge when the merged supernode is this narrow
 #define GP_TILE 64             // dense tile edge of the large-front kernels
 #define GP_SMALL_M 96          // fronts up to this order are factored by one CTA in shared memory
+#define GP_FLOW_SB_MIN_NB 16   // levels whose largest front has this many 64-column blocks: 2 per solve chain task
 
 // ------------------------------------------------------------------------------------------ errors
 struct GpError {
@@ -199,6 +200,7 @@ struct SymPlan {
     std::vector<EaLaunch> ea;        // one per child slot
     int64_t small_off = 0; int32_t nsmall = 0;   // into small_list
     std::vector<StepLaunch> steps;   // large fronts, one per block column
+    int32_t flow_sb = 1;             // 64-column blocks per chain task of this level's solve tasks (1 or 2)
   };
   std::vector<Level> levels;
   std::vector<int2> ea_tab;          // (child supernode, first column) per extend-add CTA (8 columns each)
@@ -209,10 +211,11 @@ struct SymPlan {
   std::vector<LevelLarge> level_large;
   std::vector<int64_t> step_pre;     // per step: prefix of TRSM tasks then of UPDATE tasks (2*(nfront+1))
   std::vector<int64_t> pair_pre;     // per step pair: prefix of the paired forward-solve row tiles
-  // Solves of the large fronts as one launch per level (tasks that wait for the blocks they need):
-  //   flow_fwd: per level, the forward tasks (front, i): i < nb the front's block row i, i >= nb the 64-row tile
-  //     i - nb of the rows below its columns; ordered by i, then by the level's large-front order;
-  //   flow_bwd: per level, the backward tasks (front, block column J), ordered by nb - 1 - J, then front order.
+  // Solves of the large fronts as one launch per level (tasks that wait for the blocks they need), with SB =
+  // the level's flow_sb blocks per chain task and nbs = ceil(nb / SB) chain tasks per front:
+  //   flow_fwd: per level, the forward tasks (front, k): k < nbs the block rows SB k + [0, SB), k >= nbs the
+  //     (64 SB)-row tile k - nbs of the rows below the front's columns;
+  //   flow_bwd: per level, the backward tasks (front, k): the block columns SB k + [0, SB);
   //   sn_fl: first readiness flag of each large front (one per 64-column block; -1 for small fronts).
   // Every task waits only for tasks earlier in its list.
   std::vector<int2> flow_fwd, flow_bwd;

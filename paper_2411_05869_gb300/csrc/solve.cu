@@ -19,6 +19,7 @@
 // Sums use fixed-shape trees, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "factor_access.cuh"
@@ -262,202 +263,349 @@ __device__ __forceinline__ void block_apply(const V* Ms, const V* fvec, V* y, V 
   __syncthreads();
 }
 
-template <class St>
-__global__ void __launch_bounds__(256, sizeof(typename St::V) == 4 ? 4 : 1)
+constexpr int FS = T + 1;   // row stride of the shared 64 x 64 tiles
+// Dynamic shared memory of a flow kernel with SB blocks per chain task: the blocks' inverses and, for SB = 2,
+// the tile between the two blocks.
+template <class V, int SB>
+constexpr size_t flow_smem_bytes() { return (SB == 1 ? 1 : 3) * (size_t)T * FS * sizeof(V); }
+template <class V, int SB>
+constexpr int flow_min_blocks() { return sizeof(V) == 4 ? (SB == 1 ? 4 : 2) : 1; }
+
+// Forward, SB (1 or 2) blocks per chain task; rows below the columns in tasks of 64 SB rows.
+template <class St, int SB>
+__global__ void __launch_bounds__(256, flow_min_blocks<typename St::V, SB>())
     k_fwd_flow(const int2* __restrict__ tasks, int B, DevPlan dp, St store, typename St::V* __restrict__ work,
                int64_t ws, int64_t xv_off, int32_t* __restrict__ ticket, int32_t* __restrict__ flags, int64_t nfl,
                int32_t* __restrict__ err, tcg::WaitLimit lim) {
   using V = typename St::V;
-  __shared__ V Ms[T * (T + 1)];   // Ms[l][q] = inv(L_ii)[q][l]
-  __shared__ V fb[T], x[T], part[4][T];
+  extern __shared__ __align__(16) unsigned char flow_sh[];
+  V* Ms0 = reinterpret_cast<V*>(flow_sh);   // Ms_k[l][q] = inv(L_{i0+k})[q][l]
+  V* Ms1 = Ms0 + T * FS;
+  V* Tl = Ms1 + T * FS;                      // Tl[q][l] = L[64 (i0 + 1) + q, 64 i0 + l] (SB = 2)
+  __shared__ V fsh[SB * T], tots[SB * T], fb[T], x[T], part[4][T];
   __shared__ int tk_s;
   const int tk = draw_ticket(ticket, &tk_s);
   const int2 task = tasks[tk / B];
   const int b = tk % B;
   const int32_t s = task.x;
-  const int i = task.y;
   auto A = store.acc(dp, s, b);
   V* W = work + (int64_t)b * ws;
   V* fv = W + dp.frow_off[s];
   V* xs = W + xv_off + dp.sn_first[s];   // x on the front's columns
   const int w = dp.w[s];
   const int64_t m = (int64_t)w + dp.r[s];
-  const int nb = (w + T - 1) / T;
-  const int32_t* fl = flags + (int64_t)b * nfl + dp.sn_fl[s];
-  const bool own = i < nb;
-  const int64_t r0 = own ? (int64_t)i * T : (int64_t)w + (int64_t)(i - nb) * T;
-  const int nr = (int)imin64(T, (own ? (int64_t)w : m) - r0);
-  const int nJ = own ? i : nb;
-  V fpre = 0;
-  if (own) {   // the block's inverse and f_i, staged while the earlier blocks arrive
-    const V* inv = store.inv(dp, s, b) + (int64_t)i * T * T;
-#pragma unroll
-    for (int u = 0; u < T * T / 256; u++) {
-      const int q = threadIdx.x + u * 256;
-      Ms[(q & 63) * (T + 1) + (q >> 6)] = inv[q];
+  const int nb = (w + T - 1) / T, nbs = (nb + SB - 1) / SB;
+  int32_t* fl = flags + (int64_t)b * nfl + dp.sn_fl[s];
+  const bool own = task.y < nbs;
+  const int i0 = own ? task.y * SB : 0;
+  const int nblk = own ? min(SB, nb - i0) : 0;
+  const int64_t r0 = own ? (int64_t)i0 * T : (int64_t)w + (int64_t)(task.y - nbs) * (SB * T);
+  const int nr = (int)imin64(SB * T, (own ? (int64_t)w : m) - r0);   // rows of the task
+  const int nJ = own ? i0 : nb;
+  if (own) {   // the blocks' inverses, the tile between them and f, staged while the earlier blocks arrive
+    for (int k = 0; k < nblk; k++) {
+      const V* inv = store.inv(dp, s, b) + (int64_t)(i0 + k) * T * T;
+      V* Ms = k == 0 ? Ms0 : Ms1;
+#pragma unroll 4
+      for (int u = 0; u < T * T / 256; u++) {
+        const int q = threadIdx.x + u * 256;
+        Ms[(q & 63) * FS + (q >> 6)] = inv[q];
+      }
     }
-    if (threadIdx.x < nr) fpre = fv[r0 + threadIdx.x];
+    if (SB == 2 && nblk == 2) {
+#pragma unroll 4
+      for (int u = 0; u < T * T / 256; u++) {
+        const int e = threadIdx.x + u * 256;
+        const int q = St::kRowMajor ? e >> 6 : e & 63, l = St::kRowMajor ? e & 63 : e >> 6;
+        Tl[q * FS + l] = T + q < nr ? (V)A.L(r0 + T + q, (int64_t)i0 * T + l) : V(0);
+      }
+    }
+    if (threadIdx.x < SB * T) fsh[threadIdx.x] = threadIdx.x < nr ? fv[r0 + threadIdx.x] : V(0);
   }
   int ready = -1;   // blocks [0, ready] are known published
-  auto need = [&](int J) {
+  auto need = [&](int J) {   // one acquire also covers the next 8 blocks when they are already out
     if (J <= ready) return;
-    if (ld_acquire_gpu(fl + nJ - 1) != 0) {
-      ready = nJ - 1;
+    const int ahead = min(nJ - 1, J + 8);
+    if (ld_acquire_gpu(fl + ahead) != 0) {
+      ready = ahead;
       return;
     }
     wait_flag(fl + J, lim, err);
     ready = J;
   };
-  V tot = 0;   // row r0 + threadIdx.x (threads < 64): sum over J of L[row, J] x_J
+  // tots[q] = sum_{J < nJ} L[r0 + q, J] x_J for the task's rows
   if constexpr (St::kRowMajor) {
-    // a half-warp reads one row's 64 entries of a tile as 16 float4, rows hw + 16 u of the tile
+    // a half-warp reads one row's 64 entries of a tile as 16 float4: rows hw + 16 u of the task (u < RU); the
+    // next tile is read while the current one is used, and so are its x values once they are known published;
+    // a lane sums its four columns over all tiles, the row's 16 lanes are combined at the end
+    constexpr int RU = SB * T / 16;
     const int hw = threadIdx.x >> 4, l = (threadIdx.x & 15) * 4;
-    auto load = [&](int J, float4 (&v)[4]) {
+    auto load = [&](int J, float4 (&v)[RU]) {
       const int c0 = J * T, bw = min(T, w - c0);
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
+      for (int u = 0; u < RU; u++) {
         const int rr = hw + 16 * u;
         v[u] = (rr < nr && l < bw) ? *reinterpret_cast<const float4*>(A.P + (r0 + rr) * A.ldw + c0 + l)
                                    : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    float4 v[4], vn[4];
+    auto loadx = [&](int J, float (&xq)[4]) {
+      const int c0 = J * T, bw = min(T, w - c0);
+#pragma unroll
+      for (int e = 0; e < 4; e++) xq[e] = l + e < bw ? __ldcg(xs + c0 + l + e) : 0.f;
+    };
+    float acc[RU];
+#pragma unroll
+    for (int u = 0; u < RU; u++) acc[u] = 0.f;
+    float4 v[RU], vn[RU];
+    float xq[4], xn[4];
+    bool have_x = false;
     if (nJ > 0) load(0, v);
     for (int J = 0; J < nJ; J++) {
       if (J + 1 < nJ) load(J + 1, vn);
       need(J);
-      const int c0 = J * T, bw = min(T, w - c0);
-      float xq[4];
+      if (!have_x) loadx(J, xq);
+      const bool have_xn = J + 1 < nJ && J + 1 <= ready;
+      if (have_xn) loadx(J + 1, xn);
 #pragma unroll
-      for (int e = 0; e < 4; e++) xq[e] = l + e < bw ? __ldcg(xs + c0 + l + e) : 0.f;
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        float a = v[u].x * xq[0] + v[u].y * xq[1] + v[u].z * xq[2] + v[u].w * xq[3];
-        for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        acc[u] += a;
-      }
+      for (int u = 0; u < RU; u++) acc[u] += v[u].x * xq[0] + v[u].y * xq[1] + v[u].z * xq[2] + v[u].w * xq[3];
       if (J + 1 < nJ) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = vn[u];
+        for (int u = 0; u < RU; u++) v[u] = vn[u];
+#pragma unroll
+        for (int e = 0; e < 4; e++) xq[e] = xn[e];
       }
+      have_x = have_xn;
+    }
+#pragma unroll
+    for (int u = 0; u < RU; u++) {   // the 16 lanes of a row: a fixed tree
+      for (int o = 8; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
     }
     if ((threadIdx.x & 15) == 0) {
 #pragma unroll
-      for (int u = 0; u < 4; u++) part[0][hw + 16 * u] = acc[u];
+      for (int u = 0; u < RU; u++) tots[hw + 16 * u] = acc[u];
     }
-    __syncthreads();
-    if (threadIdx.x < T) tot = part[0][threadIdx.x];
   } else {
-    // thread (g, q): row r0 + q, the 16 columns 16 g + [0, 16) of each tile
-    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+    // thread (g, q): row r0 + q (q < 64 SB), the columns 64 / G g + [0, 64 / G) of each tile (G = 256 / (64 SB))
+    constexpr int NQ = SB * T, G = 256 / NQ, CW = T / G;
+    const int g = threadIdx.x / NQ, q = threadIdx.x % NQ;
     V acc = 0;
     for (int J = 0; J < nJ; J++) {
       need(J);
       const int c0 = J * T, bw = min(T, w - c0);
       if (q < nr)
-        for (int e = 0; e < 16; e++) {
-          const int l = g * 16 + e;
+        for (int e = 0; e < CW; e++) {
+          const int l = g * CW + e;
           if (l < bw) acc += A.L(r0 + q, c0 + l) * __ldcg(xs + c0 + l);
         }
     }
-    part[g][q] = acc;
+    V* pp = &part[0][0];   // 4 x 64 entries: G - 1 partial rows of NQ
+    if (g > 0) pp[(g - 1) * NQ + q] = acc;
     __syncthreads();
-    if (threadIdx.x < T) tot = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
+    if (g == 0) {
+      for (int k = 1; k < G; k++) acc += pp[(k - 1) * NQ + q];
+      tots[q] = acc;
+    }
   }
+  __syncthreads();
   if (!own) {
-    if (threadIdx.x < nr) fv[r0 + threadIdx.x] -= tot;
+    if (threadIdx.x < nr) fv[r0 + threadIdx.x] -= tots[threadIdx.x];
     return;
   }
-  __syncthreads();   // part is reused
-  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < nr ? fpre - tot : V(0);
+  // block i0
+  const int nr0 = min(T, nr);
+  if (threadIdx.x < T) fb[threadIdx.x] = threadIdx.x < nr0 ? fsh[threadIdx.x] - tots[threadIdx.x] : V(0);
   __syncthreads();
-  block_apply(Ms, fb, x, part, nr);
-  if (threadIdx.x < nr) xs[r0 + threadIdx.x] = x[threadIdx.x];
+  block_apply(Ms0, fb, x, part, nr0);
+  if (threadIdx.x < nr0) xs[r0 + threadIdx.x] = x[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) st_release_gpu(const_cast<int32_t*>(fl) + i, 1);
+  if (threadIdx.x == 0) st_release_gpu(fl + i0, 1);
+  if (SB == 1 || nblk < 2) return;
+  // block i0 + 1: f -= L[i0 + 1, i0] x_{i0}
+  const int nr1 = nr - T;
+  {
+    const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
+    V a = 0;
+#pragma unroll
+    for (int l = g * 16; l < g * 16 + 16; l++) a += Tl[q * FS + l] * x[l];
+    part[g][q] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const int q = threadIdx.x;
+    fb[q] = q < nr1 ? (fsh[T + q] - tots[T + q]) - ((part[0][q] + part[1][q]) + (part[2][q] + part[3][q])) : V(0);
+  }
+  __syncthreads();
+  block_apply(Ms1, fb, x, part, nr1);
+  if (threadIdx.x < nr1) xs[r0 + T + threadIdx.x] = x[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_gpu(fl + i0 + 1, 1);
 }
 
-template <class St>
-__global__ void __launch_bounds__(256, sizeof(typename St::V) == 4 ? 3 : 1)
+// Backward, SB (1 or 2) blocks per chain task.
+template <class St, int SB>
+__global__ void __launch_bounds__(256, flow_min_blocks<typename St::V, SB>())
     k_bwd_flow(const int2* __restrict__ tasks, int B, DevPlan dp, St store, typename St::V* __restrict__ work,
                int64_t ws, int64_t apv_off, int32_t* __restrict__ ticket, int32_t* __restrict__ flags, int64_t nfl,
                int32_t* __restrict__ err, tcg::WaitLimit lim) {
   using V = typename St::V;
-  __shared__ V Ms[T * (T + 1)];   // Ms[l][q] = inv(L_JJ)[l][q]: z_q = sum_l inv[l][q] t_l
-  __shared__ V tb[T], z[T], part[4][T];
+  extern __shared__ __align__(16) unsigned char flow_sh[];
+  V* Ms0 = reinterpret_cast<V*>(flow_sh);   // Ms_k[l][q] = inv(L_{J0+k})[l][q]: z_q = sum_l inv[l][q] t_l
+  V* Ms1 = Ms0 + T * FS;
+  V* Tl = Ms1 + T * FS;                      // Tl[l][q] = L[64 (J0 + 1) + l, 64 J0 + q] (SB = 2)
+  __shared__ V tsh[SB * T], psum[SB * T], tb[T], z[T], part[4][T];
+  __shared__ V red[256 / (SB * T / 4)][SB * T];   // row groups x columns
   __shared__ int tk_s;
   const int tk = draw_ticket(ticket, &tk_s);
   const int2 task = tasks[tk / B];
   const int b = tk % B;
   const int32_t s = task.x;
-  const int J = task.y;
+  const int J0 = task.y * SB;
   auto A = store.acc(dp, s, b);
   V* W = work + (int64_t)b * ws;
   V* fv = W + dp.frow_off[s];
   V* zs = W + apv_off + dp.sn_first[s];   // alpha' on the front's columns
   const int w = dp.w[s];
   const int nb = (w + T - 1) / T;
-  const int c0 = J * T, bw = min(T, w - c0);
+  const int nblk = min(SB, nb - J0);
+  const int c0 = J0 * T, nc = min(SB * T, w - c0);   // the task's columns
   int32_t* fl = flags + (int64_t)b * nfl + dp.sn_fl[s];
-  {
-    const V* inv = store.inv(dp, s, b) + (int64_t)J * T * T;
-#pragma unroll
+  for (int k = 0; k < nblk; k++) {
+    const V* inv = store.inv(dp, s, b) + (int64_t)(J0 + k) * T * T;
+    V* Ms = k == 0 ? Ms0 : Ms1;
+#pragma unroll 4
     for (int u = 0; u < T * T / 256; u++) {
       const int q = threadIdx.x + u * 256;
-      Ms[(q >> 6) * (T + 1) + (q & 63)] = inv[q];
+      Ms[(q >> 6) * FS + (q & 63)] = inv[q];
     }
   }
-  V tpre = 0;
-  if (threadIdx.x < bw) tpre = fv[c0 + threadIdx.x];
-  int ready = nb;   // blocks [ready, nb) are known published
-  auto need = [&](int I) {
+  if (SB == 2 && nblk == 2) {
+    const int bw1 = nc - T;
+#pragma unroll 4
+    for (int u = 0; u < T * T / 256; u++) {
+      const int e = threadIdx.x + u * 256;
+      const int l = St::kRowMajor ? e >> 6 : e & 63, q = St::kRowMajor ? e & 63 : e >> 6;
+      Tl[l * FS + q] = l < bw1 ? (V)A.L((int64_t)c0 + T + l, c0 + q) : V(0);
+    }
+  }
+  if (threadIdx.x < SB * T) tsh[threadIdx.x] = threadIdx.x < nc ? fv[c0 + threadIdx.x] : V(0);
+  const int Itop = J0 + nblk;   // the blocks above the task: I = nb - 1 down to Itop
+  int ready = nb;               // blocks [ready, nb) are known published
+  auto need = [&](int I) {      // one acquire also covers the next 8 blocks when they are already out
     if (I >= ready) return;
-    if (ld_acquire_gpu(fl + J + 1) != 0) {
-      ready = J + 1;
+    const int ahead = max(Itop, I - 8);
+    if (ld_acquire_gpu(fl + ahead) != 0) {
+      ready = ahead;
       return;
     }
     wait_flag(fl + I, lim, err);
     ready = I;
   };
-  // thread (g, q): column c0 + q, rows 16 g + [0, 16) of tile (I, J)
-  const int g = threadIdx.x >> 6, q = threadIdx.x & 63;
-  auto load = [&](int I, V (&v)[16]) {
+  // warp k: rows RPT k + [0, RPT) of tile I; lane c: columns c0 + 4 c + [0, 4) (a warp reads RPT row segments of
+  // 64 SB entries); the next tile is read while the current one is used, and so are its alpha' values once they
+  // are known published
+  constexpr int NQ4 = SB * T / 4, G = 256 / NQ4, RPT = T / G;
+  const int g = threadIdx.x / NQ4, c4 = (threadIdx.x % NQ4) * 4;
+  using V4 = typename std::conditional<sizeof(V) == 4, float4, double4>::type;
+  auto load = [&](int I, V4 (&v)[RPT]) {
     const int bwI = min(T, w - I * T);
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
-      const int l = g * 16 + e;
-      v[e] = (l < bwI && q < bw) ? (V)A.L((int64_t)I * T + l, c0 + q) : V(0);
+    for (int e = 0; e < RPT; e++) {
+      const int l = g * RPT + e;
+      const int64_t row = (int64_t)I * T + l;
+      if (l < bwI && c4 < nc) {
+        if constexpr (St::kRowMajor) {
+          v[e] = *reinterpret_cast<const V4*>(A.P + row * A.ldw + c0 + c4);
+        } else {
+          v[e].x = A.L(row, c0 + c4);
+          v[e].y = c4 + 1 < nc ? A.L(row, c0 + c4 + 1) : V(0);
+          v[e].z = c4 + 2 < nc ? A.L(row, c0 + c4 + 2) : V(0);
+          v[e].w = c4 + 3 < nc ? A.L(row, c0 + c4 + 3) : V(0);
+        }
+      } else {
+        v[e].x = v[e].y = v[e].z = v[e].w = V(0);
+      }
     }
   };
-  V acc = 0;
+  auto loadz = [&](int I, V (&zq)[RPT]) {
+    const int bwI = min(T, w - I * T);
+#pragma unroll
+    for (int e = 0; e < RPT; e++) {
+      const int l = g * RPT + e;
+      zq[e] = l < bwI ? __ldcg(zs + I * T + l) : V(0);
+    }
+  };
+  V acc[4] = {0, 0, 0, 0};
   {
-    V v[16], vn[16];
-    if (J + 1 < nb) load(nb - 1, v);
-    for (int I = nb - 1; I > J; I--) {
-      if (I - 1 > J) load(I - 1, vn);
+    V4 v[RPT], vn[RPT];
+    V zq[RPT], zn[RPT];
+    bool have_z = false;
+    if (nb - 1 >= Itop) load(nb - 1, v);
+    for (int I = nb - 1; I >= Itop; I--) {
+      if (I - 1 >= Itop) load(I - 1, vn);
       need(I);
-      const int bwI = min(T, w - I * T);
+      if (!have_z) loadz(I, zq);
+      const bool have_zn = I - 1 >= Itop && I - 1 >= ready;
+      if (have_zn) loadz(I - 1, zn);
 #pragma unroll
-      for (int e = 0; e < 16; e++) {
-        const int l = g * 16 + e;
-        acc += v[e] * (l < bwI ? __ldcg(zs + I * T + l) : V(0));
+      for (int e = 0; e < RPT; e++) {
+        acc[0] += v[e].x * zq[e];
+        acc[1] += v[e].y * zq[e];
+        acc[2] += v[e].z * zq[e];
+        acc[3] += v[e].w * zq[e];
       }
-      if (I - 1 > J) {
+      if (I - 1 >= Itop) {
 #pragma unroll
-        for (int e = 0; e < 16; e++) v[e] = vn[e];
+        for (int e = 0; e < RPT; e++) {
+          v[e] = vn[e];
+          zq[e] = zn[e];
+        }
       }
+      have_z = have_zn;
     }
   }
-  part[g][q] = acc;
+  // psum[col] = sum over the row groups (warps) of the partial sums, in group order
+  {
+#pragma unroll
+    for (int k = 0; k < 4; k++) red[g][c4 + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < SB * T) {
+      V t = 0;
+      for (int k = 0; k < G; k++) t += red[k][threadIdx.x];
+      psum[threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (SB == 2 && nblk == 2) {   // block J0 + 1 first
+    const int bw1 = nc - T;
+    if (threadIdx.x < T) tb[threadIdx.x] = threadIdx.x < bw1 ? tsh[T + threadIdx.x] - psum[T + threadIdx.x] : V(0);
+    __syncthreads();
+    block_apply(Ms1, tb, z, part, bw1);
+    if (threadIdx.x < bw1) zs[c0 + T + threadIdx.x] = z[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_gpu(fl + J0 + 1, 1);
+    // block J0: t -= L[J0 + 1, J0]^T z_{J0 + 1}
+    {
+      const int gg = threadIdx.x >> 6, qq = threadIdx.x & 63;
+      V a = 0;
+#pragma unroll
+      for (int l = gg * 16; l < gg * 16 + 16; l++) a += Tl[l * FS + qq] * z[l];
+      part[gg][qq] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < T) {
+      const int qq = threadIdx.x;
+      tb[qq] = (tsh[qq] - psum[qq]) - ((part[0][qq] + part[1][qq]) + (part[2][qq] + part[3][qq]));
+    }
+  } else if (threadIdx.x < T) {
+    tb[threadIdx.x] = threadIdx.x < nc ? tsh[threadIdx.x] - psum[threadIdx.x] : V(0);
+  }
   __syncthreads();
-  if (threadIdx.x < T)
-    tb[threadIdx.x] = threadIdx.x < bw ? tpre - ((part[0][q] + part[1][q]) + (part[2][q] + part[3][q])) : V(0);
+  const int bw0 = min(T, nc);
+  block_apply(Ms0, tb, z, part, bw0);
+  if (threadIdx.x < bw0) zs[c0 + threadIdx.x] = z[threadIdx.x];
   __syncthreads();
-  block_apply(Ms, tb, z, part, bw);
-  if (threadIdx.x < bw) zs[c0 + threadIdx.x] = z[threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) st_release_gpu(fl + J, 1);
+  if (threadIdx.x == 0) st_release_gpu(fl + J0, 1);
 }
 
 // Per-block partial sums: log L_jj and x_j^2 (x = forward solution on own columns).
@@ -648,6 +796,18 @@ int bwd_chunks(const SymPlan& sp, int32_t L) {
   return nch;
 }
 
+// Dynamic shared memory of the flow kernels (above the 48 KB default), set once per process.
+template <class St, int SB>
+void flow_attrs() {
+  static const bool done = [] {
+    const int bytes = (int)flow_smem_bytes<typename St::V, SB>();
+    cudaFuncSetAttribute(k_fwd_flow<St, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_bwd_flow<St, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return true;
+  }();
+  (void)done;
+}
+
 template <class St>
 void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs, double* alpha_out, bool partials) {
   gp_pointset* ps = f->ps;
@@ -665,6 +825,8 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
   GP_CUDA(cudaMemsetAsync(f->flow_sync, 0, sizeof(int32_t) * (size_t)flow_sync_entries(sp, B), st));
   int32_t* fwd_flags = f->flow_sync + 2 * sp.nlevels;
   int32_t* bwd_flags = fwd_flags + (int64_t)B * sp.n_fl;
+  flow_attrs<St, 1>();
+  flow_attrs<St, 2>();
   k_rhs<<<dim3(grid_for(n, 256), B), 256, 0, st>>>(rhs, ps->perm, n, dp, work, ws);
   GP_CHECK_LAUNCH(ctx);
   for (int32_t L = 0; L < sp.nlevels; L++) {
@@ -681,9 +843,10 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
     }
     const int64_t nt = sp.flow_fwd_ptr[L + 1] - sp.flow_fwd_ptr[L];
     if (nt > 0) {
-      k_fwd_flow<St><<<(unsigned)(nt * B), 256, 0, st>>>(dp.flow_fwd + sp.flow_fwd_ptr[L], B, dp, store, work, ws,
-                                                          xv_off, f->flow_sync + 2 * L, fwd_flags, sp.n_fl,
-                                                          f->tiles_err, f->wait_lim);
+      const auto kf = lv.flow_sb == 2 ? k_fwd_flow<St, 2> : k_fwd_flow<St, 1>;
+      const size_t sm = lv.flow_sb == 2 ? flow_smem_bytes<V, 2>() : flow_smem_bytes<V, 1>();
+      kf<<<(unsigned)(nt * B), 256, sm, st>>>(dp.flow_fwd + sp.flow_fwd_ptr[L], B, dp, store, work, ws, xv_off,
+                                              f->flow_sync + 2 * L, fwd_flags, sp.n_fl, f->tiles_err, f->wait_lim);
       GP_CHECK_LAUNCH(ctx);
     }
   }
@@ -710,9 +873,11 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
                                                                    (int)ll.count, nch, dp, work, ws, xv_off, part);
       GP_CHECK_LAUNCH(ctx);
       const int64_t nt = sp.flow_bwd_ptr[L + 1] - sp.flow_bwd_ptr[L];
-      k_bwd_flow<St><<<(unsigned)(nt * B), 256, 0, st>>>(dp.flow_bwd + sp.flow_bwd_ptr[L], B, dp, store, work, ws,
-                                                          apv_off, f->flow_sync + 2 * L + 1, bwd_flags, sp.n_fl,
-                                                          f->tiles_err, f->wait_lim);
+      const auto kb = lv.flow_sb == 2 ? k_bwd_flow<St, 2> : k_bwd_flow<St, 1>;
+      const size_t sm = lv.flow_sb == 2 ? flow_smem_bytes<V, 2>() : flow_smem_bytes<V, 1>();
+      kb<<<(unsigned)(nt * B), 256, sm, st>>>(dp.flow_bwd + sp.flow_bwd_ptr[L], B, dp, store, work, ws, apv_off,
+                                              f->flow_sync + 2 * L + 1, bwd_flags, sp.n_fl, f->tiles_err,
+                                              f->wait_lim);
       GP_CHECK_LAUNCH(ctx);
     }
   }

@@ -506,24 +506,37 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
-    // dataflow solve tasks of this level's large fronts
-    int64_t imax = 0, nbmax = 0;
+    // dataflow solve tasks of this level's large fronts (SB blocks of 64 columns per chain task: 2 where the
+    // level's chains are long, else 1; rows below the columns in tasks of 64 SB rows): forward tasks ordered by
+    // their first block (the rows below a front's columns count as blocks nb, nb + 1, ...), backward tasks by
+    // their distance from the last block; within either, the level's large-front order
+    int64_t nbmax_l = 0;
+    for (int32_t s : large) nbmax_l = std::max<int64_t>(nbmax_l, ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE);
+    lv.flow_sb = nbmax_l >= GP_FLOW_SB_MIN_NB ? 2 : 1;
+    const int64_t SBk = lv.flow_sb;
+    int64_t imax = 0, nbsmax = 0;
     for (int32_t s : large) {
       const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
       sp.sn_fl[s] = (int32_t)sp.n_fl;
       sp.n_fl += nb;
-      imax = std::max<int64_t>(imax, nb + ((int64_t)sp.sn_r[s] + GP_TILE - 1) / GP_TILE);
-      nbmax = std::max<int64_t>(nbmax, nb);
+      const int64_t nl = ((int64_t)sp.sn_r[s] + SBk * GP_TILE - 1) / (SBk * GP_TILE);
+      imax = std::max<int64_t>(imax, nb + SBk * nl);
+      nbsmax = std::max<int64_t>(nbsmax, (nb + SBk - 1) / SBk);
     }
-    for (int64_t i = 0; i < imax; i++)
+    for (int64_t key = 0; key < imax; key++)
       for (int32_t s : large) {
-        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
-        if (i < nb + ((int64_t)sp.sn_r[s] + GP_TILE - 1) / GP_TILE) sp.flow_fwd.push_back(make_int2(s, (int)i));
+        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE, nbs = (nb + SBk - 1) / SBk;
+        const int64_t nl = ((int64_t)sp.sn_r[s] + SBk * GP_TILE - 1) / (SBk * GP_TILE);
+        if (key < nb) {
+          if (key % SBk == 0) sp.flow_fwd.push_back(make_int2(s, (int)(key / SBk)));
+        } else if ((key - nb) % SBk == 0 && (key - nb) / SBk < nl) {
+          sp.flow_fwd.push_back(make_int2(s, (int)(nbs + (key - nb) / SBk)));
+        }
       }
-    for (int64_t d = 0; d < nbmax; d++)
+    for (int64_t d = 0; d < nbsmax; d++)
       for (int32_t s : large) {
-        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE;
-        if (d < nb) sp.flow_bwd.push_back(make_int2(s, (int)(nb - 1 - d)));
+        const int64_t nb = ((int64_t)sp.sn_w[s] + GP_TILE - 1) / GP_TILE, nbs = (nb + SBk - 1) / SBk;
+        if (d < nbs) sp.flow_bwd.push_back(make_int2(s, (int)(nbs - 1 - d)));
       }
     sp.flow_fwd_ptr.push_back((int64_t)sp.flow_fwd.size());
     sp.flow_bwd_ptr.push_back((int64_t)sp.flow_bwd.size());
