@@ -293,9 +293,10 @@ GP_API gp_status gp_loglik_iterative(gp_ctx* ctx, gp_factor_t* f, int b, const d
  * kernel classes with CUDA events on the context stream; gp_profile(ctx, 0) stops. gp_profile_read
  * synchronises the stream and returns, for one class, the summed device time (ms), the launch count and the
  * useful flops those launches performed (0 where no flop count applies). Classes:
- *   0 A4 kernel values, 1 A7 extend-add, 2 A7 small fronts, 3 A7 diagonal-block POTRF, 4 A7 TRSM,
- *   5 A7 trailing update (SYRK/GEMM; with GP_MIXED the group-end updates), 6 A8-A10 solve sweep (one span per
- *   gp_loglik), 7 A12 prediction, 8 A1-A6 assembly, 9 A7 left-looking block-column updates (GP_MIXED).
+ *   0 A4 kernel values, 1 A7 extend-add (GP_MIXED: with the zeroing of the update matrices), 2 A7 small
+ *   fronts, 3 A7 diagonal-block POTRF, 4 A7 TRSM, 5 A7 trailing update (SYRK/GEMM; with GP_MIXED the
+ *   group-end updates), 6 A8-A10 solve sweep (one span per gp_loglik), 7 A12 prediction, 8 A1-A6 assembly,
+ *   9 A7 left-looking block-column updates (GP_MIXED).
  * Errors: GP_ERR_ARG (class out of range), GP_ERR_CUDA. */
 GP_API gp_status gp_profile(gp_ctx* ctx, int enable);
 GP_API gp_status gp_profile_read(gp_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops);

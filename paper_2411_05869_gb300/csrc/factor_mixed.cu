@@ -85,66 +85,92 @@ __device__ __forceinline__ double checked_sqrt(double d, int32_t* notpd, int32_t
   return sqrt(d);
 }
 
-// Zeroes the lower triangle (row a, columns b <= a) of the update matrices of a list of fronts, a warp per row:
-// nothing writes or reads their upper triangles.
-__global__ void k_zero_updates32(const int32_t* __restrict__ list, DevPlan dp, float* __restrict__ upd, int64_t UE) {
-  int32_t s = list[blockIdx.x];
-  float* U = upd + (int64_t)blockIdx.z * UE + dp.uoff[s];
-  const int64_t r = dp.r[s];
-  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t a = (int64_t)blockIdx.y * warps + (threadIdx.x >> 5); a < r; a += (int64_t)gridDim.y * warps) {
-    float* row = U + a * r;
-    for (int64_t b = lane; b <= a; b += 32) row[b] = 0.f;
+// Row a and column b of entry e of a lower triangle stored by rows (e = a (a + 1) / 2 + b, b <= a).
+__device__ __forceinline__ void tri_decode(int64_t e, int64_t& a, int64_t& b) {
+  int64_t r = (int64_t)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= e) r++;
+  while (r * (r + 1) / 2 > e) r--;
+  a = r;
+  b = e - r * (r + 1) / 2;
+}
+
+// The update matrices' lower triangles (row a, columns b <= a; nothing reads or writes the upper ones) are zeroed
+// and extend-added in chunks of GP_EA_CHUNK entries in row order, one CTA per (supernode, chunk): every thread
+// has work however short the rows are (the small fronts' update matrices are thousands of short rows). Thread t
+// takes the chunk's entries t, t + 256, ..., EA_G of them at a time with all their loads in flight, stepping
+// (row, column) along instead of decoding every entry.
+constexpr int EA_THREADS = 256, EA_PER = GP_EA_CHUNK / EA_THREADS, EA_G = 4;
+__device__ __forceinline__ void tri_step(int64_t e, int64_t& a, int64_t& b) {   // entry e = the previous + 256
+  b += EA_THREADS;
+  if (b > a) tri_decode(e, a, b);
+}
+
+__global__ void __launch_bounds__(EA_THREADS) k_zero_updates32(const int2* __restrict__ tab, DevPlan dp,
+                                                               float* __restrict__ upd, int64_t UE) {
+  const int2 task = tab[blockIdx.x];
+  const int32_t s = task.x;
+  float* U = upd + (int64_t)blockIdx.y * UE + dp.uoff[s];
+  const int64_t r = dp.r[s], E = r * (r + 1) / 2;
+  int64_t e = (int64_t)task.y * GP_EA_CHUNK + threadIdx.x, a, b;
+  if (e >= E) return;
+  tri_decode(e, a, b);
+  for (int k = 0; k < EA_PER && e < E; k++) {
+    U[a * r + b] = 0.f;
+    e += EA_THREADS;
+    if (e < E) tri_step(e, a, b);
   }
 }
 
-// One CTA per (child, 8 rows of its update matrix): row a of U_child, columns b <= a, into the parent front
-// (row rel[a], columns rel[b]). A thread takes EA_U entries of a row per round with all their loads in flight
-// before any store; the targets of a row are distinct (rel is increasing), as are those of different rows, and a
-// launch takes one child of each parent, so no two threads of a launch touch one target.
-constexpr int EA_THREADS = 256, EA_U = 4;
+// Entries a, b <= a of the child's update matrix into the parent front (row rel[a], column rel[b]). The targets of
+// distinct entries are distinct (rel is increasing) and a launch takes one child of each parent, so no two
+// threads of a launch touch one target.
 __global__ void __launch_bounds__(EA_THREADS) k_extend_add32(const int2* __restrict__ tab, DevPlan dp,
                                                              float* __restrict__ p32, double* __restrict__ dg,
                                                              float* __restrict__ u32, int64_t P32E, int64_t DE,
                                                              int64_t UE) {
   const int2 task = tab[blockIdx.x];
-  const int32_t c = task.x, a0 = task.y;
-  const int b = blockIdx.y;
-  float* pp = p32 + (int64_t)b * P32E;
-  double* pd = dg + (int64_t)b * DE;
-  float* pu = u32 + (int64_t)b * UE;
+  const int32_t c = task.x;
+  const int bp = blockIdx.y;
+  float* pp = p32 + (int64_t)bp * P32E;
+  double* pd = dg + (int64_t)bp * DE;
+  float* pu = u32 + (int64_t)bp * UE;
   const int32_t p = dp.sn_parent[c];
-  const int32_t rc = dp.r[c];
+  const int64_t rc = dp.r[c], E = rc * (rc + 1) / 2;
   const float* Uc = pu + dp.uoff[c];
   const int32_t* rel = dp.relidx + dp.relidx_off[c];
   const MixFront fp = mix_front(dp, p, pp, pd, pu);
-  const int32_t a1 = min(a0 + 8, rc);
-  for (int32_t a = a0; a < a1; a++) {
-    const int32_t tr = rel[a];
-    const float* ur = Uc + (int64_t)a * rc;
-    for (int32_t base = 0; base <= a; base += EA_U * EA_THREADS) {
-      int32_t cc[EA_U];
-      float vv[EA_U];
+  int64_t e = (int64_t)task.y * GP_EA_CHUNK + threadIdx.x, a = 0, b = 0;
+  if (e >= E) return;
+  tri_decode(e, a, b);
+  for (int k0 = 0; k0 < EA_PER && e < E; k0 += EA_G) {
+    int32_t tr[EA_G], cc[EA_G];
+    float vv[EA_G];
 #pragma unroll
-      for (int k = 0; k < EA_U; k++) {
-        const int32_t bb = base + k * EA_THREADS + (int32_t)threadIdx.x;
-        cc[k] = bb <= a ? rel[bb] : -1;
-        vv[k] = bb <= a ? ur[bb] : 0.f;
+    for (int k = 0; k < EA_G; k++) {
+      tr[k] = -1;
+      if (e < E) {
+        tr[k] = rel[a];
+        cc[k] = rel[b];
+        vv[k] = Uc[a * rc + b];
+        e += EA_THREADS;
+        if (e < E) tri_step(e, a, b);
       }
-      if (tr >= fp.w) {   // a row below the parent's columns: its update-matrix row or its FP32 panel row
-        float* urow = fp.Uu + (int64_t)(tr - fp.w) * fp.r - fp.w;   // indexed by the parent column
-        float* prow = fp.P + (int64_t)tr * fp.ldw;
-        float old[EA_U];
+    }
+    float old[EA_G];
 #pragma unroll
-        for (int k = 0; k < EA_U; k++)
-          if (cc[k] >= 0) old[k] = cc[k] >= fp.w ? urow[cc[k]] : prow[cc[k]];
+    for (int k = 0; k < EA_G; k++)   // a row below the parent's columns: its update-matrix row or FP32 panel row
+      if (tr[k] >= fp.w)
+        old[k] = cc[k] >= fp.w ? fp.Uu[(int64_t)(tr[k] - fp.w) * fp.r + (cc[k] - fp.w)]
+                               : fp.P[(int64_t)tr[k] * fp.ldw + cc[k]];
 #pragma unroll
-        for (int k = 0; k < EA_U; k++)
-          if (cc[k] >= 0) (cc[k] >= fp.w ? urow[cc[k]] : prow[cc[k]]) = old[k] + vv[k];
+    for (int k = 0; k < EA_G; k++) {
+      if (tr[k] < 0) continue;
+      if (tr[k] >= fp.w) {
+        float* t = cc[k] >= fp.w ? fp.Uu + (int64_t)(tr[k] - fp.w) * fp.r + (cc[k] - fp.w)
+                                 : fp.P + (int64_t)tr[k] * fp.ldw + cc[k];
+        *t = old[k] + vv[k];
       } else {   // a row of the parent's columns: panel or FP64 diagonal tile
-#pragma unroll
-        for (int k = 0; k < EA_U; k++)
-          if (cc[k] >= 0) mix_add(fp, tr, cc[k], vv[k]);
+        mix_add(fp, tr[k], cc[k], vv[k]);
       }
     }
   }
@@ -390,6 +416,141 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
     }
 }
 
+// The FP32 Cholesky factor and inverse of one 64 x 64 tile by the CTA's 256 threads, in blocks of 32: each
+// diagonal block is factored (and inverted) by one warp holding a row per lane in registers, with no block-wide
+// barrier inside its 32 steps; the coupling blocks are products over all warps:
+//   L11 = chol(A11), X11 = inv(L11); L21 = A21 X11^T; A22 -= L21 L21^T; L22 = chol(A22), X22 = inv(L22);
+//   X21 = -X22 (L21 X11).
+// D: the FP64 tile (in: the accumulated entries; out, if STORE_L: L); DI: its FP32 inverse (zeros above the
+// diagonal and past bw); rows and columns past bw enter as the identity. A failed pivot records the smallest
+// such global column (first + k) in *flag and continues with 1.
+constexpr int PS = 65;   // row stride of the shared 64 x 64 FP32 tiles
+struct PotrfSmem {
+  float A[64 * PS];   // the tile, then L
+  float X[64 * PS];   // inv(L)
+  float W[32 * PS];   // coupling products
+};
+
+// Block [o, o + 32)^2 of S.A (lower triangle) factored in place by the calling warp; inv(L) of the block to S.X.
+__device__ __forceinline__ void chol32_warp(PotrfSmem& S, int o, int bw, int32_t first, int32_t* __restrict__ flag) {
+  const int i = threadIdx.x & 31;
+  float a[32], x[32];
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    a[k] = k <= i ? S.A[(o + i) * PS + o + k] : 0.f;
+    x[k] = k == i ? 1.f : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; j++) {
+    float d = __shfl_sync(0xffffffffu, a[j], j);
+    if (!(d > 0.f)) {
+      if (i == 0 && o + j < bw) atomicMin(flag, first + o + j);
+      d = 1.f;
+    }
+    const float sj = sqrtf(d), rj = 1.f / sj;
+    const float l = i == j ? sj : a[j] * rj;   // L_ij (lanes i >= j)
+#pragma unroll
+    for (int k = j + 1; k < 32; k++) {
+      const float lk = __shfl_sync(0xffffffffu, l, k);
+      if (i >= k) a[k] = fmaf(-l, lk, a[k]);
+    }
+    a[j] = i >= j ? l : 0.f;
+    // row j of inv(L) is final once divided by L_jj; the rows below eliminate it
+    if (i == j) {
+#pragma unroll
+      for (int m = 0; m <= j; m++) x[m] *= rj;
+    }
+#pragma unroll
+    for (int m = 0; m <= j; m++) {
+      const float xm = __shfl_sync(0xffffffffu, x[m], j);
+      if (i > j) x[m] = fmaf(-l, xm, x[m]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    if (k <= i) {
+      S.A[(o + i) * PS + o + k] = a[k];
+      S.X[(o + i) * PS + o + k] = x[k];
+    }
+  }
+}
+
+template <bool STORE_L>
+__device__ __forceinline__ void potrf64_fast(PotrfSmem& S, double* __restrict__ D, float* __restrict__ DI, int bw,
+                                             int32_t first, int32_t* __restrict__ flag) {
+  const int tid = threadIdx.x;
+  __syncthreads();   // an earlier call's readers of S are done
+#pragma unroll 4
+  for (int u = 0; u < 16; u++) {
+    const int e = tid + u * 256, i = e >> 6, j = e & 63;
+    float v = 0.f;
+    if (j <= i) v = i < bw ? (float)D[i * T + j] : (i == j ? 1.f : 0.f);
+    S.A[i * PS + j] = v;
+    S.X[i * PS + j] = 0.f;
+  }
+  __syncthreads();
+  if (tid < 32) chol32_warp(S, 0, bw, first, flag);
+  __syncthreads();
+  // thread: row 32 + (tid >> 3), columns 4 (tid & 7) + [0, 4)
+  const int ri = 32 + (tid >> 3), c4 = (tid & 7) * 4;
+  {   // L21 = A21 X11^T: L21[i][k] = sum_{m <= k} A21[i][m] X11[k][m]
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m = 0; m < 32; m++) {
+      const float av = S.A[ri * PS + m];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fmaf(av, S.X[(c4 + q) * PS + m], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) S.W[(ri - 32) * PS + c4 + q] = acc[q];
+  }
+  __syncthreads();
+  {   // L21 into A; A22 -= L21 L21^T (lower triangle)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m = 0; m < 32; m++) {
+      const float lv = S.W[(ri - 32) * PS + m];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fmaf(lv, S.W[(c4 + q) * PS + m], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      S.A[ri * PS + c4 + q] = S.W[(ri - 32) * PS + c4 + q];
+      if (32 + c4 + q <= ri) S.A[ri * PS + 32 + c4 + q] -= acc[q];
+    }
+  }
+  __syncthreads();
+  if (tid < 32) chol32_warp(S, 32, bw, first, flag);
+  __syncthreads();
+  {   // W = L21 X11: W[i][k] = sum_{m >= k} L21[i][m] X11[m][k]
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m = 0; m < 32; m++) {
+      const float lv = S.A[ri * PS + m];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fmaf(lv, S.X[m * PS + c4 + q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) S.W[(ri - 32) * PS + c4 + q] = acc[q];
+  }
+  __syncthreads();
+  {   // X21 = -X22 W: X21[i][k] = -sum_{j <= i} X22[i][j] W[j][k]
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = 0; j < 32; j++) {
+      const float xv = S.X[ri * PS + 32 + j];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fmaf(xv, S.W[j * PS + c4 + q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) S.X[ri * PS + c4 + q] = -acc[q];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int u = 0; u < 16; u++) {
+    const int e = tid + u * 256, i = e >> 6, j = e & 63;
+    const bool in = j <= i && i < bw;
+    DI[i * T + j] = in ? S.X[i * PS + j] : 0.f;
+    if (STORE_L && in) D[i * T + j] = (double)S.A[i * PS + j];
+  }
+}
+
 // The FP32 elimination of diagonal tile kb of each front of a step (its inverse; L_11 too if STORE_L).
 template <bool STORE_L>
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
@@ -398,8 +559,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(const int32_t* __r
   const int32_t s = fronts[blockIdx.x];
   const int b = blockIdx.y;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T,
-                                   notpd + b);
+  __shared__ __align__(16) PotrfSmem S;
+  potrf64_fast<STORE_L>(S, dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T, notpd + b);
 }
 
 // L_11 of every diagonal tile of the large fronts in FP64 (tile t of the launch: front fronts[t], block kb[t];
@@ -537,8 +698,12 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
                                                               float* __restrict__ oph, float* __restrict__ opl,
                                                               double* __restrict__ dg, float* __restrict__ dinv32,
                                                               int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
-  __shared__ __align__(16) float BsT[T * TS];
-  __shared__ __align__(16) float IsT[T * TS];
+  // the tiles' factorization workspace, and then the operands of the coupling block, share one buffer
+  constexpr int POOL = sizeof(PotrfSmem) > 2 * T * TS * sizeof(float) ? sizeof(PotrfSmem) : 2 * T * TS * sizeof(float);
+  __shared__ __align__(16) unsigned char pool[POOL];
+  PotrfSmem& S = *reinterpret_cast<PotrfSmem*>(pool);
+  float* BsT = reinterpret_cast<float*>(pool);
+  float* IsT = BsT + T * TS;
   const int fi = blockIdx.x;
   const int32_t s = fronts[fi];
   const int b = blockIdx.y;
@@ -546,7 +711,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
   const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int32_t first = dp.sn_first[s] + c0;
-  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, bw1, first, notpd + b);
+  potrf64_fast<STORE_L>(S, dg + off, dinv32 + off, bw1, first, notpd + b);
   if (fi >= n2) return;
   const int bw2 = min(T, w - c1);
   const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
@@ -571,7 +736,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
       const int i = tr + e, j = tc + f;
       if (j <= i && i < bw2) D2[i * T + j] -= (double)g[e][f];
     }
-  potrf_tile<float, true, STORE_L>(D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
+  potrf64_fast<STORE_L>(S, D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
 }
 
 // The TRSM of a pair of block columns kb, kb + 1: for each 64-row tile below the pair (below block kb alone for
@@ -1223,18 +1388,15 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
     ctx->prof_level = L;
-    int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
-    int64_t r2max = 1;   // CTAs per front sized by the level's largest update matrix
-    for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
-      const int64_t r = sp.sn_r[sp.lev_sn[q]];
-      r2max = std::max(r2max, r * r);
+    if (lv.zero_n > 0) {
+      ProfScope ps_(ctx, KC_EXTEND_ADD);   // the update matrices this level's fronts will fill
+      k_zero_updates32<<<dim3((unsigned)lv.zero_n, B), EA_THREADS, 0, st>>>(dp.zero_tab + lv.zero_off, dp, f->upd32,
+                                                                             UE);
+      GP_CHECK_LAUNCH(ctx);
     }
-    const unsigned zy = (unsigned)std::min<int64_t>(2048, (r2max + 8191) / 8192);
-    k_zero_updates32<<<dim3(nl, zy, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, f->upd32, UE);
-    GP_CHECK_LAUNCH(ctx);
-    for (const auto& ea : lv.ea) {
+    for (const auto& ea : lv.ea32) {
       ProfScope ps_(ctx, KC_EXTEND_ADD);
-      k_extend_add32<<<dim3((unsigned)ea.ncta, B), EA_THREADS, 0, st>>>(dp.ea_tab + ea.tab_off, dp, f->panels32,
+      k_extend_add32<<<dim3((unsigned)ea.ncta, B), EA_THREADS, 0, st>>>(dp.ea32_tab + ea.tab_off, dp, f->panels32,
                                                                         f->diag, f->upd32, P32E, DE, UE);
       GP_CHECK_LAUNCH(ctx);
     }

@@ -349,6 +349,8 @@ gp_status assemble_common(gp_ctx* ctx, const double* d_X, int64_t n, int d, cons
     dp.sn_first = upload(ctx, ps->bufs, sp.sn_first);
     dp.sn_of_col = upload(ctx, ps->bufs, sp.sn_of_col);
     dp.ea_tab = upload(ctx, ps->bufs, sp.ea_tab);
+    dp.ea32_tab = upload(ctx, ps->bufs, sp.ea32_tab);
+    dp.zero_tab = upload(ctx, ps->bufs, sp.zero_tab);
     dp.small_list = upload(ctx, ps->bufs, sp.small_list);
     dp.large_fronts = upload(ctx, ps->bufs, sp.large_fronts);
     dp.step_pre = upload(ctx, ps->bufs, sp.step_pre);

@@ -28,6 +28,7 @@
 #define GP_RELAX_WIDTH 16      // relaxed amalgamation: merge when the merged supernode is this narrow
 #define GP_TILE 64             // dense tile edge of the large-front kernels
 #define GP_SMALL_M 96          // fronts up to this order are factored by one CTA in shared memory
+#define GP_EA_CHUNK 8192       // update-matrix entries per CTA of the mixed path's extend-add and zeroing
 #define GP_FLOW_SB_MIN_NB 16   // levels whose largest front has this many 64-column blocks: 2 per solve chain task
 
 // ------------------------------------------------------------------------------------------ errors
@@ -198,12 +199,17 @@ struct SymPlan {
                       double potrf_flops, trsm_flops, upd_flops; };   // useful flops of the step's launches
   struct Level {
     std::vector<EaLaunch> ea;        // one per child slot
+    std::vector<EaLaunch> ea32;      // the same in chunks of GP_EA_CHUNK update-matrix entries (mixed path)
+    int64_t zero_off = 0, zero_n = 0; // into zero_tab: this level's update matrices in chunks (mixed path)
     int64_t small_off = 0; int32_t nsmall = 0;   // into small_list
     std::vector<StepLaunch> steps;   // large fronts, one per block column
     int32_t flow_sb = 1;             // 64-column blocks per chain task of this level's solve tasks (1 or 2)
   };
   std::vector<Level> levels;
   std::vector<int2> ea_tab;          // (child supernode, first column) per extend-add CTA (8 columns each)
+  // mixed path: (child supernode, chunk) per extend-add CTA and (supernode, chunk) per zeroing CTA, a chunk being
+  // GP_EA_CHUNK consecutive entries of the lower triangle of the update matrix in row order
+  std::vector<int2> ea32_tab, zero_tab;
   std::vector<int32_t> small_list;   // supernodes factored in shared memory
   std::vector<int32_t> large_fronts; // per step: fronts (sorted by width descending within a level)
   std::vector<int32_t> large_kb;     // block-column index of each large_fronts entry (its step)
@@ -235,6 +241,7 @@ struct DevPlan {
   int32_t* sn_first;
   int32_t* sn_of_col;
   int2* ea_tab;
+  int2 *ea32_tab, *zero_tab;
   int32_t* small_list;
   int32_t* large_fronts;
   int64_t* step_pre;

@@ -423,7 +423,25 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       }
       ea.ncta = (int64_t)sp.ea_tab.size() - ea.tab_off;
       if (ea.ncta > 0) lv.ea.push_back(ea);
+      SymPlan::EaLaunch e32{(int64_t)sp.ea32_tab.size(), 0};
+      for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
+        int32_t s = sp.lev_sn[q];
+        if (sp.ch_ptr[s] + k >= sp.ch_ptr[s + 1]) continue;
+        int32_t c = sp.ch_idx[sp.ch_ptr[s] + k];
+        const int64_t rc = sp.sn_r[c], nch = (rc * (rc + 1) / 2 + GP_EA_CHUNK - 1) / GP_EA_CHUNK;
+        GP_REQUIRE(nch < INT32_MAX, "update matrix too large");
+        for (int64_t h = 0; h < nch; h++) sp.ea32_tab.push_back(make_int2(c, (int)h));
+      }
+      e32.ncta = (int64_t)sp.ea32_tab.size() - e32.tab_off;
+      if (e32.ncta > 0) lv.ea32.push_back(e32);
     }
+    lv.zero_off = (int64_t)sp.zero_tab.size();
+    for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
+      const int32_t s = sp.lev_sn[q];
+      const int64_t r = sp.sn_r[s], nch = (r * (r + 1) / 2 + GP_EA_CHUNK - 1) / GP_EA_CHUNK;
+      for (int64_t h = 0; h < nch; h++) sp.zero_tab.push_back(make_int2(s, (int)h));
+    }
+    lv.zero_n = (int64_t)sp.zero_tab.size() - lv.zero_off;
     // fronts
     lv.small_off = (int64_t)sp.small_list.size();
     std::vector<int32_t> large;
