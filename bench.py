@@ -410,6 +410,23 @@ def run_gpu(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
 
+    # settings of the batched leg, evaluated one at a time here for the comparison with their batched results
+    leg_B = args.batch_leg if (prec == gp.GP_MIXED and B == 1 and args.batch_leg > 1) else 0
+    leg_single = None
+    if leg_B:
+        per_leg = ps.factor_bytes(hp, leg_B, prec)
+        while leg_B > 1 and per_leg > args.batch_leg_budget_gb * 1e9:
+            leg_B -= 1
+            per_leg = ps.factor_bytes(hp, leg_B, prec)
+        leg_thetas = [synth.perturb(rng, hp, 0.05) for _ in range(leg_B * (args.batch_leg_steps + 1))]
+        leg_single = []
+        for th in leg_thetas[:leg_B]:
+            with torch.cuda.stream(stream):
+                f.update([th])
+                f.loglik(resid, out=out)
+            stream.synchronize()   # out is written on the library's stream
+            leg_single.append(float(out.cpu()[0]))
+
     res = dict(total_ms=total_ms, per=per_ms, launches=launches, B=B, Bc=Bc, nchunk=nchunk, predict=predict_info,
                variance=var_info, iterative=it_info,
                autotune=tune, clk=clk, info=info, t_assemble=t_assemble,
@@ -454,9 +471,54 @@ def run_gpu(args, rank, world, local_rank):
         f = None
     if f is not None:
         f.free()
+    if leg_B > 1:   # leg_B settings in one factorization and one batched solve per step, within the budget
+        res["batched"] = batched_leg(ctx, ps, stream, resid, leg_thetas, leg_single, leg_B, args.batch_leg_steps,
+                                     per_leg, args.batch_leg_budget_gb)
     ps.free()
     res["ctx"] = ctx
     return res
+
+
+def batched_leg(ctx, ps, stream, resid, thetas, single, Bl, steps, nbytes, budget_gb):
+    """Bl settings per factorization on the same point set: every launch of A3-A11 spans all Bl. One warm-up
+    step, then `steps` timed steps (new settings each step) with CUDA events; the first step's settings are also
+    compared with their one-at-a-time evaluations."""
+    import torch
+    from paper_2411_05869_gb300 import gp
+    dev = resid.device
+    fb = ctx.factor(ps, thetas[:Bl], gp.GP_MIXED)
+    rb = resid.expand(Bl, -1).contiguous()
+    outb = torch.empty(Bl, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        fb.loglik(rb, out=outb)
+    stream.synchronize()
+    llb = outb.cpu().numpy().copy()
+    rel = [abs(a - b) / abs(b) for a, b in zip(llb, single)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            fb.update(thetas[(k + 1) * Bl:(k + 2) * Bl])
+            fb.loglik(rb, out=outb)
+            ev[k + 1].record(stream)
+    stream.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    ctx.profile(True)
+    fb.update(thetas[:Bl])
+    fb.loglik(rb, out=outb)
+    stream.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    fb.free()
+    return {"B": Bl, "steps": steps, "evals_per_s": Bl * steps * 1e3 / sum(per), "ms_per_step": float(np.mean(per)),
+            "ms_per_eval": float(np.mean(per)) / Bl,
+            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+            "factor_bytes": int(nbytes), "budget_gb": budget_gb,
+            "rel_diff_vs_one_at_a_time": float(max(rel)),
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
+            "note": f"{Bl} settings per factorization (every launch spans all of them); steady-state update + loglik "
+                    "steps timed with CUDA events; rel_diff compares the first step's log-likelihoods with the same "
+                    "settings evaluated one at a time"}
 
 
 # ------------------------------------------------------------------------------------------------ MCMC leg
@@ -612,6 +674,11 @@ def main():
                                                                    "(0: all cores)")
     ap.add_argument("--subwindow-parity", type=int, default=1, help="1: the GPU path on the oracle's sub-window "
                                                                     "against the oracle (FP64 and mixed)")
+    ap.add_argument("--batch-leg", type=int, default=-1, help="mixed runs at B = 1: also time this many settings "
+                    "per factorization (default 3 on station_1.2M, else 0)")
+    ap.add_argument("--batch-leg-steps", type=int, default=3)
+    ap.add_argument("--batch-leg-budget-gb", type=float, default=180.0, help="device memory the batched leg's "
+                    "factor may take (the leg's B shrinks to fit)")
     ap.add_argument("--serve-sets", type=int, default=20)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
@@ -621,6 +688,8 @@ def main():
     args = ap.parse_args()
     if args.batch <= 0:
         args.batch = {"batched_200k": 64, "mcmc_200k": 16}.get(args.workload, 1)
+    if args.batch_leg < 0:
+        args.batch_leg = 3 if args.workload == "station_1.2M" else 0
     if args.autotune < 0:   # the library's autotuner picks the update blocking of mixed runs (compact core)
         args.autotune = 1 if args.precision == "mixed" and args.workload != "noncompact_50k" else 0
 
@@ -743,6 +812,8 @@ def main():
     }
     if "fp64" in res:
         line["fp64"] = res["fp64"]
+    if "batched" in res:
+        line["batched"] = res["batched"]
     if res.get("predict"):
         line["predict"] = res["predict"]
     if res.get("variance"):

@@ -416,141 +416,6 @@ __device__ __forceinline__ void potrf_tile(double* __restrict__ D, float* __rest
     }
 }
 
-// The FP32 Cholesky factor and inverse of one 64 x 64 tile by the CTA's 256 threads, in blocks of 32: each
-// diagonal block is factored (and inverted) by one warp holding a row per lane in registers, with no block-wide
-// barrier inside its 32 steps; the coupling blocks are products over all warps:
-//   L11 = chol(A11), X11 = inv(L11); L21 = A21 X11^T; A22 -= L21 L21^T; L22 = chol(A22), X22 = inv(L22);
-//   X21 = -X22 (L21 X11).
-// D: the FP64 tile (in: the accumulated entries; out, if STORE_L: L); DI: its FP32 inverse (zeros above the
-// diagonal and past bw); rows and columns past bw enter as the identity. A failed pivot records the smallest
-// such global column (first + k) in *flag and continues with 1.
-constexpr int PS = 65;   // row stride of the shared 64 x 64 FP32 tiles
-struct PotrfSmem {
-  float A[64 * PS];   // the tile, then L
-  float X[64 * PS];   // inv(L)
-  float W[32 * PS];   // coupling products
-};
-
-// Block [o, o + 32)^2 of S.A (lower triangle) factored in place by the calling warp; inv(L) of the block to S.X.
-__device__ __forceinline__ void chol32_warp(PotrfSmem& S, int o, int bw, int32_t first, int32_t* __restrict__ flag) {
-  const int i = threadIdx.x & 31;
-  float a[32], x[32];
-#pragma unroll
-  for (int k = 0; k < 32; k++) {
-    a[k] = k <= i ? S.A[(o + i) * PS + o + k] : 0.f;
-    x[k] = k == i ? 1.f : 0.f;
-  }
-#pragma unroll
-  for (int j = 0; j < 32; j++) {
-    float d = __shfl_sync(0xffffffffu, a[j], j);
-    if (!(d > 0.f)) {
-      if (i == 0 && o + j < bw) atomicMin(flag, first + o + j);
-      d = 1.f;
-    }
-    const float sj = sqrtf(d), rj = 1.f / sj;
-    const float l = i == j ? sj : a[j] * rj;   // L_ij (lanes i >= j)
-#pragma unroll
-    for (int k = j + 1; k < 32; k++) {
-      const float lk = __shfl_sync(0xffffffffu, l, k);
-      if (i >= k) a[k] = fmaf(-l, lk, a[k]);
-    }
-    a[j] = i >= j ? l : 0.f;
-    // row j of inv(L) is final once divided by L_jj; the rows below eliminate it
-    if (i == j) {
-#pragma unroll
-      for (int m = 0; m <= j; m++) x[m] *= rj;
-    }
-#pragma unroll
-    for (int m = 0; m <= j; m++) {
-      const float xm = __shfl_sync(0xffffffffu, x[m], j);
-      if (i > j) x[m] = fmaf(-l, xm, x[m]);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 32; k++) {
-    if (k <= i) {
-      S.A[(o + i) * PS + o + k] = a[k];
-      S.X[(o + i) * PS + o + k] = x[k];
-    }
-  }
-}
-
-template <bool STORE_L>
-__device__ __forceinline__ void potrf64_fast(PotrfSmem& S, double* __restrict__ D, float* __restrict__ DI, int bw,
-                                             int32_t first, int32_t* __restrict__ flag) {
-  const int tid = threadIdx.x;
-  __syncthreads();   // an earlier call's readers of S are done
-#pragma unroll 4
-  for (int u = 0; u < 16; u++) {
-    const int e = tid + u * 256, i = e >> 6, j = e & 63;
-    float v = 0.f;
-    if (j <= i) v = i < bw ? (float)D[i * T + j] : (i == j ? 1.f : 0.f);
-    S.A[i * PS + j] = v;
-    S.X[i * PS + j] = 0.f;
-  }
-  __syncthreads();
-  if (tid < 32) chol32_warp(S, 0, bw, first, flag);
-  __syncthreads();
-  // thread: row 32 + (tid >> 3), columns 4 (tid & 7) + [0, 4)
-  const int ri = 32 + (tid >> 3), c4 = (tid & 7) * 4;
-  {   // L21 = A21 X11^T: L21[i][k] = sum_{m <= k} A21[i][m] X11[k][m]
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < 32; m++) {
-      const float av = S.A[ri * PS + m];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fmaf(av, S.X[(c4 + q) * PS + m], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) S.W[(ri - 32) * PS + c4 + q] = acc[q];
-  }
-  __syncthreads();
-  {   // L21 into A; A22 -= L21 L21^T (lower triangle)
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < 32; m++) {
-      const float lv = S.W[(ri - 32) * PS + m];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fmaf(lv, S.W[(c4 + q) * PS + m], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      S.A[ri * PS + c4 + q] = S.W[(ri - 32) * PS + c4 + q];
-      if (32 + c4 + q <= ri) S.A[ri * PS + 32 + c4 + q] -= acc[q];
-    }
-  }
-  __syncthreads();
-  if (tid < 32) chol32_warp(S, 32, bw, first, flag);
-  __syncthreads();
-  {   // W = L21 X11: W[i][k] = sum_{m >= k} L21[i][m] X11[m][k]
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < 32; m++) {
-      const float lv = S.A[ri * PS + m];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fmaf(lv, S.X[m * PS + c4 + q], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) S.W[(ri - 32) * PS + c4 + q] = acc[q];
-  }
-  __syncthreads();
-  {   // X21 = -X22 W: X21[i][k] = -sum_{j <= i} X22[i][j] W[j][k]
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int j = 0; j < 32; j++) {
-      const float xv = S.X[ri * PS + 32 + j];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fmaf(xv, S.W[j * PS + c4 + q], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) S.X[ri * PS + c4 + q] = -acc[q];
-  }
-  __syncthreads();
-#pragma unroll 4
-  for (int u = 0; u < 16; u++) {
-    const int e = tid + u * 256, i = e >> 6, j = e & 63;
-    const bool in = j <= i && i < bw;
-    DI[i * T + j] = in ? S.X[i * PS + j] : 0.f;
-    if (STORE_L && in) D[i * T + j] = (double)S.A[i * PS + j];
-  }
-}
-
 // The FP32 elimination of diagonal tile kb of each front of a step (its inverse; L_11 too if STORE_L).
 template <bool STORE_L>
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(const int32_t* __restrict__ fronts, int kb, DevPlan dp,
@@ -559,8 +424,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(const int32_t* __r
   const int32_t s = fronts[blockIdx.x];
   const int b = blockIdx.y;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
-  __shared__ __align__(16) PotrfSmem S;
-  potrf64_fast<STORE_L>(S, dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T, notpd + b);
+  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, min(T, dp.w[s] - kb * T), dp.sn_first[s] + kb * T,
+                                   notpd + b);
 }
 
 // L_11 of every diagonal tile of the large fronts in FP64 (tile t of the launch: front fronts[t], block kb[t];
@@ -584,7 +449,7 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // FP32 TRSM of the rows below diagonal tile kb as a product with the inverse the POTRF left behind:
 // X = B L^{-T}, X[r][j] = sum_{l <= j} B[r][l] Inv[j][l], one CTA of 256 threads per 64-row tile, each thread a
 // 4 x 4 block of X (no dependency chains, unlike a column-by-column substitution). The L entries are written
-// with their TF32 pair (hi = rn(x), lo = rn(x - hi)), the tensor-core operands of the updates.
+// with the low parts of their TF32 pairs (tf32_lo), the tensor-core operands of the updates.
 constexpr int TS = T + 4;   // transposed shared tiles, rows 16-byte aligned for vector reads
 
 // dst[l][r] = src[r][l] for a 64 x 64 block at src (row stride lds), rows >= nr and columns >= nc read as zero;
@@ -622,34 +487,39 @@ __device__ __forceinline__ void prod_tile(const float* BT, const float* CT, int 
   }
 }
 
-// Rows tr..tr+3 x columns tc..tc+3 of X into the panel at P + o (row stride ldw) and into its TF32 pair (the
-// same offsets in oph, opl), for rows < nr and columns < bw.
-__device__ __forceinline__ void store_x(const float (&acc)[4][4], float* __restrict__ P, float* __restrict__ oph,
-                                        float* __restrict__ opl, int64_t o0, int ldw, int nr, int bw) {
+// The TF32 operand pair of an L entry x: the high part is x itself as the TF32 MMAs read it (they ignore the low
+// 13 mantissa bits, i.e. truncate), the low part lo = x - trunc_tf32(x), exact in FP32 and rounded to TF32 here.
+__device__ __forceinline__ float tf32_lo(float x) {
+  return tf32_rn(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
+}
+
+// Rows tr..tr+3 x columns tc..tc+3 of X into the front's panel at P + o (row stride ldw) and the low parts of
+// their TF32 pairs into the front's low-part region at L + o, for rows < nr and columns < bw. The padding
+// columns of a row (from the front's width up to ldw, inside the last 4-column group) get a zero low part: the
+// region is reused by the fronts of other levels, and the updates read those columns (times a zero high part).
+__device__ __forceinline__ void store_x(const float (&acc)[4][4], float* __restrict__ P, float* __restrict__ L,
+                                        int64_t o0, int ldw, int nr, int bw) {
   const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int i = tr + e;
     if (i >= nr) continue;
-    const int64_t o = o0 + (int64_t)i * ldw + tc;   // 16-byte aligned: ldw, the columns, tc and the panel offset are x4
+    const int64_t o = o0 + (int64_t)i * ldw + tc;   // 16-byte aligned: ldw, the columns, tc and the offsets are x4
     if (tc + 4 <= bw) {
-      float4 x, hi, lo;
-      x = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
-      hi = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-      lo = make_float4(tf32_rn(x.x - hi.x), tf32_rn(x.y - hi.y), tf32_rn(x.z - hi.z), tf32_rn(x.w - hi.w));
+      const float4 x = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
       *reinterpret_cast<float4*>(P + o) = x;
-      *reinterpret_cast<float4*>(oph + o) = hi;
-      *reinterpret_cast<float4*>(opl + o) = lo;
-    } else {
+      *reinterpret_cast<float4*>(L + o) = make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
+    } else if (tc < bw) {   // the front's last columns (bw < 64 only at its last block) and the padding after them
+      float lo[4];
 #pragma unroll
       for (int f = 0; f < 4; f++) {
-        if (tc + f >= bw) continue;
-        const float x = acc[e][f];
-        P[o + f] = x;
-        const float hi = tf32_rn(x);
-        oph[o + f] = hi;
-        opl[o + f] = tf32_rn(x - hi);
+        lo[f] = 0.f;
+        if (tc + f < bw) {
+          P[o + f] = acc[e][f];
+          lo[f] = tf32_lo(acc[e][f]);
+        }
       }
+      *reinterpret_cast<float4*>(L + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
 }
@@ -665,7 +535,7 @@ __device__ __forceinline__ void stash_t(const float (&acc)[4][4], float* BT) {
 
 __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                                 int nfront, int kb, DevPlan dp, float* __restrict__ p32,
-                                                float* __restrict__ oph, float* __restrict__ opl,
+                                                float* __restrict__ opl, int64_t LOE,
                                                 const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
   __shared__ __align__(16) float BsT[T * TS];   // BsT[l][r] = B[r][l]
   __shared__ __align__(16) float IsT[T * TS];   // IsT[l][j] = Inv[j][l]
@@ -685,7 +555,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw, acc);
-  store_x(acc, p32 + ob, oph + ob, opl + ob, r0 * ldw + c0, ldw, nr, bw);
+  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], r0 * ldw + c0, ldw, nr, bw);
 }
 
 // Block columns kb and kb + 1 at once (the mixed path's block steps in pairs, for an even group width): fronts
@@ -695,15 +565,11 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
 template <bool STORE_L>
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __restrict__ fronts, int n2, int kb,
                                                               DevPlan dp, float* __restrict__ p32,
-                                                              float* __restrict__ oph, float* __restrict__ opl,
+                                                              float* __restrict__ opl, int64_t LOE,
                                                               double* __restrict__ dg, float* __restrict__ dinv32,
                                                               int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
-  // the tiles' factorization workspace, and then the operands of the coupling block, share one buffer
-  constexpr int POOL = sizeof(PotrfSmem) > 2 * T * TS * sizeof(float) ? sizeof(PotrfSmem) : 2 * T * TS * sizeof(float);
-  __shared__ __align__(16) unsigned char pool[POOL];
-  PotrfSmem& S = *reinterpret_cast<PotrfSmem*>(pool);
-  float* BsT = reinterpret_cast<float*>(pool);
-  float* IsT = BsT + T * TS;
+  __shared__ __align__(16) float BsT[T * TS];
+  __shared__ __align__(16) float IsT[T * TS];
   const int fi = blockIdx.x;
   const int32_t s = fronts[fi];
   const int b = blockIdx.y;
@@ -711,7 +577,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
   const int c0 = kb * T, bw1 = min(T, w - c0), c1 = c0 + bw1;
   const int64_t off = (int64_t)b * DE + dp.doff[s] + (int64_t)kb * T * T;
   const int32_t first = dp.sn_first[s] + c0;
-  potrf64_fast<STORE_L>(S, dg + off, dinv32 + off, bw1, first, notpd + b);
+  potrf_tile<float, true, STORE_L>(dg + off, dinv32 + off, bw1, first, notpd + b);
   if (fi >= n2) return;
   const int bw2 = min(T, w - c1);
   const int64_t ob = (int64_t)b * P32E + dp.loff32[s];
@@ -721,7 +587,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw1, acc);   // L_21
-  store_x(acc, p32 + ob, oph + ob, opl + ob, (int64_t)c1 * ldw + c0, ldw, bw2, bw1);
+  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], (int64_t)c1 * ldw + c0, ldw, bw2, bw1);
   __syncthreads();
   stash_t(acc, BsT);   // BsT[l][r] = L_21[r][l]; rows past bw2 hold zeros
   __syncthreads();
@@ -736,14 +602,14 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
       const int i = tr + e, j = tc + f;
       if (j <= i && i < bw2) D2[i * T + j] -= (double)g[e][f];
     }
-  potrf64_fast<STORE_L>(S, D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
+  potrf_tile<float, true, STORE_L>(D2, dinv32 + off + T * T, bw2, first + T, notpd + b);   // begins with a barrier
 }
 
 // The TRSM of a pair of block columns kb, kb + 1: for each 64-row tile below the pair (below block kb alone for
 // fronts past n2), X_1 = B_1 inv(L_11)^T, B_2' = B_2 - X_1 L_21^T, X_2 = B_2' inv(L_22)^T.
 __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                                      int nfront, int n2, int kb, DevPlan dp, float* __restrict__ p32,
-                                                     float* __restrict__ oph, float* __restrict__ opl,
+                                                     float* __restrict__ opl, int64_t LOE,
                                                      const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
   __shared__ __align__(16) float BsT[T * TS];
   __shared__ __align__(16) float IsT[T * TS];
@@ -761,12 +627,13 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
   const int64_t r0 = c2 + (t - pre[fi]) * T;
   const int nr = (int)imin64(T, m - r0);
   float* P = p32 + ob;
+  float* Lo = opl + (int64_t)b * LOE + dp.lo_off[s];
   load_tile_t(IsT, DI, T, T, T);
   load_tile_t(BsT, P + r0 * ldw + c0, ldw, nr, bw1);
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw1, acc);   // X_1
-  store_x(acc, P, oph + ob, opl + ob, r0 * ldw + c0, ldw, nr, bw1);
+  store_x(acc, P, Lo, r0 * ldw + c0, ldw, nr, bw1);
   if (!two) return;
   __syncthreads();
   stash_t(acc, BsT);                                            // BsT[l][r] = X_1[r][l]
@@ -788,7 +655,7 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
   }
   __syncthreads();
   prod_tile(BsT, IsT, bw2, acc);   // X_2
-  store_x(acc, P, oph + ob, opl + ob, r0 * ldw + c1, ldw, nr, bw2);
+  store_x(acc, P, Lo, r0 * ldw + c1, ldw, nr, bw2);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -798,9 +665,11 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
 //      (the group's earlier blocks); 4: the same for block columns kb and kb + 1 at once, 128 x 128 tiles;
 //   2: group end: rows/columns >= gend, tiles on and below the diagonal (the plan's tile width: 256 x 256 per
 //      CTA pair, or 128 x 128), K = the whole group [g0, gend).
-// The operands are the TF32 pair (hi, lo) of each L entry, written by the TRSM next to the FP32 panel, and each
-// tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo and Yokota, 2022: about 21
-// significant bits survive the products instead of the 11 of one TF32 pass). The wide tiles of mode 2 halve
+// The operands are the TF32 pair (hi, lo) of each L entry: hi is the FP32 panel entry itself, read through the
+// TF32 MMA's truncation of the low 13 mantissa bits, and lo the rounded remainder the TRSM writes into the
+// level's low-part workspace. Each tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo
+// and Yokota, 2022, with a truncated high part: about 20 significant bits survive the products instead of the 11
+// of one TF32 pass). The wide tiles of mode 2 halve
 // the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
 // bounds this kernel). Mode 2 runs in clusters of two CTAs on the tile pairs (rows 2p and 2p + 1 of 128, the same
 // 256 columns) as one 256 x 256 CTA-pair MMA: each CTA loads its own 128 A rows and its half of the 256 B rows,
@@ -1329,9 +1198,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 // Tensor maps of the TF32 operand pair of every large front (those with tensor-core updates under any
-// blocking of plan_mixed_updates): per front two 3-D maps
-// (columns x rows x proposals) over op_hi and op_lo, 128 x 32 boxes with the 128-byte swizzle; rows past the
-// front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
+// blocking of plan_mixed_updates): per front two 3-D maps (columns x rows x proposals), the high part over the
+// FP32 panel and the low part over the front's region of op_lo, 128 x 32 boxes with the 128-byte swizzle; rows
+// past the front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
   const SymPlan& sp = f->ps->sp;
   const int64_t ns = (int64_t)sp.sn_w.size();
@@ -1351,10 +1220,12 @@ void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
     const int32_t s = order[k];
     const int64_t ldw = sp.sn_ldw[s], m = (int64_t)sp.sn_w[s] + sp.sn_r[s];
     GP_REQUIRE(ldw % 4 == 0 && sp.sn_loff32[s] % 4 == 0, "FP32 panel rows must start on 16-byte boundaries");
+    GP_REQUIRE(sp.sn_lo_off[s] % 4 == 0 && sp.lo_entries % 4 == 0, "low-part rows must start on 16-byte boundaries");
     for (int part = 0; part < 2; part++) {
-      float* base = (part == 0 ? f->op_hi : f->op_lo) + sp.sn_loff32[s];
+      float* base = part == 0 ? f->panels32 + sp.sn_loff32[s] : f->op_lo + sp.sn_lo_off[s];
+      const int64_t pstride = part == 0 ? sp.panel32_entries : sp.lo_entries;
       cuuint64_t dims[3] = {(cuuint64_t)ldw, (cuuint64_t)m, (cuuint64_t)f->B};
-      cuuint64_t strides[2] = {(cuuint64_t)ldw * 4, (cuuint64_t)sp.panel32_entries * 4};
+      cuuint64_t strides[2] = {(cuuint64_t)ldw * 4, (cuuint64_t)pstride * 4};
       cuuint32_t box[3] = {32, 128, 1};
       cuuint32_t es[3] = {1, 1, 1};
       CUresult r = enc(&maps[2 * k + part], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
@@ -1379,7 +1250,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   cudaStream_t st = ctx->stream;
   set_attrs();
   const int B = f->B;
-  const int64_t P32E = sp.panel32_entries, DE = sp.diag_entries, UE = sp.update_entries;
+  const int64_t P32E = sp.panel32_entries, DE = sp.diag_entries, UE = sp.update_entries, LOE = sp.lo_entries;
   values_run_mixed(ctx, f);   // A3, A4 into the FP32 panels and FP64 tiles (zeroed first)
   k_fill_i32<<<grid_for(B, 128), 128, 0, st>>>(f->notpd, B, INT_MAX);
   GP_CHECK_LAUNCH(ctx);
@@ -1424,15 +1295,15 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
         {
           ProfScope ps_(ctx, KC_POTRF, B * (stp.potrf_flops + st2.potrf_flops));
           auto kp = f->diag_fp32 ? k_potrf_pair<true> : k_potrf_pair<false>;
-          kp<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp, f->panels32, f->op_hi,
-                                                            f->op_lo, f->diag, f->dinv32, P32E, DE, f->notpd);
+          kp<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp, f->panels32, f->op_lo,
+                                                            LOE, f->diag, f->dinv32, P32E, DE, f->notpd);
           GP_CHECK_LAUNCH(ctx);
         }
         if (stp.pair_total > 0) {
           ProfScope ps_(ctx, KC_TRSM, B * (stp.trsm_flops + st2.trsm_flops));
           k_trsm32_pair<<<dim3((unsigned)stp.pair_total, B), 256, 0, st>>>(
-              fronts, dp.pair_pre + stp.pair_pre_off, stp.nfront, st2.nfront, stp.kb, dp, f->panels32, f->op_hi,
-              f->op_lo, f->dinv32, P32E, DE);
+              fronts, dp.pair_pre + stp.pair_pre_off, stp.nfront, st2.nfront, stp.kb, dp, f->panels32, f->op_lo,
+              LOE, f->dinv32, P32E, DE);
           GP_CHECK_LAUNCH(ctx);
         }
         for (const auto* sg : {&stp, &st2})
@@ -1460,7 +1331,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       if (stp.trsm_total > 0) {
         ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
         k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
-                                                                    f->panels32, f->op_hi, f->op_lo, f->dinv32, P32E,
+                                                                    f->panels32, f->op_lo, LOE, f->dinv32, P32E,
                                                                     DE);
         GP_CHECK_LAUNCH(ctx);
       }

@@ -359,6 +359,7 @@ gp_status assemble_common(gp_ctx* ctx, const double* d_X, int64_t n, int d, cons
     dp.sn_parent = upload(ctx, ps->bufs, sp.sn_parent);
     dp.ldw = upload(ctx, ps->bufs, sp.sn_ldw);
     dp.loff32 = upload(ctx, ps->bufs, sp.sn_loff32);
+    dp.lo_off = upload(ctx, ps->bufs, sp.sn_lo_off);
     dp.doff = upload(ctx, ps->bufs, sp.sn_doff);
     dp.large_kb = upload(ctx, ps->bufs, sp.large_kb);
     dp.sn_fl = upload(ctx, ps->bufs, sp.sn_fl);
@@ -578,11 +579,8 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->refine_runs = dalloc<unsigned long long>(ctx, f->bufs, 1);
       GP_CUDA(cudaMemsetAsync(f->refine_runs, 0, sizeof(unsigned long long), ctx->stream));
       f->dinv32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.diag_entries);
-      f->op_hi = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
-      f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.panel32_entries);
-      // entries the TRSM never writes (padding columns) must read as zeros
-      GP_CUDA(cudaMemsetAsync(f->op_hi, 0, (size_t)B * sp.panel32_entries * sizeof(float), ctx->stream));
-      GP_CUDA(cudaMemsetAsync(f->op_lo, 0, (size_t)B * sp.panel32_entries * sizeof(float), ctx->stream));
+      f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.lo_entries);
+      GP_CUDA(cudaMemsetAsync(f->op_lo, 0, (size_t)B * sp.lo_entries * sizeof(float), ctx->stream));
       build_update_maps(ctx, f);
     }
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
@@ -638,7 +636,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
     t += alloc_bytes(b * sp.panel32_entries * 4) + alloc_bytes(b * sp.diag_entries * 8) +
          alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
          alloc_bytes(8) +
-         alloc_bytes(b * sp.diag_entries * 4) + 2 * alloc_bytes(b * sp.panel32_entries * 4) +
+         alloc_bytes(b * sp.diag_entries * 4) + alloc_bytes(b * sp.lo_entries * 4) +
          alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
   }
   t += alloc_bytes(b * ps->nnz * 8) + alloc_bytes(b * 4) + alloc_bytes(b * n * 8);

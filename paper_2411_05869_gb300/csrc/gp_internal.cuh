@@ -178,6 +178,11 @@ struct SymPlan {
   std::vector<int32_t> sn_ldw;
   std::vector<int64_t> sn_loff32, sn_doff;
   int64_t panel32_entries = 0, diag_entries = 0;
+  // the low parts of the TF32 operand pairs (lo = x - the TF32 truncation of x; the high part is the FP32 panel
+  // itself, whose low 13 mantissa bits the TF32 MMAs ignore): large fronts only, at sn_lo_off in a per-level
+  // workspace of lo_entries (the largest level's total; a multiple of 4)
+  std::vector<int64_t> sn_lo_off;
+  int64_t lo_entries = 4;
   int group = GP_GROUP, tn_group = GP_TN_GROUP;   // mixed-path update blocking (plan_mixed_updates)
   std::vector<int32_t> upd_fronts;   // per step: fronts of the left-looking and of the group update
   std::vector<int64_t> upd_pre;      // their tile prefixes
@@ -249,6 +254,7 @@ struct DevPlan {
   int32_t* sn_parent;
   int32_t* ldw;
   int64_t *loff32, *doff;
+  int64_t* lo_off;
   int32_t* large_kb;
   int32_t* upd_fronts;
   int64_t* upd_pre;
@@ -309,9 +315,10 @@ struct gp_factor_s {
   int n1max = 0;
   double* panels = nullptr;     // FP64 panels, B x panel_entries
   float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
-  float* op_hi = nullptr;       // GP_MIXED: TF32 pair (hi, lo) of each panel entry below its diagonal tile,
-  float* op_lo = nullptr;       //   same layout as panels32: the tensor-core update operands
-  uint8_t* op_maps = nullptr;   // GP_MIXED: TMA maps of op_hi / op_lo, 2 x 128 bytes per updated front
+  float* op_lo = nullptr;       // GP_MIXED: low TF32 parts of the factored panel entries of one level's large
+                                //   fronts, B x lo_entries (the high parts are panels32 itself)
+  uint8_t* op_maps = nullptr;   // GP_MIXED: TMA maps of the high (panels32) and low (op_lo) operands, 2 x 128
+                                //   bytes per updated front
   int32_t* op_slot = nullptr;   // GP_MIXED: per supernode, its map pair (-1 = none)
   double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
   double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n

@@ -398,6 +398,8 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
 
   // ---- launch schedule
   sp.levels.assign(sp.nlevels, SymPlan::Level());
+  sp.sn_lo_off.assign(sp.ns, 0);
+  sp.lo_entries = 4;
   sp.level_large.assign(sp.nlevels, SymPlan::LevelLarge());
   sp.sn_fl.assign(sp.ns, -1);
   sp.n_fl = 0;
@@ -524,6 +526,16 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
+    // the low TF32 parts of this level's large fronts: one region per front in a workspace that every level
+    // reuses (the parts are read only by the updates of the front they belong to, inside its level)
+    {
+      int64_t lo = 0;
+      for (int32_t s : large) {
+        sp.sn_lo_off[s] = lo;
+        lo += ((int64_t)(sp.sn_w[s] + sp.sn_r[s]) * sp.sn_ldw[s] + 3) / 4 * 4;
+      }
+      sp.lo_entries = std::max(sp.lo_entries, lo);
+    }
     // dataflow solve tasks of this level's large fronts (SB blocks of 64 columns per chain task: 2 where the
     // level's chains are long, else 1; rows below the columns in tasks of 64 SB rows): forward tasks ordered by
     // their first block (the rows below a front's columns count as blocks nb, nb + 1, ...), backward tasks by
