@@ -118,11 +118,14 @@ typedef struct {
  *     launch of that factorization skips its tiles; a solve task goes on with what it has. The factor then
  *     reports GP_ERR_TIMEOUT: gp_factor_info (timed_out = 1) and gp_loglik return it, and the log-likelihoods are
  *     NaN. No legitimate wait comes near the defaults; tiny limits make waits run out on purpose (a test of this
- *     path). The next gp_factor_update of the factor starts clean. */
+ *     path). The next gp_factor_update of the factor starts clean.
+ *   GP_OPT_REFINE_EXP (default 12, 6..15): GP_MIXED refinement stops once every proposal's FP64 relative residual
+ *     |r - C alpha| / |r| is at most 10^-value (or after 10 corrections). */
 typedef enum {
   GP_OPT_DIAG_FP32 = 0,
   GP_OPT_WAIT_POLLS = 1,
-  GP_OPT_WAIT_NS = 2
+  GP_OPT_WAIT_NS = 2,
+  GP_OPT_REFINE_EXP = 3
 } gp_option;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
@@ -210,7 +213,11 @@ GP_API gp_status gp_assemble_sparse_support(gp_ctx* ctx, const double* d_X, int6
  * (fused with the scatter into supernodal panels) and the supernodal numeric Cholesky of P C_z P^T.
  * thetas: host array of B settings. Allocates the factor (B copies of the panels plus workspace).
  * A non-positive pivot does not fail the call: it marks that proposal (gp_factor_info, and gp_loglik then
- * returns -inf for it). Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA. Asynchronous after allocation. */
+ * returns -inf for it). GP_MIXED stores only the low half of each TF32 operand pair of the tensor-core updates
+ * and lets the MMA read the high half from the FP32 factor, which needs TF32 MMAs that truncate FP32 operands:
+ * the first GP_MIXED factor on a device checks that with one small MMA (and synchronises the stream once).
+ * Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA, GP_ERR_STATE (GP_MIXED on a GPU whose TF32 MMAs round instead of
+ * truncating). Asynchronous after allocation. */
 GP_API gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, gp_precision precision,
                     gp_factor_t** f);
 /* Re-run A3, A4, A7 on an existing factor with B new settings (same B, precision and point set): the
@@ -230,7 +237,7 @@ GP_API gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, in
 
 /* Steps A8-A11: forward/backward supernodal solves, quadratic form r^T C_z^{-1} r, log-determinant
  * 2 sum_j log L_jj in a fixed-order tree, and (GP_MIXED) FP64 iterative refinement of alpha = C_z^{-1} r with
- * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-12 or 10 sweeps.
+ * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-12 (GP_OPT_REFINE_EXP) or 10 sweeps.
  *   d_resid: B x n FP64 (r = z - mu per proposal, original point order); d_out: B FP64 log-likelihoods
  *   (-inf for proposals with a non-positive pivot, NaN after a timed-out factorization); d_err_est: B FP64 final
  *   relative residual (nullable).

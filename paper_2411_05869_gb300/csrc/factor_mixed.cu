@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "gp_internal.cuh"
 #include "tc_gemm.cuh"
@@ -1197,11 +1198,97 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
+// The operand split stores only the low half of each TF32 pair and lets the MMA read the high half from the FP32
+// panel, which is exact only if kind::tf32 truncates an FP32 operand (ignores its low 13 mantissa bits). One CTA
+// checks that once per device: a 128 x 32 x 8 MMA of A rows that each repeat one value (so the tile's 128-byte
+// swizzle does not matter) by B = 1 gives 8 x the value as the tensor core reads it. Row 0 holds 1 + 0.75 ulp
+// (rounding would give 1 + 1 ulp), row 1 its negative, row 2 1 + 1.5 ulp (a tie), the rest 1. The wait is
+// bounded; *out = 1 when every row matches the truncated value, 0 when one does not, -1 when the wait ran out.
+__global__ void __launch_bounds__(128) k_tf32_trunc_check(int32_t* __restrict__ out) {
+  extern __shared__ __align__(1024) uint8_t cs_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)cs_raw + 1023) & ~(uintptr_t)1023);
+  float* A = reinterpret_cast<float*>(sm);            // 128 rows x 32 FP32
+  float* Bt = reinterpret_cast<float*>(sm + 16384);   // 32 rows x 32 FP32
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  const float a = t == 0 ? __uint_as_float(0x3F801800u) : t == 1 ? __uint_as_float(0xBF801800u)
+                : t == 2 ? __uint_as_float(0x3F803000u) : 1.f;
+  for (int k = 0; k < 32; k++) A[t * 32 + k] = a;
+  if (t < 32)
+    for (int k = 0; k < 32; k++) Bt[t * 32 + k] = 1.f;
+  if (t == 0) {
+    tcg::mbar_init(&bar, 1);
+    bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (t < 32) tcg::tmem_alloc(&tslot, 32);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // the tiles are visible to the tensor core
+  tcg::tc_fence_before();
+  __syncthreads();
+  tcg::tc_fence_after();
+  const uint32_t tm = tslot;
+  if (t == 0) {
+    tcg::mma_tf32(tm, tcg::smem_desc_sw128(tcg::smem_u32(A)), tcg::smem_desc_sw128(tcg::smem_u32(Bt)),
+                  tcg::idesc_tf32(128, 32), 0);
+    tcg::mma_commit(&bar);
+  }
+  __syncwarp();
+  const bool ok = __syncthreads_and(tcg::mbar_wait(&bar, 0)) != 0;   // the same answer in every thread
+  if (ok) {
+    tcg::tc_fence_after();
+    float v[32];
+    tcg::tmem_ld32(tm + ((uint32_t)((t >> 5) * 32) << 16), v);
+    const float want = 8.f * __uint_as_float(__float_as_uint(a) & 0xFFFFE000u);
+    if (v[0] != want || v[31] != want) atomicExch(&bad, 1);
+  }
+  tcg::tc_fence_before();
+  __syncthreads();
+  if (t < 32) {
+    if (ok) tcg::tmem_dealloc(tm, 32);
+    else {   // the MMA may still be in flight: wait once more before freeing its accumulator
+      const bool ok2 = tcg::mbar_wait(&bar, 0);
+      tcg::tmem_dealloc(tm, 32);
+      (void)ok2;
+    }
+  }
+  if (t == 0) *out = !ok ? -1 : (bad ? 0 : 1);
+}
+
+// Runs k_tf32_trunc_check once per device (the first mixed factor on it; synchronises ctx's stream then) and
+// refuses the mixed path on a GPU whose TF32 MMAs do not truncate.
+void require_tf32_truncation(gp_ctx* ctx) {
+  static std::mutex mu;
+  static int state[64] = {};   // per device: 0 unknown, 1 truncates
+  std::lock_guard<std::mutex> lock(mu);
+  GP_REQUIRE(ctx->device >= 0 && ctx->device < 64, "device index out of range");
+  if (state[ctx->device] == 1) return;
+  constexpr int smem = 16384 + 4096 + 1024;
+  GP_CUDA(cudaFuncSetAttribute(k_tf32_trunc_check, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int32_t* d_out = nullptr;
+  GP_CUDA(cudaMallocAsync((void**)&d_out, sizeof(int32_t), ctx->stream));
+  int32_t h = 0;
+  cudaError_t e = cudaSuccess;
+  k_tf32_trunc_check<<<1, 128, smem, ctx->stream>>>(d_out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_out, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(d_out, ctx->stream);
+  GP_CUDA(e);
+  if (h == -1) throw GpError{GP_ERR_TIMEOUT, "the TF32 truncation check's MMA did not complete"};
+  if (h != 1)
+    throw GpError{GP_ERR_STATE, "this GPU's TF32 MMAs do not truncate FP32 operands, which the mixed path's "
+                                "operand split relies on"};
+  state[ctx->device] = 1;
+}
+
 // Tensor maps of the TF32 operand pair of every large front (those with tensor-core updates under any
 // blocking of plan_mixed_updates): per front two 3-D maps (columns x rows x proposals), the high part over the
 // FP32 panel and the low part over the front's region of op_lo, 128 x 32 boxes with the 128-byte swizzle; rows
 // past the front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
+  require_tf32_truncation(ctx);
   const SymPlan& sp = f->ps->sp;
   const int64_t ns = (int64_t)sp.sn_w.size();
   std::vector<int32_t> slot(ns, -1);

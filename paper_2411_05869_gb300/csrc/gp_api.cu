@@ -202,6 +202,10 @@ extern "C" gp_status gp_set_option(gp_ctx* ctx, int option, int64_t value) {
       if (value < 0) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_WAIT_NS takes a value >= 0"});
       ctx->opt_wait.ns = (uint64_t)value;
       return GP_OK;
+    case GP_OPT_REFINE_EXP:
+      if (value < 6 || value > 15) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_REFINE_EXP takes 6..15"});
+      ctx->opt_refine_exp = (int)value;
+      return GP_OK;
     default:
       return fail(ctx, GpError{GP_ERR_ARG, "unknown option " + std::to_string(option)});
   }
@@ -213,6 +217,7 @@ extern "C" gp_status gp_get_option(const gp_ctx* ctx, int option, int64_t* value
     case GP_OPT_DIAG_FP32: *value = ctx->opt_diag_fp32; return GP_OK;
     case GP_OPT_WAIT_POLLS: *value = (int64_t)ctx->opt_wait.polls; return GP_OK;
     case GP_OPT_WAIT_NS: *value = (int64_t)ctx->opt_wait.ns; return GP_OK;
+    case GP_OPT_REFINE_EXP: *value = ctx->opt_refine_exp; return GP_OK;
     default: return GP_ERR_ARG;
   }
 }
@@ -556,6 +561,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
     f->prec = prec;
     f->diag_fp32 = prec == GP_MIXED && ctx->opt_diag_fp32 != 0;
     f->wait_lim = ctx->opt_wait;
+    f->refine_tol = std::pow(10.0, -(double)ctx->opt_refine_exp);
     f->core_kind = cores ? cores[0].kind : GP_CORE_WENDLAND;
     ThetaDims td{thetas[0].d, thetas[0].n1, thetas[0].n2, thetas[0].bump_dims};
     GP_REQUIRE(td.d == ps->d, "theta.d differs from the point set dimension");

@@ -89,6 +89,7 @@ struct gp_ctx {
   // options (gp_set_option); they apply to factors created afterwards
   int opt_diag_fp32 = 0;     // GP_MIXED: diagonal blocks factored in FP32
   tcg::WaitLimit opt_wait = tcg::DEFAULT_WAIT;   // GP_MIXED: limits of the tensor-core kernels' bounded waits
+  int opt_refine_exp = 12;   // GP_MIXED: refinement stops at |r - C alpha| / |r| <= 10^-opt_refine_exp
 };
 
 // RAII timer of one launch (no-op unless profiling); `flops` is the useful work the launch performs.
@@ -307,6 +308,7 @@ struct gp_factor_s {
   gp_precision prec = GP_FP64;
   bool diag_fp32 = false;       // GP_MIXED: diagonal blocks factored in FP32 (default FP64)
   tcg::WaitLimit wait_lim = tcg::DEFAULT_WAIT;   // bounded-wait limits (tensor-core kernels, solve tasks)
+  double refine_tol = 1e-12;    // GP_MIXED: relative residual at which the refinement stops
   double* theta_dev = nullptr;  // B packed settings
   int64_t theta_stride = 0;
   double* F = nullptr;          // B x n x n1 bump features

@@ -14,7 +14,7 @@
 // panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the solves run in FP64 and the quadratic form is
 // |L^{-1} P r|^2. In GP_MIXED the solves run in FP32 (FP32 inverses, FP32 vectors): they only precondition
 // the FP64 refinement of alpha (residual r - C alpha from the FP64 CSR values, correction through the same
-// factor) until |r - C alpha| / |r| <= 1e-12 or 10 sweeps; the quadratic form is r^T alpha in FP64 and the
+// factor) until |r - C alpha| / |r| <= 1e-12 (the factor's tolerance) or 10 sweeps; the quadratic form is r^T alpha in FP64 and the
 // log-determinant is summed in FP64 from the FP64 diagonal tiles.
 // Sums use fixed-shape trees, so results are bitwise reproducible.
 #include <algorithm>
@@ -44,18 +44,39 @@ __global__ void k_rhs(const double* __restrict__ rhs, const int32_t* __restrict_
   work[(int64_t)b * ws + dp.frow_off[s] + (j - dp.sn_first[s])] = (V)rhs[(int64_t)b * n + perm[j]];
 }
 
-// Children's update vectors into the front vector of each supernode of the list.
+// Children's update vectors into the front vector of each supernode of the list: CTA (x, y, z) takes rows
+// [GATHER_ROWS y, GATHER_ROWS (y + 1)) of front list[x] for proposal z, and adds, child by child in child order,
+// the entries whose relative index falls there (rel is increasing, so they are one range per child). Every row
+// receives its children's entries in child order whatever the row split, so the sums do not depend on it.
+constexpr int GATHER_ROWS = 1024;
+__device__ __forceinline__ int32_t lower_bound_i32(const int32_t* __restrict__ a, int32_t n, int32_t key) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
 template <class V>
 __global__ void k_fwd_gather(const int32_t* __restrict__ list, DevPlan dp, V* __restrict__ work, int64_t ws) {
-  int32_t s = list[blockIdx.x];
-  V* W = work + (int64_t)blockIdx.y * ws;
+  const int32_t s = list[blockIdx.x];
+  const int64_t m = (int64_t)dp.w[s] + dp.r[s];
+  const int64_t lo = (int64_t)blockIdx.y * GATHER_ROWS;
+  if (lo >= m) return;
+  const int32_t rlo = (int32_t)lo, rhi = (int32_t)min(m, lo + GATHER_ROWS);
+  V* W = work + (int64_t)blockIdx.z * ws;
   V* fv = W + dp.frow_off[s];
+  __shared__ int32_t rng[2];
   for (int32_t q = dp.ch_ptr[s]; q < dp.ch_ptr[s + 1]; q++) {
-    int32_t c = dp.ch_idx[q];
+    const int32_t c = dp.ch_idx[q];
     const V* uc = W + dp.frow_off[c] + dp.w[c];
     const int32_t* rel = dp.relidx + dp.relidx_off[c];
-    for (int32_t a = threadIdx.x; a < dp.r[c]; a += blockDim.x) fv[rel[a]] += uc[a];
+    if (threadIdx.x < 2) rng[threadIdx.x] = lower_bound_i32(rel, dp.r[c], threadIdx.x == 0 ? rlo : rhi);
     __syncthreads();
+    const int32_t a0 = rng[0], a1 = rng[1];
+    for (int32_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) fv[rel[a]] += uc[a];
+    __syncthreads();   // this child's entries land before the next child's, and rng is free again
   }
 }
 
@@ -762,17 +783,17 @@ __global__ void __launch_bounds__(RELRES_THREADS) k_relres(const double* __restr
   }
 }
 
-// The refinement loop's test on the device: continue while some proposal's |r - C alpha| / |r| exceeds 1e-12 (or
+// The refinement loop's test on the device: continue while some proposal's |r - C alpha| / |r| exceeds tol (or
 // is not finite) and fewer than 10 corrections have run. it[0] counts the corrections; a factorization whose
 // bounded waits ran out (tc_err) stops the loop at once (its outputs become NaN).
-__global__ void k_refine_test(const double* __restrict__ err, int B, int32_t* __restrict__ it,
+__global__ void k_refine_test(const double* __restrict__ err, int B, double tol, int32_t* __restrict__ it,
                               unsigned long long* __restrict__ runs, const int32_t* __restrict__ tc_err, int reset,
                               cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0) return;
   if (reset) it[0] = 0;
   double worst = 0.0;
   for (int b = 0; b < B; b++) worst = fmax(worst, isfinite(err[b]) ? err[b] : 1.0);
-  const bool more = worst > 1e-12 && it[0] < 10 && !(tc_err && *tc_err);
+  const bool more = worst > tol && it[0] < 10 && !(tc_err && *tc_err);
   if (more) {
     it[0] += 1;
     runs[0] += 1;   // corrections run by the loop over the factor's life (launch accounting)
@@ -833,7 +854,13 @@ void solve_impl(gp_ctx* ctx, gp_factor_t* f, const St& store, const double* rhs,
     const SymPlan::Level& lv = sp.levels[L];
     int32_t nl = sp.lev_ptr[L + 1] - sp.lev_ptr[L];
     if (L > 0) {
-      k_fwd_gather<<<dim3(nl, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, work, ws);
+      int64_t mmax = 1;   // row chunks of the level's largest front
+      for (int32_t q = sp.lev_ptr[L]; q < sp.lev_ptr[L + 1]; q++) {
+        const int32_t s = sp.lev_sn[q];
+        mmax = std::max<int64_t>(mmax, (int64_t)sp.sn_w[s] + sp.sn_r[s]);
+      }
+      const unsigned nch = (unsigned)((mmax + GATHER_ROWS - 1) / GATHER_ROWS);
+      k_fwd_gather<<<dim3(nl, nch, B), 256, 0, st>>>(dp.lev_sn + sp.lev_ptr[L], dp, work, ws);
       GP_CHECK_LAUNCH(ctx);
     }
     if (lv.nsmall > 0) {
@@ -936,7 +963,7 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     // [residual, test]
     GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->refine_runs, f->tiles_err, 1, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, f->refine_tol, it, f->refine_runs, f->tiles_err, 1, h);
     GP_CHECK_LAUNCH(ctx);
     cudaGraph_t gg = nullptr;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
@@ -965,7 +992,7 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, st>>>(f->alpha, cor, (int64_t)B * n);
     GP_CHECK_LAUNCH(ctx);
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, it, f->refine_runs, f->tiles_err, 0, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, f->refine_tol, it, f->refine_runs, f->tiles_err, 0, h);
     GP_CHECK_LAUNCH(ctx);
     f->n_refine_body = ctx->launches - lb;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
@@ -1051,7 +1078,7 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
     if (terr != 0) break;   // the factorization timed out: the outputs become NaN below
     double worst = 0.0;
     for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
-    if (worst <= 1e-12) break;
+    if (worst <= f->refine_tol) break;
     run_maybe_graph(ctx, &f->gx_cor, &f->n_cor, [&] {
       solve_impl(ctx, f, store, res, cor, false);
       k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);

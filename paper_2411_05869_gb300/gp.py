@@ -53,8 +53,9 @@ class FactorInfo(ctypes.Structure):
                 ("diag_fp32", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
 
 
-GP_OPT_DIAG_FP32, GP_OPT_WAIT_POLLS, GP_OPT_WAIT_NS = 0, 1, 2
-OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32, "wait_polls": GP_OPT_WAIT_POLLS, "wait_ns": GP_OPT_WAIT_NS}
+GP_OPT_DIAG_FP32, GP_OPT_WAIT_POLLS, GP_OPT_WAIT_NS, GP_OPT_REFINE_EXP = 0, 1, 2, 3
+OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32, "wait_polls": GP_OPT_WAIT_POLLS, "wait_ns": GP_OPT_WAIT_NS,
+           "refine_exp": GP_OPT_REFINE_EXP}
 
 
 class GpRequest(ctypes.Structure):
