@@ -797,9 +797,12 @@ def main():
                                     f"{alg_ratio:.4f} (sum_j eta_j^2 = {flops:.4g} per proposal over the relaxed-front "
                                     f"flops of all A7 classes)",
                      "peak_source": peak_note,
-                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over the class's "
-                                        "launches of one factorization at this blocking (L2 cold at each launch under "
-                                        "ncu)") if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
+                     "traffic_source": (("ncu dram__bytes_read.sum + dram__bytes_write.sum of all the class's launches "
+                                         "in a factorization of station_120k at this blocking (L2 cold at each launch "
+                                         "under ncu), " + ("per launch" if args.workload == "station_120k" else
+                                         "as bytes per algorithmic flop times this workload's flops per launch "
+                                         "(an estimate: traffic taken in proportion to the work)")))
+                                       if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
                      "traffic_before_wind_down": _TRAFFIC_EARLIER.get((args.workload, dom) + _blocking_of(res)),
                      "a7_total": {"ms": t_a7, "proposals": res["B"],
                                   "achieved": res["B"] * flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
@@ -860,11 +863,15 @@ KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 2
 KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
                         "extend_add": "k_extend_add"}
 
-# DRAM bytes per launch of the dominant kernel, from an ncu capture of this kernel's launches, by (workload, class,
-# update blocking); None where no capture of the current kernel at that blocking exists. The one capture of the
-# group-end update at 1.2M (16, 256) read 2.712e9 bytes per launch before the kernel gained its wind-down code (no
-# operand data moves there); it is reported beside the line, not as the current kernel's traffic.
-_TRAFFIC = {}
+# DRAM bytes per launch of the dominant kernel by (workload, class, update blocking), from ncu captures of the
+# current kernel; None where there is none. station_120k: all 83 group-end launches of a factorization at (16, 256)
+# read and wrote 2.924e9 bytes for 3.03e11 algorithmic flops (0.0097 bytes per flop). station_1.2M is too large
+# for a multi-metric capture: its figure is that rate times the 1.711e11 algorithmic flops of an average launch
+# there (an estimate that assumes traffic in proportion to the work). The one direct capture at 1.2M, with both
+# TF32 halves of the operands stored beside the panel and before the kernel's wind-down code, read 2.712e9 bytes
+# per launch; it is reported beside the line.
+_TRAFFIC = {("station_120k", "update", 16, 256): 2.924e9 / 83,
+            ("station_1.2M", "update", 16, 256): 2.924e9 / 3.03e11 * 1.711e11}
 _TRAFFIC_EARLIER = {("station_1.2M", "update", 16, 256): 2.712e9}
 
 

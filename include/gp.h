@@ -119,8 +119,10 @@ typedef struct {
  *     reports GP_ERR_TIMEOUT: gp_factor_info (timed_out = 1) and gp_loglik return it, and the log-likelihoods are
  *     NaN. No legitimate wait comes near the defaults; tiny limits make waits run out on purpose (a test of this
  *     path). The next gp_factor_update of the factor starts clean.
- *   GP_OPT_REFINE_EXP (default 12, 6..15): GP_MIXED refinement stops once every proposal's FP64 relative residual
- *     |r - C alpha| / |r| is at most 10^-value (or after 10 corrections). */
+ *   GP_OPT_REFINE_EXP (default 10, 6..15): gp_loglik's GP_MIXED refinement stops once every proposal's FP64
+ *     relative residual |r - C alpha| / |r| is at most 10^-value (or after 10 corrections). Its quadratic form is
+ *     second order in that residual, so the log-likelihood does not need more; gp_predict refines alpha to 1e-12
+ *     first. */
 typedef enum {
   GP_OPT_DIAG_FP32 = 0,
   GP_OPT_WAIT_POLLS = 1,
@@ -237,7 +239,8 @@ GP_API gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info, in
 
 /* Steps A8-A11: forward/backward supernodal solves, quadratic form r^T C_z^{-1} r, log-determinant
  * 2 sum_j log L_jj in a fixed-order tree, and (GP_MIXED) FP64 iterative refinement of alpha = C_z^{-1} r with
- * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-12 (GP_OPT_REFINE_EXP) or 10 sweeps.
+ * residuals from the FP64 CSR matrix, until |r - C alpha| / |r| <= 1e-10 (GP_OPT_REFINE_EXP) or 10 sweeps, and the
+ * quadratic form r^T C_z^{-1} r as alpha^T (2 r - C_z alpha) in FP64 (exact to second order in the residual).
  *   d_resid: B x n FP64 (r = z - mu per proposal, original point order); d_out: B FP64 log-likelihoods
  *   (-inf for proposals with a non-positive pivot, NaN after a timed-out factorization); d_err_est: B FP64 final
  *   relative residual (nullable).
@@ -251,6 +254,8 @@ GP_API gp_status gp_loglik(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, d
 /* Step A12: m*_k = mu*_k + sum_j C_y(x*_k, x_j) alpha_j over the training neighbours of x*_k found in the
  * cell list (no noise term; Sec. 3.2), for proposal b of the factor, after gp_loglik.
  *   d_Xtest: m x d FP64; d_mu_test: m FP64 or NULL (zero mean); d_mean: m FP64 output.
+ * GP_MIXED: the first prediction after a gp_loglik refines alpha (all proposals) to a relative residual of 1e-12
+ * if gp_loglik stopped above it (the same corrections, on the device).
  * Asynchronous. Errors: GP_ERR_ARG, GP_ERR_STATE (no alpha yet), GP_ERR_CUDA. */
 GP_API gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xtest, int64_t m,
                      const double* d_mu_test, double* d_mean);

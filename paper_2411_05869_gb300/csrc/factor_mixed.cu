@@ -1343,20 +1343,43 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   GP_CHECK_LAUNCH(ctx);
   GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), st));
   ProfLevelScope pls_(ctx);
+  // Work off the level chain goes to the context's side stream (not while profiling, which times every launch on
+  // the main stream): zeroing level L + 1's update matrices once level L's extend-add has read the matrices they
+  // may reuse, and the FP64 L_11 of level L's diagonal tiles once its block steps are done (nothing later touches
+  // them). The main stream waits for a level's zeroing before its extend-add, and for everything at the end.
+  const bool overlap = ctx->side != nullptr && !ctx->prof;
+  const bool tiles64 = !f->diag_fp32 && !sp.large_fronts.empty();
+  auto zero_level = [&](int32_t L, cudaStream_t s) {
+    const SymPlan::Level& lz = sp.levels[L];
+    if (lz.zero_n == 0) return;
+    ProfScope ps_(ctx, KC_EXTEND_ADD);   // the update matrices this level's fronts will fill
+    k_zero_updates32<<<dim3((unsigned)lz.zero_n, B), EA_THREADS, 0, s>>>(dp.zero_tab + lz.zero_off, dp, f->upd32, UE);
+    GP_CHECK_LAUNCH(ctx);
+  };
+  auto fork = [&]() {
+    GP_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    GP_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  };
+  if (overlap && sp.nlevels > 0) {
+    fork();
+    zero_level(0, ctx->side);
+    GP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
+  }
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
     ctx->prof_level = L;
-    if (lv.zero_n > 0) {
-      ProfScope ps_(ctx, KC_EXTEND_ADD);   // the update matrices this level's fronts will fill
-      k_zero_updates32<<<dim3((unsigned)lv.zero_n, B), EA_THREADS, 0, st>>>(dp.zero_tab + lv.zero_off, dp, f->upd32,
-                                                                             UE);
-      GP_CHECK_LAUNCH(ctx);
-    }
+    if (overlap) GP_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));   // this level's zeroing
+    else zero_level(L, st);
     for (const auto& ea : lv.ea32) {
       ProfScope ps_(ctx, KC_EXTEND_ADD);
       k_extend_add32<<<dim3((unsigned)ea.ncta, B), EA_THREADS, 0, st>>>(dp.ea32_tab + ea.tab_off, dp, f->panels32,
                                                                         f->diag, f->upd32, P32E, DE, UE);
       GP_CHECK_LAUNCH(ctx);
+    }
+    if (overlap && L + 1 < sp.nlevels) {   // the next level's zeroing, beside this level's steps
+      fork();
+      zero_level(L + 1, ctx->side);
+      GP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     }
     if (lv.nsmall > 0) {
       int32_t mmax = 1;
@@ -1428,9 +1451,19 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                       stp.n_group, stp.kb, 2);
       }
     }
+    const auto& ll = sp.level_large[L];
+    if (overlap && tiles64 && ll.count > 0) {   // this level's diagonal tiles are final: their FP64 L_11 beside
+      fork();                                   // the next levels
+      k_potrf_tiles64<<<dim3((unsigned)ll.count, B), POTRF_THREADS, 0, ctx->side>>>(
+          dp.large_fronts + ll.off, dp.large_kb + ll.off, dp, f->diag, DE, f->notpd);
+      GP_CHECK_LAUNCH(ctx);
+    }
   }
   ctx->prof_level = -1;   // one launch over all levels
-  if (!f->diag_fp32 && !sp.large_fronts.empty()) {   // L_11 of every diagonal tile in FP64
+  if (overlap) {
+    GP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
+    GP_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  } else if (tiles64) {   // L_11 of every diagonal tile in FP64
     ProfScope ps_(ctx, KC_POTRF);
     k_potrf_tiles64<<<dim3((unsigned)sp.large_fronts.size(), B), POTRF_THREADS, 0, st>>>(
         dp.large_fronts, dp.large_kb, dp, f->diag, DE, f->notpd);

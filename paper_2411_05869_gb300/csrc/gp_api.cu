@@ -161,6 +161,11 @@ extern "C" gp_status gp_create(gp_ctx** out, int device, void* cuda_stream, size
     GP_CUDA(cudaSetDevice(device));
     GP_CUDA(cudaFree(nullptr));
     GP_CUDA(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device));
+    if (ctx->stream) {
+      GP_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
   });
   if (st != GP_OK) {
     delete ctx;
@@ -607,7 +612,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
   });
   if (st != GP_OK) {
     dev_free_all(ctx, f->bufs);
-    for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine})
+    for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine, f->gx_tail})
       if (g) cudaGraphExecDestroy(g);
     delete f;
     return st;
@@ -760,7 +765,7 @@ extern "C" void gp_factor_free(gp_factor_t* f) {
     cudaSetDevice(ctx->device);
     dev_free_all(ctx, f->bufs);
   }
-  for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine})
+  for (cudaGraphExec_t g : {f->gx_factor, f->gx_solve, f->gx_cor, f->gx_refine, f->gx_tail})
     if (g) cudaGraphExecDestroy(g);
   delete f;
   if (ctx) ctx_release(ctx);
@@ -846,6 +851,9 @@ extern "C" gp_status gp_predict(gp_ctx* ctx, gp_factor_t* f, int b, const double
     GP_REQUIRE(b >= 0 && b < f->B, "proposal index out of range");
     GP_REQUIRE(m >= 0 && (m == 0 || (d_Xtest && d_mean)), "d_Xtest and d_mean are required");
     if (!f->have_alpha) throw GpError{GP_ERR_STATE, "gp_predict needs gp_loglik first (alpha = C_z^-1 r)"};
-    if (m > 0) predict_run(ctx, f, b, d_Xtest, m, d_mu_test, d_mean);
+    if (m > 0) {
+      refine_alpha_for_predict(ctx, f);   // GP_MIXED: alpha to 1e-12 (gp_loglik may have stopped earlier)
+      predict_run(ctx, f, b, d_Xtest, m, d_mu_test, d_mean);
+    }
   });
 }

@@ -67,6 +67,10 @@ struct gp_ctx {
   int device = 0;
   int nsm = 1;           // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
+  // a second stream for work the factorization overlaps with its level chain (explicit streams only), and the
+  // two events that fork it from and join it back to `stream` (re-recorded at each use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t budget = 0;     // 0 = unlimited
   std::atomic<size_t> held{0};   // bytes currently held by this context's handles
   int64_t launches = 0;
@@ -89,7 +93,12 @@ struct gp_ctx {
   // options (gp_set_option); they apply to factors created afterwards
   int opt_diag_fp32 = 0;     // GP_MIXED: diagonal blocks factored in FP32
   tcg::WaitLimit opt_wait = tcg::DEFAULT_WAIT;   // GP_MIXED: limits of the tensor-core kernels' bounded waits
-  int opt_refine_exp = 12;   // GP_MIXED: refinement stops at |r - C alpha| / |r| <= 10^-opt_refine_exp
+  int opt_refine_exp = 10;   // GP_MIXED: gp_loglik's refinement stops at |r - C alpha| / |r| <= 10^-opt_refine_exp
+  ~gp_ctx() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+  }
 };
 
 // RAII timer of one launch (no-op unless profiling); `flops` is the useful work the launch performs.
@@ -308,7 +317,7 @@ struct gp_factor_s {
   gp_precision prec = GP_FP64;
   bool diag_fp32 = false;       // GP_MIXED: diagonal blocks factored in FP32 (default FP64)
   tcg::WaitLimit wait_lim = tcg::DEFAULT_WAIT;   // bounded-wait limits (tensor-core kernels, solve tasks)
-  double refine_tol = 1e-12;    // GP_MIXED: relative residual at which the refinement stops
+  double refine_tol = 1e-10;    // GP_MIXED: relative residual at which gp_loglik's refinement stops
   double* theta_dev = nullptr;  // B packed settings
   int64_t theta_stride = 0;
   double* F = nullptr;          // B x n x n1 bump features
@@ -331,6 +340,9 @@ struct gp_factor_s {
   cudaGraphExec_t gx_factor = nullptr, gx_solve = nullptr, gx_cor = nullptr;
   int64_t n_factor = 0, n_solve = 0, n_cor = 0;
   cudaGraphExec_t gx_refine = nullptr;   // GP_MIXED: the refinement loop with its test on the device
+  cudaGraphExec_t gx_tail = nullptr;     // GP_MIXED: the loop alone, to the residual prediction needs
+  int64_t n_tail = 0;
+  double alpha_tol = 1.0;                // GP_MIXED: the residual tolerance alpha was last refined to
   int64_t n_refine = 0;
   const double* refine_out = nullptr;    // the output pointers gx_refine was built for
   const double* refine_err = nullptr;
@@ -394,6 +406,7 @@ void assemble_pointset(gp_ctx* ctx, gp_pointset* ps, const double* d_X);
 // values.cu / factor.cu / solve.cu / predict.cu
 void factor_run(gp_ctx* ctx, gp_factor_t* f);
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err);
+void refine_alpha_for_predict(gp_ctx* ctx, gp_factor_t* f);
 void predict_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, const double* d_mu, double* d_mean);
 void variance_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_Xt, int64_t m, double* d_var);
 void iterative_run(gp_ctx* ctx, gp_factor_t* f, int b, const double* d_resid, const double* d_probes,

@@ -14,7 +14,8 @@
 // panels with FP64 diagonal tiles (GP_MIXED). In GP_FP64 the solves run in FP64 and the quadratic form is
 // |L^{-1} P r|^2. In GP_MIXED the solves run in FP32 (FP32 inverses, FP32 vectors): they only precondition
 // the FP64 refinement of alpha (residual r - C alpha from the FP64 CSR values, correction through the same
-// factor) until |r - C alpha| / |r| <= 1e-12 (the factor's tolerance) or 10 sweeps; the quadratic form is r^T alpha in FP64 and the
+// factor) until |r - C alpha| / |r| <= 1e-10 (the factor's tolerance; 1e-12 before a prediction) or 10 sweeps;
+// the quadratic form is alpha^T (2 r - C alpha) in FP64, exact to second order in the residual, and the
 // log-determinant is summed in FP64 from the FP64 diagonal tiles.
 // Sums use fixed-shape trees, so results are bitwise reproducible.
 #include <algorithm>
@@ -729,7 +730,7 @@ __global__ void k_residual(const int64_t* __restrict__ rowptr, const int32_t* __
   if (i < n && lane == 0) {
     ri = resid[(int64_t)b * n + i];
     rr = ri - acc;
-    ra = ri * a[i];
+    ra = a[i] * (ri + rr);   // alpha_i (2 r_i - (C alpha)_i): the second-order form of r^T C^-1 r
     if (res) res[(int64_t)b * n + i] = rr;
   }
   if (lane == 0) {
@@ -949,7 +950,7 @@ static void run_maybe_graph(gp_ctx* ctx, cudaGraphExec_t* gx, int64_t* nl, F&& b
 template <class St>
 static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St& store, double* res, double* cor,
                                           double* errv, double* s_log, double* s_quad, double* d_out, double* d_err,
-                                          int64_t* nl) {
+                                          int64_t* nl, double tol, bool finish) {
   const int B = f->B;
   const int64_t n = f->ps->n;
   cudaStream_t st = ctx->stream;
@@ -963,7 +964,7 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     // [residual, test]
     GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, f->refine_tol, it, f->refine_runs, f->tiles_err, 1, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, tol, it, f->refine_runs, f->tiles_err, 1, h);
     GP_CHECK_LAUNCH(ctx);
     cudaGraph_t gg = nullptr;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
@@ -992,16 +993,17 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
     k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, st>>>(f->alpha, cor, (int64_t)B * n);
     GP_CHECK_LAUNCH(ctx);
     residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    k_refine_test<<<1, 32, 0, st>>>(errv, B, f->refine_tol, it, f->refine_runs, f->tiles_err, 0, h);
+    k_refine_test<<<1, 32, 0, st>>>(errv, B, tol, it, f->refine_runs, f->tiles_err, 0, h);
     GP_CHECK_LAUNCH(ctx);
     f->n_refine_body = ctx->launches - lb;
     GP_CUDA(cudaStreamEndCapture(st, &gg));
-    // after the loop: r . alpha and the log-likelihood
-    GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-    residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
-    k_finish<<<grid_for(B, 128), 128, 0, st>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
-    GP_CHECK_LAUNCH(ctx);
-    GP_CUDA(cudaStreamEndCapture(st, &gg));
+    if (finish) {   // after the loop: the quadratic form and the log-likelihood
+      GP_CUDA(cudaStreamBeginCaptureToGraph(st, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+      residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
+      k_finish<<<grid_for(B, 128), 128, 0, st>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
+      GP_CHECK_LAUNCH(ctx);
+      GP_CUDA(cudaStreamEndCapture(st, &gg));
+    }
   } catch (...) {
     cudaStreamCaptureStatus cs;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
@@ -1019,9 +1021,37 @@ static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St&
   if (e != cudaSuccess) throw GpError{GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
   *nl = ctx->launches - l0 - f->n_refine_body;   // a replay counts the loop body only as it runs (below)
   ctx->launches = l0;
-  f->refine_out = d_out;
-  f->refine_err = d_err;
+  if (finish) {
+    f->refine_out = d_out;
+    f->refine_err = d_err;
+  }
   return ex;
+}
+
+// Host-driven refinement of alpha (the legacy default stream, where graphs are not used) until every proposal's
+// relative residual is at most tol or 10 corrections have run; *terr receives the factorization's timeout flag.
+template <class St>
+static void refine_host_loop(gp_ctx* ctx, gp_factor_t* f, const St& store, double* res, double* cor, double* errv,
+                             double tol, int32_t* terr) {
+  const int B = f->B;
+  const int64_t n = f->ps->n;
+  std::vector<double> herr(B);
+  *terr = 0;
+  for (int it = 0; it < 10; it++) {
+    residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
+    d2h(ctx, herr.data(), errv, B);
+    if (it == 0) d2h(ctx, terr, f->tiles_err, 1);
+    GP_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (*terr != 0) break;   // the factorization timed out: the outputs become NaN
+    double worst = 0.0;
+    for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
+    if (worst <= tol) break;
+    run_maybe_graph(ctx, &f->gx_cor, &f->n_cor, [&] {
+      solve_impl(ctx, f, store, res, cor, false);
+      k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);
+      GP_CHECK_LAUNCH(ctx);
+    });
+  }
 }
 
 void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_out, double* d_err) {
@@ -1064,31 +1094,42 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
       f->gx_refine = nullptr;
     }
     if (!f->gx_refine) f->gx_refine = build_refine_graph(ctx, f, store, res, cor, errv, s_log, s_quad, d_out, d_err,
-                                                         &f->n_refine);
+                                                         &f->n_refine, f->refine_tol, true);
     replay_graph(ctx, f->gx_refine, f->n_refine);
+    f->alpha_tol = f->refine_tol;
     return;
   }
-  std::vector<double> herr(B);
   int32_t terr = 0;
-  for (int it = 0; it < 10; it++) {
-    residual_impl(ctx, f, f->rhs, f->alpha, res, errv, nullptr);
-    d2h(ctx, herr.data(), errv, B);
-    if (it == 0) d2h(ctx, &terr, f->tiles_err, 1);
-    GP_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (terr != 0) break;   // the factorization timed out: the outputs become NaN below
-    double worst = 0.0;
-    for (int b = 0; b < B; b++) worst = std::max(worst, std::isfinite(herr[b]) ? herr[b] : 1.0);
-    if (worst <= f->refine_tol) break;
-    run_maybe_graph(ctx, &f->gx_cor, &f->n_cor, [&] {
-      solve_impl(ctx, f, store, res, cor, false);
-      k_axpy<<<grid_for((int64_t)B * n, 256), 256, 0, ctx->stream>>>(f->alpha, cor, (int64_t)B * n);
-      GP_CHECK_LAUNCH(ctx);
-    });
-  }
+  refine_host_loop(ctx, f, store, res, cor, errv, f->refine_tol, &terr);
+  f->alpha_tol = f->refine_tol;
   residual_impl(ctx, f, f->rhs, f->alpha, nullptr, d_err ? d_err : errv, s_quad);
   k_finish<<<grid_for(B, 128), 128, 0, ctx->stream>>>(B, n, s_log, s_quad, f->notpd, f->tiles_err, d_out);
   GP_CHECK_LAUNCH(ctx);
   if (terr != 0) throw GpError{GP_ERR_TIMEOUT, "a bounded wait of the factorization's tensor-core updates ran out"};
+}
+
+// alpha of a GP_MIXED factor refined to a relative residual of at most ALPHA_TOL before a prediction uses it:
+// gp_loglik may stop its refinement earlier (GP_OPT_REFINE_EXP), since its second-order quadratic form does not
+// need more. Runs the remaining corrections, if any (a residual and its test when there are none).
+constexpr double ALPHA_TOL = 1e-12;
+void refine_alpha_for_predict(gp_ctx* ctx, gp_factor_t* f) {
+  if (f->prec != GP_MIXED || f->alpha_tol <= ALPHA_TOL) return;
+  gp_pointset* ps = f->ps;
+  const int64_t n = ps->n;
+  StoreMix store{f->panels32, f->diag, ps->sp.panel32_entries, ps->sp.diag_entries, f->dinv32};
+  double* res = f->delta;
+  double* cor = f->delta + (size_t)f->B * n;
+  double* errv = f->red;
+  if (use_graphs(ctx)) {
+    if (!f->gx_tail)
+      f->gx_tail = build_refine_graph(ctx, f, store, res, cor, errv, nullptr, nullptr, nullptr, nullptr, &f->n_tail,
+                                      ALPHA_TOL, false);
+    replay_graph(ctx, f->gx_tail, f->n_tail);
+  } else {
+    int32_t terr = 0;
+    refine_host_loop(ctx, f, store, res, cor, errv, ALPHA_TOL, &terr);
+  }
+  f->alpha_tol = ALPHA_TOL;
 }
 
 // Entries (per proposal) of the backward partial-sum scratch: the largest level's tasks x row chunks x 64.

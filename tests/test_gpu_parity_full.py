@@ -106,7 +106,7 @@ def test_mixed_full_size(case, ctx, diag_fp32):
     ll = f.loglik(_dev(np.stack([case["r"], case["r"]])), err=err).cpu().numpy()
     for b in range(2):
         assert abs(ll[b] - g["loglik"][b]) <= 1e-6 * abs(g["loglik"][b]), (b, ll[b], g["loglik"][b])
-    assert float(err.max().cpu()) <= 1e-12
+    assert float(err.max().cpu()) <= 1e-10   # gp_loglik's default stopping residual; predict refines to 1e-12
     ref = np.array(g["predict_mean"])
     m = f.predict(_dev(case["Xt"]), b=0).cpu().numpy()
     assert np.abs(m - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
