@@ -586,6 +586,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->diag = dalloc<double>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->upd32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.update_entries);
       f->delta = dalloc<double>(ctx, f->bufs, (size_t)B * ps->n * 2);
+      f->ll_buf = dalloc<double>(ctx, f->bufs, (size_t)2 * B);
       f->refine_it = dalloc<int32_t>(ctx, f->bufs, 1);
       f->refine_runs = dalloc<unsigned long long>(ctx, f->bufs, 1);
       GP_CUDA(cudaMemsetAsync(f->refine_runs, 0, sizeof(unsigned long long), ctx->stream));
@@ -648,7 +649,7 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
          alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
          alloc_bytes(8) +
          alloc_bytes(b * sp.diag_entries * 4) + alloc_bytes(b * sp.lo_entries * 4) +
-         alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4);
+         alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4) + alloc_bytes(b * 2 * 8);
   }
   t += alloc_bytes(b * ps->nnz * 8) + alloc_bytes(b * 4) + alloc_bytes(b * n * 8);
   if (prec == GP_FP64) t += alloc_bytes(b * sp.diag_entries * 8);

@@ -344,8 +344,9 @@ struct gp_factor_s {
   int64_t n_tail = 0;
   double alpha_tol = 1.0;                // GP_MIXED: the residual tolerance alpha was last refined to
   int64_t n_refine = 0;
-  const double* refine_out = nullptr;    // the output pointers gx_refine was built for
+  const double* refine_out = nullptr;    // the output pointers gx_refine writes (ll_buf)
   const double* refine_err = nullptr;
+  double* ll_buf = nullptr;              // GP_MIXED: 2B, the refinement graph's log-likelihoods and residuals
   int32_t* refine_it = nullptr;          // GP_MIXED: its correction counter
   unsigned long long* refine_runs = nullptr;   // corrections the loop has run (device, for launch accounting)
   int64_t n_refine_body = 0;             // launches of one pass of the loop body

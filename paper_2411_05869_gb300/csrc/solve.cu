@@ -944,9 +944,10 @@ static void run_maybe_graph(gp_ctx* ctx, cudaGraphExec_t* gx, int64_t* nl, F&& b
 
 // The mixed path's refinement (A11) as one executable graph, so that gp_loglik neither waits for the device nor
 // reads back a residual: [residual, test] then a conditional WHILE node whose body is [correction solve, alpha +=
-// correction, residual, test], then [final residual with r . alpha, log-likelihood]. The test kernel sets the loop's
-// condition (cudaGraphSetConditional). The output pointers are baked into the graph, so it is rebuilt when they
-// change. *nl receives the launches of one pass (the body counted once).
+// correction, residual, test], then, if finish, [final residual with the quadratic form, log-likelihood] into
+// d_out / d_err (gp_loglik passes the factor's own result buffer, so one graph serves every caller). The test kernel
+// sets the loop's condition (cudaGraphSetConditional); the loop stops at relative residual tol. *nl receives the
+// launches of one pass (the body counted once).
 template <class St>
 static cudaGraphExec_t build_refine_graph(gp_ctx* ctx, gp_factor_t* f, const St& store, double* res, double* cor,
                                           double* errv, double* s_log, double* s_quad, double* d_out, double* d_err,
@@ -1089,13 +1090,15 @@ void loglik_run(gp_ctx* ctx, gp_factor_t* f, const double* d_resid, double* d_ou
   double* cor = f->delta + (size_t)B * n;       // B x n correction
   double* errv = f->red;                        // B relative residuals (partials are consumed already)
   if (use_graphs(ctx)) {   // the whole refinement as one graph: the loop's test runs on the device
-    if (f->gx_refine && (f->refine_out != d_out || f->refine_err != d_err)) {
-      GP_CUDA(cudaGraphExecDestroy(f->gx_refine));
-      f->gx_refine = nullptr;
-    }
-    if (!f->gx_refine) f->gx_refine = build_refine_graph(ctx, f, store, res, cor, errv, s_log, s_quad, d_out, d_err,
+    // the graph writes the factor's own result buffer (so one graph serves every caller's output pointers), and
+    // plain copies move the results out
+    double* g_out = f->ll_buf;
+    double* g_err = f->ll_buf + B;
+    if (!f->gx_refine) f->gx_refine = build_refine_graph(ctx, f, store, res, cor, errv, s_log, s_quad, g_out, g_err,
                                                          &f->n_refine, f->refine_tol, true);
     replay_graph(ctx, f->gx_refine, f->n_refine);
+    GP_CUDA(cudaMemcpyAsync(d_out, g_out, sizeof(double) * B, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_err) GP_CUDA(cudaMemcpyAsync(d_err, g_err, sizeof(double) * B, cudaMemcpyDeviceToDevice, ctx->stream));
     f->alpha_tol = f->refine_tol;
     return;
   }
