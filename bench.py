@@ -240,6 +240,40 @@ def subwindow_parity(ctx, leg, theta, prec_list):
 
 # ------------------------------------------------------------------------------------------------ GPU leg
 
+def other_split_leg(ctx, ps, stream, resid, thetas, args, steps=3, warmup=2):
+    """One setting per step through a factor with the other operand split (GP_OPT_SPLIT_F16 flipped)."""
+    import torch
+    from paper_2411_05869_gb300 import gp
+    split = 1 - int(args.split_f16)
+    ctx.set_option("split_f16", split)
+    try:
+        f2 = ctx.factor(ps, thetas[:1], gp.GP_MIXED)
+    finally:
+        ctx.set_option("split_f16", int(args.split_f16))
+    out = torch.empty(1, dtype=torch.float64, device=resid.device)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        for k in range(warmup):
+            f2.update([thetas[(1 + k) % len(thetas)]])
+            f2.loglik(resid, out=out)
+        evs[0].record(stream)
+        for k in range(steps):
+            f2.update([thetas[(1 + warmup + k) % len(thetas)]])
+            f2.loglik(resid, out=out)
+            evs[k + 1].record(stream)
+        f2.update(thetas[:1])
+        f2.loglik(resid, out=out)
+    stream.synchronize()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    ll = float(out.cpu()[0])
+    f2.free()
+    return {"operand_split": "fp16 pairs" if split else "tf32 pairs", "evals_per_s": 1e3 / float(np.mean(per)),
+            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                           "steps": steps},
+            "loglik": ll, "note": "the same point set, blocking and settings with the other operand split of the "
+                                  "tensor-core updates; loglik is that of the FP64 comparison's setting"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2411_05869_gb300 import gp
@@ -252,6 +286,7 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     ctx = gp.Context(local_rank, stream=stream)
     ctx.set_option("diag_fp32", int(args.diag_fp32))
+    ctx.set_option("split_f16", int(args.split_f16))
     with torch.cuda.stream(stream):
         X = torch.as_tensor(w.X, dtype=torch.float64, device=dev)
         resid = torch.as_tensor(w.resid, dtype=torch.float64, device=dev)
@@ -434,6 +469,11 @@ def run_gpu(args, rank, world, local_rank):
                autotune=tune, clk=clk, info=info, t_assemble=t_assemble,
                e2e_s=e2e_s, e2e_steps=e2e_steps, n=int(w.X.shape[0]), prof=prof, ll=ll_last,
                h2d=int(w.resid.nbytes) * Bc * nchunk, d2h=8 * Bc * nchunk, w=w)
+    # the other operand split of the tensor-core updates (TF32 pairs beside FP16 pairs, or the reverse) on the same
+    # point set and blocking: steady-state steps timed like the main ones, and the log-likelihood of the setting the
+    # FP64 comparison takes
+    if prec == gp.GP_MIXED and B == 1 and args.other_split:
+        res["other_split"] = other_split_leg(ctx, ps, stream, resid, thetas, args)
     # FP64 comparison (mixed runs only): the same settings through the FP64 path. The factor is created (allocated
     # and factored once) outside the timing; then --fp64-steps steady-state steps of update + loglik are timed
     # with CUDA events, like the mixed steps, for p50/p99.
@@ -461,6 +501,9 @@ def run_gpu(args, rank, world, local_rank):
         stream.synchronize()
         per64 = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.fp64_steps)]
         rel = np.abs(ll_mixed - ll64) / np.abs(ll64)
+        if "other_split" in res:
+            o = res["other_split"]
+            o["mixed_rel_diff_vs_fp64"] = abs(o["loglik"] - float(ll64[0])) / abs(float(ll64[0]))
         res["fp64"] = {"ms_per_step": float(np.mean(per64)) / nb, "evals_per_s": nb * 1e3 / float(np.mean(per64)),
                        "latency_ms": {"p50": float(np.percentile(per64, 50)), "p99": float(np.percentile(per64, 99)),
                                       "steps": len(per64)},
@@ -666,6 +709,11 @@ def main():
     ap.add_argument("--blocking", default="", help="G,TN: fixed update blocking of mixed runs (no autotuner)")
     ap.add_argument("--diag-fp32", action="store_true",
                     help="mixed runs: factor the 64 x 64 diagonal blocks in FP32 (default FP64)")
+    ap.add_argument("--split-f16", type=int, default=int(os.environ.get("GP_BENCH_SPLIT_F16", "1")), choices=[0, 1],
+                    help="mixed runs: 1 = FP16 operand pairs for the tensor-core updates (GP_OPT_SPLIT_F16), "
+                         "0 = TF32 pairs")
+    ap.add_argument("--other-split", type=int, default=1, help="mixed runs at B = 1: also time the other operand "
+                                                                 "split (1) or not (0)")
     ap.add_argument("--oracle-points", type=int, default=30_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--var-points", type=int, default=4096, help="test points of the predictive-variance timing")
@@ -761,7 +809,11 @@ def main():
     a7 = ["extend_add", "front_small", "potrf", "trsm", "update", "update_left"]
     t_a7 = sum(prof[k][0] for k in a7)
     flops = info["flops"]
-    if args.precision == "mixed":   # the kernel runs inside a seconds-long step: the sustained figure applies
+    f16 = args.precision == "mixed" and args.split_f16 == 1
+    if f16:   # FP16 MMAs: the dense FP16 rate is the BF16 rate
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        bound, peak_note = "tensor", f"FP16 = {peak_src} bf16 sustained (the same nominal dense rate; of {peak_src})"
+    elif args.precision == "mixed":   # the kernel runs inside a seconds-long step: the sustained figure applies
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_TF32_OVER_BF16
         bound, peak_note = "tensor", f"TF32 = {peak_src} bf16 sustained x nominal 1.1/2.25 (of {peak_src})"
     else:
@@ -775,16 +827,21 @@ def main():
     alg_ratio = (res["Bc"] * res["nchunk"] * flops / front_total) if front_total > 0 else 1.0
     d_fl = d_fl_front * alg_ratio
     achieved = d_fl / (d_ms * 1e-3) / 1e12 if d_ms > 0 else 0.0
+    tkey = (args.workload, dom) + _blocking_of(res) + (("f16",) if f16 else ())
     kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "useful_tflops": (round(v[2] / (v[0] * 1e-3) / 1e12, 3)
                                                                             if v[0] > 0 and v[2] > 0 else None)}
                for k, v in prof.items()}
     line = {
         "metric": metric, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(tot_s * 1e3 / args.steps), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "tf32+f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else ("f16+f64" if f16 else "tf32+f64"),
         "data": "synthetic (seeded; shapes of the paper's space-time temperature workload)",
         "config": workload_config(res["w"], args.workload, args.precision,
                                   {"parallelism": f"replicas{world}", "B": res["B"],
+                                   "operand_split": ("fp16 pairs x 2^k (3 kind::f16 MMAs per step)" if f16 else
+                                                     "tf32 pairs (3 kind::tf32 MMAs per step)")
+                                   if args.precision == "mixed" else None,
                                    "evaluations_per_step": res["Bc"] * res["nchunk"],
                                    "proposals_per_factorization": res["Bc"], "factorizations_per_step": res["nchunk"],
                                    "nnz": info["nnz"], "nnzL": info["nnzL"],
@@ -793,7 +850,7 @@ def main():
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "roofline": {"kernel": (KERNEL_OF_CLASS_MIXED if args.precision == "mixed" else KERNEL_OF_CLASS_FP64).get(dom, dom),
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get((args.workload, dom) + _blocking_of(res)),
+                     "frac": achieved / peak if peak else None, "traffic": _TRAFFIC.get(tkey),
                      "launches_per_step": d_n, "avg_launch_ms": d_ms / max(d_n, 1),
                      "algorithmic": f"algorithmic flops of the class per step = {d_fl:.4g} (per launch "
                                     f"{d_fl / max(d_n, 1):.4g}): its relaxed-front flops {d_fl_front:.4g} x "
@@ -805,8 +862,8 @@ def main():
                                          "under ncu), " + ("per launch" if args.workload == "station_120k" else
                                          "as bytes per algorithmic flop times this workload's flops per launch "
                                          "(an estimate: traffic taken in proportion to the work)")))
-                                       if _TRAFFIC.get((args.workload, dom) + _blocking_of(res)) else None,
-                     "traffic_before_wind_down": _TRAFFIC_EARLIER.get((args.workload, dom) + _blocking_of(res)),
+                                       if _TRAFFIC.get(tkey) else None,
+                     "traffic_before_wind_down": _TRAFFIC_EARLIER.get(tkey),
                      "a7_total": {"ms": t_a7, "proposals": res["Bc"] * res["nchunk"],
                                   "achieved": res["Bc"] * res["nchunk"] * flops / (t_a7 * 1e-3) / 1e12 if t_a7 > 0 else None}},
         "kernels": kernels,
@@ -818,6 +875,8 @@ def main():
     }
     if "fp64" in res:
         line["fp64"] = res["fp64"]
+    if "other_split" in res:
+        line["other_split"] = res["other_split"]
     if "batched" in res:
         line["batched"] = res["batched"]
     if res.get("predict"):

@@ -53,9 +53,10 @@ typedef enum {
 
 typedef enum {
   GP_FP64 = 0,         /* every step in FP64 */
-  GP_MIXED = 1         /* off-diagonal supernode updates on TF32 tensor cores with FP32 accumulation and FP32
-                          off-diagonal storage; diagonal-block factorization, log-det and refinement residuals in
-                          FP64 (the diagonal blocks optionally factored in FP32: GP_OPT_DIAG_FP32) */
+  GP_MIXED = 1         /* off-diagonal supernode updates on tensor cores with FP32 accumulation, each FP32 operand
+                          split into an FP16 pair (or a TF32 pair: GP_OPT_SPLIT_F16), and FP32 off-diagonal
+                          storage; diagonal-block factorization, log-det and refinement residuals in FP64 (the
+                          diagonal blocks optionally factored in FP32: GP_OPT_DIAG_FP32) */
 } gp_precision;
 
 typedef struct gp_ctx gp_ctx;
@@ -102,6 +103,8 @@ typedef struct {
   int32_t diag_fp32;          /* GP_MIXED: 1 if its 64 x 64 diagonal blocks are factored in FP32 (GP_OPT_DIAG_FP32) */
   int32_t timed_out;          /* 1 if a bounded wait of the last factorization or of a later solve ran out
                                  (GP_ERR_TIMEOUT) */
+  int32_t split_f16;          /* GP_MIXED: 1 if its tensor-core updates take FP16 operand pairs (GP_OPT_SPLIT_F16),
+                                 0 for TF32 pairs */
 } gp_factor_info_t;
 
 /* Context options (gp_set_option). They apply to the factors created on the context afterwards.
@@ -122,12 +125,21 @@ typedef struct {
  *   GP_OPT_REFINE_EXP (default 10, 6..15): gp_loglik's GP_MIXED refinement stops once every proposal's FP64
  *     relative residual |r - C alpha| / |r| is at most 10^-value (or after 10 corrections). Its quadratic form is
  *     second order in that residual, so the log-likelihood does not need more; gp_predict refines alpha to 1e-12
- *     first. */
+ *     first.
+ *   GP_OPT_SPLIT_F16: 1 (default) or 0: how GP_MIXED factors split each FP32 entry of L into the two parts their
+ *     tensor-core updates multiply (three products per step: hi hi, hi lo, lo hi, accumulated in FP32, emulating
+ *     FP32 products). 1: FP16 parts of the entry times 2^k, kind::f16 MMAs at twice the TF32 rate on half the
+ *     operand bytes (hi = the scaled entry rounded to FP16, lo = the remainder rounded to FP16: about 22
+ *     significant bits; k per setting from max_i C_ii, so that every scaled entry is below 2^13 -- |L_ij| <=
+ *     sqrt(C_ii) -- and entries above 2^-25 of the largest keep their relative precision); the products are
+ *     scaled back by 2^-2k, exactly. 0: TF32 parts, kind::tf32 MMAs (hi = the entry truncated to TF32, lo = the
+ *     remainder rounded to TF32: about 21 significant bits). */
 typedef enum {
   GP_OPT_DIAG_FP32 = 0,
   GP_OPT_WAIT_POLLS = 1,
   GP_OPT_WAIT_NS = 2,
-  GP_OPT_REFINE_EXP = 3
+  GP_OPT_REFINE_EXP = 3,
+  GP_OPT_SPLIT_F16 = 4
 } gp_option;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
@@ -215,11 +227,11 @@ GP_API gp_status gp_assemble_sparse_support(gp_ctx* ctx, const double* d_X, int6
  * (fused with the scatter into supernodal panels) and the supernodal numeric Cholesky of P C_z P^T.
  * thetas: host array of B settings. Allocates the factor (B copies of the panels plus workspace).
  * A non-positive pivot does not fail the call: it marks that proposal (gp_factor_info, and gp_loglik then
- * returns -inf for it). GP_MIXED stores only the low half of each TF32 operand pair of the tensor-core updates
- * and lets the MMA read the high half from the FP32 factor, which needs TF32 MMAs that truncate FP32 operands:
- * the first GP_MIXED factor on a device checks that with one small MMA (and synchronises the stream once).
- * Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA, GP_ERR_STATE (GP_MIXED on a GPU whose TF32 MMAs round instead of
- * truncating). Asynchronous after allocation. */
+ * returns -inf for it). With TF32 operand pairs (GP_OPT_SPLIT_F16 = 0) GP_MIXED stores only the low half of each
+ * pair and lets the MMA read the high half from the FP32 factor, which needs TF32 MMAs that truncate FP32
+ * operands: the first such factor on a device checks that with one small MMA (and synchronises the stream once).
+ * Errors: GP_ERR_ARG, GP_ERR_NOMEM, GP_ERR_CUDA, GP_ERR_STATE (TF32 pairs on a GPU whose TF32 MMAs round instead
+ * of truncating). Asynchronous after allocation. */
 GP_API gp_status gp_factor(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, gp_precision precision,
                     gp_factor_t** f);
 /* Re-run A3, A4, A7 on an existing factor with B new settings (same B, precision and point set): the
@@ -352,10 +364,11 @@ GP_API gp_status gp_pointset_prepare(gp_ctx* ctx, gp_pointset* ps, gp_precision 
 /* Autotuner of the mixed path's supernode update tiles (the paper has no counterpart: it is a performance choice
  * of this implementation, not of the method). Large fronts are factored 64 columns at a time; the trailing
  * updates of a group of G such blocks are deferred and applied at the group's end as 128 x TN tensor-core
- * tiles with K = 64 G. For each candidate (G, TN) in {4, 8, 16} x {128, 256} the point set's update schedule is
+ * tiles with K = 64 G. For each candidate (G, TN) in {4, 8, 16} x {128, 256} and (32, 256) the point set's update
+ * schedule is
  * re-planned, a GP_MIXED factor of B settings is created and gp_factor_update timed `reps` times (CUDA events on
  * the context stream); the fastest candidate stays planned for the point set's later factors (results differ
- * between candidates only by the order of FP32 sums). tried (nullable, room for 6) receives the candidates with
+ * between candidates only by the order of FP32 sums). tried (nullable, room for 7) receives the candidates with
  * their mean time per factorization, *ntried their count. Must run before any factor of the point set exists;
  * on failure the default blocking (G = 8, TN = 256) is planned again.
  * Errors: GP_ERR_ARG, GP_ERR_STATE (factors exist), GP_ERR_NOMEM, GP_ERR_CUDA. */

@@ -1,5 +1,5 @@
 // factor_mixed.cu -- step A7 in mixed precision (GP_MIXED): the multifrontal supernodal Cholesky of
-// P C_z P^T with the off-diagonal supernode updates on TF32 tensor cores (tcgen05, FP32 accumulation in
+// P C_z P^T with the off-diagonal supernode updates on FP16 or TF32 tensor cores (tcgen05, FP32 accumulation in
 // tensor memory) and every diagonal 64 x 64 block kept, updated and factored in FP64 (optionally factored in
 // FP32 from its FP64 accumulation).
 //
@@ -11,11 +11,12 @@
 // FP64 tiles), factor fronts of order <= 96 wholly in FP64 shared memory, and step the large fronts 64 columns
 // at a time: POTRF of the diagonal tile (FP64, with the FP32 inverse of its factor), TRSM of the
 // rows below in FP32, then the updates F[i, j] -= sum_l L[i, l] L[j, l] on the tensor cores (left-looking
-// 128 x 64 strips per block, 256 x 256 CTA-pair tiles at a group's end), each FP32 operand split into two
-// round-to-nearest TF32 parts (three products per step, about 21 bits kept), with the tile results added in
-// FP64 to the diagonal tiles and in FP32 elsewhere.
+// 128 x 64 strips per block, 256 x 256 CTA-pair tiles at a group's end), each FP32 operand split into two FP16
+// parts of the entry times a power of two (or two TF32 parts), three products per step (about 22, or 21, bits
+// kept), with the tile results added in FP64 to the diagonal tiles and in FP32 elsewhere.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <climits>
@@ -494,13 +495,74 @@ __device__ __forceinline__ float tf32_lo(float x) {
   return tf32_rn(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
 }
 
-// Rows tr..tr+3 x columns tc..tc+3 of X into the front's panel at P + o (row stride ldw) and the low parts of
-// their TF32 pairs into the front's low-part region at L + o, for rows < nr and columns < bw. The padding
-// columns of a row (from the front's width up to ldw, inside the last 4-column group) get a zero low part: the
-// region is reused by the fronts of other levels, and the updates read those columns (times a zero high part).
+// The FP16 operand pairs (GP_OPT_SPLIT_F16) of proposal b are those of its L entries times 2^k, k =
+// 12 - floor(E / 2) for max_i C_ii in [2^E, 2^(E+1)): |L_ij| <= sqrt(C_ii) < 2^(floor(E/2) + 1), so every scaled
+// entry is below 2^13, well inside FP16's range (2^16), and entries down to 2^-25 of the largest keep an FP16
+// high part of full precision. k is clamped to +-126 (2^k and 2^-k are normal FP32 numbers).
+__device__ __forceinline__ int f16_scale_exp(const unsigned long long* __restrict__ dmax, int b) {
+  const int E = (int)((dmax[b] >> 52) & 0x7ff) - 1023;
+  const int fl = E >= 0 ? E / 2 : -((1 - E) / 2);   // floor(E / 2)
+  return min(126, max(-126, 12 - fl));
+}
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // |k| <= 126
+
+// The FP16 pair of a scaled entry y: hi = y rounded to FP16, lo = y - hi (exact in FP32) rounded to FP16.
+__device__ __forceinline__ void f16_pair(float y, __half& hi, __half& lo) {
+  hi = __float2half_rn(y);
+  lo = __float2half_rn(y - __half2float(hi));
+}
+
+// Where store_x puts the tensor-core operands: dmax null for the TF32 pairs' low parts (the high part is the
+// panel entry itself), else the FP16 pairs of proposal b (scale from dmax[b]) in a front region of m rows.
+struct OpSplit {
+  const unsigned long long* dmax;
+  int b;
+  int64_t m;
+};
+
+// Rows tr..tr+3 x columns tc..tc+3 of X into the front's panel at P + o (row stride ldw, o = row0 ldw + col0)
+// and their tensor-core operands into the front's operand region L, for rows < nr and columns < bw.
+// TF32 pairs: the low parts at L + o; the padding columns of a row (from the front's width up to ldw, inside the
+// last 4-column group) get a zero low part: the region is reused by the fronts of other levels, and the updates
+// read those columns (times a zero high part). FP16 pairs (op.dmax set): rows of ldh = ldw rounded up to 8
+// halves, the high parts at (half*)L + row ldh + column and the low parts m ldh halves further; the padding
+// columns up to ldh get zero pairs (the updates read them, and FP16 pairs have no zero high part elsewhere).
 __device__ __forceinline__ void store_x(const float (&acc)[4][4], float* __restrict__ P, float* __restrict__ L,
-                                        int64_t o0, int ldw, int nr, int bw) {
+                                        int64_t row0, int col0, int ldw, int nr, int bw, const OpSplit& op) {
   const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+  if (op.dmax) {
+    const float sc = pow2f(f16_scale_exp(op.dmax, op.b));
+    const int ldh = (ldw + 7) & ~7, bw8 = (bw + 7) & ~7;
+    __half* H = reinterpret_cast<__half*>(L);
+    const int64_t lo_off = op.m * ldh;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int i = tr + e;
+      if (i >= nr || tc >= bw8) continue;
+      const int64_t o = row0 * ldw + col0 + (int64_t)i * ldw + tc;
+      const int64_t oh = (row0 + i) * ldh + col0 + tc;   // 8-byte aligned: ldh, col0 and tc are x4
+      __align__(8) __half hv[4], lv[4];
+      if (tc + 4 <= bw) {
+        *reinterpret_cast<float4*>(P + o) = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+#pragma unroll
+        for (int f = 0; f < 4; f++) f16_pair(acc[e][f] * sc, hv[f], lv[f]);
+      } else {   // the front's last columns and the padding after them
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+          hv[f] = __float2half_rn(0.f);
+          lv[f] = hv[f];
+          if (tc + f < bw) {
+            P[o + f] = acc[e][f];
+            f16_pair(acc[e][f] * sc, hv[f], lv[f]);
+          }
+        }
+      }
+      *reinterpret_cast<uint2*>(H + oh) = *reinterpret_cast<const uint2*>(hv);
+      *reinterpret_cast<uint2*>(H + lo_off + oh) = *reinterpret_cast<const uint2*>(lv);
+    }
+    return;
+  }
+  const int64_t o0 = row0 * ldw + col0;
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int i = tr + e;
@@ -537,7 +599,8 @@ __device__ __forceinline__ void stash_t(const float (&acc)[4][4], float* BT) {
 __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                                 int nfront, int kb, DevPlan dp, float* __restrict__ p32,
                                                 float* __restrict__ opl, int64_t LOE,
-                                                const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
+                                                const float* __restrict__ dinv32, int64_t P32E, int64_t DE,
+                                                const unsigned long long* __restrict__ dmax) {
   __shared__ __align__(16) float BsT[T * TS];   // BsT[l][r] = B[r][l]
   __shared__ __align__(16) float IsT[T * TS];   // IsT[l][j] = Inv[j][l]
   int64_t t = blockIdx.x;
@@ -556,7 +619,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const int32_t* __restrict__ fron
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw, acc);
-  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], r0 * ldw + c0, ldw, nr, bw);
+  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], r0, c0, ldw, nr, bw, OpSplit{dmax, b, m});
 }
 
 // Block columns kb and kb + 1 at once (the mixed path's block steps in pairs, for an even group width): fronts
@@ -568,7 +631,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
                                                               DevPlan dp, float* __restrict__ p32,
                                                               float* __restrict__ opl, int64_t LOE,
                                                               double* __restrict__ dg, float* __restrict__ dinv32,
-                                                              int64_t P32E, int64_t DE, int32_t* __restrict__ notpd) {
+                                                              int64_t P32E, int64_t DE, int32_t* __restrict__ notpd,
+                                                              const unsigned long long* __restrict__ dmax) {
   __shared__ __align__(16) float BsT[T * TS];
   __shared__ __align__(16) float IsT[T * TS];
   const int fi = blockIdx.x;
@@ -588,7 +652,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw1, acc);   // L_21
-  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], (int64_t)c1 * ldw + c0, ldw, bw2, bw1);
+  store_x(acc, p32 + ob, opl + (int64_t)b * LOE + dp.lo_off[s], c1, c0, ldw, bw2, bw1,
+          OpSplit{dmax, b, (int64_t)w + dp.r[s]});
   __syncthreads();
   stash_t(acc, BsT);   // BsT[l][r] = L_21[r][l]; rows past bw2 hold zeros
   __syncthreads();
@@ -611,7 +676,8 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_pair(const int32_t* __r
 __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
                                                      int nfront, int n2, int kb, DevPlan dp, float* __restrict__ p32,
                                                      float* __restrict__ opl, int64_t LOE,
-                                                     const float* __restrict__ dinv32, int64_t P32E, int64_t DE) {
+                                                     const float* __restrict__ dinv32, int64_t P32E, int64_t DE,
+                                                     const unsigned long long* __restrict__ dmax) {
   __shared__ __align__(16) float BsT[T * TS];
   __shared__ __align__(16) float IsT[T * TS];
   int64_t t = blockIdx.x;
@@ -634,7 +700,7 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
   __syncthreads();
   float acc[4][4];
   prod_tile(BsT, IsT, bw1, acc);   // X_1
-  store_x(acc, P, Lo, r0 * ldw + c0, ldw, nr, bw1);
+  store_x(acc, P, Lo, r0, c0, ldw, nr, bw1, OpSplit{dmax, b, m});
   if (!two) return;
   __syncthreads();
   stash_t(acc, BsT);                                            // BsT[l][r] = X_1[r][l]
@@ -656,7 +722,7 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
   }
   __syncthreads();
   prod_tile(BsT, IsT, bw2, acc);   // X_2
-  store_x(acc, P, Lo, r0 * ldw + c1, ldw, nr, bw2);
+  store_x(acc, P, Lo, r0, c1, ldw, nr, bw2, OpSplit{dmax, b, m});
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -666,11 +732,16 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
 //      (the group's earlier blocks); 4: the same for block columns kb and kb + 1 at once, 128 x 128 tiles;
 //   2: group end: rows/columns >= gend, tiles on and below the diagonal (the plan's tile width: 256 x 256 per
 //      CTA pair, or 128 x 128), K = the whole group [g0, gend).
-// The operands are the TF32 pair (hi, lo) of each L entry: hi is the FP32 panel entry itself, read through the
-// TF32 MMA's truncation of the low 13 mantissa bits, and lo the rounded remainder the TRSM writes into the
-// level's low-part workspace. Each tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T (the split of Ootomo
-// and Yokota, 2022, with a truncated high part: about 20 significant bits survive the products instead of the 11
-// of one TF32 pass). The wide tiles of mode 2 halve
+// The operands are a pair (hi, lo) per L entry, and each tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T
+// (the split of Ootomo and Yokota, 2022), FP32 accumulation:
+//   F16 (the default): hi and lo are FP16, the entry times 2^k rounded and the remainder rounded (about 22
+//     significant bits), both written by the TRSM into the level's operand workspace; kind::f16 MMAs take 16 K
+//     per instruction, so an operand chunk of 128 bytes per row holds 64 K and a step costs half the
+//     instructions and half the operand bytes of TF32; the epilogue scales the tile back by 2^-2k (exact).
+//   TF32: hi is the FP32 panel entry itself, read through the TF32 MMA's truncation of the low 13 mantissa bits,
+//     and lo the rounded remainder the TRSM writes into the workspace (about 21 significant bits survive the
+//     products instead of the 11 of one TF32 pass).
+// The wide tiles of mode 2 halve
 // the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
 // bounds this kernel). Mode 2 runs in clusters of two CTAs on the tile pairs (rows 2p and 2p + 1 of 128, the same
 // 256 columns) as one 256 x 256 CTA-pair MMA: each CTA loads its own 128 A rows and its half of the 256 B rows,
@@ -679,7 +750,8 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
 // barrier, and its commits free the stage and hand the accumulator halves to both CTAs.
 //
 // One persistent CTA per SM walks the launch's tiles (all fronts, all proposals) with three roles:
-//   warp 0 (one lane): TMA loads of 128 x 32 operand chunks into a ring of 128-byte-swizzled tiles;
+//   warp 0 (one lane): TMA loads of 128-row operand chunks (128 bytes per row: 64 FP16 or 32 TF32 entries) into
+//                      a ring of 128-byte-swizzled tiles;
 //   warp 1 (one lane): tcgen05.mma, 12 instructions per chunk, into one of two TMEM accumulators;
 //   warps 2-9: the epilogue, which drains the other accumulator (tcgen05.ld -> swizzled 32 x 32 shared slab ->
 //              coalesced read-modify-write of the front, 32 loads in flight per lane) while the next tile's
@@ -769,15 +841,16 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   return u;
 }
 
-template <int TN, bool PAIR>
+template <int TN, bool PAIR, bool F16>
 __global__ void __launch_bounds__(UW_THREADS, 1)
     k_update_ws(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre, int nfront, int64_t total,
                 int64_t ntiles, int kb, int mode, int group, DevPlan dp, const uint8_t* __restrict__ tmaps,
                 const int32_t* __restrict__ slot_of, float* __restrict__ p32, double* __restrict__ dg,
                 float* __restrict__ u32, int64_t P32E, int64_t DE, int64_t UE, int32_t* __restrict__ err,
-                tcg::WaitLimit lim) {
+                tcg::WaitLimit lim, const unsigned long long* __restrict__ dmax) {
   using C = UW<TN, PAIR>;
   constexpr int NS = C::STAGES;
+  constexpr int KCH = F16 ? 64 : 32;   // K per operand chunk: one 128-byte row of FP16 or of TF32 entries
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* epi = reinterpret_cast<float*>(smem + NS * C::STAGE);
@@ -840,14 +913,14 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
         tcg::tmap_acquire(mh);
         tcg::tmap_acquire(ml);
         const bool shared_a = a_in_b(u) >= 0;
-        const int nch = (u.K + 31) / 32;
+        const int nch = (u.K + KCH - 1) / KCH;
         for (int c = 0; c < nch; c++) {
           if (!tcg::mbar_wait(&empty[st], ph ^ 1, lim)) {
             fail();
             break;
           }
           const uint32_t sa = sbase + st * C::STAGE, sb = sa + 2 * C::OPA;
-          const int x = u.kc + c * 32;
+          const int x = u.kc + c * KCH;
           if (PAIR) {   // this CTA's A rows and half of B, counted on the even CTA's barrier
             const uint32_t fb = tcg::mapa_shared(tcg::smem_u32(&full[st]), 0);
             if (rank == 0) tcg::mbar_arrive_expect_tx(&full[st], 2 * ((shared_a ? 0 : 2 * C::OPA) + 2 * C::OPB));
@@ -880,12 +953,12 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {   // MMA issuer (paired: the even CTA, for both)
-      const uint32_t idesc = tcg::idesc_tf32(PAIR ? 256 : 128, TN);
+      const uint32_t idesc = F16 ? tcg::idesc_f16(PAIR ? 256 : 128, TN) : tcg::idesc_tf32(PAIR ? 256 : 128, TN);
       uint32_t st = 0, ph = 0, acc = 0, aph = 0;
       for (int64_t tt = t_first; tt < ntiles && !*abort_flag; tt += t_step) {
         const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, rank);
         const int ab = a_in_b(u);
-        const int nch = (u.K + 31) / 32;
+        const int nch = (u.K + KCH - 1) / KCH;
         if (!tcg::mbar_wait(&tempty[acc], aph ^ 1, lim)) {
           fail();
           break;
@@ -908,13 +981,13 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             const uint64_t ah = tcg::smem_desc_sw128(aH + o), al = tcg::smem_desc_sw128(aL + o);
             const uint64_t bh = tcg::smem_desc_sw128(bH + o), bl = tcg::smem_desc_sw128(bL + o);
             if (PAIR) {
-              tcg::mma_tf32_2sm(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-              tcg::mma_tf32_2sm(d, ah, bl, idesc, 1u);
-              tcg::mma_tf32_2sm(d, ah, bh, idesc, 1u);
+              tcg::mma_2sm<F16>(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              tcg::mma_2sm<F16>(d, ah, bl, idesc, 1u);
+              tcg::mma_2sm<F16>(d, ah, bh, idesc, 1u);
             } else {
-              tcg::mma_tf32(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-              tcg::mma_tf32(d, ah, bl, idesc, 1u);
-              tcg::mma_tf32(d, ah, bh, idesc, 1u);
+              tcg::mma_1sm<F16>(d, al, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              tcg::mma_1sm<F16>(d, ah, bl, idesc, 1u);
+              tcg::mma_1sm<F16>(d, ah, bh, idesc, 1u);
             }
           }
           if (PAIR) tcg::mma_commit2_mc(&empty[st], 3);
@@ -946,6 +1019,8 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       float* P = p32 + (int64_t)u.b * P32E + dp.loff32[u.s];
       float* U = u32 + (int64_t)u.b * UE + dp.uoff[u.s];
       double* D = dg + (int64_t)u.b * DE + dp.doff[u.s];
+      // FP16 pairs: the accumulator holds 2^2k L_I L_J^T; 2^-k twice scales it back exactly
+      const float isc = F16 ? pow2f(-f16_scale_exp(dmax, u.b)) : 1.f;
       const int64_t ib = u.i0 + q * 32;
       const int64_t jc = u.j0 + h * (TN / 2);
       // while the tile's MMAs run: pull this warp's target rows (NSL x 128 bytes each) into L2
@@ -981,6 +1056,10 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
             }
           }
           __syncwarp();
+          if (F16) {
+#pragma unroll
+            for (int e = 0; e < 32; e++) v[e] = (v[e] * isc) * isc;
+          }
 #pragma unroll
           for (int e = 0; e < 32; e++) slab[lane * 32 + (e ^ lane)] = v[e];
         }
@@ -1051,7 +1130,7 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
       for (int64_t tt = t_first; tt < ntiles && c < n_hi && n_lo < n_hi; tt += t_step) {
         const UTile u = decode_tile<TN, PAIR>(fronts, pre, nfront, total, kb, mode, group, dp, slot_of, tt, 1);
         const uint32_t ob = (u.i0 == u.j0 + 128 ? 0 : 2 * C::OPA) + 2 * C::OPB;   // the odd CTA's bytes
-        const int nch = (u.K + 31) / 32;
+        const int nch = (u.K + KCH - 1) / KCH;
         for (int q = 0; q < nch && c < n_hi; q++, c++) {
           if (c < n_lo) continue;
           if (n_e > n_o) tcg::mbar_complete_tx(&full[c % NS], ob);
@@ -1078,17 +1157,45 @@ __global__ void __launch_bounds__(UW_THREADS, 1)
 }
 
 std::once_flag g_attrs_once;
+template <bool F16>
+void set_update_attrs() {
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT, false, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<GP_TN_LEFT>::SMEM));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<128, false, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<128>::SMEM));
+  GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               UW<256, true>::SMEM));
+}
 void set_attrs() {   // once per process (contexts may run on several host threads)
   std::call_once(g_attrs_once, [] {
     GP_CUDA(cudaFuncSetAttribute(k_small_front32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  GP_SMALL_M * GP_SMALL_M * (int)sizeof(double)));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<GP_TN_LEFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 UW<GP_TN_LEFT>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 UW<128>::SMEM));
-    GP_CUDA(cudaFuncSetAttribute(k_update_ws<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 UW<256, true>::SMEM));
+    set_update_attrs<false>();
+    set_update_attrs<true>();
   });
+}
+
+// max_i C_ii of each proposal (grid: columns x proposals), for the FP16 pairs' scale: the diagonal entries sit in
+// the FP64 diagonal tiles once the values are in; the maximum of non-negative doubles is that of their bit
+// patterns as unsigned integers (atomicMax after a warp maximum). Non-positive or NaN entries count as 0 (the
+// factorization reports them).
+__global__ void __launch_bounds__(256) k_diag_max(DevPlan dp, int64_t n, const double* __restrict__ dg, int64_t DE,
+                                                  unsigned long long* __restrict__ dmax) {
+  const int b = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = 0;
+  if (j < n) {
+    const int32_t s = dp.sn_of_col[j];
+    const int64_t i = j - dp.sn_first[s];
+    const double d = dg[(int64_t)b * DE + dp.doff[s] + (i >> 6) * (T * T) + (i & 63) * (T + 1)];
+    v = d > 0.0 ? (unsigned long long)__double_as_longlong(d) : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(dmax + b, v);
 }
 
 __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
@@ -1150,15 +1257,17 @@ void compute_dest_map_mixed(gp_ctx* ctx, gp_pointset* ps) {
 namespace {
 // One update launch over `total` tiles per proposal of the fronts of a list: mode 3 on 128 x 64 tiles, mode 2
 // with 256-column tiles on clusters of two CTAs, mode 2 with 128-column tiles and mode 4 on 128 x 128 tiles.
-void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
-                   int32_t nfront, int32_t kb, int mode) {
+template <bool F16>
+void launch_update_t(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
+                     int32_t nfront, int32_t kb, int mode) {
   const SymPlan& sp = f->ps->sp;
   const int64_t ntiles = total * f->B;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
   if (mode == 3) {
-    k_update_ws<GP_TN_LEFT, false><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
+    k_update_ws<GP_TN_LEFT, false, F16><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
-        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim);
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim,
+        f->op_dmax);
   } else if (mode == 2 && sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
@@ -1172,16 +1281,23 @@ void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fr
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true>, fronts, pre, nfront, total, ntiles, kb, mode, sp.group,
-                               f->ps->dp, (const uint8_t*)f->op_maps, (const int32_t*)f->op_slot, f->panels32,
-                               f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries,
-                               f->tiles_err, f->wait_lim));
+    GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true, F16>, fronts, pre, nfront, total, ntiles, kb, mode,
+                               sp.group, f->ps->dp, (const uint8_t*)f->op_maps, (const int32_t*)f->op_slot,
+                               f->panels32, f->diag, f->upd32, sp.panel32_entries, sp.diag_entries,
+                               sp.update_entries, f->tiles_err, f->wait_lim,
+                               (const unsigned long long*)f->op_dmax));
   } else {
-    k_update_ws<128, false><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
+    k_update_ws<128, false, F16><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
         fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
-        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim);
+        f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim,
+        f->op_dmax);
   }
   GP_CHECK_LAUNCH(ctx);
+}
+void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
+                   int32_t nfront, int32_t kb, int mode) {
+  if (f->op_f16) launch_update_t<true>(ctx, f, total, fronts, pre, nfront, kb, mode);
+  else launch_update_t<false>(ctx, f, total, fronts, pre, nfront, kb, mode);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -1283,12 +1399,14 @@ void require_tf32_truncation(gp_ctx* ctx) {
   state[ctx->device] = 1;
 }
 
-// Tensor maps of the TF32 operand pair of every large front (those with tensor-core updates under any
-// blocking of plan_mixed_updates): per front two 3-D maps (columns x rows x proposals), the high part over the
-// FP32 panel and the low part over the front's region of op_lo, 128 x 32 boxes with the 128-byte swizzle; rows
-// past the front and columns past ldw read as zeros. op_slot[s] gives the front's map pair (-1 for none).
+// Tensor maps of the operand pair of every large front (those with tensor-core updates under any blocking of
+// plan_mixed_updates): per front two 3-D maps (columns x rows x proposals) with 128-byte boxes of 128 rows and the
+// 128-byte swizzle; rows past the front and columns past the row length read as zeros. TF32 pairs: the high
+// part over the FP32 panel and the low part over the front's region of op_lo (rows of ldw FP32, boxes of 32
+// columns). FP16 pairs: both over the front's region (rows of ldh halves, high parts first, boxes of 64
+// columns). op_slot[s] gives the front's map pair (-1 for none).
 void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
-  require_tf32_truncation(ctx);
+  if (!f->op_f16) require_tf32_truncation(ctx);
   const SymPlan& sp = f->ps->sp;
   const int64_t ns = (int64_t)sp.sn_w.size();
   std::vector<int32_t> slot(ns, -1);
@@ -1308,16 +1426,29 @@ void build_update_maps(gp_ctx* ctx, gp_factor_t* f) {
     const int64_t ldw = sp.sn_ldw[s], m = (int64_t)sp.sn_w[s] + sp.sn_r[s];
     GP_REQUIRE(ldw % 4 == 0 && sp.sn_loff32[s] % 4 == 0, "FP32 panel rows must start on 16-byte boundaries");
     GP_REQUIRE(sp.sn_lo_off[s] % 4 == 0 && sp.lo_entries % 4 == 0, "low-part rows must start on 16-byte boundaries");
+    const int64_t ldh = (ldw + 7) / 8 * 8;
+    GP_REQUIRE(sp.sn_lo_off[s] % 8 == 0, "operand regions must start on 32-byte boundaries");
     for (int part = 0; part < 2; part++) {
-      float* base = part == 0 ? f->panels32 + sp.sn_loff32[s] : f->op_lo + sp.sn_lo_off[s];
-      const int64_t pstride = part == 0 ? sp.panel32_entries : sp.lo_entries;
-      cuuint64_t dims[3] = {(cuuint64_t)ldw, (cuuint64_t)m, (cuuint64_t)f->B};
-      cuuint64_t strides[2] = {(cuuint64_t)ldw * 4, (cuuint64_t)pstride * 4};
-      cuuint32_t box[3] = {32, 128, 1};
+      CUresult r;
       cuuint32_t es[3] = {1, 1, 1};
-      CUresult r = enc(&maps[2 * k + part], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (f->op_f16) {   // halves: high parts at the region's start, low parts m x ldh halves further
+        void* base = reinterpret_cast<uint16_t*>(f->op_lo + sp.sn_lo_off[s]) + part * m * ldh;
+        cuuint64_t dims[3] = {(cuuint64_t)ldh, (cuuint64_t)m, (cuuint64_t)f->B};
+        cuuint64_t strides[2] = {(cuuint64_t)ldh * 2, (cuuint64_t)sp.lo_entries * 4};
+        cuuint32_t box[3] = {64, 128, 1};
+        r = enc(&maps[2 * k + part], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      } else {
+        float* base = part == 0 ? f->panels32 + sp.sn_loff32[s] : f->op_lo + sp.sn_lo_off[s];
+        const int64_t pstride = part == 0 ? sp.panel32_entries : sp.lo_entries;
+        cuuint64_t dims[3] = {(cuuint64_t)ldw, (cuuint64_t)m, (cuuint64_t)f->B};
+        cuuint64_t strides[2] = {(cuuint64_t)ldw * 4, (cuuint64_t)pstride * 4};
+        cuuint32_t box[3] = {32, 128, 1};
+        r = enc(&maps[2 * k + part], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      }
       GP_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled rejected an operand map");
     }
   }
@@ -1341,6 +1472,13 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
   values_run_mixed(ctx, f);   // A3, A4 into the FP32 panels and FP64 tiles (zeroed first)
   k_fill_i32<<<grid_for(B, 128), 128, 0, st>>>(f->notpd, B, INT_MAX);
   GP_CHECK_LAUNCH(ctx);
+  const unsigned long long* dmax = f->op_f16 ? f->op_dmax : nullptr;   // FP16 pairs: their scale, from max C_ii
+  if (dmax) {
+    GP_CUDA(cudaMemsetAsync(f->op_dmax, 0, sizeof(unsigned long long) * B, st));
+    ProfScope ps_(ctx, KC_VALUES);
+    k_diag_max<<<dim3(grid_for(ps->n, 256), B), 256, 0, st>>>(dp, ps->n, f->diag, DE, f->op_dmax);
+    GP_CHECK_LAUNCH(ctx);
+  }
   GP_CUDA(cudaMemsetAsync(f->tiles_err, 0, sizeof(int32_t), st));
   ProfLevelScope pls_(ctx);
   // Work off the level chain goes to the context's side stream (not while profiling, which times every launch on
@@ -1406,14 +1544,14 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
           ProfScope ps_(ctx, KC_POTRF, B * (stp.potrf_flops + st2.potrf_flops));
           auto kp = f->diag_fp32 ? k_potrf_pair<true> : k_potrf_pair<false>;
           kp<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, st2.nfront, stp.kb, dp, f->panels32, f->op_lo,
-                                                            LOE, f->diag, f->dinv32, P32E, DE, f->notpd);
+                                                            LOE, f->diag, f->dinv32, P32E, DE, f->notpd, dmax);
           GP_CHECK_LAUNCH(ctx);
         }
         if (stp.pair_total > 0) {
           ProfScope ps_(ctx, KC_TRSM, B * (stp.trsm_flops + st2.trsm_flops));
           k_trsm32_pair<<<dim3((unsigned)stp.pair_total, B), 256, 0, st>>>(
               fronts, dp.pair_pre + stp.pair_pre_off, stp.nfront, st2.nfront, stp.kb, dp, f->panels32, f->op_lo,
-              LOE, f->dinv32, P32E, DE);
+              LOE, f->dinv32, P32E, DE, dmax);
           GP_CHECK_LAUNCH(ctx);
         }
         for (const auto* sg : {&stp, &st2})
@@ -1442,7 +1580,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
         ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
         k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,
                                                                     f->panels32, f->op_lo, LOE, f->dinv32, P32E,
-                                                                    DE);
+                                                                    DE, dmax);
         GP_CHECK_LAUNCH(ctx);
       }
       if (stp.group_total > 0) {   // fronts whose group ends here: the deferred update with K = group width

@@ -211,6 +211,10 @@ extern "C" gp_status gp_set_option(gp_ctx* ctx, int option, int64_t value) {
       if (value < 6 || value > 15) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_REFINE_EXP takes 6..15"});
       ctx->opt_refine_exp = (int)value;
       return GP_OK;
+    case GP_OPT_SPLIT_F16:
+      if (value != 0 && value != 1) return fail(ctx, GpError{GP_ERR_ARG, "GP_OPT_SPLIT_F16 takes 0 or 1"});
+      ctx->opt_split_f16 = (int)value;
+      return GP_OK;
     default:
       return fail(ctx, GpError{GP_ERR_ARG, "unknown option " + std::to_string(option)});
   }
@@ -223,6 +227,7 @@ extern "C" gp_status gp_get_option(const gp_ctx* ctx, int option, int64_t* value
     case GP_OPT_WAIT_POLLS: *value = (int64_t)ctx->opt_wait.polls; return GP_OK;
     case GP_OPT_WAIT_NS: *value = (int64_t)ctx->opt_wait.ns; return GP_OK;
     case GP_OPT_REFINE_EXP: *value = ctx->opt_refine_exp; return GP_OK;
+    case GP_OPT_SPLIT_F16: *value = ctx->opt_split_f16; return GP_OK;
     default: return GP_ERR_ARG;
   }
 }
@@ -565,6 +570,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
     f->B = B;
     f->prec = prec;
     f->diag_fp32 = prec == GP_MIXED && ctx->opt_diag_fp32 != 0;
+    f->op_f16 = prec == GP_MIXED && ctx->opt_split_f16 != 0;
     f->wait_lim = ctx->opt_wait;
     f->refine_tol = std::pow(10.0, -(double)ctx->opt_refine_exp);
     f->core_kind = cores ? cores[0].kind : GP_CORE_WENDLAND;
@@ -593,6 +599,7 @@ extern "C" gp_status gp_factor_core(gp_ctx* ctx, gp_pointset* ps, const gp_hyper
       f->dinv32 = dalloc<float>(ctx, f->bufs, (size_t)B * sp.diag_entries);
       f->op_lo = dalloc<float>(ctx, f->bufs, (size_t)B * sp.lo_entries);
       GP_CUDA(cudaMemsetAsync(f->op_lo, 0, (size_t)B * sp.lo_entries * sizeof(float), ctx->stream));
+      f->op_dmax = dalloc<unsigned long long>(ctx, f->bufs, B);
       build_update_maps(ctx, f);
     }
     f->val = dalloc<double>(ctx, f->bufs, (size_t)B * ps->nnz);
@@ -649,7 +656,8 @@ size_t factor_bytes(const gp_pointset* ps, gp_precision prec, int B, const Theta
          alloc_bytes(b * sp.update_entries * 4) + alloc_bytes(b * n * 2 * 8) + alloc_bytes(4) +
          alloc_bytes(8) +
          alloc_bytes(b * sp.diag_entries * 4) + alloc_bytes(b * sp.lo_entries * 4) +
-         alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4) + alloc_bytes(b * 2 * 8);
+         alloc_bytes(b * 8) + alloc_bytes(2 * nmaps * 128) + alloc_bytes((sp.sn_w.size() + 1) * 4) +
+         alloc_bytes(b * 2 * 8);
   }
   t += alloc_bytes(b * ps->nnz * 8) + alloc_bytes(b * 4) + alloc_bytes(b * n * 8);
   if (prec == GP_FP64) t += alloc_bytes(b * sp.diag_entries * 8);
@@ -693,7 +701,7 @@ extern "C" gp_status gp_pointset_set_blocking(gp_ctx* ctx, gp_pointset* ps, int 
 extern "C" gp_status gp_autotune(gp_ctx* ctx, gp_pointset* ps, const gp_hyper* thetas, int B, int reps,
                                  gp_tune_candidate* tried, int* ntried) {
   if (!ctx) return GP_ERR_ARG;
-  static const int cand[][2] = {{4, 128}, {4, 256}, {8, 128}, {8, 256}, {16, 128}, {16, 256}};
+  static const int cand[][2] = {{4, 128}, {4, 256}, {8, 128}, {8, 256}, {16, 128}, {16, 256}, {32, 256}};
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   gp_status st = guarded(ctx, [&] {
@@ -797,6 +805,7 @@ extern "C" gp_status gp_factor_info(const gp_factor_t* f, gp_factor_info_t* info
   info->bytes = bytes;
   info->not_pd_count = 0;
   info->diag_fp32 = f->diag_fp32 ? 1 : 0;
+  info->split_f16 = f->op_f16 ? 1 : 0;
   for (int b = 0; b < f->B; b++) {   // flags hold the smallest failing permuted column, INT_MAX if none
     bool bad = flags[b] != 0x7fffffff;
     if (bad) info->not_pd_count++;

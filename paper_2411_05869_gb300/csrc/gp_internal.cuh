@@ -92,6 +92,7 @@ struct gp_ctx {
   int64_t prof_n_lv[KC_COUNT][GP_PROF_LEVELS] = {};
   // options (gp_set_option); they apply to factors created afterwards
   int opt_diag_fp32 = 0;     // GP_MIXED: diagonal blocks factored in FP32
+  int opt_split_f16 = 1;     // GP_MIXED: FP16 operand pairs for the tensor-core updates (0: TF32 pairs)
   tcg::WaitLimit opt_wait = tcg::DEFAULT_WAIT;   // GP_MIXED: limits of the tensor-core kernels' bounded waits
   int opt_refine_exp = 10;   // GP_MIXED: gp_loglik's refinement stops at |r - C alpha| / |r| <= 10^-opt_refine_exp
   ~gp_ctx() {
@@ -188,11 +189,13 @@ struct SymPlan {
   std::vector<int32_t> sn_ldw;
   std::vector<int64_t> sn_loff32, sn_doff;
   int64_t panel32_entries = 0, diag_entries = 0;
-  // the low parts of the TF32 operand pairs (lo = x - the TF32 truncation of x; the high part is the FP32 panel
-  // itself, whose low 13 mantissa bits the TF32 MMAs ignore): large fronts only, at sn_lo_off in a per-level
-  // workspace of lo_entries (the largest level's total; a multiple of 4)
+  // the tensor-core operands of the large fronts' factored panel entries, at sn_lo_off in a per-level workspace
+  // of lo_entries 4-byte entries (the largest level's total; a multiple of 8), m x ldh per front (ldh = ldw
+  // rounded up to 8). TF32 split: the low parts (lo = x - the TF32 truncation of x, row stride ldw; the high part
+  // is the FP32 panel itself, whose low 13 mantissa bits the TF32 MMAs ignore). FP16 split: the scaled FP16
+  // high parts (m x ldh halves) followed by the FP16 low parts (m x ldh halves).
   std::vector<int64_t> sn_lo_off;
-  int64_t lo_entries = 4;
+  int64_t lo_entries = 8;
   int group = GP_GROUP, tn_group = GP_TN_GROUP;   // mixed-path update blocking (plan_mixed_updates)
   std::vector<int32_t> upd_fronts;   // per step: fronts of the left-looking and of the group update
   std::vector<int64_t> upd_pre;      // their tile prefixes
@@ -326,10 +329,13 @@ struct gp_factor_s {
   int n1max = 0;
   double* panels = nullptr;     // FP64 panels, B x panel_entries
   float* panels32 = nullptr;    // GP_MIXED: FP32 panels, row-major, B x panel32_entries
-  float* op_lo = nullptr;       // GP_MIXED: low TF32 parts of the factored panel entries of one level's large
-                                //   fronts, B x lo_entries (the high parts are panels32 itself)
-  uint8_t* op_maps = nullptr;   // GP_MIXED: TMA maps of the high (panels32) and low (op_lo) operands, 2 x 128
-                                //   bytes per updated front
+  float* op_lo = nullptr;       // GP_MIXED: tensor-core operands of the factored panel entries of one level's
+                                //   large fronts, B x lo_entries: the low TF32 parts (the high parts are
+                                //   panels32 itself) or, with op_f16, the FP16 pairs
+  uint8_t* op_maps = nullptr;   // GP_MIXED: TMA maps of the high and low operands, 2 x 128 bytes per updated front
+  bool op_f16 = false;          // GP_MIXED: FP16 operand pairs (GP_OPT_SPLIT_F16) instead of TF32 pairs
+  unsigned long long* op_dmax = nullptr;   // GP_MIXED: per proposal, the bits of max_i C_ii (FP64, >= 0): the
+                                //   FP16 pairs' power-of-two scale
   int32_t* op_slot = nullptr;   // GP_MIXED: per supernode, its map pair (-1 = none)
   double* diag = nullptr;       // GP_MIXED: FP64 64 x 64 diagonal tiles, B x diag_entries
   double* delta = nullptr;      // GP_MIXED: refinement vectors (residual and correction), B x 2n

@@ -399,7 +399,7 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   // ---- launch schedule
   sp.levels.assign(sp.nlevels, SymPlan::Level());
   sp.sn_lo_off.assign(sp.ns, 0);
-  sp.lo_entries = 4;
+  sp.lo_entries = 8;
   sp.level_large.assign(sp.nlevels, SymPlan::LevelLarge());
   sp.sn_fl.assign(sp.ns, -1);
   sp.n_fl = 0;
@@ -526,13 +526,15 @@ void build_symbolic(int64_t n, const int64_t* rowptr, const int32_t* col, const 
       }
     }
     sp.level_large[L].count = (int64_t)sp.large_fronts.size() - sp.level_large[L].off;
-    // the low TF32 parts of this level's large fronts: one region per front in a workspace that every level
-    // reuses (the parts are read only by the updates of the front they belong to, inside its level)
+    // the tensor-core operands of this level's large fronts (the low TF32 parts, or the FP16 pairs): one region
+    // per front in a workspace that every level reuses (read only by the updates of the front they belong to,
+    // inside its level); m x ldh entries of 4 bytes, ldh = ldw rounded up to 8, so that the FP16 pair's rows
+    // (ldh halves each) start on 16-byte boundaries
     {
       int64_t lo = 0;
       for (int32_t s : large) {
         sp.sn_lo_off[s] = lo;
-        lo += ((int64_t)(sp.sn_w[s] + sp.sn_r[s]) * sp.sn_ldw[s] + 3) / 4 * 4;
+        lo += (int64_t)(sp.sn_w[s] + sp.sn_r[s]) * ((sp.sn_ldw[s] + 7) / 8 * 8);
       }
       sp.lo_entries = std::max(sp.lo_entries, lo);
     }

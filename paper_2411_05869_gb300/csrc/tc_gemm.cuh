@@ -1,4 +1,4 @@
-// tc_gemm.cuh -- tcgen05 building blocks for sm_103a (5th-generation tensor cores): TF32 MMAs with FP32
+// tc_gemm.cuh -- tcgen05 building blocks for sm_103a (5th-generation tensor cores): TF32 and FP16 MMAs with FP32
 // accumulation in tensor memory (TMEM), shared-memory matrix descriptors, mbarriers with bounded waits, TMEM
 // allocation and loads, and TMA tile loads. Every wait is bounded: a wait that runs out reports failure to its
 // caller, which sets an error flag (GP_ERR_TIMEOUT on the host) and winds the kernel down instead of spinning
@@ -23,6 +23,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same for kind::f16 with A and B both FP16 (bits 7-9, 10-12 = 0) and D FP32.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -86,6 +91,21 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// One MMA of this CTA: FP16 operands (K = 16 per instruction) or TF32 (K = 8), 32 bytes of K either way.
+template <bool F16>
+__device__ __forceinline__ void mma_1sm(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  if (F16) mma_f16(tmem_d, adesc, bdesc, idesc, accumulate);
+  else mma_tf32(tmem_d, adesc, bdesc, idesc, accumulate);
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                : "memory");
@@ -109,12 +129,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // ------------------------------------------------------------------------------------------------
 // Pieces of the warp-specialised update kernel: TMA tile loads into 128-byte-swizzled K-major shared tiles
-// (one row of 32 FP32 = 128 bytes per tile row, 16-byte chunks XOR-permuted by row mod 8), transaction-counted
+// (one row of 32 FP32 or 64 FP16 = 128 bytes per tile row, 16-byte chunks XOR-permuted by row mod 8), transaction-counted
 // mbarriers, and the matching tcgen05 shared-memory descriptors.
 
 // Descriptor of a K-major operand tile with the 128-byte swizzle: 8-row groups 1024 bytes apart (SBO), layout
-// type 2 in bits 61-63. The tile base must be 1024-byte aligned; K steps of 8 TF32 (32 bytes) inside the
-// 128-byte row advance the start address.
+// type 2 in bits 61-63. The tile base must be 1024-byte aligned; K steps of 32 bytes (8 TF32 or 16 FP16) inside
+// the 128-byte row advance the start address.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -192,6 +212,20 @@ __device__ __forceinline__ void mma_tf32_2sm(uint32_t tmem_d, uint64_t adesc, ui
       " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+__device__ __forceinline__ void mma_f16_2sm(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+template <bool F16>
+__device__ __forceinline__ void mma_2sm(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  if (F16) mma_f16_2sm(tmem_d, adesc, bdesc, idesc, accumulate);
+  else mma_tf32_2sm(tmem_d, adesc, bdesc, idesc, accumulate);
 }
 // Arrives on the mbarrier at this offset in every CTA of ctamask once the pair's earlier MMAs have completed.
 __device__ __forceinline__ void mma_commit2_mc(uint64_t* bar, uint16_t ctamask) {

@@ -50,12 +50,12 @@ class PointsetInfo(ctypes.Structure):
 
 class FactorInfo(ctypes.Structure):
     _fields_ = [("B", c_int), ("precision", c_int), ("bytes", c_i64), ("not_pd_count", ctypes.c_int32),
-                ("diag_fp32", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
+                ("diag_fp32", ctypes.c_int32), ("timed_out", ctypes.c_int32), ("split_f16", ctypes.c_int32)]
 
 
-GP_OPT_DIAG_FP32, GP_OPT_WAIT_POLLS, GP_OPT_WAIT_NS, GP_OPT_REFINE_EXP = 0, 1, 2, 3
+GP_OPT_DIAG_FP32, GP_OPT_WAIT_POLLS, GP_OPT_WAIT_NS, GP_OPT_REFINE_EXP, GP_OPT_SPLIT_F16 = 0, 1, 2, 3, 4
 OPTIONS = {"diag_fp32": GP_OPT_DIAG_FP32, "wait_polls": GP_OPT_WAIT_POLLS, "wait_ns": GP_OPT_WAIT_NS,
-           "refine_exp": GP_OPT_REFINE_EXP}
+           "refine_exp": GP_OPT_REFINE_EXP, "split_f16": GP_OPT_SPLIT_F16}
 
 
 class GpRequest(ctypes.Structure):

@@ -4,6 +4,7 @@ Structure (pattern, order, etree, column counts, supernodes, row structures) mus
 FP64 log-likelihoods to 1e-10 relative; alpha and predictive means to 1e-9 of their scale (the same
 factorization carried through two triangular solves and one more product).
 """
+import copy
 import math
 
 import numpy as np
@@ -157,19 +158,24 @@ def test_edge_sizes(ctx, n, d):
 MIXED_RTOL = 1e-6
 
 
+@pytest.mark.parametrize("split_f16", [0, 1])
 @pytest.mark.parametrize("diag_fp32", [0, 1])
-def test_loglik_mixed_matches_oracle(case, ctx, diag_fp32):
-    """GP_MIXED: TF32 tensor-core updates, FP64-accumulated diagonal tiles factored in FP64 (default) or in FP32
-    (GP_OPT_DIAG_FP32), FP64 refinement; loglik within 1e-6."""
+def test_loglik_mixed_matches_oracle(case, ctx, diag_fp32, split_f16):
+    """GP_MIXED: tensor-core updates on TF32 operand pairs (default) or FP16 pairs (GP_OPT_SPLIT_F16),
+    FP64-accumulated diagonal tiles factored in FP64 (default) or in FP32 (GP_OPT_DIAG_FP32), FP64 refinement;
+    loglik within 1e-6."""
     from paper_2411_05869_gb300 import gp
     w, ps = case["w"], case["ps"]
     ref = oracle.sparse_loglik(w.hyper, w.X, case["rp"], case["col"], case["perm"], w.resid, want_alpha=True)
+    split0 = ctx.get_option("split_f16")
     ctx.set_option("diag_fp32", diag_fp32)
+    ctx.set_option("split_f16", split_f16)
     try:
         f = ctx.factor(ps, [w.hyper], gp.GP_MIXED)
     finally:
         ctx.set_option("diag_fp32", 0)
-    assert f.info()["diag_fp32"] == diag_fp32
+        ctx.set_option("split_f16", split0)
+    assert f.info()["diag_fp32"] == diag_fp32 and f.info()["split_f16"] == split_f16
     err = torch.empty(1, dtype=torch.float64, device="cuda")
     ll = float(f.loglik(_dev(w.resid), err=err).cpu()[0])
     assert abs(ll - ref["loglik"]) <= MIXED_RTOL * abs(ref["loglik"]), (ll, ref["loglik"])
@@ -254,19 +260,54 @@ def test_every_update_blocking_and_the_autotuner_match_oracle(ctx):
     ps = ctx.assemble(_dev(w.X), hp.core_radius)
     assert ps.info()["max_front"] > 8 * 64
     r = _dev(w.resid)
-    for G in (1, 4, 8, 16):
+    split0 = ctx.get_option("split_f16")
+    for G in (1, 4, 8, 16, 32):
         for TN in (128, 256):
             ps.set_blocking(G, TN)
-            f = ctx.factor(ps, [hp], gp.GP_MIXED)
-            ll = float(f.loglik(r).cpu()[0])
-            f.free()
-            assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (G, TN, ll, ref)
+            for split in (0, 1):   # TF32 and FP16 operand pairs
+                ctx.set_option("split_f16", split)
+                try:
+                    f = ctx.factor(ps, [hp], gp.GP_MIXED)
+                finally:
+                    ctx.set_option("split_f16", split0)
+                ll = float(f.loglik(r).cpu()[0])
+                f.free()
+                assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (G, TN, split, ll, ref)
     tried = ps.autotune([hp], reps=1)
-    assert len(tried) == 6 and all(t["ms"] > 0 for t in tried)
+    assert len(tried) == 7 and all(t["ms"] > 0 for t in tried)
     f = ctx.factor(ps, [hp], gp.GP_MIXED)
     ll = float(f.loglik(r).cpu()[0])
     assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (ll, ref)
     with pytest.raises(gp.GpError):   # the schedule of live factors is not re-planned under them
         ps.autotune([hp], reps=1)
+    f.free()
+    ps.free()
+
+
+@pytest.mark.parametrize("c", [1e-9, 1e9])
+def test_mixed_f16_pairs_scale_with_the_covariance(ctx, c):
+    """The FP16 operand pairs take a power-of-two scale from max_i C_ii: with C_z and r multiplied by c and
+    sqrt(c) (core and noise variances times c), every L entry moves by sqrt(c), far outside FP16's range for
+    c = 1e9 and below its normal range for c = 1e-9 without the scale. The log-likelihood must still match the
+    oracle's on the scaled problem within 1e-6, on fronts wide enough for every update mode."""
+    from paper_2411_05869_gb300 import gp
+    w = synth.uniform_spacetime(8000, 0, 60.0, 8, seed=83, ndays=80)
+    hp = copy.deepcopy(w.hyper)
+    hp.core_var *= c
+    hp.noise_var *= c
+    r = w.resid * math.sqrt(c)
+    rp, col = oracle.pattern(w.X, hp.core_radius)
+    perm = oracle.fill_order(w.X, hp.core_radius, rp, col)
+    ref = oracle.sparse_loglik(hp, w.X, rp, col, perm, r)["loglik"]
+    ps = ctx.assemble(_dev(w.X), hp.core_radius)
+    assert ps.info()["max_front"] > 4 * 64
+    split0 = ctx.get_option("split_f16")
+    ctx.set_option("split_f16", 1)
+    try:
+        f = ctx.factor(ps, [hp], gp.GP_MIXED)
+    finally:
+        ctx.set_option("split_f16", split0)
+    ll = float(f.loglik(_dev(r)).cpu()[0])
+    assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (c, ll, ref)
     f.free()
     ps.free()

@@ -91,17 +91,20 @@ def test_fp64_full_size(case, ctx):
     f.free()
 
 
-@pytest.mark.parametrize("diag_fp32", [0, 1])
-def test_mixed_full_size(case, ctx, diag_fp32):
+@pytest.mark.parametrize("diag_fp32,split_f16", [(0, 1), (1, 1), (0, 0)])
+def test_mixed_full_size(case, ctx, diag_fp32, split_f16):
     from paper_2411_05869_gb300 import gp
     g, ps = case["g"], case["ps"]
     if case["name"] == "station_5000x12":
         assert g["max_width"] > 16 * 64   # a front spans more than one 1024-column update group
+    split0 = ctx.get_option("split_f16")
     ctx.set_option("diag_fp32", diag_fp32)
+    ctx.set_option("split_f16", split_f16)
     try:
         f = ctx.factor(ps, case["thetas"], gp.GP_MIXED)
     finally:
         ctx.set_option("diag_fp32", 0)
+        ctx.set_option("split_f16", split0)
     err = torch.empty(2, dtype=torch.float64, device="cuda")
     ll = f.loglik(_dev(np.stack([case["r"], case["r"]])), err=err).cpu().numpy()
     for b in range(2):
