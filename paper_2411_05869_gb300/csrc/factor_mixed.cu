@@ -784,15 +784,19 @@ struct UTile {
 
 // Tile tt of a launch: proposal, front (prefix search), then its position. Mode 2 with TN = 256 (paired): tile
 // pair p (rows 2p and 2p + 1 of 128) holds p + 1 tiles of 256 columns; CTA `rank` of the pair takes row 2p + rank.
+// Modes 3 and 4 may cover part of the strip's 128-row tiles (mode + 8 part): part 0 all of them, part 1 only the
+// first (the rows of the step's diagonal tiles, one tile per front: pre is not read), part 2 the others (pre
+// counts a front's tiles after its first).
 template <int TN, bool PAIR>
 __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts, const int64_t* __restrict__ pre,
-                                             int nfront, int64_t total, int kb, int mode, int group,
+                                             int nfront, int64_t total, int kb, int mode_part, int group,
                                              const DevPlan& dp, const int32_t* __restrict__ slot_of, int64_t tt,
                                              int rank) {
   UTile u;
+  const int mode = mode_part & 7, part = mode_part >> 3;
   u.b = (int)(tt / total);
   const int64_t t = tt - (int64_t)u.b * total;
-  const int fi = find_front(pre, nfront, t);
+  const int fi = part == 1 ? (int)t : find_front(pre, nfront, t);
   u.s = fronts[fi];
   u.slot = slot_of[u.s];
   u.w = dp.w[u.s];
@@ -802,10 +806,10 @@ __device__ __forceinline__ UTile decode_tile(const int32_t* __restrict__ fronts,
   const int c0 = kb * T, bw = min(T, u.w - c0), c1 = c0 + bw;
   const int g0 = (kb / group) * group * T, gend = min(g0 + group * T, u.w);
   (void)bw;
-  const int64_t loc = t - pre[fi];
+  const int64_t loc = part == 1 ? 0 : t - pre[fi];
   int64_t I, J, base;
   if (mode >= 3) {   // 4: the strip of block columns kb and kb + 1 (the block steps in pairs)
-    I = loc;
+    I = part == 2 ? loc + 1 : loc;
     J = 0;
     base = c0;
     u.jlim = mode == 4 ? min(c0 + 2 * T, u.w) : c1;
@@ -1259,21 +1263,22 @@ namespace {
 // with 256-column tiles on clusters of two CTAs, mode 2 with 128-column tiles and mode 4 on 128 x 128 tiles.
 template <bool F16>
 void launch_update_t(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
-                     int32_t nfront, int32_t kb, int mode) {
+                     int32_t nfront, int32_t kb, int mode_part, cudaStream_t st, int reserve) {
   const SymPlan& sp = f->ps->sp;
+  const int mode = mode_part & 7;
   const int64_t ntiles = total * f->B;
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, ctx->nsm);
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, std::max(1, ctx->nsm - reserve));
   if (mode == 3) {
-    k_update_ws<GP_TN_LEFT, false, F16><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, ctx->stream>>>(
-        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
+    k_update_ws<GP_TN_LEFT, false, F16><<<grid, UW_THREADS, UW<GP_TN_LEFT>::SMEM, st>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode_part, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
         f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim,
         f->op_dmax);
   } else if (mode == 2 && sp.tn_group == 256) {   // clusters of two CTAs, one tile pair each
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, ctx->nsm / 2)));
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(ntiles, std::max(1, (ctx->nsm - reserve) / 2))));
     cfg.blockDim = dim3(UW_THREADS);
     cfg.dynamicSmemBytes = UW<256, true>::SMEM;
-    cfg.stream = ctx->stream;
+    cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
@@ -1281,23 +1286,26 @@ void launch_update_t(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true, F16>, fronts, pre, nfront, total, ntiles, kb, mode,
+    GP_CUDA(cudaLaunchKernelEx(&cfg, k_update_ws<256, true, F16>, fronts, pre, nfront, total, ntiles, kb, mode_part,
                                sp.group, f->ps->dp, (const uint8_t*)f->op_maps, (const int32_t*)f->op_slot,
                                f->panels32, f->diag, f->upd32, sp.panel32_entries, sp.diag_entries,
                                sp.update_entries, f->tiles_err, f->wait_lim,
                                (const unsigned long long*)f->op_dmax));
   } else {
-    k_update_ws<128, false, F16><<<grid, UW_THREADS, UW<128>::SMEM, ctx->stream>>>(
-        fronts, pre, nfront, total, ntiles, kb, mode, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
+    k_update_ws<128, false, F16><<<grid, UW_THREADS, UW<128>::SMEM, st>>>(
+        fronts, pre, nfront, total, ntiles, kb, mode_part, sp.group, f->ps->dp, f->op_maps, f->op_slot, f->panels32,
         f->diag, f->upd32, sp.panel32_entries, sp.diag_entries, sp.update_entries, f->tiles_err, f->wait_lim,
         f->op_dmax);
   }
   GP_CHECK_LAUNCH(ctx);
 }
+// mode_part: the mode, plus 8 x the part of the strip for modes 3 and 4 (decode_tile); st: the stream; reserve:
+// SMs the launch leaves free (for a concurrent launch on another stream).
 void launch_update(gp_ctx* ctx, gp_factor_t* f, int64_t total, const int32_t* fronts, const int64_t* pre,
-                   int32_t nfront, int32_t kb, int mode) {
-  if (f->op_f16) launch_update_t<true>(ctx, f, total, fronts, pre, nfront, kb, mode);
-  else launch_update_t<false>(ctx, f, total, fronts, pre, nfront, kb, mode);
+                   int32_t nfront, int32_t kb, int mode_part, cudaStream_t st = nullptr, int reserve = 0) {
+  if (!st) st = ctx->stream;
+  if (f->op_f16) launch_update_t<true>(ctx, f, total, fronts, pre, nfront, kb, mode_part, st, reserve);
+  else launch_update_t<false>(ctx, f, total, fronts, pre, nfront, kb, mode_part, st, reserve);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -1503,6 +1511,28 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
     zero_level(0, ctx->side);
     GP_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
   }
+  // The left-looking update of a step (mode 3, or 4 for a pair of block columns). With a third stream (explicit
+  // streams, not while profiling) and at most half the SMs taken by the step's fronts, the strip's first 128-row
+  // tile of each front -- the rows of the step's diagonal tiles, which the POTRF factors -- runs on the main
+  // stream, and the other tiles on side2 beside the POTRF, on all SMs but those the POTRF's CTAs take; the caller
+  // joins side2 back before the TRSM (returns true). Otherwise one launch on the main stream. Each tile computes
+  // the same sums either way.
+  auto left_update = [&](const SymPlan::StepLaunch& sl, double flops, int mode) -> bool {
+    const int32_t* lf = dp.upd_fronts + sl.left_off;
+    const int reserve = sl.nfront * B;
+    if (!overlap || !ctx->side2 || sl.lrest_total == 0 || reserve > ctx->nsm / 2) {
+      ProfScope ps_(ctx, KC_UPDATE_LEFT, B * flops);
+      launch_update(ctx, f, sl.left_total, lf, dp.upd_pre + sl.left_pre_off, sl.n_left, sl.kb, mode);
+      return false;
+    }
+    GP_CUDA(cudaEventRecord(ctx->ev_fork2, st));
+    GP_CUDA(cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0));
+    launch_update(ctx, f, sl.lrest_total, lf, dp.upd_pre + sl.lrest_pre_off, sl.n_left, sl.kb, mode + 16, ctx->side2,
+                  reserve);
+    GP_CUDA(cudaEventRecord(ctx->ev_join2, ctx->side2));
+    launch_update(ctx, f, sl.n_left, lf, dp.upd_pre + sl.left_pre_off, sl.n_left, sl.kb, mode + 8);
+    return true;
+  };
   for (int32_t L = 0; L < sp.nlevels; L++) {
     const SymPlan::Level& lv = sp.levels[L];
     ctx->prof_level = L;
@@ -1535,11 +1565,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       const int32_t* fronts = dp.large_fronts + stp.fr_off;
       if (sp.group % 2 == 0 && q + 1 < lv.steps.size()) {   // block columns kb and kb + 1 (never across a group)
         const auto& st2 = lv.steps[q + 1];
-        if (stp.left_total > 0) {
-          ProfScope ps_(ctx, KC_UPDATE_LEFT, B * stp.left2_flops);
-          launch_update(ctx, f, stp.left_total, dp.upd_fronts + stp.left_off, dp.upd_pre + stp.left_pre_off,
-                        stp.n_left, stp.kb, 4);
-        }
+        const bool joined = stp.left_total > 0 && left_update(stp, stp.left2_flops, 4);
         {
           ProfScope ps_(ctx, KC_POTRF, B * (stp.potrf_flops + st2.potrf_flops));
           auto kp = f->diag_fp32 ? k_potrf_pair<true> : k_potrf_pair<false>;
@@ -1547,6 +1573,7 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
                                                             LOE, f->diag, f->dinv32, P32E, DE, f->notpd, dmax);
           GP_CHECK_LAUNCH(ctx);
         }
+        if (joined) GP_CUDA(cudaStreamWaitEvent(st, ctx->ev_join2, 0));   // the rows below, for the TRSM
         if (stp.pair_total > 0) {
           ProfScope ps_(ctx, KC_TRSM, B * (stp.trsm_flops + st2.trsm_flops));
           k_trsm32_pair<<<dim3((unsigned)stp.pair_total, B), 256, 0, st>>>(
@@ -1565,17 +1592,15 @@ void factor_run_mixed(gp_ctx* ctx, gp_factor_t* f) {
       }
       q += 1;
       const int64_t* pre_tr = dp.step_pre + stp.pre_off;
-      if (stp.left_total > 0) {   // this block column from the earlier blocks of its group
-        ProfScope ps_(ctx, KC_UPDATE_LEFT, B * stp.left_flops);
-        launch_update(ctx, f, stp.left_total, dp.upd_fronts + stp.left_off, dp.upd_pre + stp.left_pre_off,
-                      stp.n_left, stp.kb, 3);
-      }
+      // this block column from the earlier blocks of its group
+      const bool joined = stp.left_total > 0 && left_update(stp, stp.left_flops, 3);
       {
         ProfScope ps_(ctx, KC_POTRF, B * stp.potrf_flops);
         auto kd = f->diag_fp32 ? k_potrf_diag<true> : k_potrf_diag<false>;
         kd<<<dim3(stp.nfront, B), POTRF_THREADS, 0, st>>>(fronts, stp.kb, dp, f->diag, DE, f->notpd, f->dinv32);
         GP_CHECK_LAUNCH(ctx);
       }
+      if (joined) GP_CUDA(cudaStreamWaitEvent(st, ctx->ev_join2, 0));
       if (stp.trsm_total > 0) {
         ProfScope ps_(ctx, KC_TRSM, B * stp.trsm_flops);
         k_trsm32<<<dim3((unsigned)stp.trsm_total, B), 256, 0, st>>>(fronts, pre_tr, stp.nfront, stp.kb, dp,

@@ -165,6 +165,9 @@ extern "C" gp_status gp_create(gp_ctx** out, int device, void* cuda_stream, size
       GP_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
       GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
       GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+      GP_CUDA(cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking));
+      GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming));
+      GP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming));
     }
   });
   if (st != GP_OK) {

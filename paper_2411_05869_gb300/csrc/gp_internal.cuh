@@ -71,6 +71,10 @@ struct gp_ctx {
   // two events that fork it from and join it back to `stream` (re-recorded at each use)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // a third stream, for the left-looking updates of the rows below a block step's diagonal tiles beside the step's
+  // POTRF (GP_MIXED), with its own fork and join events
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   size_t budget = 0;     // 0 = unlimited
   std::atomic<size_t> held{0};   // bytes currently held by this context's handles
   int64_t launches = 0;
@@ -99,6 +103,9 @@ struct gp_ctx {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (side) cudaStreamDestroy(side);
+    if (ev_fork2) cudaEventDestroy(ev_fork2);
+    if (ev_join2) cudaEventDestroy(ev_join2);
+    if (side2) cudaStreamDestroy(side2);
   }
 };
 
@@ -211,6 +218,9 @@ struct SymPlan {
                       // the deferred group update (rows/columns after the group, K = the group's width); fronts
                       // and tile prefixes of each
                       int64_t left_off, left_pre_off, left_total; int32_t n_left;
+                      // the same left update without the strip's first 128-row tile of each front (the rows of
+                      // the step's diagonal tiles): prefix of the other tiles, and their total
+                      int64_t lrest_pre_off, lrest_total;
                       int64_t group_off, group_pre_off, group_total; int32_t n_group;
                       double left_flops, group_flops;
                       double left2_flops;   // the left update of block columns kb and kb + 1 together

@@ -595,6 +595,7 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
       stp.left2_flops = 0.0;
       int64_t acc = 0;
       sp.upd_pre.push_back(0);
+      std::vector<int64_t> rest_pre(1, 0);
       for (int32_t t = 0; t < cnt; t++) {   // block column kb from the earlier blocks of its group
         int32_t s = sp.large_fronts[stp.fr_off + t];
         int64_t w = sp.sn_w[s], m = w + sp.sn_r[s];
@@ -604,6 +605,7 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
         sp.upd_fronts.push_back(s);
         acc += (m - c0 + 127) / 128;
         sp.upd_pre.push_back(acc);
+        rest_pre.push_back(rest_pre.back() + (m - c0 + 127) / 128 - 1);
         stp.n_left++;
         double bw = (double)(c1 - c0);
         stp.left_flops += 2.0 * (double)(c0 - g0) * (bw * (bw + 1.0) / 2.0 + (double)(m - c1) * bw);
@@ -612,6 +614,9 @@ void plan_mixed_updates(SymPlan& sp, int group, int tn) {
         stp.left2_flops += 2.0 * (double)(c0 - g0) * (cw * (cw + 1.0) / 2.0 + (double)(m - c2) * cw);
       }
       stp.left_total = acc;
+      stp.lrest_pre_off = (int64_t)sp.upd_pre.size();
+      stp.lrest_total = rest_pre.back();
+      sp.upd_pre.insert(sp.upd_pre.end(), rest_pre.begin(), rest_pre.end());
       stp.group_off = (int64_t)sp.upd_fronts.size();
       stp.group_pre_off = (int64_t)sp.upd_pre.size();
       stp.n_group = 0;

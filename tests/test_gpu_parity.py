@@ -311,3 +311,43 @@ def test_mixed_f16_pairs_scale_with_the_covariance(ctx, c):
     assert abs(ll - ref) <= MIXED_RTOL * abs(ref), (c, ll, ref)
     f.free()
     ps.free()
+
+
+def test_left_updates_beside_the_potrf_match_one_launch(ctx):
+    """On an explicit stream the mixed factorization runs the left-looking update of a block step in two launches
+    (the rows of the step's diagonal tiles first, the rows below on a second stream beside the step's POTRF); on
+    the legacy default stream it is one launch. Every tile computes the same sums either way, so the
+    log-likelihoods must agree bit for bit, for both operand splits, on fronts wide enough for left updates at
+    every level of the chain."""
+    from paper_2411_05869_gb300 import gp
+    w = synth.uniform_spacetime(20000, 0, 60.0, 8, seed=79, ndays=120)
+    hp = w.hyper
+    rng = np.random.default_rng(13)
+    th = [synth.perturb(rng, hp) for _ in range(2)]
+    r = np.stack([w.resid, 0.5 * w.resid])
+    s = torch.cuda.Stream()
+    ctx2 = gp.Context(0, stream=s)
+    ps = ctx.assemble(_dev(w.X), hp.core_radius)
+    with torch.cuda.stream(s):
+        ps2 = ctx2.assemble(_dev(w.X), hp.core_radius)
+    s.synchronize()
+    assert ps.info()["max_front"] > 8 * 64
+    split0 = ctx.get_option("split_f16")
+    for split in (1, 0):
+        ctx.set_option("split_f16", split)
+        ctx2.set_option("split_f16", split)
+        try:
+            f = ctx.factor(ps, th, gp.GP_MIXED)
+            a = f.loglik(_dev(r)).cpu().numpy().copy()
+            with torch.cuda.stream(s):
+                f2 = ctx2.factor(ps2, th, gp.GP_MIXED)
+                b = f2.loglik(_dev(r)).cpu().numpy().copy()
+            s.synchronize()
+        finally:
+            ctx.set_option("split_f16", split0)
+            ctx2.set_option("split_f16", split0)
+        assert a.tobytes() == b.tobytes(), (split, a, b)
+        f.free()
+        f2.free()
+    ps.free()
+    ps2.free()
