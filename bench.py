@@ -578,6 +578,7 @@ def run_mcmc(args):
     hp = w.hyper
     B = args.batch
     ctx = gp.Context(0)
+    ctx.set_option("split_f16", int(args.split_f16))
     ps = ctx.assemble(torch.as_tensor(w.X, dtype=torch.float64, device="cuda"), hp.core_radius)
     rng = np.random.default_rng(7)
     tried = ps.autotune([synth_perturb(rng, hp) for _ in range(B)], reps=1)
@@ -600,7 +601,8 @@ def run_mcmc(args):
     acc = {k: v / float(B * s.iterations) for k, v in s.accept_counts.items()}
     line = {"metric": "MCMC iterations/s (App. C blocks, lockstep chains)", "value": args.steps / dt,
             "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "dtype": "tf32+f64",
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "dtype": "f16+f64" if args.split_f16 else "tf32+f64",
             "data": "synthetic (seeded; the 200k-point batched workload)",
             "config": {"workload": "mcmc_200k", "n": int(w.X.shape[0]), "chains": B,
                        "blocking": {"group_blocks": best["group_blocks"], "group_tile_n": best["group_tile_n"]}},
@@ -684,7 +686,8 @@ def run_serving(args):
     ns = [int(w.X.shape[0]) for w in sets]
     line = {"metric": "serving mix requests/s and p50/p99 latency (mixed vs FP64)",
             "value": result["mixed"]["saturation"]["req_per_s"], "unit": "requests/s", "n_gpus": 1,
-            "higher_is_better": True, "data": "synthetic", "dtype": "tf32+f64",
+            "higher_is_better": True, "data": "synthetic",
+            "dtype": "f16+f64 (the server's contexts take the library's default operand split)",
             "config": {"workload": "serving", "sets": len(sets), "n_min": min(ns), "n_max": max(ns),
                        "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
                        "mix": "70% loglik, 30% predict (m ~ U{1000..50000})"},
@@ -819,7 +822,8 @@ def main():
     else:
         peak = MEASURED_FP64_TFLOPS
         bound, peak_note = "alu", "FP64 FMA throughput measured on this pool"
-    dom = max(a7, key=lambda k: prof[k][0])
+    # the dominant kernel among the classes with a flop count (the tensor-core updates, POTRF, TRSM)
+    dom = max(["potrf", "trsm", "update", "update_left"], key=lambda k: prof[k][0])
     d_ms, d_n, d_fl_front = prof[dom]
     # The classes count the flops of the relaxed fronts (explicit zeros included); the algorithmic work is
     # sum_j eta_j^2 over the exact column counts, so each class's count is scaled by the ratio of the two totals.
@@ -925,14 +929,15 @@ KERNEL_OF_CLASS_MIXED = {"update": "k_update_ws<256, pair> (group-end updates: 2
 KERNEL_OF_CLASS_FP64 = {"update": "k_update (FP64 trailing updates)", "potrf": "k_potrf", "trsm": "k_trsm",
                         "extend_add": "k_extend_add"}
 
-# DRAM bytes per launch of the dominant kernel by (workload, class, update blocking), from ncu captures of the
-# current kernel; None where there is none. station_120k: all 83 group-end launches of a factorization at (16, 256)
-# read and wrote 2.924e9 bytes for 3.03e11 algorithmic flops (0.0097 bytes per flop). station_1.2M is too large
-# for a multi-metric capture: its figure is that rate times the 1.711e11 algorithmic flops of an average launch
-# there (an estimate that assumes traffic in proportion to the work). The one direct capture at 1.2M, with both
-# TF32 halves of the operands stored beside the panel and before the kernel's wind-down code, read 2.712e9 bytes
-# per launch; it is reported beside the line.
-_TRAFFIC = {("station_120k", "update", 16, 256): 2.924e9 / 83,
+# DRAM bytes per launch of the dominant kernel by (workload, class, update blocking[, operand split]), from ncu
+# captures of the current kernel; None where there is none. FP16 pairs, station_120k: all 79 group-end launches of
+# a factorization at (32, 256) read and wrote 1.8894e9 bytes for 2.612e11 algorithmic flops (0.00723 bytes per
+# flop). station_1.2M is too large for a multi-metric capture: its figure is that rate times the 1.901e11
+# algorithmic flops of an average launch there (an estimate that assumes traffic in proportion to the work). TF32
+# pairs at (16, 256): 2.924e9 bytes over 83 launches for 3.03e11 flops at 120k, 1.711e11 flops per launch at 1.2M.
+_TRAFFIC = {("station_120k", "update", 32, 256, "f16"): 1.8894e9 / 79,
+            ("station_1.2M", "update", 32, 256, "f16"): 1.8894e9 / 2.612e11 * 1.901e11,
+            ("station_120k", "update", 16, 256): 2.924e9 / 83,
             ("station_1.2M", "update", 16, 256): 2.924e9 / 3.03e11 * 1.711e11}
 _TRAFFIC_EARLIER = {("station_1.2M", "update", 16, 256): 2.712e9}
 
