@@ -144,6 +144,10 @@ typedef enum {
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy
  * default stream). mem_budget_bytes caps the device memory the context's handles may hold (0 = no cap).
+ * With an explicit stream the context also creates two non-blocking streams of its own; GP_MIXED
+ * factorizations fork work off their chain of dependent launches onto them and join it back into the context
+ * stream, so later work on that stream waits for it and the calls can be captured in a CUDA graph. The results
+ * are bitwise those of the legacy default stream, where everything runs in order.
  * Errors: GP_ERR_ARG (bad device), GP_ERR_CUDA. */
 GP_API gp_status gp_create(gp_ctx** ctx, int device, void* cuda_stream, size_t mem_budget_bytes);
 GP_API void gp_destroy(gp_ctx* ctx);
