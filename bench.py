@@ -240,6 +240,20 @@ def subwindow_parity(ctx, leg, theta, prec_list):
 
 # ------------------------------------------------------------------------------------------------ GPU leg
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (all ranks call it; torch.distributed is initialised)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units all ranks processed (each rank the same number: weak scaling) per second of the slowest rank."""
+    return units_per_rank * world / max_seconds
+
+
 def other_split_leg(ctx, ps, stream, resid, thetas, args, steps=3, warmup=2):
     """One setting per step through a factor with the other operand split (GP_OPT_SPLIT_F16 flipped)."""
     import torch
@@ -348,6 +362,8 @@ def run_gpu(args, rank, world, local_rank):
             step(args.warmup + k)
             ev[k + 1].record(stream)
     stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
     f.info()   # adds the refinement loop's device-decided passes to the launch count
     launches = ctx.launches() - launches0
@@ -799,13 +815,10 @@ def main():
     res = run_gpu(args, rank, world, local_rank)
     tot_s = res["total_ms"] / 1e3
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_s], dtype=torch.float64, device=f"cuda:{local_rank}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
+        tot_s = max_over_ranks(tot_s, f"cuda:{local_rank}")
     if rank != 0:
         return
-    value = args.steps * res["Bc"] * res["nchunk"] * world / tot_s
+    value = whole_job_rate(args.steps * res["Bc"] * res["nchunk"], world, tot_s)
     per = np.array(res["per"])
     info = res["info"]
     prof = res["prof"]
