@@ -33,7 +33,7 @@ def _rank(rank, world, port, seconds, out):
 
 def test_replicas_take_the_slowest_rank_and_count_every_rank():
     world, seconds = 2, [1.5, 2.0]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.start_processes(_rank, args=(world, _free_port(), seconds, out), nprocs=world, join=True,
                        start_method="spawn")
     for r in range(world):
