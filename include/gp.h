@@ -129,11 +129,12 @@ typedef struct {
  *   GP_OPT_SPLIT_F16: 1 (default) or 0: how GP_MIXED factors split each FP32 entry of L into the two parts their
  *     tensor-core updates multiply (three products per step: hi hi, hi lo, lo hi, accumulated in FP32, emulating
  *     FP32 products). 1: FP16 parts of the entry times 2^k, kind::f16 MMAs at twice the TF32 rate on half the
- *     operand bytes (hi = the scaled entry rounded to FP16, lo = the remainder rounded to FP16: about 22
- *     significant bits; k per setting from max_i C_ii, so that every scaled entry is below 2^13 -- |L_ij| <=
- *     sqrt(C_ii) -- and entries above 2^-25 of the largest keep their relative precision); the products are
- *     scaled back by 2^-2k, exactly. 0: TF32 parts, kind::tf32 MMAs (hi = the entry truncated to TF32, lo = the
- *     remainder rounded to TF32: about 21 significant bits). */
+ *     operand bytes (hi = the scaled entry rounded to FP16, lo = the remainder rounded to FP16; k per setting from
+ *     max_i C_ii, so that every scaled entry is below 2^13 -- |L_ij| <= sqrt(C_ii)); the pair holds the scaled
+ *     entry to within 2^-22 of it, or 2^-25 absolute below 2^-3, and the dropped lo lo term is at most 2^-22 of a
+ *     product; the products are scaled back by 2^-2k, exactly. 0: TF32 parts, kind::tf32 MMAs (hi = the entry
+ *     truncated to TF32, lo = the remainder rounded to TF32): the pair holds the entry to within 2^-22 of it, the
+ *     dropped lo lo term is at most 2^-20 of a product. */
 typedef enum {
   GP_OPT_DIAG_FP32 = 0,
   GP_OPT_WAIT_POLLS = 1,

@@ -12,8 +12,8 @@
 // at a time: POTRF of the diagonal tile (FP64, with the FP32 inverse of its factor), TRSM of the
 // rows below in FP32, then the updates F[i, j] -= sum_l L[i, l] L[j, l] on the tensor cores (left-looking
 // 128 x 64 strips per block, 256 x 256 CTA-pair tiles at a group's end), each FP32 operand split into two FP16
-// parts of the entry times a power of two (or two TF32 parts), three products per step (about 22, or 21, bits
-// kept), with the tile results added in FP64 to the diagonal tiles and in FP32 elsewhere.
+// parts of the entry times a power of two (or two TF32 parts), three products per step (the pair holds the entry
+// to about 2^-22 of it), with the tile results added in FP64 to the diagonal tiles and in FP32 elsewhere.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -497,8 +497,9 @@ __device__ __forceinline__ float tf32_lo(float x) {
 
 // The FP16 operand pairs (GP_OPT_SPLIT_F16) of proposal b are those of its L entries times 2^k, k =
 // 12 - floor(E / 2) for max_i C_ii in [2^E, 2^(E+1)): |L_ij| <= sqrt(C_ii) < 2^(floor(E/2) + 1), so every scaled
-// entry is below 2^13, well inside FP16's range (2^16), and entries down to 2^-25 of the largest keep an FP16
-// high part of full precision. k is clamped to +-126 (2^k and 2^-k are normal FP32 numbers).
+// entry is below 2^13, well inside FP16's range (2^16). A pair holds its scaled entry y to within 2^-22 |y|, or
+// 2^-25 absolute below 2^-3 (where the low part is subnormal), i.e. to 2^-38 of the bound. k is clamped to +-126
+// (2^k and 2^-k are normal FP32 numbers).
 __device__ __forceinline__ int f16_scale_exp(const unsigned long long* __restrict__ dmax, int b) {
   const int E = (int)((dmax[b] >> 52) & 0x7ff) - 1023;
   const int fl = E >= 0 ? E / 2 : -((1 - E) / 2);   // floor(E / 2)
@@ -734,13 +735,15 @@ __global__ void __launch_bounds__(256, 3) k_trsm32_pair(const int32_t* __restric
 //      CTA pair, or 128 x 128), K = the whole group [g0, gend).
 // The operands are a pair (hi, lo) per L entry, and each tile accumulates A_lo B_hi^T + A_hi B_lo^T + A_hi B_hi^T
 // (the split of Ootomo and Yokota, 2022), FP32 accumulation:
-//   F16 (the default): hi and lo are FP16, the entry times 2^k rounded and the remainder rounded (about 22
-//     significant bits), both written by the TRSM into the level's operand workspace; kind::f16 MMAs take 16 K
-//     per instruction, so an operand chunk of 128 bytes per row holds 64 K and a step costs half the
-//     instructions and half the operand bytes of TF32; the epilogue scales the tile back by 2^-2k (exact).
+//   F16 (the default): hi and lo are FP16, the entry times 2^k rounded and the remainder rounded (the pair holds
+//     the entry to 2^-22 of it; the dropped lo lo term is at most 2^-22 of a product), both written by the TRSM
+//     into the level's operand workspace; kind::f16 MMAs take 16 K per instruction, so an operand chunk of 128
+//     bytes per row holds 64 K and a step costs half the instructions and half the operand bytes of TF32; the
+//     epilogue scales the tile back by 2^-2k (exact).
 //   TF32: hi is the FP32 panel entry itself, read through the TF32 MMA's truncation of the low 13 mantissa bits,
-//     and lo the rounded remainder the TRSM writes into the workspace (about 21 significant bits survive the
-//     products instead of the 11 of one TF32 pass).
+//     and lo the rounded remainder the TRSM writes into the workspace (the pair holds the entry to 2^-22 of it;
+//     the dropped lo lo term, up to 2^-20 of a product with the truncated high part, is the larger error; one
+//     TF32 pass keeps 11 significant bits).
 // The wide tiles of mode 2 halve
 // the MMA instructions and cut the operand bytes per flop by a quarter (the L2 -> SM operand stream is what
 // bounds this kernel). Mode 2 runs in clusters of two CTAs on the tile pairs (rows 2p and 2p + 1 of 128, the same
